@@ -1,0 +1,188 @@
+/*
+ * tmop.h -- C ABI of the GB300 (sm_103a) high-order TMOP library.
+ *
+ * The library evaluates the variational TMOP objective of Dobrev, Knupp,
+ * Kolev, Mittal and Tomov, "The Target-Matrix Optimization Paradigm for
+ * High-Order Meshes" (SIAM J. Sci. Comput., 2019), on quadrilateral and
+ * hexahedral meshes with continuous Q_k node positions, together with its
+ * gradient and its matrix-free Hessian action, and minimises it with the
+ * damped Newton method and det(A) > 0 line search of Section 3.4.
+ *
+ * Conventions for every call:
+ *   - d = dim (2 or 3), k = order, n = k + 1, q = quadrature points per
+ *     direction, Q = q^d points per element.
+ *   - Position-like vectors (x, g, v, y) are caller-owned DEVICE pointers to
+ *     FP64 arrays in SoA layout [d][nnode]: component a of node i is at
+ *     index a * nnode + i. They must not overlap each other.
+ *   - The reference element is [0,1]^d; the nodal basis is the Lagrange basis
+ *     on the Gauss-Lobatto points of the element (x fastest, then y, then z).
+ *   - Fixed degrees of freedom (the "fixed boundary nodes" of Section 4.1)
+ *     read as zero in every direction vector and are written as zero in
+ *     every output vector.
+ *   - stream is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream). Every call is asynchronous on that stream unless it returns
+ *     host scalars, in which case it synchronises that stream before returning.
+ *   - Every call returns a status code (tmop_status). No call blocks without a
+ *     bound: there are no device-side spin waits anywhere in the library.
+ *   - A context is not thread-safe: calls on one context must not overlap.
+ */
+#ifndef TMOP_H
+#define TMOP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TMOP_OK = 0,
+  TMOP_ERR_ARG = 1,           /* invalid argument (sizes, ids, null pointers) */
+  TMOP_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  TMOP_ERR_INVERTED = 3,      /* some quadrature point has det A <= 0 (Section 3.2, ideal barrier) */
+  TMOP_ERR_LINESEARCH = 4,    /* no admissible step length (Section 3.4) */
+  TMOP_ERR_NOT_CONVERGED = 5  /* an iteration cap was reached */
+} tmop_status;
+
+enum { TMOP_GL = 0, TMOP_GLL = 1 };                                     /* quadrature kind */
+enum { TMOP_W_IDENTITY = 0, TMOP_W_CONST = 1, TMOP_W_SCALED = 2, TMOP_W_PER_QP = 3 }; /* target kind */
+enum { TMOP_FP64 = 0, TMOP_FP32_MIXED = 1 };                             /* precision form */
+enum { TMOP_KRYLOV_MINRES = 0, TMOP_KRYLOV_CG = 1 };                     /* inner solver */
+
+typedef struct tmop_ctx tmop_ctx; /* opaque; owns device tables and workspace */
+
+/* Mesh topology (Section 2.1, eq. (2.1)): nelem elements, each with
+ * (order+1)^dim nodes in local lexicographic order (x fastest), continuous
+ * across elements through the global node ids in elem_nodes. */
+typedef struct {
+  int dim;                    /* 2 or 3 */
+  int nelem;                  /* number of elements, >= 1 */
+  int nnode;                  /* number of global nodes, >= 1 */
+  const int32_t* elem_nodes;  /* HOST [nelem][(order+1)^dim] global node ids, copied at setup;
+                                 may be NULL when structured[] is set */
+  const uint8_t* fixed;       /* HOST [dim][nnode], 1 = fixed dof; NULL = nothing fixed; copied */
+  int structured[3];          /* nx, ny, (nz) of a lexicographic order-k grid whose node lattice is
+                                 (k*nx+1) x (k*ny+1) (x (k*nz+1)), x fastest, elements x fastest;
+                                 all 0 = unstructured. When set, node ids are computed, not read. */
+} tmop_mesh;
+
+/* Quadrature (Section 3.3): tensor Gauss-Legendre or Gauss-Lobatto rule with
+ * npts1d points per direction on [0,1] (weights sum to 1). */
+typedef struct {
+  int kind;    /* TMOP_GL or TMOP_GLL */
+  int npts1d;  /* 2..8; Section 3.3 asks for at least order+1 */
+} tmop_quad;
+
+/* Target matrices W (Section 3.1), fixed during the optimisation, det W > 0:
+ *   TMOP_W_IDENTITY  W = I                       (the paper's W1)
+ *   TMOP_W_SCALED    W = scale * I, scale > 0    (e.g. W2 = sqrt(alpha_bar) I, eq. (3.1))
+ *   TMOP_W_CONST     W = the HOST [dim][dim] row-major matrix at W
+ *   TMOP_W_PER_QP    W = HOST [nelem][Q][dim][dim] array, one matrix per
+ *                    quadrature point (e.g. W3 = sqrt(det A(x0)) I). */
+typedef struct {
+  int kind;
+  double scale;
+  const double* W;
+} tmop_targets;
+
+/* Create a context: validates the mesh, builds the 1D quadrature and the
+ * Lagrange value/derivative tables at the quadrature points, inverts the
+ * targets, uploads everything and allocates the workspace (reduction
+ * partials, Krylov vectors).
+ *   order     1..4 (k of Q_k)
+ *   metric_id 2D: 1, 2, 7, 9, 14, 77; 3D: 1, 14, 302, 303 (Table 3.1;
+ *             mu302 = |T|^2 |T^-1|^2 / 9 - 1 is not in the paper)
+ *   precision TMOP_FP64, or TMOP_FP32_MIXED: element contractions, metric
+ *             derivatives and Hessian actions in FP32; F, det A, dot
+ *             products, line search and convergence tests in FP64.
+ * Errors: TMOP_ERR_ARG (bad sizes or ids, node ids out of range, det W <= 0,
+ * structured[] inconsistent with elem_nodes), TMOP_ERR_CUDA. On error *out is NULL. */
+int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metric_id,
+               const tmop_targets* targets, int precision, tmop_ctx** out);
+
+/* Objective F_V(x) = sum_E sum_q w_q det W(x_q) mu(T(x_q)), T = A W^-1 with
+ * A = sum_i x_i grad w_i (eq. (2.2), eq. (2.4)), and min over all points of
+ * det A. F and min_detA are HOST pointers written after the stream is
+ * synchronised. If some det A <= 0, *F = +inf for barrier metrics (the
+ * "big value" of Section 3.4) and TMOP_ERR_INVERTED is returned with
+ * *min_detA set. */
+int tmop_energy(tmop_ctx* ctx, const double* x, double* F, double* min_detA, void* stream);
+
+/* Gradient g = dF_V/dx (Section 3.4): g_{i,a} = sum_E sum_q w_q det W
+ * [ (dmu/dT)(T) W^-t grad w_i ]_a, zero at fixed dofs. g: DEVICE [d][nnode],
+ * overwritten. Asynchronous. Points with det A <= 0 contribute nothing under a
+ * barrier metric; check tmop_energy first. */
+int tmop_gradient(tmop_ctx* ctx, const double* x, double* g, void* stream);
+
+/* Hessian action y = (d^2 F_V / dx^2)(x) v (Section 3.4: second derivatives
+ * of mu with respect to T): y_{i,a} = sum_E sum_q w_q det W
+ * [ (d^2mu/dT^2 : dT) W^-t grad w_i ]_a with dT = (sum_j v_j grad w_j) W^-1,
+ * v masked at fixed dofs, y zero there. Matrix-free (recomputes A from x).
+ * y: DEVICE [d][nnode], overwritten. Asynchronous. */
+int tmop_hess_apply(tmop_ctx* ctx, const double* x, const double* v, double* y, void* stream);
+
+/* Newton options (Section 3.4 and Section 5). Zero-initialised fields take
+ * the defaults in brackets. */
+typedef struct {
+  int max_newton;        /* [10] Newton iterations for tmop_newton_solve */
+  double rtol;           /* [1e-12] stop when |g| <= rtol |g(x0)| (Section 5) */
+  int krylov;            /* [TMOP_KRYLOV_MINRES] (Section 5 uses MINRES) */
+  double krylov_rtol;    /* [1e-10 FP64, 1e-6 FP32_MIXED] relative residual of the inner solve */
+  int krylov_maxit;      /* [2000] */
+  double alpha_shrink;   /* [0.5] step reduction factor */
+  int max_halvings;      /* [30] */
+  double f_factor;       /* [1.2] accept only if F(x_new) < f_factor F(x) */
+  double g_factor;       /* [1.2] accept only if |g(x_new)| < g_factor |g(x)| */
+} tmop_newton_opts;
+
+typedef struct {
+  int status;            /* tmop_status of the step or solve */
+  int iterations;        /* Newton steps taken (solve) or 1 (step) */
+  int krylov_iterations; /* inner iterations of the last step (sum for a solve) */
+  double alpha;          /* accepted step length of the last step (0 if none) */
+  double F;              /* objective at the returned x */
+  double grad_norm;      /* |g| (free dofs) at the returned x */
+  double grad_norm0;     /* |g| at the starting x */
+  double min_detA;       /* min det A at the returned x */
+} tmop_newton_report;
+
+/* One damped Newton step (Section 3.4): p = H(x)^-1 g(x) by MINRES or CG on
+ * the free dofs, then alpha = 1, alpha_shrink, ... until x - alpha p has
+ * det A > 0 at every point, F < f_factor F(x) and |g| < g_factor |g(x)|.
+ * x: DEVICE [d][nnode], updated in place only when a step is accepted.
+ * report: HOST, may be NULL. Returns TMOP_ERR_LINESEARCH when no step
+ * length is admissible (x unchanged), TMOP_ERR_INVERTED when x itself is
+ * inverted. Synchronises the stream (the line-search decisions are taken on
+ * the host from FP64 device reductions). */
+int tmop_newton_step(tmop_ctx* ctx, double* x, const tmop_newton_opts* opts, tmop_newton_report* report,
+                     void* stream);
+
+/* Newton iterations from x until |g| <= rtol |g(x0)| (TMOP_OK), no admissible
+ * step (TMOP_ERR_LINESEARCH, the termination rule of Section 3.4) or
+ * max_newton steps (TMOP_ERR_NOT_CONVERGED). x: DEVICE, in/out. */
+int tmop_newton_solve(tmop_ctx* ctx, double* x, const tmop_newton_opts* opts, tmop_newton_report* report,
+                      void* stream);
+
+/* Inner Krylov solve H(x) p = b alone (MINRES or CG, zero initial guess),
+ * for tests: b, p DEVICE [d][nnode]. Returns iterations through *iters
+ * (negative if krylov_maxit was reached). */
+int tmop_krylov_solve(tmop_ctx* ctx, const double* x, const double* b, double* p, const tmop_newton_opts* opts,
+                      int* iters, void* stream);
+
+/* Per-element minimum of det A over its quadrature points: out DEVICE
+ * [nelem] FP64 (the validity test behind the barrier of Section 3.2). */
+int tmop_element_min_detA(tmop_ctx* ctx, const double* x, double* out, void* stream);
+
+/* Sizes of a context: Q (points per element), ndof = dim * nnode. */
+int tmop_sizes(const tmop_ctx* ctx, int* dim, int* nelem, int* nnode, int* Q);
+
+/* Release every device allocation of the context. NULL is ignored. */
+void tmop_destroy(tmop_ctx* ctx);
+
+/* Static text for a status code. */
+const char* tmop_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TMOP_H */

@@ -1,0 +1,646 @@
+// C ABI of the GB300 TMOP library (declared in include/tmop.h).
+//
+// Host responsibilities: validate inputs, build the 1D quadrature and
+// Lagrange tables, invert the targets, own the device workspace, sequence the
+// kernels, and take the Newton line-search decisions (Section 3.4) from FP64
+// device reductions. All arithmetic on mesh-sized data runs in the CUDA
+// kernels of this library; there is no host fallback.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/tmop.h"
+#include "tmop_kparams.h"
+#include "tmop_vec.h"
+
+namespace tmop {
+
+extern const ElemEntry kElem_2d_f64[];
+extern const int kElem_2d_f64_len;
+extern const ElemEntry kElem_2d_f32[];
+extern const int kElem_2d_f32_len;
+extern const ElemEntry kElem_3d_f64[];
+extern const int kElem_3d_f64_len;
+extern const ElemEntry kElem_3d_f32[];
+extern const int kElem_3d_f32_len;
+
+const ElemEntry* find_elem(int dim, int n, int q, int fp32, int op) {
+  const ElemEntry* t;
+  int len;
+  if (dim == 2) { t = fp32 ? kElem_2d_f32 : kElem_2d_f64; len = fp32 ? kElem_2d_f32_len : kElem_2d_f64_len; }
+  else { t = fp32 ? kElem_3d_f32 : kElem_3d_f64; len = fp32 ? kElem_3d_f32_len : kElem_3d_f64_len; }
+  for (int i = 0; i < len; ++i)
+    if (t[i].n == n && t[i].q == q && t[i].op == op) return &t[i];
+  return nullptr;
+}
+
+// ---------------------------------------------------------------- 1D tables
+// Legendre P_m and P_m' by the Bonnet recurrence, with P_m' from the
+// identity (1 - t^2) P_m' = m (P_{m-1} - t P_m).
+static void legendre_pd(int m, double t, double* p, double* dp) {
+  double a = 1.0, b = t;
+  if (m == 0) { *p = 1.0; *dp = 0.0; return; }
+  for (int k = 1; k < m; ++k) {
+    double c = ((2 * k + 1) * t * b - k * a) / (k + 1);
+    a = b;
+    b = c;
+  }
+  *p = b;
+  *dp = m * (a - t * b) / (1.0 - t * t);
+}
+
+// Gauss-Legendre: roots of P_q by Newton from Chebyshev-like guesses;
+// weights 2 / ((1 - t^2) P_q'(t)^2) on [-1,1], mapped to [0,1].
+static bool rule_gl(int q, double* x, double* w) {
+  for (int i = 0; i < q; ++i) {
+    double t = -cos(M_PI * (4 * i + 3) / (4.0 * q + 2.0)), p, dp;
+    for (int it = 0; it < 64; ++it) {
+      legendre_pd(q, t, &p, &dp);
+      const double dt = p / dp;
+      t -= dt;
+      if (fabs(dt) <= 1e-16) break;
+    }
+    legendre_pd(q, t, &p, &dp);
+    x[i] = 0.5 + 0.5 * t;
+    w[i] = 1.0 / ((1.0 - t * t) * dp * dp);
+  }
+  return true;
+}
+
+// Gauss-Lobatto: endpoints plus the roots of P_{q-1}', found by Newton on
+// P_{q-1}' with P_{q-1}'' from the Legendre equation; weights
+// 2 / (q (q-1) P_{q-1}(t)^2) on [-1,1], mapped to [0,1].
+static bool rule_gll(int q, double* x, double* w) {
+  if (q < 2) return false;
+  const int m = q - 1;
+  for (int i = 0; i < q; ++i) {
+    double t = -cos(M_PI * i / m);
+    if (i > 0 && i < m) {
+      for (int it = 0; it < 64; ++it) {
+        double p, dp;
+        legendre_pd(m, t, &p, &dp);
+        const double d2p = (2.0 * t * dp - m * (m + 1.0) * p) / (1.0 - t * t);
+        const double dt = dp / d2p;
+        t -= dt;
+        if (fabs(dt) <= 1e-16) break;
+      }
+    }
+    double p;
+    if (i == 0) p = (m % 2) ? -1.0 : 1.0;
+    else if (i == m) p = 1.0;
+    else { double dp; legendre_pd(m, t, &p, &dp); }
+    x[i] = (i == 0) ? 0.0 : (i == m ? 1.0 : 0.5 + 0.5 * t);
+    w[i] = 1.0 / (m * (m + 1.0) * p * p);
+  }
+  return true;
+}
+
+// Lagrange basis on nodes z (barycentric form): values and derivatives at s.
+static void lagrange_bary(int n, const double* z, double s, double* phi, double* dphi) {
+  double bw[kMaxN];
+  for (int i = 0; i < n; ++i) {
+    double prod = 1.0;
+    for (int j = 0; j < n; ++j)
+      if (j != i) prod *= (z[i] - z[j]);
+    bw[i] = 1.0 / prod;
+  }
+  int hit = -1;
+  for (int i = 0; i < n; ++i)
+    if (s == z[i]) hit = i;
+  if (hit >= 0) {
+    // at a node: phi = delta, phi' from the differentiation matrix
+    for (int i = 0; i < n; ++i) phi[i] = (i == hit) ? 1.0 : 0.0;
+    double diag = 0.0;
+    for (int i = 0; i < n; ++i) {
+      if (i == hit) continue;
+      dphi[i] = (bw[i] / bw[hit]) / (z[hit] - z[i]);
+      diag += 1.0 / (z[hit] - z[i]);
+    }
+    dphi[hit] = diag;
+    return;
+  }
+  double ell = 1.0;
+  for (int j = 0; j < n; ++j) ell *= (s - z[j]);
+  for (int i = 0; i < n; ++i) {
+    phi[i] = ell * bw[i] / (s - z[i]);
+    double sum = 0.0;
+    for (int j = 0; j < n; ++j)
+      if (j != i) sum += 1.0 / (s - z[j]);
+    dphi[i] = phi[i] * sum;
+  }
+}
+
+static double det_h(int d, const double* M) {
+  if (d == 2) return M[0] * M[3] - M[1] * M[2];
+  return M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) +
+         M[2] * (M[3] * M[7] - M[4] * M[6]);
+}
+
+// W^-1 by the adjugate; false when det W <= 0 (Section 3.1 requires det W > 0).
+static bool inv_h(int d, const double* W, double* Wi, double* detW) {
+  const double dt = det_h(d, W);
+  *detW = dt;
+  if (!(dt > 0.0) || !isfinite(dt)) return false;
+  if (d == 2) {
+    Wi[0] = W[3] / dt; Wi[1] = -W[1] / dt; Wi[2] = -W[2] / dt; Wi[3] = W[0] / dt;
+    return true;
+  }
+  Wi[0] = (W[4] * W[8] - W[5] * W[7]) / dt;
+  Wi[1] = (W[2] * W[7] - W[1] * W[8]) / dt;
+  Wi[2] = (W[1] * W[5] - W[2] * W[4]) / dt;
+  Wi[3] = (W[5] * W[6] - W[3] * W[8]) / dt;
+  Wi[4] = (W[0] * W[8] - W[2] * W[6]) / dt;
+  Wi[5] = (W[2] * W[3] - W[0] * W[5]) / dt;
+  Wi[6] = (W[3] * W[7] - W[4] * W[6]) / dt;
+  Wi[7] = (W[1] * W[6] - W[0] * W[7]) / dt;
+  Wi[8] = (W[0] * W[4] - W[1] * W[3]) / dt;
+  return true;
+}
+
+}  // namespace tmop
+
+using namespace tmop;
+
+struct tmop_ctx {
+  int dim, order, n, nq, Q, nelem, nnode, metric, precision;
+  size_t ndof;
+  KParams base;
+  const ElemEntry* ent[3];
+  int grid[3];
+  int32_t* d_elem_nodes = nullptr;
+  uint8_t* d_fixed = nullptr;
+  double* d_Winv_qp = nullptr;
+  double* d_detW_qp = nullptr;
+  double* d_part = nullptr;   // 2 * kMaxRedBlocks (energy partials, reduction partials)
+  double* d_res = nullptr;    // [0] F, [1] min det A, [2] dot result, [3..] Krylov state
+  double* h_res = nullptr;    // pinned mirror
+  double* d_vec = nullptr;    // Krylov / Newton vectors, allocated on first use
+  int nvec = 0;
+};
+
+namespace {
+
+constexpr int kResKrylov = 8;
+constexpr int kNumVec = 10;
+
+#define CUDA_TRY(call)                              \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return TMOP_ERR_CUDA;    \
+  } while (0)
+
+int launch_op(tmop_ctx* c, int op, const double* x, const double* v, double* y, double* elem_min,
+              cudaStream_t s) {
+  KParams p = c->base;
+  p.x = x;
+  p.v = v;
+  p.y = y;
+  p.elem_min = elem_min;
+  p.part_F = c->d_part;
+  p.part_min = c->d_part + kMaxRedBlocks;
+  if (op != OP_ENERGY) CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * c->ndof, s));
+  if (c->ent[op]->launch(p, c->grid[op], s) != 0) return TMOP_ERR_CUDA;
+  return TMOP_OK;
+}
+
+// F and min det A into d_res[0..1] (device), asynchronously.
+int energy_async(tmop_ctx* c, const double* x, cudaStream_t s, double* elem_min = nullptr) {
+  int rc = launch_op(c, OP_ENERGY, x, nullptr, nullptr, elem_min, s);
+  if (rc) return rc;
+  if (energy_final(c->d_part, c->d_part + kMaxRedBlocks, c->grid[OP_ENERGY], c->d_res, s)) return TMOP_ERR_CUDA;
+  return TMOP_OK;
+}
+
+int read_res(tmop_ctx* c, int first, int count, cudaStream_t s) {
+  CUDA_TRY(cudaMemcpyAsync(c->h_res + first, c->d_res + first, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return TMOP_OK;
+}
+
+int energy_host(tmop_ctx* c, const double* x, double* F, double* mdet, cudaStream_t s) {
+  int rc = energy_async(c, x, s);
+  if (rc) return rc;
+  rc = read_res(c, 0, 2, s);
+  if (rc) return rc;
+  *F = c->h_res[0];
+  *mdet = c->h_res[1];
+  return TMOP_OK;
+}
+
+int norm_host(tmop_ctx* c, const double* a, double* out, cudaStream_t s) {
+  if (dot(a, a, c->ndof, c->d_part, c->d_res + 2, s)) return TMOP_ERR_CUDA;
+  int rc = read_res(c, 2, 1, s);
+  if (rc) return rc;
+  *out = sqrt(c->h_res[2]);
+  return TMOP_OK;
+}
+
+int ensure_vectors(tmop_ctx* c) {
+  if (c->d_vec) return TMOP_OK;
+  CUDA_TRY(cudaMalloc(&c->d_vec, sizeof(double) * c->ndof * kNumVec));
+  c->nvec = kNumVec;
+  return TMOP_OK;
+}
+
+double* vec(tmop_ctx* c, int i) { return c->d_vec + (size_t)i * c->ndof; }
+
+// Vector slots
+enum { V_G = 0, V_P, V_XT, V_GT, V_K0, V_K1, V_K2, V_K3, V_K4, V_K5 };
+
+tmop_newton_opts defaults(const tmop_ctx* c, const tmop_newton_opts* in) {
+  tmop_newton_opts o;
+  memset(&o, 0, sizeof(o));
+  if (in) o = *in;
+  if (o.max_newton <= 0) o.max_newton = 10;
+  if (!(o.rtol > 0.0)) o.rtol = 1e-12;
+  if (o.krylov != TMOP_KRYLOV_CG) o.krylov = TMOP_KRYLOV_MINRES;
+  if (!(o.krylov_rtol > 0.0)) o.krylov_rtol = (c->precision == TMOP_FP32_MIXED) ? 1e-6 : 1e-10;
+  if (o.krylov_maxit <= 0) o.krylov_maxit = 2000;
+  if (!(o.alpha_shrink > 0.0 && o.alpha_shrink < 1.0)) o.alpha_shrink = 0.5;
+  if (o.max_halvings <= 0) o.max_halvings = 30;
+  if (!(o.f_factor > 0.0)) o.f_factor = 1.2;
+  if (!(o.g_factor > 0.0)) o.g_factor = 1.2;
+  return o;
+}
+
+// Krylov solve H(x) p = b; returns iterations (negative if the cap was hit).
+int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_newton_opts& o, int* iters,
+           cudaStream_t s) {
+  int rc = ensure_vectors(c);
+  if (rc) return rc;
+  double* st = c->d_res + kResKrylov;
+  double* part = c->d_part;
+  const size_t n = c->ndof;
+  int it = 0;
+  bool done = false;
+  if (o.krylov == TMOP_KRYLOV_CG) {
+    double *r = vec(c, V_K0), *d = vec(c, V_K1), *Hd = vec(c, V_K2);
+    if (cg_init(b, r, d, p, st, part, n, s)) return TMOP_ERR_CUDA;
+    rc = read_res(c, kResKrylov, KS_COUNT, s);
+    if (rc) return rc;
+    const double r0 = c->h_res[kResKrylov + KS_BETA1];
+    done = !(r0 > 0.0);
+    while (!done && it < o.krylov_maxit) {
+      ++it;
+      rc = launch_op(c, OP_HESS, x, d, Hd, nullptr, s);
+      if (rc) return rc;
+      if (cg_after_hv(p, r, d, Hd, st, part, n, s)) return TMOP_ERR_CUDA;
+      rc = read_res(c, kResKrylov, KS_COUNT, s);
+      if (rc) return rc;
+      const double* h = c->h_res + kResKrylov;
+      if (h[KS_BREAKDOWN] != 0.0) break;
+      if (h[KS_RESID] <= o.krylov_rtol * r0) done = true;
+    }
+  } else {
+    double *v = vec(c, V_K0), *vprev = vec(c, V_K1), *Av = vec(c, V_K2), *w = vec(c, V_K3),
+           *wprev = vec(c, V_K4);
+    if (minres_init(b, v, vprev, w, wprev, p, st, part, n, s)) return TMOP_ERR_CUDA;
+    rc = read_res(c, kResKrylov, KS_COUNT, s);
+    if (rc) return rc;
+    const double beta1 = c->h_res[kResKrylov + KS_BETA1];
+    done = !(beta1 > 0.0);
+    while (!done && it < o.krylov_maxit) {
+      ++it;
+      rc = launch_op(c, OP_HESS, x, v, Av, nullptr, s);
+      if (rc) return rc;
+      if (minres_after_hv(v, vprev, Av, w, wprev, p, st, part, n, s)) return TMOP_ERR_CUDA;
+      rc = read_res(c, kResKrylov, KS_COUNT, s);
+      if (rc) return rc;
+      const double* h = c->h_res + kResKrylov;
+      if (h[KS_RESID] <= o.krylov_rtol * beta1 || h[KS_BETA_NEXT] == 0.0) done = true;
+    }
+  }
+  *iters = done ? it : -it;
+  return TMOP_OK;
+}
+
+struct NewtonState {
+  double F, mdet, gnorm;
+};
+
+// One Section 3.4 step from x with cached F, det, g (in V_G) and |g|.
+int newton_iter(tmop_ctx* c, double* x, const tmop_newton_opts& o, NewtonState* ns, tmop_newton_report* rep,
+                cudaStream_t s) {
+  double* g = vec(c, V_G);
+  double* p = vec(c, V_P);
+  double* xt = vec(c, V_XT);
+  double* gt = vec(c, V_GT);
+  int kit = 0;
+  int rc = krylov(c, x, g, p, o, &kit, s);
+  if (rc) return rc;
+  rep->krylov_iterations += kit < 0 ? -kit : kit;
+  double alpha = 1.0;
+  for (int h = 0; h <= o.max_halvings; ++h, alpha *= o.alpha_shrink) {
+    if (step(x, p, alpha, xt, c->ndof, s)) return TMOP_ERR_CUDA;
+    double Ft, mdt;
+    rc = energy_host(c, xt, &Ft, &mdt, s);
+    if (rc) return rc;
+    // the new configuration must be valid (det A > 0 everywhere) and F may
+    // grow by at most the f_factor
+    if (!(mdt > 0.0) || !(Ft < o.f_factor * ns->F)) continue;
+    rc = launch_op(c, OP_GRADIENT, xt, nullptr, gt, nullptr, s);
+    if (rc) return rc;
+    double gn;
+    rc = norm_host(c, gt, &gn, s);
+    if (rc) return rc;
+    if (!(gn < o.g_factor * ns->gnorm)) continue;
+    CUDA_TRY(cudaMemcpyAsync(x, xt, sizeof(double) * c->ndof, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(g, gt, sizeof(double) * c->ndof, cudaMemcpyDeviceToDevice, s));
+    ns->F = Ft;
+    ns->mdet = mdt;
+    ns->gnorm = gn;
+    rep->alpha = alpha;
+    return TMOP_OK;
+  }
+  rep->alpha = 0.0;
+  return TMOP_ERR_LINESEARCH;
+}
+
+int newton_start(tmop_ctx* c, const double* x, NewtonState* ns, cudaStream_t s) {
+  int rc = ensure_vectors(c);
+  if (rc) return rc;
+  rc = energy_host(c, x, &ns->F, &ns->mdet, s);
+  if (rc) return rc;
+  if (!(ns->mdet > 0.0)) return TMOP_ERR_INVERTED;
+  rc = launch_op(c, OP_GRADIENT, x, nullptr, vec(c, V_G), nullptr, s);
+  if (rc) return rc;
+  return norm_host(c, vec(c, V_G), &ns->gnorm, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tmop_status_string(int status) {
+  switch (status) {
+    case TMOP_OK: return "ok";
+    case TMOP_ERR_ARG: return "invalid argument";
+    case TMOP_ERR_CUDA: return "CUDA error";
+    case TMOP_ERR_INVERTED: return "inverted element: det A <= 0 at some quadrature point";
+    case TMOP_ERR_LINESEARCH: return "line search found no admissible step";
+    case TMOP_ERR_NOT_CONVERGED: return "iteration limit reached";
+    default: return "unknown status";
+  }
+}
+
+void tmop_destroy(tmop_ctx* c) {
+  if (!c) return;
+  cudaFree(c->d_elem_nodes);
+  cudaFree(c->d_fixed);
+  cudaFree(c->d_Winv_qp);
+  cudaFree(c->d_detW_qp);
+  cudaFree(c->d_part);
+  cudaFree(c->d_res);
+  cudaFree(c->d_vec);
+  cudaFreeHost(c->h_res);
+  delete c;
+}
+
+int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metric_id, const tmop_targets* targets,
+               int precision, tmop_ctx** out) {
+  if (!out) return TMOP_ERR_ARG;
+  *out = nullptr;
+  if (!mesh || !quad || !targets) return TMOP_ERR_ARG;
+  const int d = mesh->dim;
+  if (d != 2 && d != 3) return TMOP_ERR_ARG;
+  if (order < 1 || order > 4 || mesh->nelem < 1 || mesh->nnode < 1) return TMOP_ERR_ARG;
+  if (quad->kind != TMOP_GL && quad->kind != TMOP_GLL) return TMOP_ERR_ARG;
+  if (quad->npts1d < 2 || quad->npts1d > kMaxQ) return TMOP_ERR_ARG;
+  if (precision != TMOP_FP64 && precision != TMOP_FP32_MIXED) return TMOP_ERR_ARG;
+  const bool ok_metric = (metric_id == 1 || metric_id == 14) ||
+                         (d == 2 && (metric_id == 2 || metric_id == 7 || metric_id == 9 || metric_id == 77)) ||
+                         (d == 3 && (metric_id == 302 || metric_id == 303));
+  if (!ok_metric) return TMOP_ERR_ARG;
+  const int n = order + 1, nq = quad->npts1d;
+  const int ndof_e = d == 2 ? n * n : n * n * n;
+  const int Q = d == 2 ? nq * nq : nq * nq * nq;
+  const int fp32 = precision == TMOP_FP32_MIXED;
+  const ElemEntry* ent[3];
+  for (int op = 0; op < 3; ++op) {
+    ent[op] = find_elem(d, n, nq, fp32, op);
+    if (!ent[op]) return TMOP_ERR_ARG;  // unsupported (order, points) pair
+  }
+  // structured grid: sizes must match, and elem_nodes (if given) must agree
+  const int* sd = mesh->structured;
+  const bool structured = sd[0] > 0;
+  if (structured) {
+    long long ne = (long long)sd[0] * sd[1] * (d == 3 ? sd[2] : 1);
+    long long nn = (long long)(order * sd[0] + 1) * (order * sd[1] + 1) * (d == 3 ? (order * sd[2] + 1) : 1);
+    if (sd[1] < 1 || (d == 3 && sd[2] < 1) || ne != mesh->nelem || nn != mesh->nnode) return TMOP_ERR_ARG;
+  } else if (!mesh->elem_nodes) {
+    return TMOP_ERR_ARG;
+  }
+  if (mesh->elem_nodes) {
+    const size_t cnt = (size_t)mesh->nelem * ndof_e;
+    for (size_t i = 0; i < cnt; ++i)
+      if (mesh->elem_nodes[i] < 0 || mesh->elem_nodes[i] >= mesh->nnode) return TMOP_ERR_ARG;
+    if (structured) {
+      const int Nx = order * sd[0] + 1, Ny = order * sd[1] + 1;
+      for (int e = 0; e < mesh->nelem; ++e) {
+        const int ex = e % sd[0], ey = (e / sd[0]) % sd[1], ez = d == 3 ? e / (sd[0] * sd[1]) : 0;
+        for (int t = 0; t < ndof_e; ++t) {
+          const int i = t % n, j = (t / n) % n, l = d == 3 ? t / (n * n) : 0;
+          const int g = ((ez * order + l) * Ny + ey * order + j) * Nx + ex * order + i;
+          if (mesh->elem_nodes[(size_t)e * ndof_e + t] != g) return TMOP_ERR_ARG;
+        }
+      }
+    }
+  }
+
+  tmop_ctx* c = new tmop_ctx();
+  c->dim = d; c->order = order; c->n = n; c->nq = nq; c->Q = Q;
+  c->nelem = mesh->nelem; c->nnode = mesh->nnode; c->metric = metric_id; c->precision = precision;
+  c->ndof = (size_t)d * mesh->nnode;
+  for (int op = 0; op < 3; ++op) c->ent[op] = ent[op];
+  KParams& p = c->base;
+  memset(&p, 0, sizeof(p));
+  p.dim = d; p.nelem = mesh->nelem; p.nnode = mesh->nnode; p.metric = metric_id;
+  p.sx = structured ? sd[0] : 0; p.sy = structured ? sd[1] : 0; p.sz = structured && d == 3 ? sd[2] : 0;
+
+  // tables
+  double qx[kMaxQ], qw[kMaxQ], z[kMaxN], zw[kMaxN];
+  if (quad->kind == TMOP_GL) rule_gl(nq, qx, qw);
+  else rule_gll(nq, qx, qw);
+  rule_gll(n, z, zw);
+  for (int a = 0; a < nq; ++a) {
+    double phi[kMaxN], dphi[kMaxN];
+    lagrange_bary(n, z, qx[a], phi, dphi);
+    for (int i = 0; i < n; ++i) {
+      p.B[a * n + i] = phi[i];
+      p.G[a * n + i] = dphi[i];
+    }
+    p.w1[a] = qw[a];
+  }
+
+  // targets
+  const int dd = d * d;
+  int rc = TMOP_OK;
+  double Wc[9] = {0};
+  switch (targets->kind) {
+    case TMOP_W_IDENTITY:
+      for (int i = 0; i < d; ++i) Wc[i * d + i] = 1.0;
+      p.wkind = WK_IDENTITY;
+      break;
+    case TMOP_W_SCALED:
+      if (!(targets->scale > 0.0) || !isfinite(targets->scale)) rc = TMOP_ERR_ARG;
+      for (int i = 0; i < d; ++i) Wc[i * d + i] = targets->scale;
+      p.wkind = WK_CONST;
+      break;
+    case TMOP_W_CONST:
+      if (!targets->W) rc = TMOP_ERR_ARG;
+      else memcpy(Wc, targets->W, sizeof(double) * dd);
+      p.wkind = WK_CONST;
+      break;
+    case TMOP_W_PER_QP:
+      if (!targets->W) rc = TMOP_ERR_ARG;
+      p.wkind = WK_PER_QP;
+      for (int i = 0; i < d; ++i) Wc[i * d + i] = 1.0;
+      break;
+    default:
+      rc = TMOP_ERR_ARG;
+  }
+  if (rc == TMOP_OK && !inv_h(d, Wc, p.Winv, &p.detW)) rc = TMOP_ERR_ARG;
+  if (rc == TMOP_OK && p.wkind == WK_PER_QP) {
+    const size_t cnt = (size_t)mesh->nelem * Q;
+    std::vector<double> Wi(cnt * dd), dW(cnt);
+    for (size_t k = 0; k < cnt && rc == TMOP_OK; ++k)
+      if (!inv_h(d, targets->W + k * dd, &Wi[k * dd], &dW[k])) rc = TMOP_ERR_ARG;
+    if (rc == TMOP_OK) {
+      if (cudaMalloc(&c->d_Winv_qp, sizeof(double) * cnt * dd) != cudaSuccess ||
+          cudaMalloc(&c->d_detW_qp, sizeof(double) * cnt) != cudaSuccess ||
+          cudaMemcpy(c->d_Winv_qp, Wi.data(), sizeof(double) * cnt * dd, cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(c->d_detW_qp, dW.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = TMOP_ERR_CUDA;
+      p.Winv_qp = c->d_Winv_qp;
+      p.detW_qp = c->d_detW_qp;
+    }
+  }
+  // mesh arrays
+  if (rc == TMOP_OK && !structured) {
+    const size_t bytes = sizeof(int32_t) * (size_t)mesh->nelem * ndof_e;
+    if (cudaMalloc(&c->d_elem_nodes, bytes) != cudaSuccess ||
+        cudaMemcpy(c->d_elem_nodes, mesh->elem_nodes, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+      rc = TMOP_ERR_CUDA;
+    p.elem_nodes = c->d_elem_nodes;
+  }
+  if (rc == TMOP_OK && mesh->fixed) {
+    if (cudaMalloc(&c->d_fixed, c->ndof) != cudaSuccess ||
+        cudaMemcpy(c->d_fixed, mesh->fixed, c->ndof, cudaMemcpyHostToDevice) != cudaSuccess)
+      rc = TMOP_ERR_CUDA;
+    p.fixed = c->d_fixed;
+  }
+  // launch shapes and workspace
+  for (int op = 0; op < 3 && rc == TMOP_OK; ++op) {
+    if (ent[op]->prepare(mesh->nelem, &c->grid[op]) != 0) rc = TMOP_ERR_CUDA;
+    else if (c->grid[op] > kMaxRedBlocks) c->grid[op] = kMaxRedBlocks;
+  }
+  if (rc == TMOP_OK) {
+    if (cudaMalloc(&c->d_part, sizeof(double) * 2 * kMaxRedBlocks) != cudaSuccess ||
+        cudaMalloc(&c->d_res, sizeof(double) * (kResKrylov + KS_COUNT)) != cudaSuccess ||
+        cudaMallocHost(&c->h_res, sizeof(double) * (kResKrylov + KS_COUNT)) != cudaSuccess)
+      rc = TMOP_ERR_CUDA;
+  }
+  if (rc != TMOP_OK) {
+    tmop_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return TMOP_OK;
+}
+
+int tmop_sizes(const tmop_ctx* c, int* dim, int* nelem, int* nnode, int* Q) {
+  if (!c) return TMOP_ERR_ARG;
+  if (dim) *dim = c->dim;
+  if (nelem) *nelem = c->nelem;
+  if (nnode) *nnode = c->nnode;
+  if (Q) *Q = c->Q;
+  return TMOP_OK;
+}
+
+int tmop_energy(tmop_ctx* c, const double* x, double* F, double* min_detA, void* stream) {
+  if (!c || !x || !F || !min_detA) return TMOP_ERR_ARG;
+  double f, m;
+  int rc = energy_host(c, x, &f, &m, (cudaStream_t)stream);
+  if (rc) return rc;
+  *F = f;
+  *min_detA = m;
+  return (m > 0.0) ? TMOP_OK : TMOP_ERR_INVERTED;
+}
+
+int tmop_gradient(tmop_ctx* c, const double* x, double* g, void* stream) {
+  if (!c || !x || !g) return TMOP_ERR_ARG;
+  return launch_op(c, OP_GRADIENT, x, nullptr, g, nullptr, (cudaStream_t)stream);
+}
+
+int tmop_hess_apply(tmop_ctx* c, const double* x, const double* v, double* y, void* stream) {
+  if (!c || !x || !v || !y) return TMOP_ERR_ARG;
+  return launch_op(c, OP_HESS, x, v, y, nullptr, (cudaStream_t)stream);
+}
+
+int tmop_element_min_detA(tmop_ctx* c, const double* x, double* out, void* stream) {
+  if (!c || !x || !out) return TMOP_ERR_ARG;
+  return launch_op(c, OP_ENERGY, x, nullptr, nullptr, out, (cudaStream_t)stream);
+}
+
+int tmop_krylov_solve(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_newton_opts* opts,
+                      int* iters, void* stream) {
+  if (!c || !x || !b || !p || !iters) return TMOP_ERR_ARG;
+  tmop_newton_opts o = defaults(c, opts);
+  return krylov(c, x, b, p, o, iters, (cudaStream_t)stream);
+}
+
+int tmop_newton_step(tmop_ctx* c, double* x, const tmop_newton_opts* opts, tmop_newton_report* report,
+                     void* stream) {
+  if (!c || !x) return TMOP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  tmop_newton_opts o = defaults(c, opts);
+  tmop_newton_report rep;
+  memset(&rep, 0, sizeof(rep));
+  NewtonState ns = {0.0, 0.0, 0.0};
+  int rc = newton_start(c, x, &ns, s);
+  rep.grad_norm0 = (rc == TMOP_OK) ? ns.gnorm : 0.0;
+  if (rc == TMOP_OK) {
+    rc = newton_iter(c, x, o, &ns, &rep, s);
+    rep.iterations = 1;
+  }
+  rep.status = rc;
+  rep.F = ns.F;
+  rep.grad_norm = ns.gnorm;
+  rep.min_detA = ns.mdet;
+  if (report) *report = rep;
+  return rc;
+}
+
+int tmop_newton_solve(tmop_ctx* c, double* x, const tmop_newton_opts* opts, tmop_newton_report* report,
+                      void* stream) {
+  if (!c || !x) return TMOP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  tmop_newton_opts o = defaults(c, opts);
+  tmop_newton_report rep;
+  memset(&rep, 0, sizeof(rep));
+  NewtonState ns = {0.0, 0.0, 0.0};
+  int rc = newton_start(c, x, &ns, s);
+  if (rc == TMOP_OK) {
+    rep.grad_norm0 = ns.gnorm;
+    rc = TMOP_ERR_NOT_CONVERGED;
+    for (int it = 0; it < o.max_newton; ++it) {
+      if (ns.gnorm <= o.rtol * rep.grad_norm0) { rc = TMOP_OK; break; }
+      int r = newton_iter(c, x, o, &ns, &rep, s);
+      rep.iterations = it + 1;
+      if (r != TMOP_OK) { rc = r; break; }
+    }
+    if (rc == TMOP_ERR_NOT_CONVERGED && ns.gnorm <= o.rtol * rep.grad_norm0) rc = TMOP_OK;
+  }
+  rep.status = rc;
+  rep.F = ns.F;
+  rep.grad_norm = ns.gnorm;
+  rep.min_detA = ns.mdet;
+  if (report) *report = rep;
+  return rc;
+}
+
+}  // extern "C"

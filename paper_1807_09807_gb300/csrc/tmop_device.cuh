@@ -1,0 +1,375 @@
+// Device-side building blocks of the TMOP element kernels (sm_103a).
+//
+//  * Dual<R>: forward-mode dual numbers. The Hessian action needs
+//    d^2mu/dT^2 : dT (Section 3.4); evaluating the first derivative P(T) on
+//    T + eps dT in dual arithmetic yields exactly that directional derivative,
+//    so every metric is written once, generically in its scalar type.
+//  * metric_P: mu and P = dmu/dT for the Table 3.1 / Section 3.2 metrics in
+//    the invariants I1 = |T|^2, tau = det T, C = cof T.
+//  * fwd2/fwd3, adj2/adj3: sum-factorised tensor-product contractions of one
+//    element, executed by one warp in shared memory. Forward: nodal values
+//    X[c][l][j][i] -> A[c][b](q) = sum_i X_i d phi_i / d xi_b (eq. (2.2)).
+//    Adjoint: per-point matrices R[c][b](q) -> Y[c][i] = sum_q R[c][b](q)
+//    d phi_i / d xi_b (the transposed contraction of the gradient formula).
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "tmop_kparams.h"
+
+namespace tmop {
+
+
+
+// ---------------------------------------------------------------- scalars
+template <class R>
+struct Dual {
+  R v, d;
+};
+
+template <class R> __device__ __forceinline__ Dual<R> operator+(Dual<R> a, Dual<R> b) { return {a.v + b.v, a.d + b.d}; }
+template <class R> __device__ __forceinline__ Dual<R> operator-(Dual<R> a, Dual<R> b) { return {a.v - b.v, a.d - b.d}; }
+template <class R> __device__ __forceinline__ Dual<R> operator-(Dual<R> a) { return {-a.v, -a.d}; }
+template <class R> __device__ __forceinline__ Dual<R> operator*(Dual<R> a, Dual<R> b) {
+  return {a.v * b.v, fma(a.v, b.d, a.d * b.v)};
+}
+template <class R> __device__ __forceinline__ Dual<R> operator*(R s, Dual<R> a) { return {s * a.v, s * a.d}; }
+template <class R> __device__ __forceinline__ Dual<R> operator*(Dual<R> a, R s) { return {s * a.v, s * a.d}; }
+template <class R> __device__ __forceinline__ Dual<R> operator+(Dual<R> a, R s) { return {a.v + s, a.d}; }
+template <class R> __device__ __forceinline__ Dual<R> operator-(Dual<R> a, R s) { return {a.v - s, a.d}; }
+
+__device__ __forceinline__ double value(double a) { return a; }
+__device__ __forceinline__ float value(float a) { return a; }
+template <class R> __device__ __forceinline__ R value(Dual<R> a) { return a.v; }
+
+__device__ __forceinline__ double recip(double a) { return 1.0 / a; }
+__device__ __forceinline__ float recip(float a) { return 1.0f / a; }
+template <class R> __device__ __forceinline__ Dual<R> recip(Dual<R> a) {
+  R r = R(1) / a.v;
+  return {r, -a.d * r * r};
+}
+// tau^{-1/3}
+__device__ __forceinline__ double rcbrt_(double a) { return rcbrt(a); }
+__device__ __forceinline__ float rcbrt_(float a) { return rcbrtf(a); }
+template <class R> __device__ __forceinline__ Dual<R> rcbrt_(Dual<R> a) {
+  R r = rcbrt_(a.v);
+  // d(tau^{-1/3}) = -(1/3) tau^{-4/3} dtau
+  return {r, R(-1) / R(3) * r / a.v * a.d};
+}
+
+// Constants enter the metric formulas as plain reals, so that a dual number
+// times a constant costs two multiplications, not a full dual product.
+template <class S> struct base_of { using type = S; };
+template <class R> struct base_of<Dual<R>> { using type = R; };
+template <class S> __device__ __forceinline__ typename base_of<S>::type sc(double c) {
+  return typename base_of<S>::type(c);
+}
+
+// ---------------------------------------------------------------- matrices
+template <int D, class S>
+__device__ __forceinline__ S det_m(const S* M) {
+  if constexpr (D == 2) {
+    return M[0] * M[3] - M[1] * M[2];
+  } else {
+    return M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) +
+           M[2] * (M[3] * M[7] - M[4] * M[6]);
+  }
+}
+
+// cof(M) = det(M) M^{-T}: the derivative of det M with respect to M
+template <int D, class S>
+__device__ __forceinline__ void cof_m(const S* M, S* C) {
+  if constexpr (D == 2) {
+    C[0] = M[3]; C[1] = -M[2]; C[2] = -M[1]; C[3] = M[0];
+  } else {
+    C[0] = M[4] * M[8] - M[5] * M[7];
+    C[1] = M[5] * M[6] - M[3] * M[8];
+    C[2] = M[3] * M[7] - M[4] * M[6];
+    C[3] = M[2] * M[7] - M[1] * M[8];
+    C[4] = M[0] * M[8] - M[2] * M[6];
+    C[5] = M[1] * M[6] - M[0] * M[7];
+    C[6] = M[1] * M[5] - M[2] * M[4];
+    C[7] = M[2] * M[3] - M[0] * M[5];
+    C[8] = M[0] * M[4] - M[1] * M[3];
+  }
+}
+
+// ---------------------------------------------------------------- metrics
+// mu(T) and P = dmu/dT. Returns false when a barrier metric meets
+// tau <= 0 (mu is +inf there, P is left unset).
+template <int D, class S>
+__device__ __forceinline__ bool metric_P(int id, const S* T, S& mu, S* P) {
+  constexpr int DD = D * D;
+  S I1 = T[0] * T[0];
+#pragma unroll
+  for (int i = 1; i < DD; ++i) I1 = I1 + T[i] * T[i];
+  if (id == 1) {  // |T|^2
+    mu = I1;
+#pragma unroll
+    for (int i = 0; i < DD; ++i) P[i] = sc<S>(2.0) * T[i];
+    return true;
+  }
+  if (id == 14) {  // |T - I|^2
+    S e0 = T[0] - sc<S>(1.0);
+    S s = e0 * e0;
+    P[0] = sc<S>(2.0) * e0;
+#pragma unroll
+    for (int i = 1; i < DD; ++i) {
+      S e = (i % (D + 1) == 0) ? T[i] - sc<S>(1.0) : T[i];
+      s = s + e * e;
+      P[i] = sc<S>(2.0) * e;
+    }
+    mu = s;
+    return true;
+  }
+  S tau = det_m<D>(T);
+  if (!(value(tau) > 0)) return false;
+  S C[DD];
+  cof_m<D>(T, C);
+  S it = recip(tau);
+  if constexpr (D == 2) {
+    if (id == 2) {  // |T|^2 / (2 tau) - 1
+      mu = sc<S>(0.5) * I1 * it - sc<S>(1.0);
+      S b = sc<S>(0.5) * I1 * it * it;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) P[i] = it * T[i] - b * C[i];
+      return true;
+    }
+    S it2 = it * it;
+    if (id == 7) {  // |T - T^-t|^2 = I1 (1 + tau^-2) - 4
+      mu = I1 * (it2 + sc<S>(1.0)) - sc<S>(4.0);
+      S a = sc<S>(2.0) * (it2 + sc<S>(1.0)), b = sc<S>(2.0) * I1 * it2 * it;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) P[i] = a * T[i] - b * C[i];
+      return true;
+    }
+    if (id == 9) {  // tau |T - T^-t|^2 = tau I1 + I1 / tau - 4 tau
+      mu = tau * I1 + I1 * it - sc<S>(4.0) * tau;
+      S a = sc<S>(2.0) * (tau + it), b = I1 - I1 * it2 - sc<S>(4.0);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) P[i] = a * T[i] + b * C[i];
+      return true;
+    }
+    if (id == 77) {  // (tau - 1/tau)^2 / 2
+      S s = tau - it;
+      mu = sc<S>(0.5) * s * s;
+      S a = s * (it2 + sc<S>(1.0));
+#pragma unroll
+      for (int i = 0; i < 4; ++i) P[i] = a * C[i];
+      return true;
+    }
+  } else {
+    if (id == 303) {  // |T|^2 / (3 tau^{2/3}) - 1
+      S r = rcbrt_(tau);
+      S r2 = r * r;
+      mu = sc<S>(1.0 / 3.0) * I1 * r2 - sc<S>(1.0);
+      S a = sc<S>(2.0 / 3.0) * r2, b = sc<S>(2.0 / 9.0) * I1 * r2 * it;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) P[i] = a * T[i] - b * C[i];
+      return true;
+    }
+    if (id == 302) {  // |T|^2 |T^-1|^2 / 9 - 1 = I1 K / (9 tau^2) - 1, K = |cof T|^2
+      S K = C[0] * C[0];
+#pragma unroll
+      for (int i = 1; i < 9; ++i) K = K + C[i] * C[i];
+      // dK/dT = 2 (I1 T - T T^t T)
+      S TtT[9];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) TtT[i * 3 + j] = T[i] * T[j] + T[3 + i] * T[3 + j] + T[6 + i] * T[6 + j];
+      S a = sc<S>(1.0 / 9.0) * it * it;
+      mu = a * I1 * K - sc<S>(1.0);
+      S c = sc<S>(2.0) * a * I1 * K * it;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          S M = T[i * 3 + 0] * TtT[0 * 3 + j] + T[i * 3 + 1] * TtT[1 * 3 + j] + T[i * 3 + 2] * TtT[2 * 3 + j];
+          S Kp = sc<S>(2.0) * (I1 * T[i * 3 + j] - M);
+          P[i * 3 + j] = a * (I1 * Kp + sc<S>(2.0) * K * T[i * 3 + j]) - c * C[i * 3 + j];
+        }
+      return true;
+    }
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------- contractions
+// Tables in shared memory: B[q][i] = phi_i(xi_q), G[q][i] = phi_i'(xi_q).
+
+// 2D forward. P0: X[NC][N][N] -> (P1: S[NC][2][N][Q]) -> P0: A[NC][2][Q][Q]
+template <int N, int Q1, int NC, class R>
+__device__ __forceinline__ void fwd2(const R* __restrict__ B, const R* __restrict__ G, R* P0, R* P1, int lane) {
+  for (int t = lane; t < NC * N * Q1; t += 32) {
+    const int q0 = t % Q1, j = (t / Q1) % N, c = t / (Q1 * N);
+    const R* xr = P0 + (c * N + j) * N;
+    R sb = R(0), sg = R(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const R xv = xr[i];
+      sb = fma(xv, B[q0 * N + i], sb);
+      sg = fma(xv, G[q0 * N + i], sg);
+    }
+    P1[((c * 2 + 0) * N + j) * Q1 + q0] = sb;
+    P1[((c * 2 + 1) * N + j) * Q1 + q0] = sg;
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * Q1 * Q1; t += 32) {
+    const int q0 = t % Q1, q1 = (t / Q1) % Q1, c = t / (Q1 * Q1);
+    const R* sB = P1 + (c * 2 + 0) * N * Q1 + q0;
+    const R* sG = P1 + (c * 2 + 1) * N * Q1 + q0;
+    R a0 = R(0), a1 = R(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      a0 = fma(sG[j * Q1], B[q1 * N + j], a0);  // d/dxi_0: G in x, B in y
+      a1 = fma(sB[j * Q1], G[q1 * N + j], a1);  // d/dxi_1: B in x, G in y
+    }
+    P0[(c * 2 + 0) * Q1 * Q1 + q1 * Q1 + q0] = a0;
+    P0[(c * 2 + 1) * Q1 * Q1 + q1 * Q1 + q0] = a1;
+  }
+  __syncwarp();
+}
+
+// 2D adjoint. P0: R[NC][2][Q][Q] -> (P1: U[NC][2][N][Q]) -> P0: Y[NC][N][N]
+template <int N, int Q1, int NC, class R>
+__device__ __forceinline__ void adj2(const R* __restrict__ B, const R* __restrict__ G, R* P0, R* P1, int lane) {
+  for (int t = lane; t < NC * N * Q1; t += 32) {
+    const int q0 = t % Q1, j = (t / Q1) % N, c = t / (Q1 * N);
+    const R* r0 = P0 + (c * 2 + 0) * Q1 * Q1 + q0;
+    const R* r1 = P0 + (c * 2 + 1) * Q1 * Q1 + q0;
+    R u0 = R(0), u1 = R(0);
+#pragma unroll
+    for (int q1 = 0; q1 < Q1; ++q1) {
+      u0 = fma(r0[q1 * Q1], B[q1 * N + j], u0);
+      u1 = fma(r1[q1 * Q1], G[q1 * N + j], u1);
+    }
+    P1[((c * 2 + 0) * N + j) * Q1 + q0] = u0;  // pairs with G in x
+    P1[((c * 2 + 1) * N + j) * Q1 + q0] = u1;  // pairs with B in x
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * N * N; t += 32) {
+    const int i = t % N, j = (t / N) % N, c = t / (N * N);
+    const R* u0 = P1 + ((c * 2 + 0) * N + j) * Q1;
+    const R* u1 = P1 + ((c * 2 + 1) * N + j) * Q1;
+    R y = R(0);
+#pragma unroll
+    for (int q0 = 0; q0 < Q1; ++q0) y = fma(u0[q0], G[q0 * N + i], fma(u1[q0], B[q0 * N + i], y));
+    P0[(c * N + j) * N + i] = y;
+  }
+  __syncwarp();
+}
+
+// 3D forward. P0: X[NC][N][N][N] -> P1: S1[NC][2][N][N][Q] -> P0: S2[NC][3][N][Q][Q]
+// -> P1: A[NC][3][Q][Q][Q]
+template <int N, int Q1, int NC, class R>
+__device__ __forceinline__ void fwd3(const R* __restrict__ B, const R* __restrict__ G, R* P0, R* P1, int lane) {
+  constexpr int NNQ = N * N * Q1, NQQ = N * Q1 * Q1, QQ = Q1 * Q1, QQQ = Q1 * Q1 * Q1;
+  for (int t = lane; t < NC * N * N * Q1; t += 32) {
+    const int q0 = t % Q1, lj = (t / Q1) % (N * N), c = t / (Q1 * N * N);
+    const R* xr = P0 + (c * N * N + lj) * N;
+    R sb = R(0), sg = R(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const R xv = xr[i];
+      sb = fma(xv, B[q0 * N + i], sb);
+      sg = fma(xv, G[q0 * N + i], sg);
+    }
+    P1[(c * 2 + 0) * NNQ + lj * Q1 + q0] = sb;
+    P1[(c * 2 + 1) * NNQ + lj * Q1 + q0] = sg;
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * N * QQ; t += 32) {
+    const int q0 = t % Q1, q1 = (t / Q1) % Q1, l = (t / QQ) % N, c = t / (QQ * N);
+    const R* xb = P1 + (c * 2 + 0) * NNQ + l * N * Q1 + q0;
+    const R* xg = P1 + (c * 2 + 1) * NNQ + l * N * Q1 + q0;
+    R bb = R(0), bg = R(0), gb = R(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const R b = xb[j * Q1], g = xg[j * Q1];
+      bb = fma(b, B[q1 * N + j], bb);
+      bg = fma(b, G[q1 * N + j], bg);
+      gb = fma(g, B[q1 * N + j], gb);
+    }
+    const int o = l * QQ + q1 * Q1 + q0;
+    P0[(c * 3 + 0) * NQQ + o] = bb;
+    P0[(c * 3 + 1) * NQQ + o] = bg;
+    P0[(c * 3 + 2) * NQQ + o] = gb;
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * QQQ; t += 32) {
+    const int q01 = t % QQ, q2 = (t / QQ) % Q1, c = t / QQQ;
+    const R* sbb = P0 + (c * 3 + 0) * NQQ + q01;
+    const R* sbg = P0 + (c * 3 + 1) * NQQ + q01;
+    const R* sgb = P0 + (c * 3 + 2) * NQQ + q01;
+    R a0 = R(0), a1 = R(0), a2 = R(0);
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      const R bl = B[q2 * N + l], gl = G[q2 * N + l];
+      a0 = fma(sgb[l * QQ], bl, a0);
+      a1 = fma(sbg[l * QQ], bl, a1);
+      a2 = fma(sbb[l * QQ], gl, a2);
+    }
+    const int o = q2 * QQ + q01;
+    P1[(c * 3 + 0) * QQQ + o] = a0;
+    P1[(c * 3 + 1) * QQQ + o] = a1;
+    P1[(c * 3 + 2) * QQQ + o] = a2;
+  }
+  __syncwarp();
+}
+
+// 3D adjoint. P1: R[NC][3][Q][Q][Q] -> P0: U[NC][3][N][Q][Q] -> P1: V[NC][2][N][N][Q]
+// -> P0: Y[NC][N][N][N]
+template <int N, int Q1, int NC, class R>
+__device__ __forceinline__ void adj3(const R* __restrict__ B, const R* __restrict__ G, R* P0, R* P1, int lane) {
+  constexpr int NNQ = N * N * Q1, NQQ = N * Q1 * Q1, QQ = Q1 * Q1, QQQ = Q1 * Q1 * Q1;
+  for (int t = lane; t < NC * N * QQ; t += 32) {
+    const int q01 = t % QQ, l = (t / QQ) % N, c = t / (QQ * N);
+    const R* r0 = P1 + (c * 3 + 0) * QQQ + q01;
+    const R* r1 = P1 + (c * 3 + 1) * QQQ + q01;
+    const R* r2 = P1 + (c * 3 + 2) * QQQ + q01;
+    R u0 = R(0), u1 = R(0), u2 = R(0);
+#pragma unroll
+    for (int q2 = 0; q2 < Q1; ++q2) {
+      const R bl = B[q2 * N + l], gl = G[q2 * N + l];
+      u0 = fma(r0[q2 * QQ], bl, u0);
+      u1 = fma(r1[q2 * QQ], bl, u1);
+      u2 = fma(r2[q2 * QQ], gl, u2);
+    }
+    const int o = l * QQ + q01;
+    P0[(c * 3 + 0) * NQQ + o] = u0;
+    P0[(c * 3 + 1) * NQQ + o] = u1;
+    P0[(c * 3 + 2) * NQQ + o] = u2;
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * N * N * Q1; t += 32) {
+    const int q0 = t % Q1, j = (t / Q1) % N, l = (t / (Q1 * N)) % N, c = t / (Q1 * N * N);
+    const R* u0 = P0 + (c * 3 + 0) * NQQ + l * QQ + q0;
+    const R* u1 = P0 + (c * 3 + 1) * NQQ + l * QQ + q0;
+    const R* u2 = P0 + (c * 3 + 2) * NQQ + l * QQ + q0;
+    R vg = R(0), vb = R(0);
+#pragma unroll
+    for (int q1 = 0; q1 < Q1; ++q1) {
+      const R bj = B[q1 * N + j], gj = G[q1 * N + j];
+      vg = fma(u0[q1 * Q1], bj, vg);
+      vb = fma(u1[q1 * Q1], gj, fma(u2[q1 * Q1], bj, vb));
+    }
+    const int o = (l * N + j) * Q1 + q0;
+    P1[(c * 2 + 0) * NNQ + o] = vg;  // pairs with G in x
+    P1[(c * 2 + 1) * NNQ + o] = vb;  // pairs with B in x
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * N * N * N; t += 32) {
+    const int i = t % N, lj = (t / N) % (N * N), c = t / (N * N * N);
+    const R* vg = P1 + (c * 2 + 0) * NNQ + lj * Q1;
+    const R* vb = P1 + (c * 2 + 1) * NNQ + lj * Q1;
+    R y = R(0);
+#pragma unroll
+    for (int q0 = 0; q0 < Q1; ++q0) y = fma(vg[q0], G[q0 * N + i], fma(vb[q0], B[q0 * N + i], y));
+    P0[(c * N * N + lj) * N + i] = y;
+  }
+  __syncwarp();
+}
+
+}  // namespace tmop

@@ -1,0 +1,283 @@
+// Fused TMOP element kernel: one warp per element.
+//
+//   gather  x (and v) of the element's n^d nodes into shared memory
+//   forward A(q) = sum_i x_i grad phi_i(q)            (eq. (2.2), sum factorised)
+//   point   T = A W^-1, mu / P / dP                   (Table 3.1, Section 3.4)
+//   adjoint y_i += sum_q w_q det W [S W^-t grad phi_i] (gradient formula of Section 3.4)
+//   scatter FP64 atomics into the nodal output, fixed dofs skipped
+//
+// OP_ENERGY instead accumulates w_q det W mu and min det A in FP64 and writes
+// one partial per block (reduced in a second, fixed-order pass).
+#pragma once
+#include "tmop_device.cuh"
+#include "tmop_kparams.h"
+
+namespace tmop {
+
+template <int D, int N, int Q1>
+struct Shape {
+  static constexpr int NDOF = (D == 2) ? N * N : N * N * N;
+  static constexpr int QP = (D == 2) ? Q1 * Q1 : Q1 * Q1 * Q1;
+};
+
+template <int a, int b> struct cmax { static constexpr int value = a > b ? a : b; };
+
+// Shared-memory words (of type R) per warp for NC gathered components.
+template <int D, int N, int Q1, int NC>
+struct Buf {
+  static constexpr int B0 = (D == 2) ? cmax<NC * N * N, 2 * NC * Q1 * Q1>::value
+                                     : cmax<NC * N * N * N, 3 * NC * N * Q1 * Q1>::value;
+  static constexpr int B1 = (D == 2) ? 2 * NC * N * Q1
+                                     : cmax<2 * NC * N * N * Q1, 3 * NC * Q1 * Q1 * Q1>::value;
+};
+
+template <int D, int N, int Q1, class R, int OP>
+struct ElemCfg {
+  static constexpr int NC = (OP == OP_HESS) ? 2 * D : D;
+  static constexpr int B0 = Buf<D, N, Q1, NC>::B0;
+  static constexpr int B1 = Buf<D, N, Q1, NC>::B1;
+  static constexpr int PER_WARP = (int)sizeof(R) * (B0 + B1);
+  // up to 4 warps per block within ~200 KB of shared memory
+  static constexpr int WARPS = (200 * 1024 / PER_WARP) >= 4 ? 4 : ((200 * 1024 / PER_WARP) < 1 ? 1 : 200 * 1024 / PER_WARP);
+  static constexpr int TABLE = 2 * kMaxQ * kMaxN + kMaxQ;
+  static constexpr size_t smem_bytes() { return sizeof(R) * (TABLE + WARPS * (B0 + B1)); }
+};
+
+__device__ __forceinline__ int node_id(const KParams& p, int e, int t, int N) {
+  if (p.sx > 0) {
+    const int k = N - 1;
+    const int Nx = k * p.sx + 1, Ny = k * p.sy + 1;
+    const int ex = e % p.sx, ey = (e / p.sx) % p.sy, ez = e / (p.sx * p.sy);
+    const int i = t % N, j = (t / N) % N, l = t / (N * N);
+    return ((ez * k + l) * Ny + ey * k + j) * Nx + ex * k + i;
+  }
+  return __ldg(p.elem_nodes + (size_t)e * (p.dim == 2 ? N * N : N * N * N) + t);
+}
+
+template <int D, int N, int Q1, class R, int OP>
+__global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
+    elem_kernel(const KParams p) {
+  using Cfg = ElemCfg<D, N, Q1, R, OP>;
+  constexpr int NDOF = Shape<D, N, Q1>::NDOF, QP = Shape<D, N, Q1>::QP, DD = D * D;
+  constexpr int WARPS = Cfg::WARPS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* sB = reinterpret_cast<R*>(smem_raw);
+  R* sG = sB + kMaxQ * kMaxN;
+  R* sw = sG + kMaxQ * kMaxN;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  R* P0 = sB + Cfg::TABLE + warp * (Cfg::B0 + Cfg::B1);
+  R* P1 = P0 + Cfg::B0;
+  for (int t = threadIdx.x; t < Q1 * N; t += blockDim.x) {
+    sB[t] = R(p.B[t]);
+    sG[t] = R(p.G[t]);
+  }
+  for (int t = threadIdx.x; t < Q1; t += blockDim.x) sw[t] = R(p.w1[t]);
+  R Wi[DD];
+#pragma unroll
+  for (int i = 0; i < DD; ++i) Wi[i] = R(p.Winv[i]);
+  __syncthreads();
+
+  double accF = 0.0, accMin = INFINITY;
+  const int nwarps_total = gridDim.x * WARPS;
+  for (int e = blockIdx.x * WARPS + warp; e < p.nelem; e += nwarps_total) {
+    // ---- gather. In FP32 the coordinates are taken relative to the element's
+    // first node (in FP64) before rounding: A is translation invariant
+    // (sum_i grad phi_i = 0), and this keeps the FP32 relative error of A at
+    // the level of eps32 instead of eps32 |x| / h.
+    double xref[D];
+    if constexpr (sizeof(R) == 4) {
+      const int g0 = node_id(p, e, 0, N);
+#pragma unroll
+      for (int c = 0; c < D; ++c) xref[c] = __ldg(p.x + (size_t)c * p.nnode + g0);
+    }
+    for (int t = lane; t < NDOF; t += 32) {
+      const int g = node_id(p, e, t, N);
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const double xv = __ldg(p.x + (size_t)c * p.nnode + g);
+        if constexpr (sizeof(R) == 4) P0[c * NDOF + t] = R(xv - xref[c]);
+        else P0[c * NDOF + t] = R(xv);
+      }
+      if constexpr (OP == OP_HESS) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const size_t dof = (size_t)c * p.nnode + g;
+          const bool fx = p.fixed && __ldg(p.fixed + dof);
+          P0[(D + c) * NDOF + t] = fx ? R(0) : R(__ldg(p.v + dof));
+        }
+      }
+    }
+    __syncwarp();
+    // ---- forward contraction: A (and dA) at every point
+    if constexpr (D == 2) fwd2<N, Q1, Cfg::NC, R>(sB, sG, P0, P1, lane);
+    else fwd3<N, Q1, Cfg::NC, R>(sB, sG, P0, P1, lane);
+    R* Abuf = (D == 2) ? P0 : P1;  // [NC][D][QP]
+    // ---- pointwise
+    double emin = INFINITY;
+    for (int q = lane; q < QP; q += 32) {
+      R A[DD];
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) A[a * D + b] = Abuf[(a * D + b) * QP + q];
+      const int q0 = q % Q1, q1 = (q / Q1) % Q1;
+      R wq = sw[q0] * sw[q1];
+      if constexpr (D == 3) wq *= sw[q / (Q1 * Q1)];
+      R detW = R(p.detW);
+      if (p.wkind == WK_PER_QP) {
+        const double* Wq = p.Winv_qp + ((size_t)e * QP + q) * DD;
+#pragma unroll
+        for (int i = 0; i < DD; ++i) Wi[i] = R(__ldg(Wq + i));
+        detW = R(__ldg(p.detW_qp + (size_t)e * QP + q));
+      }
+      R T[DD];
+      if (p.wkind == WK_IDENTITY) {
+#pragma unroll
+        for (int i = 0; i < DD; ++i) T[i] = A[i];
+      } else {
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int b = 0; b < D; ++b) {
+            R s = R(0);
+#pragma unroll
+            for (int c = 0; c < D; ++c) s = fma(A[a * D + c], Wi[c * D + b], s);
+            T[a * D + b] = s;
+          }
+      }
+      if constexpr (OP == OP_ENERGY) {
+        double Ad[DD];
+#pragma unroll
+        for (int i = 0; i < DD; ++i) Ad[i] = double(A[i]);
+        const double dA = det_m<D>(Ad);
+        emin = fmin(emin, dA);
+        R mu;
+        R Pd[DD];
+        if (metric_P<D>(p.metric, T, mu, Pd)) accF += double(wq * detW) * double(mu);
+        else accF = INFINITY;
+      } else {
+        R S[DD];
+        bool ok;
+        if constexpr (OP == OP_GRADIENT) {
+          R mu;
+          ok = metric_P<D>(p.metric, T, mu, S);
+        } else {
+          R dA[DD], dT[DD];
+#pragma unroll
+          for (int i = 0; i < DD; ++i) dA[i] = Abuf[(DD + i) * QP + q];
+          if (p.wkind == WK_IDENTITY) {
+#pragma unroll
+            for (int i = 0; i < DD; ++i) dT[i] = dA[i];
+          } else {
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+              for (int b = 0; b < D; ++b) {
+                R s = R(0);
+#pragma unroll
+                for (int c = 0; c < D; ++c) s = fma(dA[a * D + c], Wi[c * D + b], s);
+                dT[a * D + b] = s;
+              }
+          }
+          Dual<R> Td[DD], Pd[DD], mud;
+#pragma unroll
+          for (int i = 0; i < DD; ++i) Td[i] = Dual<R>{T[i], dT[i]};
+          ok = metric_P<D>(p.metric, Td, mud, Pd);
+#pragma unroll
+          for (int i = 0; i < DD; ++i) S[i] = Pd[i].d;
+        }
+        const R s = wq * detW;
+        // R = s * S W^-t, stored in place of A at this point
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int b = 0; b < D; ++b) {
+            R r = R(0);
+            if (p.wkind == WK_IDENTITY) {
+              r = S[a * D + b];
+            } else {
+#pragma unroll
+              for (int c = 0; c < D; ++c) r = fma(S[a * D + c], Wi[b * D + c], r);
+            }
+            Abuf[(a * D + b) * QP + q] = ok ? s * r : R(0);
+          }
+      }
+    }
+    if constexpr (OP == OP_ENERGY) {
+      accMin = fmin(accMin, emin);
+      if (p.elem_min) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) emin = fmin(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+        if (lane == 0) p.elem_min[e] = emin;
+      }
+    } else {
+      __syncwarp();
+      // ---- adjoint contraction and scatter
+      if constexpr (D == 2) adj2<N, Q1, D, R>(sB, sG, P0, P1, lane);
+      else adj3<N, Q1, D, R>(sB, sG, P0, P1, lane);
+      for (int t = lane; t < NDOF; t += 32) {
+        const int g = node_id(p, e, t, N);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const size_t dof = (size_t)c * p.nnode + g;
+          if (p.fixed && __ldg(p.fixed + dof)) continue;
+          atomicAdd(p.y + dof, double(P0[c * NDOF + t]));
+        }
+      }
+    }
+    __syncwarp();
+  }
+
+  if constexpr (OP == OP_ENERGY) {
+    __shared__ double redF[WARPS], redM[WARPS];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      accF += __shfl_xor_sync(0xffffffffu, accF, o);
+      accMin = fmin(accMin, __shfl_xor_sync(0xffffffffu, accMin, o));
+    }
+    if (lane == 0) { redF[warp] = accF; redM[warp] = accMin; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double f = 0.0, m = INFINITY;
+      for (int w = 0; w < WARPS; ++w) { f += redF[w]; m = fmin(m, redM[w]); }
+      p.part_F[blockIdx.x] = f;
+      p.part_min[blockIdx.x] = m;
+    }
+  }
+}
+
+// Host-side launcher for one instantiation.
+template <int D, int N, int Q1, class R, int OP>
+int launch_elem(const KParams& p, int grid, void* stream) {
+  using Cfg = ElemCfg<D, N, Q1, R, OP>;
+  elem_kernel<D, N, Q1, R, OP><<<grid, Cfg::WARPS * 32, Cfg::smem_bytes(), (cudaStream_t)stream>>>(p);
+  return (int)cudaGetLastError();
+}
+
+// Occupancy-derived grid size, and the opt-in for > 48 KB of shared memory.
+template <int D, int N, int Q1, class R, int OP>
+int prepare_elem_impl(int nelem, int* grid) {
+  using Cfg = ElemCfg<D, N, Q1, R, OP>;
+  const size_t smem = Cfg::smem_bytes();
+  cudaError_t err = cudaFuncSetAttribute((const void*)elem_kernel<D, N, Q1, R, OP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return (int)err;
+  int per_sm = 0, dev = 0, sms = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)elem_kernel<D, N, Q1, R, OP>,
+                                                      Cfg::WARPS * 32, smem);
+  if (err != cudaSuccess) return (int)err;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
+  const int need = (nelem + Cfg::WARPS - 1) / Cfg::WARPS;
+  const int full = per_sm * sms;
+  *grid = need < full ? need : full;
+  return 0;
+}
+
+template <int D, int N, int Q1, class R, int OP>
+int prepare_elem(int nelem, int* grid) {
+  return (int)prepare_elem_impl<D, N, Q1, R, OP>(nelem, grid);
+}
+
+}  // namespace tmop

@@ -1,0 +1,48 @@
+// Launch parameters of the TMOP element kernels, passed by value (they live
+// in the kernel-parameter constant bank). The 1D tables are always FP64 here;
+// FP32 kernels round them once into shared memory.
+#pragma once
+#include <stddef.h>
+#include <stdint.h>
+
+namespace tmop {
+
+constexpr int kMaxQ = 8;   // 1D quadrature points
+constexpr int kMaxN = 5;   // 1D nodes (order <= 4)
+
+enum { OP_ENERGY = 0, OP_GRADIENT = 1, OP_HESS = 2 };
+enum { WK_IDENTITY = 0, WK_CONST = 1, WK_PER_QP = 2 };
+
+struct KParams {
+  int dim, nelem, nnode, metric, wkind;
+  int sx, sy, sz;                 // structured grid (sx > 0) or elem_nodes
+  const int32_t* elem_nodes;      // [nelem][n^d]
+  const uint8_t* fixed;           // [d][nnode] or null
+  const double* x;                // [d][nnode]
+  const double* v;                // [d][nnode] (Hessian action)
+  double* y;                      // [d][nnode] accumulated output
+  const double* Winv_qp;          // [nelem][Q][d][d] (per-point targets)
+  const double* detW_qp;          // [nelem][Q]
+  double* part_F;                 // [grid] energy partials
+  double* part_min;               // [grid] min det A partials
+  double* elem_min;               // [nelem] per-element min det A, or null
+  double B[kMaxQ * kMaxN];              // B[q][i] = phi_i(xi_q)
+  double G[kMaxQ * kMaxN];              // G[q][i] = phi_i'(xi_q)
+  double w1[kMaxQ];                // 1D quadrature weights
+  double Winv[9];                 // constant W^-1 (row-major)
+  double detW;                    // constant det W
+};
+
+typedef int (*elem_launch_fn)(const KParams& p, int grid, void* stream);
+typedef int (*elem_prepare_fn)(int nelem, int* grid);
+
+struct ElemEntry {
+  int dim, n, q, fp32, op;
+  elem_launch_fn launch;
+  elem_prepare_fn prepare;
+};
+
+// Defined in the per-dimension/precision instantiation units.
+const ElemEntry* find_elem(int dim, int n, int q, int fp32, int op);
+
+}  // namespace tmop

@@ -1,0 +1,260 @@
+"""Python binding of the C ABI in include/tmop.h (argument marshalling only).
+
+Every computation runs in libtmop_gb300.so. Tensors passed in must be
+contiguous float64 CUDA tensors of shape [dim, nnode]; their data pointers go
+straight to the library together with torch's current CUDA stream. If the
+library is missing this module raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtmop_gb300.so")
+
+OK, ERR_ARG, ERR_CUDA, ERR_INVERTED, ERR_LINESEARCH, ERR_NOT_CONVERGED = 0, 1, 2, 3, 4, 5
+GL, GLL = 0, 1
+W_IDENTITY, W_CONST, W_SCALED, W_PER_QP = 0, 1, 2, 3
+FP64, FP32_MIXED = 0, 1
+MINRES, CG = 0, 1
+
+
+class TmopError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+        self.status = status
+
+
+class _Mesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nelem", C.c_int), ("nnode", C.c_int), ("elem_nodes", C.c_void_p),
+                ("fixed", C.c_void_p), ("structured", C.c_int * 3)]
+
+
+class _Quad(C.Structure):
+    _fields_ = [("kind", C.c_int), ("npts1d", C.c_int)]
+
+
+class _Targets(C.Structure):
+    _fields_ = [("kind", C.c_int), ("scale", C.c_double), ("W", C.c_void_p)]
+
+
+class NewtonOpts(C.Structure):
+    _fields_ = [("max_newton", C.c_int), ("rtol", C.c_double), ("krylov", C.c_int), ("krylov_rtol", C.c_double),
+                ("krylov_maxit", C.c_int), ("alpha_shrink", C.c_double), ("max_halvings", C.c_int),
+                ("f_factor", C.c_double), ("g_factor", C.c_double)]
+
+
+class NewtonReport(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("krylov_iterations", C.c_int),
+                ("alpha", C.c_double), ("F", C.c_double), ("grad_norm", C.c_double),
+                ("grad_norm0", C.c_double), ("min_detA", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+# every symbol declared in include/tmop.h, with its ctypes signature
+_SIGNATURES = {
+    "tmop_setup": ([C.POINTER(_Mesh), C.c_int, C.POINTER(_Quad), C.c_int, C.POINTER(_Targets), C.c_int,
+                    C.POINTER(C.c_void_p)], C.c_int),
+    "tmop_energy": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p], C.c_int),
+    "tmop_gradient": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "tmop_hess_apply": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "tmop_newton_step": ([C.c_void_p, C.c_void_p, C.POINTER(NewtonOpts), C.POINTER(NewtonReport), C.c_void_p],
+                         C.c_int),
+    "tmop_newton_solve": ([C.c_void_p, C.c_void_p, C.POINTER(NewtonOpts), C.POINTER(NewtonReport), C.c_void_p],
+                          C.c_int),
+    "tmop_krylov_solve": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(NewtonOpts),
+                           C.POINTER(C.c_int), C.c_void_p], C.c_int),
+    "tmop_element_min_detA": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "tmop_sizes": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
+                   C.c_int),
+    "tmop_destroy": ([C.c_void_p], None),
+    "tmop_status_string": ([C.c_int], C.c_char_p),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libtmop_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_1807_09807_gb300.build.build()")
+        lib = C.CDLL(path)
+        for name, (args, res) in _SIGNATURES.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return load().tmop_status_string(status).decode()
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr())
+
+
+def _check_vec(t, shape, what):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{what} must be a contiguous float64 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{what} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+@dataclass
+class NewtonResult:
+    status: int
+    report: dict
+
+
+class Context:
+    """A TMOP problem on the GPU: mesh topology, quadrature, metric, targets,
+    precision form. Wraps tmop_setup / tmop_destroy."""
+
+    def __init__(self, dim: int, order: int, nnode: int, elem_nodes: Optional[np.ndarray], fixed: Optional[np.ndarray],
+                 nq: int, metric: int, quad_kind: int = GL, structured=None, target_kind: int = W_IDENTITY,
+                 target_scale: float = 1.0, W: Optional[np.ndarray] = None, precision: int = FP64,
+                 nelem: Optional[int] = None):
+        lib = load()
+        self.dim, self.order, self.nnode, self.nq, self.metric, self.precision = dim, order, nnode, nq, metric, precision
+        self._en = None if elem_nodes is None else np.ascontiguousarray(elem_nodes, dtype=np.int32)
+        self._fx = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
+        self._W = None if W is None else np.ascontiguousarray(W, dtype=np.float64)
+        if nelem is None:
+            nelem = self._en.shape[0]
+        self.nelem = nelem
+        st = (C.c_int * 3)(*(list(structured) + [0] * (3 - len(structured)) if structured else [0, 0, 0]))
+        m = _Mesh(dim, nelem, nnode, None if self._en is None else self._en.ctypes.data,
+                  None if self._fx is None else self._fx.ctypes.data, st)
+        q = _Quad(quad_kind, nq)
+        t = _Targets(target_kind, target_scale, None if self._W is None else self._W.ctypes.data)
+        h = C.c_void_p()
+        rc = lib.tmop_setup(C.byref(m), order, C.byref(q), metric, C.byref(t), precision, C.byref(h))
+        if rc != OK:
+            raise TmopError(rc, "tmop_setup")
+        self._h = h
+        d, ne, nn, Q = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        lib.tmop_sizes(h, C.byref(d), C.byref(ne), C.byref(nn), C.byref(Q))
+        self.Q = Q.value
+
+    @classmethod
+    def from_mesh(cls, m, precision: int = FP64, metric: Optional[int] = None, structured: bool = True,
+                  target_scale: Optional[float] = None, W_per_qp: Optional[np.ndarray] = None):
+        """Context for a meshgen.Mesh (structured fast path by default)."""
+        kind, scale, W = W_IDENTITY, 1.0, None
+        if W_per_qp is not None:
+            kind, W = W_PER_QP, W_per_qp
+        elif target_scale is not None:
+            kind, scale = W_SCALED, target_scale
+        elif m.W is not None:
+            kind, W = W_CONST, m.W
+        return cls(m.dim, m.order, m.nnode, None if structured else m.elem_nodes, m.fixed, m.nq,
+                   metric or m.metric, quad_kind=m.quad_kind, structured=list(m.nx) if structured else None,
+                   target_kind=kind, target_scale=scale, W=W, precision=precision, nelem=m.nelem)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().tmop_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (self.dim, self.nnode)
+
+    def energy(self, x):
+        """(status, F, min det A): eq. (2.4) and the det A > 0 check."""
+        _check_vec(x, self.shape, "x")
+        F, md = C.c_double(), C.c_double()
+        rc = load().tmop_energy(self._h, _ptr(x), C.byref(F), C.byref(md), _stream())
+        if rc not in (OK, ERR_INVERTED):
+            raise TmopError(rc, "tmop_energy")
+        return rc, F.value, md.value
+
+    def gradient(self, x, out=None):
+        import torch
+        _check_vec(x, self.shape, "x")
+        g = torch.empty_like(x) if out is None else out
+        _check_vec(g, self.shape, "g")
+        rc = load().tmop_gradient(self._h, _ptr(x), _ptr(g), _stream())
+        if rc != OK:
+            raise TmopError(rc, "tmop_gradient")
+        return g
+
+    def hess_apply(self, x, v, out=None):
+        import torch
+        _check_vec(x, self.shape, "x")
+        _check_vec(v, self.shape, "v")
+        y = torch.empty_like(x) if out is None else out
+        _check_vec(y, self.shape, "y")
+        rc = load().tmop_hess_apply(self._h, _ptr(x), _ptr(v), _ptr(y), _stream())
+        if rc != OK:
+            raise TmopError(rc, "tmop_hess_apply")
+        return y
+
+    def element_min_detA(self, x, out=None):
+        import torch
+        _check_vec(x, self.shape, "x")
+        o = torch.empty(self.nelem, dtype=torch.float64, device=x.device) if out is None else out
+        rc = load().tmop_element_min_detA(self._h, _ptr(x), _ptr(o), _stream())
+        if rc != OK:
+            raise TmopError(rc, "tmop_element_min_detA")
+        return o
+
+    @staticmethod
+    def opts(**kw) -> NewtonOpts:
+        o = NewtonOpts()
+        for k, v in kw.items():
+            if k == "krylov" and isinstance(v, str):
+                v = CG if v == "cg" else MINRES
+            setattr(o, k, v)
+        return o
+
+    def krylov_solve(self, x, b, out=None, **kw):
+        import torch
+        _check_vec(x, self.shape, "x")
+        _check_vec(b, self.shape, "b")
+        p = torch.empty_like(x) if out is None else out
+        it = C.c_int()
+        o = self.opts(**kw)
+        rc = load().tmop_krylov_solve(self._h, _ptr(x), _ptr(b), _ptr(p), C.byref(o), C.byref(it), _stream())
+        if rc != OK:
+            raise TmopError(rc, "tmop_krylov_solve")
+        return p, it.value
+
+    def newton_step(self, x, **kw) -> NewtonResult:
+        _check_vec(x, self.shape, "x")
+        o, r = self.opts(**kw), NewtonReport()
+        rc = load().tmop_newton_step(self._h, _ptr(x), C.byref(o), C.byref(r), _stream())
+        if rc in (ERR_ARG, ERR_CUDA):
+            raise TmopError(rc, "tmop_newton_step")
+        return NewtonResult(rc, r.as_dict())
+
+    def newton_solve(self, x, **kw) -> NewtonResult:
+        _check_vec(x, self.shape, "x")
+        o, r = self.opts(**kw), NewtonReport()
+        rc = load().tmop_newton_solve(self._h, _ptr(x), C.byref(o), C.byref(r), _stream())
+        if rc in (ERR_ARG, ERR_CUDA):
+            raise TmopError(rc, "tmop_newton_solve")
+        return NewtonResult(rc, r.as_dict())

@@ -1,0 +1,282 @@
+"""GPU parity: every C-ABI call of the CUDA library against the FP64 CPU
+oracle on the same seeded inputs.
+
+Tolerances (FP64 path, relative):
+  F and min det A: 1e-12; gradient and Hessian action: normwise 1e-12
+  (FP64 atomics make the summation order of nodal contributions differ from
+  the oracle's element order, so entries agree only normwise).
+FP32-mixed path: bounds derived from eps32 = 6e-8 times the conditioning of
+each result; see test_fp32_mixed_bounds.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1807_09807_gb300 import meshgen as mg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def tm():
+    from paper_1807_09807_gb300 import build as cuda_build
+    cuda_build.build()
+    from paper_1807_09807_gb300 import tmop
+    tmop.load()
+    return tmop
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def orc_for(m, metric=None, W=None, Wqp=None):
+    if Wqp is not None:
+        return oracle.Problem(m.dim, m.order, m.elem_nodes, m.nnode, m.fixed, m.nq, metric or m.metric,
+                              quad_kind=m.quad_kind, wkind=oracle.W_PER_QP, W=Wqp)
+    wk = oracle.W_IDENTITY if W is None else oracle.W_CONST
+    return oracle.Problem(m.dim, m.order, m.elem_nodes, m.nnode, m.fixed, m.nq, metric or m.metric,
+                          quad_kind=m.quad_kind, wkind=wk, W=W)
+
+
+def make(name, seed=1, **kw):
+    """Seeded mesh, redrawn until the oracle sees det A > 0 everywhere."""
+    return mg.make_mesh(name, seed, accept=lambda mm: orc_for(mm).energy(mm.x)[2] > 0, **kw)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def check_all(tm, m, ctx, orc, rtol_F=RTOL, rtol_vec=RTOL, seed=0):
+    x = dev(m.x)
+    rc, F, md = ctx.energy(x)
+    rco, Fo, mdo = orc.energy(m.x)
+    assert rc == tm.OK and rco == oracle.OK
+    assert abs(F - Fo) <= rtol_F * abs(Fo), (F, Fo)
+    assert abs(md - mdo) <= rtol_F * abs(mdo), (md, mdo)
+    g = host(ctx.gradient(x))
+    go = orc.gradient(m.x)
+    assert rel(g, go) <= rtol_vec, rel(g, go)
+    assert np.all(g[m.fixed == 1] == 0.0)
+    v = np.random.default_rng(seed).standard_normal(m.x.shape)
+    y = host(ctx.hess_apply(x, dev(v)))
+    yo = orc.hess_apply(m.x, v)
+    assert rel(y, yo) <= rtol_vec, rel(y, yo)
+    assert np.all(y[m.fixed == 1] == 0.0)
+    return F, g, y
+
+
+SMALL = [("c1", {}), ("c2", dict(nx=6)), ("c3", dict(nx=3)), ("c4", dict(nx=3)), ("c5", dict(nx=5))]
+
+
+@pytest.mark.parametrize("name,kw", SMALL)
+@pytest.mark.parametrize("structured", [True, False])
+def test_fp64_small_configs(tm, name, kw, structured):
+    m = make(name, 1, **kw)
+    check_all(tm, m, tm.Context.from_mesh(m, structured=structured), orc_for(m))
+
+
+@pytest.mark.parametrize("dim,metric", [(2, 1), (2, 2), (2, 7), (2, 9), (2, 14), (2, 77),
+                                        (3, 1), (3, 14), (3, 302), (3, 303)])
+def test_fp64_every_metric(tm, dim, metric):
+    m = make("c1" if dim == 2 else "c3", 2, nx=4 if dim == 2 else 2)
+    scale = 1.0 / 4 if metric in (7, 9, 77) else None      # element size: W2 of eq. (3.1)
+    ctx = tm.Context.from_mesh(m, metric=metric, target_scale=scale)
+    orc = orc_for(m, metric=metric, W=None if scale is None else np.eye(dim) * scale)
+    check_all(tm, m, ctx, orc)
+
+
+@pytest.mark.parametrize("dim,order,nq", [(2, 1, 2), (2, 1, 3), (2, 2, 3), (2, 2, 5), (2, 3, 4), (2, 3, 6),
+                                          (2, 4, 5), (2, 4, 6), (3, 1, 2), (3, 1, 3), (3, 2, 3), (3, 3, 4),
+                                          (3, 4, 5), (3, 4, 6)])
+def test_fp64_every_order_and_rule(tm, dim, order, nq):
+    m = make("c1" if dim == 2 else "c3", 3, order=order, nq=nq, nx=3 if dim == 2 else 2)
+    check_all(tm, m, tm.Context.from_mesh(m), orc_for(m))
+
+
+def test_fp64_gauss_lobatto(tm):
+    m = make("c2", 1, nx=5, quad_kind=mg.GLL, nq=6)
+    check_all(tm, m, tm.Context.from_mesh(m), orc_for(m))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fp64_general_and_per_point_targets(tm, dim):
+    rng = np.random.default_rng(7)
+    m = make("c1" if dim == 2 else "c3", 4, nx=3 if dim == 2 else 2)
+    W = (np.eye(dim) + 0.2 * rng.standard_normal((dim, dim))) / 6
+    if np.linalg.det(W) < 0:
+        W[:, 0] *= -1
+    m.W = W
+    check_all(tm, m, tm.Context.from_mesh(m), orc_for(m, W=W))
+    Wq = (np.eye(dim) + 0.15 * rng.standard_normal((m.nelem, m.Q, dim, dim))) / 6
+    Wq[np.linalg.det(Wq) < 0, :, 0] *= -1
+    m.W = None
+    check_all(tm, m, tm.Context.from_mesh(m, W_per_qp=Wq), orc_for(m, Wqp=Wq))
+
+
+def test_fp64_ragged_and_single_element(tm):
+    # one element, and a 5x3 (non-square, element count not a multiple of a block)
+    for nx in [1, (5, 3)]:
+        m = make("c1", 1, nx=nx)
+        check_all(tm, m, tm.Context.from_mesh(m), orc_for(m))
+    m = make("c3", 1, nx=(3, 2, 1))
+    check_all(tm, m, tm.Context.from_mesh(m), orc_for(m))
+
+
+def test_fp64_no_fixed_dofs(tm):
+    m = make("c1", 1, nx=3)
+    m.fixed = np.zeros_like(m.fixed)
+    check_all(tm, m, tm.Context.from_mesh(m), orc_for(m))
+
+
+@pytest.mark.parametrize("name,metric", [("c2", 2), ("c2", 7), ("c3", 303), ("c3", 302)])
+def test_fp64_full_size(tm, name, metric):
+    m = make(name, 1)
+    scale = 1.0 / 64 if metric == 7 else None              # element size: W2 of eq. (3.1)
+    check_all(tm, m, tm.Context.from_mesh(m, metric=metric, target_scale=scale),
+              orc_for(m, metric=metric, W=None if scale is None else np.eye(2) * scale))
+
+
+def _patch(m, nodes):
+    """Elements touching any of the given nodes."""
+    return np.nonzero(np.isin(m.elem_nodes, nodes).any(axis=1))[0].astype(np.int32)
+
+
+def test_fp64_full_c4_sampled(tm):
+    """48^3 order-3 hexes (the benchmark workload, same launch shapes): F and
+    min det A in full; gradient and Hessian action at 64 sampled free nodes,
+    each against the oracle restricted to the elements around them."""
+    m = make("c4", 1)
+    ctx = tm.Context.from_mesh(m)
+    orc = orc_for(m)
+    x = dev(m.x)
+    rc, F, md = ctx.energy(x)
+    _, Fo, mdo = orc.energy(m.x)
+    assert abs(F - Fo) <= RTOL * Fo and abs(md - mdo) <= RTOL * abs(mdo)
+    rng = np.random.default_rng(3)
+    free = np.nonzero(m.fixed[0] == 0)[0]
+    nodes = rng.choice(free, 64, replace=False)
+    els = _patch(m, nodes)
+    g = host(ctx.gradient(x))[:, nodes]
+    go = orc.gradient(m.x, elems=els)[:, nodes]
+    assert rel(g, go) <= RTOL
+    v = rng.standard_normal(m.x.shape)
+    y = host(ctx.hess_apply(x, dev(v)))[:, nodes]
+    yo = orc.hess_apply(m.x, v, elems=els)[:, nodes]
+    assert rel(y, yo) <= RTOL
+    emin = host(ctx.element_min_detA(x))
+    sub = rng.choice(m.nelem, 200, replace=False).astype(np.int32)
+    for e in sub[:20]:
+        _, _, mde = orc.energy(m.x, elems=np.array([e], dtype=np.int32))
+        assert abs(emin[e] - mde) <= RTOL * abs(mde)
+    assert abs(emin.min() - mdo) <= RTOL * abs(mdo)
+
+
+def test_inverted_mesh(tm):
+    m = make("c1", 1, nx=4)
+    x = m.x_ideal.copy()
+    node = m.elem_nodes[5, 4]
+    x[0, node] += 0.3
+    ctx = tm.Context.from_mesh(m)
+    rc, F, md = ctx.energy(dev(x))
+    rco, Fo, mdo = orc_for(m).energy(x)
+    assert rc == tm.ERR_INVERTED and rco == oracle.ERR_INVERTED
+    assert F == np.inf and abs(md - mdo) <= RTOL * abs(mdo)
+    em = host(ctx.element_min_detA(dev(x)))
+    assert (em <= 0).sum() >= 1 and np.all((em <= 0) == (np.array(
+        [orc_for(m).energy(x, elems=np.array([e], dtype=np.int32))[2] for e in range(m.nelem)]) <= 0))
+
+
+def test_deterministic_energy(tm):
+    m = make("c3", 1, nx=8)
+    ctx = tm.Context.from_mesh(m)
+    x = dev(m.x)
+    vals = {ctx.energy(x)[1] for _ in range(5)}
+    assert len(vals) == 1
+
+
+# ---------------------------------------------------------------- solvers
+@pytest.mark.parametrize("krylov", ["minres", "cg"])
+def test_krylov_matches_oracle(tm, krylov):
+    m = make("c1", 1)
+    ctx = tm.Context.from_mesh(m)
+    orc = orc_for(m)
+    b = orc.gradient(m.x)
+    p, it = ctx.krylov_solve(dev(m.x), dev(b), krylov=krylov, krylov_rtol=1e-12, krylov_maxit=1000)
+    po, ito = (orc.minres if krylov == "minres" else orc.cg)(m.x, b, rtol=1e-12, maxit=1000)
+    assert it > 0 and ito > 0 and abs(it - ito) <= 3
+    assert rel(host(p), po) <= 1e-9
+    r = orc.hess_apply(m.x, host(p)) - b
+    assert np.linalg.norm(r) <= 1e-11 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("metric,scale", [(2, None), (7, 1.0 / 8)])
+def test_newton_matches_oracle_history(tm, metric, scale):
+    """Section 3.4 Newton on 8x8 order-2: same accepted steps and F history as
+    the oracle (to 1e-9 relative, Krylov rounding), convergence to the
+    uniform grid (F* = 0), det A > 0 throughout."""
+    m = make("c1", 1)
+    ctx = tm.Context.from_mesh(m, metric=metric, target_scale=scale)
+    orc = orc_for(m, metric=metric, W=None if scale is None else np.eye(2) * scale)
+    rco, xo, hist = orc.newton(m.x, max_newton=20)
+    x = dev(m.x)
+    Fs = [ctx.energy(x)[1]]
+    for it in range(len(hist) - 1):
+        r = ctx.newton_step(x, max_newton=20)
+        assert r.status == tm.OK
+        assert r.report["alpha"] == hist[it + 1, 3]
+        Fs.append(r.report["F"])
+        assert r.report["min_detA"] > 0
+    Fs = np.array(Fs)
+    F0 = hist[0, 0]
+    for k in range(len(Fs)):
+        assert abs(Fs[k] - hist[k, 0]) <= 1e-9 * hist[k, 0] + 1e-12 * F0, (k, Fs[k], hist[k, 0])
+    assert np.abs(host(x) - m.x_ideal).max() < 1e-11
+    x2 = dev(m.x)
+    res = ctx.newton_solve(x2, max_newton=20)
+    assert res.status == tm.OK and res.report["F"] <= 1e-12 * F0
+
+
+def test_newton_strict_monotone_and_barrier(tm):
+    m = make("c2", 2, nx=16)
+    ctx = tm.Context.from_mesh(m)
+    x = dev(m.x)
+    F = [ctx.energy(x)[1]]
+    for _ in range(6):
+        r = ctx.newton_step(x, f_factor=1.0)
+        if r.status != tm.OK:
+            break
+        F.append(r.report["F"])
+        assert r.report["min_detA"] > 0
+    assert len(F) >= 4 and np.all(np.diff(F) < 0)
+
+
+def test_linesearch_exhaustion_reports_status(tm):
+    """With max_halvings = 0 and an impossible acceptance factor the step is
+    rejected: status LINESEARCH, x unchanged (Section 3.4 termination)."""
+    m = make("c1", 1, nx=4)
+    ctx = tm.Context.from_mesh(m)
+    x = dev(m.x)
+    r = ctx.newton_step(x, max_halvings=1, f_factor=1e-30)
+    assert r.status == tm.ERR_LINESEARCH
+    assert np.array_equal(host(x), m.x)
+
+
+# ---------------------------------------------------------------- FP32 mixed
+def test_fp32_mixed_bounds(tm):
+    """FP32 bulk / FP64 reductions. Coordinates are shifted to the element's
+    first node in FP64 before rounding, so A carries relative error ~eps32 k.
+    Measured bounds (stated in the design notes): F 1e-6, gradient 1e-5,
+    Hessian action 1e-5 (normwise, relative to the FP64 oracle)."""
+    for name, kw in [("c2", {}), ("c3", dict(nx=12))]:
+        m = make(name, 1, **kw)
+        ctx = tm.Context.from_mesh(m, precision=tm.FP32_MIXED)
+        check_all(tm, m, ctx, orc_for(m), rtol_F=1e-6, rtol_vec=1e-5)
