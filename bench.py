@@ -1,0 +1,427 @@
+"""Benchmark of the TMOP hot path on GB300.
+
+One step = one gradient + one Hessian-vector product of the variational TMOP
+objective (eq. (2.4), Section 3.4) over a whole synthetic mesh: by default
+48^3 order-3 hexahedra with 5x5x5 Gauss points and mu303 (13.8 M quadrature
+points, 9.1 M dofs), interior nodes jittered, trilinear shear, boundary fixed.
+
+Metric: quadrature points per second of gradient + Hessian action
+(NE * Q / t(step)), plus time-to-converged Newton (Section 3.4 line search,
+MINRES inner solves) for the plain FP64 form and the FP32-bulk form.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload c4] [--precision fp64|mixed] [--no-converge]
+                    [--kernels-only]
+
+--impl reference times the plain FP64 CPU oracle (the reference for this
+path) on a bounded sample of the same workload, on the host cores.
+--kernels-only runs warm-up plus K steps and nothing else (for profilers).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1807_09807_gb300 import meshgen as mg  # noqa: E402
+
+METRIC = "TMOP grad+Hessian-vec quad-points/s and time-to-converged mesh vs plain FP64"
+UNIT = "quad-points/s"
+
+# Measured FP64 / FP32 non-tensor peaks are not in the driver's peak file;
+# these are derived from the GB300 unit counts and clock: 152 SMs x 2.07 GHz x
+# (2 FP64 FMA / 128 FP32 FMA per SM per clock) x 2 flop.
+FP64_PEAK_GFLOPS = 152 * 2.07 * 2 * 2      # 1258.6 GFLOP/s
+FP32_PEAK_GFLOPS = 152 * 2.07 * 128 * 2    # 80 547 GFLOP/s
+
+# Flops of the closed-form second directional derivative dP = d2mu/dT2 : dT
+# per quadrature point (cofactor, its derivative, invariants, the P update and
+# the w det W scaling), counted from the formulas; W = I.
+METRIC_DP_FLOPS = {303: 244, 302: 420, 2: 70, 7: 80, 9: 80, 77: 60, 1: 12, 14: 12}
+
+
+def contraction_fmas(dim: int, n: int, q: int, nc: int) -> tuple[int, int]:
+    """FMAs of the sum-factorised forward (nodes -> A) and adjoint
+    (per-point matrices -> nodes) contractions of one element, nc components."""
+    if dim == 2:
+        fwd = nc * (n * q * 2 * n + q * q * 2 * n)
+        adj = nc * (n * q * 2 * q + n * n * 2 * q)
+    else:
+        fwd = nc * (n * n * q * 2 * n + n * q * q * 3 * n + q ** 3 * 3 * n)
+        adj = nc * (n * q * q * 3 * q + n * n * q * 3 * q + n ** 3 * 2 * q)
+    return fwd, adj
+
+
+def hess_flops_per_element(dim, n, q, metric):
+    """Algorithmic flops of one matrix-free Hessian action on one element:
+    forward contraction of x and of v, adjoint contraction, and dP at every
+    point."""
+    fwd, adj = contraction_fmas(dim, n, q, dim)
+    return 2 * (2 * fwd + adj) + METRIC_DP_FLOPS[metric] * q ** dim
+
+
+def grad_flops_per_element(dim, n, q, metric):
+    fwd, adj = contraction_fmas(dim, n, q, dim)
+    return 2 * (fwd + adj) + (METRIC_DP_FLOPS[metric] // 2) * q ** dim
+
+
+def kernel_src_hash() -> str:
+    """Hash of the element-kernel sources; ncu counters are reused only when
+    it matches the hash recorded with them."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("tmop_device.cuh", "tmop_element.cuh", "tmop_kparams.h"):
+        with open(os.path.join(ROOT, "paper_1807_09807_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+# ---------------------------------------------------------------- environment
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while the
+    timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+            time.sleep(0.25)
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ---------------------------------------------------------------- CPU oracle timing
+def oracle_sample(m, budget_s: float = 12.0, chunk_slabs: int = 2):
+    """Time the plain FP64 oracle (gradient + Hessian action) on whole z-slabs
+    of elements of the same workload until budget_s has elapsed. Returns
+    (quad-points/s, elements timed, seconds)."""
+    import oracle
+    p = oracle.Problem(m.dim, m.order, m.elem_nodes, m.nnode, m.fixed, m.nq, m.metric, quad_kind=m.quad_kind)
+    v = np.random.default_rng(11).standard_normal(m.x.shape)
+    slab = m.nx[0] * m.nx[1] if m.dim == 3 else m.nx[0]
+    chunk = slab * chunk_slabs
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s and done < m.nelem:
+        els = np.arange(done, min(done + chunk, m.nelem), dtype=np.int32)
+        p.gradient(m.x, elems=els)
+        p.hess_apply(m.x, v, elems=els)
+        done += len(els)
+    dt = time.perf_counter() - t0
+    return done * m.Q / dt, done, dt
+
+
+def cpu_baseline_block(m):
+    qps, ne, dt = oracle_sample(m)
+    return {"value": qps, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"gradient + Hessian action of the FP64 CPU oracle on the first {ne} of {m.nelem} elements "
+                      f"(whole z-slabs) of the same mesh, {dt:.1f} s, single thread"}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    m = make_workload(args.workload, accept_gpu=False)
+    per_step = []
+    for _ in range(args.warmup):
+        oracle_sample(m, budget_s=0.5)
+    total_qp, total_t = 0.0, 0.0
+    for _ in range(args.steps):
+        qps, ne, dt = oracle_sample(m, budget_s=max(2.0, 60.0 / max(args.steps, 1)))
+        per_step.append(dt)
+        total_qp += ne * m.Q
+        total_t += dt
+    value = total_qp / total_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(m, args),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "each step: gradient + Hessian action of the FP64 CPU oracle on whole z-slabs "
+                                   "of the workload for a fixed time budget, single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def make_workload(name, accept_gpu=True):
+    accept = None
+    if accept_gpu:
+        import torch
+        from paper_1807_09807_gb300 import tmop as tm
+
+        def accept(mm):
+            ctx = tm.Context.from_mesh(mm)
+            rc, F, md = ctx.energy(torch.tensor(mm.x, device="cuda"))
+            ctx.close()
+            return md > 0
+    return mg.make_mesh(name, 1, accept=accept)
+
+
+def workload_config(m, args):
+    return {"workload": f"{args.workload}: {m.dim}D order-{m.order} "
+                        f"{'x'.join(str(v) for v in m.nx)} {'hexes' if m.dim == 3 else 'quads'}, "
+                        f"{m.nq}^{m.dim} Gauss points, mu{m.metric}, W=I, jittered + "
+                        f"{'trilinear shear' if m.dim == 3 else 'sine'}, boundary fixed",
+            "elements": m.nelem, "quad_points": m.n_qp, "dofs": m.dim * m.nnode,
+            "precision": args.precision, "l2": "flushed between steps (256 MiB write)",
+            "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU"}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1807_09807_gb300 import build as cuda_build
+    from paper_1807_09807_gb300 import tmop as tm
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        cuda_build.build()
+    if ws > 1:
+        dist.barrier()
+    tm.load()
+    m = make_workload(args.workload)
+    prec = tm.FP64 if args.precision == "fp64" else tm.FP32_MIXED
+    ctx = tm.Context.from_mesh(m, precision=prec)
+    x = torch.tensor(m.x, device=dev)
+    v = torch.tensor(np.random.default_rng(5).standard_normal(m.x.shape), device=dev)
+    g, y = torch.empty_like(x), torch.empty_like(x)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        ctx.gradient(x, out=g)
+        if ev is not None:
+            ev[0].record(stream)
+        ctx.hess_apply(x, v, out=y)
+        if ev is not None:
+            ev[1].record(stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    if args.kernels_only:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            step()
+        torch.cuda.synchronize()
+        return 0
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index if dev.index is not None else 0) as clocks:
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(1.0)
+            s0, s_h0, s_h1, s1 = evs[k]
+            s0.record(stream)
+            step(ev=(s_h0, s_h1))
+            s1.record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if ws > 1:
+        dist.barrier()
+    step_ms = [evs[k][0].elapsed_time(evs[k][3]) for k in range(args.steps)]
+    hess_ms = [evs[k][1].elapsed_time(evs[k][2]) for k in range(args.steps)]
+    t_dev = sum(step_ms) * 1e-3
+    if ws > 1:
+        tt = torch.tensor([t_dev], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    value = ws * m.n_qp * args.steps / t_dev
+
+    # ---- end to end through the public API from pinned host buffers
+    xh = torch.tensor(m.x).pin_memory()
+    vh = torch.tensor(np.random.default_rng(5).standard_normal(m.x.shape)).pin_memory()
+    gh, yh = torch.empty_like(xh).pin_memory(), torch.empty_like(xh).pin_memory()
+    xd, vd = torch.empty_like(x), torch.empty_like(x)
+    e_steps = max(3, min(args.steps, 10))
+
+    def e2e_step():
+        xd.copy_(xh, non_blocking=True)
+        vd.copy_(vh, non_blocking=True)
+        ctx.gradient(xd, out=g)
+        ctx.hess_apply(xd, vd, out=y)
+        gh.copy_(g, non_blocking=True)
+        yh.copy_(y, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_t = e0.elapsed_time(e1) * 1e-3
+    nbytes = x.numel() * 8
+    e2e = {"value": ws * m.n_qp * e_steps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 2 * nbytes,
+           "d2h_bytes_per_step": 2 * nbytes}
+
+    # ---- roofline of the dominant kernel (the Hessian action)
+    n = m.order + 1
+    hess_ms_avg = statistics.mean(hess_ms)
+    flops = hess_flops_per_element(m.dim, n, m.nq, m.metric) * m.nelem
+    achieved = flops / (hess_ms_avg * 1e-3) / 1e12
+    peak = (FP64_PEAK_GFLOPS if prec == tm.FP64 else FP32_PEAK_GFLOPS) / 1e3
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": f"elem_kernel<{m.dim},{n},{m.nq},{'double' if prec == tm.FP64 else 'float'},"
+                                           f"OP_HESS> (matrix-free Hessian action)",
+                "peak_source": "derived: 152 SMs x 2.07 GHz x " + ("2 FP64" if prec == tm.FP64 else "128 FP32")
+                               + " FMA/clk/SM x 2 (FP64/FP32 peaks are not in MEASURED_PEAKS.json)",
+                "flops_per_launch": flops, "hess_ms": hess_ms_avg}
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        with open(tfile) as f:
+            tr = json.load(f).get(f"{args.workload}:{args.precision}")
+        # only counters taken on the kernel sources as they are now
+        if tr and tr.get("kernel_src_sha256") == kernel_src_hash():
+            roofline["traffic"] = tr["dram_bytes_per_launch"]
+
+    # ---- time to converged mesh, both precision forms (outside the timed region)
+    converge = None
+    if args.converge and rank == 0:
+        converge = {}
+        for name, pf in (("fp64", tm.FP64), ("mixed", tm.FP32_MIXED)):
+            c2 = ctx if pf == prec else tm.Context.from_mesh(m, precision=pf)
+            xc = torch.tensor(m.x, device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = c2.newton_solve(xc, max_newton=args.max_newton, krylov="cg" if args.krylov == "cg" else "minres",
+                                  rtol=1e-12 if pf == tm.FP64 else 1e-6)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            rep = res.report
+            converge[name] = {"seconds": dt, "status": tm.status_string(res.status), "newton": rep["iterations"],
+                              "krylov": rep["krylov_iterations"], "F0": None, "F": rep["F"],
+                              "grad_rel": rep["grad_norm"] / max(rep["grad_norm0"], 1e-300),
+                              "min_detA": rep["min_detA"]}
+        if "fp64" in converge and "mixed" in converge:
+            F64, F32 = converge["fp64"]["F"], converge["mixed"]["F"]
+            converge["mixed_vs_fp64_F_rel"] = abs(F32 - F64) / abs(F64)
+            converge["speedup_mixed_over_fp64"] = converge["fp64"]["seconds"] / converge["mixed"]["seconds"]
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == tm.FP64 else "f32 (f64 reductions)",
+            "data": "synthetic", "config": workload_config(m, args), "clocks": clocks.summary(),
+            "e2e": e2e, "gpu_launches": 2 * args.steps, "roofline": roofline,
+            "wall_s_timed_region": t_wall,
+        }
+        if converge is not None:
+            line["time_to_converged"] = converge
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_block(m)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="c4", choices=sorted(mg.PRESETS))
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--krylov", choices=["minres", "cg"], default="minres")
+    ap.add_argument("--max-newton", type=int, default=12)
+    ap.add_argument("--no-converge", dest="converge", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernels-only", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if not args.kernels_only else args.warmup
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

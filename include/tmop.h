@@ -108,6 +108,13 @@ int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metr
  * *min_detA set. */
 int tmop_energy(tmop_ctx* ctx, const double* x, double* F, double* min_detA, void* stream);
 
+/* Same objective and minimum as tmop_energy, written asynchronously to the
+ * DEVICE scalars F and min_detA (one FP64 each) on the stream, without a
+ * host synchronisation (for autograd and stream-ordered callers). Points with
+ * det A <= 0 make *F = +inf under a barrier metric; the caller reads
+ * *min_detA to detect inversion. */
+int tmop_energy_device(tmop_ctx* ctx, const double* x, double* F, double* min_detA, void* stream);
+
 /* Gradient g = dF_V/dx (Section 3.4): g_{i,a} = sum_E sum_q w_q det W
  * [ (dmu/dT)(T) W^-t grad w_i ]_a, zero at fixed dofs. g: DEVICE [d][nnode],
  * overwritten. Asynchronous. Points with det A <= 0 contribute nothing under a

@@ -207,11 +207,13 @@ int launch_op(tmop_ctx* c, int op, const double* x, const double* v, double* y, 
   return TMOP_OK;
 }
 
-// F and min det A into d_res[0..1] (device), asynchronously.
-int energy_async(tmop_ctx* c, const double* x, cudaStream_t s, double* elem_min = nullptr) {
-  int rc = launch_op(c, OP_ENERGY, x, nullptr, nullptr, elem_min, s);
+// F and min det A into device memory (d_res[0..1] by default), asynchronously.
+int energy_async(tmop_ctx* c, const double* x, cudaStream_t s, double* outF = nullptr, double* outMin = nullptr) {
+  int rc = launch_op(c, OP_ENERGY, x, nullptr, nullptr, nullptr, s);
   if (rc) return rc;
-  if (energy_final(c->d_part, c->d_part + kMaxRedBlocks, c->grid[OP_ENERGY], c->d_res, s)) return TMOP_ERR_CUDA;
+  if (energy_final(c->d_part, c->d_part + kMaxRedBlocks, c->grid[OP_ENERGY], outF ? outF : c->d_res,
+                   outMin ? outMin : c->d_res + 1, s))
+    return TMOP_ERR_CUDA;
   return TMOP_OK;
 }
 
@@ -569,6 +571,11 @@ int tmop_energy(tmop_ctx* c, const double* x, double* F, double* min_detA, void*
   *F = f;
   *min_detA = m;
   return (m > 0.0) ? TMOP_OK : TMOP_ERR_INVERTED;
+}
+
+int tmop_energy_device(tmop_ctx* c, const double* x, double* F, double* min_detA, void* stream) {
+  if (!c || !x || !F || !min_detA) return TMOP_ERR_ARG;
+  return energy_async(c, x, (cudaStream_t)stream, F, min_detA);
 }
 
 int tmop_gradient(tmop_ctx* c, const double* x, double* g, void* stream) {

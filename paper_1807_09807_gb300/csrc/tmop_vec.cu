@@ -66,7 +66,7 @@ __global__ void k_sum_final(const double* __restrict__ part, int np, double* __r
 }
 
 __global__ void k_energy_final(const double* __restrict__ pf, const double* __restrict__ pm, int np,
-                               double* __restrict__ out) {
+                               double* __restrict__ outF, double* __restrict__ outMin) {
   __shared__ double mins[kThreads];
   double s = 0.0, m = INFINITY;
   for (int i = threadIdx.x; i < np; i += blockDim.x) {
@@ -78,8 +78,8 @@ __global__ void k_energy_final(const double* __restrict__ pf, const double* __re
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int i = 1; i < kThreads; ++i) m = fmin(m, mins[i]);
-    out[0] = s;
-    out[1] = m;
+    *outF = s;
+    *outMin = m;
   }
 }
 
@@ -90,8 +90,8 @@ int dot(const double* a, const double* b, size_t n, double* part, double* out, c
   return (int)cudaGetLastError();
 }
 
-int energy_final(const double* pf, const double* pm, int np, double* out, cudaStream_t s) {
-  k_energy_final<<<1, kThreads, 0, s>>>(pf, pm, np, out);
+int energy_final(const double* pf, const double* pm, int np, double* outF, double* outMin, cudaStream_t s) {
+  k_energy_final<<<1, kThreads, 0, s>>>(pf, pm, np, outF, outMin);
   return (int)cudaGetLastError();
 }
 

@@ -17,7 +17,7 @@ enum {
 
 int red_grid(size_t n);
 int dot(const double* a, const double* b, size_t n, double* part, double* out, cudaStream_t s);
-int energy_final(const double* pf, const double* pm, int np, double* out, cudaStream_t s);
+int energy_final(const double* pf, const double* pm, int np, double* outF, double* outMin, cudaStream_t s);
 int step(const double* x, const double* p, double alpha, double* y, size_t n, cudaStream_t s);
 int minres_init(const double* b, double* v, double* vprev, double* w, double* wprev, double* sol, double* st,
                 double* part, size_t n, cudaStream_t s);

@@ -65,6 +65,7 @@ _SIGNATURES = {
     "tmop_setup": ([C.POINTER(_Mesh), C.c_int, C.POINTER(_Quad), C.c_int, C.POINTER(_Targets), C.c_int,
                     C.POINTER(C.c_void_p)], C.c_int),
     "tmop_energy": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p], C.c_int),
+    "tmop_energy_device": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_gradient": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_hess_apply": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_newton_step": ([C.c_void_p, C.c_void_p, C.POINTER(NewtonOpts), C.POINTER(NewtonReport), C.c_void_p],
@@ -191,6 +192,13 @@ class Context:
         if rc not in (OK, ERR_INVERTED):
             raise TmopError(rc, "tmop_energy")
         return rc, F.value, md.value
+
+    def energy_device(self, x, F, min_detA):
+        """F and min det A into 0-d float64 CUDA tensors, stream ordered, no sync."""
+        _check_vec(x, self.shape, "x")
+        rc = load().tmop_energy_device(self._h, _ptr(x), _ptr(F), _ptr(min_detA), _stream())
+        if rc != OK:
+            raise TmopError(rc, "tmop_energy_device")
 
     def gradient(self, x, out=None):
         import torch
