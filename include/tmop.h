@@ -46,7 +46,7 @@ typedef enum {
 
 enum { TMOP_GL = 0, TMOP_GLL = 1 };                                     /* quadrature kind */
 enum { TMOP_W_IDENTITY = 0, TMOP_W_CONST = 1, TMOP_W_SCALED = 2, TMOP_W_PER_QP = 3 }; /* target kind */
-enum { TMOP_FP64 = 0, TMOP_FP32_MIXED = 1 };                             /* precision form */
+enum { TMOP_FP64 = 0, TMOP_FP32_MIXED = 1, TMOP_FP32_BULK = 2 };        /* precision form */
 enum { TMOP_KRYLOV_MINRES = 0, TMOP_KRYLOV_CG = 1 };                     /* inner solver */
 
 typedef struct tmop_ctx tmop_ctx; /* opaque; owns device tables and workspace */
@@ -92,9 +92,14 @@ typedef struct {
  *   order     1..4 (k of Q_k)
  *   metric_id 2D: 1, 2, 7, 9, 14, 77; 3D: 1, 14, 302, 303 (Table 3.1;
  *             mu302 = |T|^2 |T^-1|^2 / 9 - 1 is not in the paper)
- *   precision TMOP_FP64, or TMOP_FP32_MIXED: element contractions, metric
- *             derivatives and Hessian actions in FP32; F, det A, dot
- *             products, line search and convergence tests in FP64.
+ *   precision TMOP_FP64: every kernel in FP64.
+ *             TMOP_FP32_MIXED: the Hessian action (the Krylov operator) in
+ *             FP32; objective, det A, gradient, dot products, line search
+ *             and convergence tests in FP64, so Newton converges to the FP64
+ *             solution with FP32 inner solves.
+ *             TMOP_FP32_BULK: every element kernel (Jacobian contractions, mu
+ *             and its derivatives, Hessian action) in FP32, with F, min det A,
+ *             dot products and norms reduced in FP64.
  * Errors: TMOP_ERR_ARG (bad sizes or ids, node ids out of range, det W <= 0,
  * structured[] inconsistent with elem_nodes), TMOP_ERR_CUDA. On error *out is NULL. */
 int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metric_id,
@@ -134,7 +139,7 @@ typedef struct {
   int max_newton;        /* [10] Newton iterations for tmop_newton_solve */
   double rtol;           /* [1e-12] stop when |g| <= rtol |g(x0)| (Section 5) */
   int krylov;            /* [TMOP_KRYLOV_MINRES] (Section 5 uses MINRES) */
-  double krylov_rtol;    /* [1e-10 FP64, 1e-6 FP32_MIXED] relative residual of the inner solve */
+  double krylov_rtol;    /* [1e-10 FP64, 1e-6 FP32 forms] relative residual of the inner solve */
   int krylov_maxit;      /* [2000] */
   double alpha_shrink;   /* [0.5] step reduction factor */
   int max_halvings;      /* [30] */

@@ -260,7 +260,7 @@ tmop_newton_opts defaults(const tmop_ctx* c, const tmop_newton_opts* in) {
   if (o.max_newton <= 0) o.max_newton = 10;
   if (!(o.rtol > 0.0)) o.rtol = 1e-12;
   if (o.krylov != TMOP_KRYLOV_CG) o.krylov = TMOP_KRYLOV_MINRES;
-  if (!(o.krylov_rtol > 0.0)) o.krylov_rtol = (c->precision == TMOP_FP32_MIXED) ? 1e-6 : 1e-10;
+  if (!(o.krylov_rtol > 0.0)) o.krylov_rtol = (c->precision == TMOP_FP64) ? 1e-10 : 1e-6;
   if (o.krylov_maxit <= 0) o.krylov_maxit = 2000;
   if (!(o.alpha_shrink > 0.0 && o.alpha_shrink < 1.0)) o.alpha_shrink = 0.5;
   if (o.max_halvings <= 0) o.max_halvings = 30;
@@ -412,7 +412,7 @@ int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metr
   if (order < 1 || order > 4 || mesh->nelem < 1 || mesh->nnode < 1) return TMOP_ERR_ARG;
   if (quad->kind != TMOP_GL && quad->kind != TMOP_GLL) return TMOP_ERR_ARG;
   if (quad->npts1d < 2 || quad->npts1d > kMaxQ) return TMOP_ERR_ARG;
-  if (precision != TMOP_FP64 && precision != TMOP_FP32_MIXED) return TMOP_ERR_ARG;
+  if (precision != TMOP_FP64 && precision != TMOP_FP32_MIXED && precision != TMOP_FP32_BULK) return TMOP_ERR_ARG;
   const bool ok_metric = (metric_id == 1 || metric_id == 14) ||
                          (d == 2 && (metric_id == 2 || metric_id == 7 || metric_id == 9 || metric_id == 77)) ||
                          (d == 3 && (metric_id == 302 || metric_id == 303));
@@ -420,9 +420,10 @@ int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metr
   const int n = order + 1, nq = quad->npts1d;
   const int ndof_e = d == 2 ? n * n : n * n * n;
   const int Q = d == 2 ? nq * nq : nq * nq * nq;
-  const int fp32 = precision == TMOP_FP32_MIXED;
   const ElemEntry* ent[3];
   for (int op = 0; op < 3; ++op) {
+    // FP32_MIXED: FP32 only for the Hessian action; FP32_BULK: every element kernel
+    const int fp32 = precision == TMOP_FP32_BULK || (precision == TMOP_FP32_MIXED && op == OP_HESS);
     ent[op] = find_elem(d, n, nq, fp32, op);
     if (!ent[op]) return TMOP_ERR_ARG;  // unsupported (order, points) pair
   }

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libtmop_gb300.so")
 OK, ERR_ARG, ERR_CUDA, ERR_INVERTED, ERR_LINESEARCH, ERR_NOT_CONVERGED = 0, 1, 2, 3, 4, 5
 GL, GLL = 0, 1
 W_IDENTITY, W_CONST, W_SCALED, W_PER_QP = 0, 1, 2, 3
-FP64, FP32_MIXED = 0, 1
+FP64, FP32_MIXED, FP32_BULK = 0, 1, 2
 MINRES, CG = 0, 1
 
 
