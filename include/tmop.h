@@ -41,7 +41,8 @@ typedef enum {
   TMOP_ERR_CUDA = 2,          /* a CUDA runtime call failed */
   TMOP_ERR_INVERTED = 3,      /* some quadrature point has det A <= 0 (Section 3.2, ideal barrier) */
   TMOP_ERR_LINESEARCH = 4,    /* no admissible step length (Section 3.4) */
-  TMOP_ERR_NOT_CONVERGED = 5  /* an iteration cap was reached */
+  TMOP_ERR_NOT_CONVERGED = 5, /* an iteration cap was reached */
+  TMOP_ERR_CAPACITY = 6       /* the problem needs more scratch than a fixed-size buffer holds */
 } tmop_status;
 
 enum { TMOP_GL = 0, TMOP_GLL = 1 };                                     /* quadrature kind */
@@ -184,6 +185,39 @@ int tmop_krylov_solve(tmop_ctx* ctx, const double* x, const double* b, double* p
 /* Per-element minimum of det A over its quadrature points: out DEVICE
  * [nelem] FP64 (the validity test behind the barrier of Section 3.2). */
 int tmop_element_min_detA(tmop_ctx* ctx, const double* x, double* out, void* stream);
+
+/* Objective and minimum det A WITHOUT ANY DEVICE ALLOCATION. The paper has
+ * no counterpart: this is a convenience for callers that may not call
+ * cudaMalloc where they evaluate mesh quality -- e.g. an application whose
+ * own allocator or memory pool owns the GPU, or code running inside another
+ * program's time step where cudaMalloc's implicit synchronisation is not
+ * acceptable -- and that therefore cannot create a tmop_setup context.
+ *
+ * Same F and min det A as tmop_energy (eq. (2.4)), FP64, on a structured
+ * order-k grid only (node ids are computed from structured[] = nx, ny, nz,
+ * laid out as for tmop_mesh.structured): dim 2 or 3, order 1..4, quad as for
+ * tmop_setup, metric_id as for tmop_setup, targets of kind IDENTITY, SCALED
+ * or CONST (TMOP_W_PER_QP is rejected with TMOP_ERR_ARG). x: DEVICE
+ * [dim][nnode] FP64. F, min_detA: DEVICE FP64 scalars, written
+ * asynchronously on stream (no host synchronisation). F = +inf under a barrier
+ * metric when some det A <= 0.
+ *
+ * Scratch: the per-block partial sums live in one file-scope device array of
+ * 2 x 32768 doubles (512 KiB) that every GPU loading this library keeps until
+ * the process exits. The launch uses one block per group of elements in
+ * flight (4 for most kernels), so the limit is about 131 000 elements (at
+ * least 32768 x the kernel's warps per block); larger grids return
+ * TMOP_ERR_CAPACITY before anything is launched. The array is shared by every
+ * call in the process and keeps the last call's contents (each call overwrites
+ * the partials it reads, so nothing has to start at zero); calls that overlap
+ * on the GPU -- on different streams, or from different host threads --
+ * race on it and must be serialised by the caller.
+ *
+ * The first call on each device looks up the device address of that array
+ * (cudaGetSymbolAddress, with the device current) and may load the kernels
+ * it launches; make that first call before any stream capture. */
+int tmop_energy_noalloc(int dim, int order, const int structured[3], const tmop_quad* quad, int metric_id,
+                        const tmop_targets* targets, const double* x, double* F, double* min_detA, void* stream);
 
 /* Sizes of a context: Q (points per element), ndof = dim * nnode. */
 int tmop_sizes(const tmop_ctx* ctx, int* dim, int* nelem, int* nnode, int* Q);

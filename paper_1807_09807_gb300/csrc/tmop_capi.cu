@@ -55,7 +55,7 @@ static void legendre_pd(int m, double t, double* p, double* dp) {
 
 // Gauss-Legendre: roots of P_q by Newton from Chebyshev-like guesses;
 // weights 2 / ((1 - t^2) P_q'(t)^2) on [-1,1], mapped to [0,1].
-static bool rule_gl(int q, double* x, double* w) {
+bool rule_gl(int q, double* x, double* w) {
   for (int i = 0; i < q; ++i) {
     double t = -cos(M_PI * (4 * i + 3) / (4.0 * q + 2.0)), p, dp;
     for (int it = 0; it < 64; ++it) {
@@ -74,7 +74,7 @@ static bool rule_gl(int q, double* x, double* w) {
 // Gauss-Lobatto: endpoints plus the roots of P_{q-1}', found by Newton on
 // P_{q-1}' with P_{q-1}'' from the Legendre equation; weights
 // 2 / (q (q-1) P_{q-1}(t)^2) on [-1,1], mapped to [0,1].
-static bool rule_gll(int q, double* x, double* w) {
+bool rule_gll(int q, double* x, double* w) {
   if (q < 2) return false;
   const int m = q - 1;
   for (int i = 0; i < q; ++i) {
@@ -100,7 +100,7 @@ static bool rule_gll(int q, double* x, double* w) {
 }
 
 // Lagrange basis on nodes z (barycentric form): values and derivatives at s.
-static void lagrange_bary(int n, const double* z, double s, double* phi, double* dphi) {
+void lagrange_bary(int n, const double* z, double s, double* phi, double* dphi) {
   double bw[kMaxN];
   for (int i = 0; i < n; ++i) {
     double prod = 1.0;
@@ -141,7 +141,7 @@ static double det_h(int d, const double* M) {
 }
 
 // W^-1 by the adjugate; false when det W <= 0 (Section 3.1 requires det W > 0).
-static bool inv_h(int d, const double* W, double* Wi, double* detW) {
+bool inv_h(int d, const double* W, double* Wi, double* detW) {
   const double dt = det_h(d, W);
   *detW = dt;
   if (!(dt > 0.0) || !isfinite(dt)) return false;
@@ -385,6 +385,7 @@ const char* tmop_status_string(int status) {
     case TMOP_ERR_INVERTED: return "inverted element: det A <= 0 at some quadrature point";
     case TMOP_ERR_LINESEARCH: return "line search found no admissible step";
     case TMOP_ERR_NOT_CONVERGED: return "iteration limit reached";
+    case TMOP_ERR_CAPACITY: return "problem too large for the fixed scratch buffer of the no-allocation entry point";
     default: return "unknown status";
   }
 }

@@ -4,7 +4,8 @@
 namespace tmop {
 
 #define TMOP_ENTRY(N, Q, OP) \
-    {2, N, Q, 1, OP, launch_elem<2, N, Q, float, OP>, prepare_elem<2, N, Q, float, OP>}
+    {2, N, Q, 1, OP, launch_elem<2, N, Q, float, OP>, prepare_elem<2, N, Q, float, OP>, \
+     ElemCfg<2, N, Q, float, OP>::WARPS}
 #define TMOP_ENTRIES(N, Q) TMOP_ENTRY(N, Q, OP_ENERGY), TMOP_ENTRY(N, Q, OP_GRADIENT), TMOP_ENTRY(N, Q, OP_HESS)
 
 extern const ElemEntry kElem_2d_f32[] = {

@@ -40,9 +40,16 @@ struct ElemEntry {
   int dim, n, q, fp32, op;
   elem_launch_fn launch;
   elem_prepare_fn prepare;
+  int warps;  // warps (elements in flight) per block of this instantiation
 };
 
 // Defined in the per-dimension/precision instantiation units.
 const ElemEntry* find_elem(int dim, int n, int q, int fp32, int op);
+
+// Host-side 1D tables and target inversion (tmop_capi.cu).
+bool rule_gl(int q, double* x, double* w);
+bool rule_gll(int q, double* x, double* w);
+void lagrange_bary(int n, const double* z, double s, double* phi, double* dphi);
+bool inv_h(int d, const double* W, double* Wi, double* detW);
 
 }  // namespace tmop

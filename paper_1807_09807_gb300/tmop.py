@@ -17,7 +17,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtmop_gb300.so")
 
-OK, ERR_ARG, ERR_CUDA, ERR_INVERTED, ERR_LINESEARCH, ERR_NOT_CONVERGED = 0, 1, 2, 3, 4, 5
+OK, ERR_ARG, ERR_CUDA, ERR_INVERTED, ERR_LINESEARCH, ERR_NOT_CONVERGED, ERR_CAPACITY = 0, 1, 2, 3, 4, 5, 6
 GL, GLL = 0, 1
 W_IDENTITY, W_CONST, W_SCALED, W_PER_QP = 0, 1, 2, 3
 FP64, FP32_MIXED, FP32_BULK = 0, 1, 2
@@ -77,6 +77,8 @@ _SIGNATURES = {
     "tmop_element_min_detA": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_sizes": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
                    C.c_int),
+    "tmop_energy_noalloc": ([C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(_Quad), C.c_int, C.POINTER(_Targets),
+                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_destroy": ([C.c_void_p], None),
     "tmop_status_string": ([C.c_int], C.c_char_p),
 }
@@ -116,6 +118,20 @@ def _check_vec(t, shape, what):
         raise TypeError(f"{what} must be a contiguous float64 CUDA tensor")
     if tuple(t.shape) != tuple(shape):
         raise ValueError(f"{what} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+def energy_noalloc(dim, order, structured, nq, metric, x, F, min_detA, quad_kind=GL, target_kind=W_IDENTITY,
+                   target_scale=1.0, W=None):
+    """tmop_energy_noalloc: F and min det A of a structured grid into 0-d
+    float64 CUDA tensors, with no device allocation by the library (for
+    callers that must not allocate GPU memory). Returns the status code."""
+    _check_vec(x, (dim, x.shape[1]), "x")
+    st = (C.c_int * 3)(*(list(structured) + [0] * (3 - len(structured))))
+    Wa = None if W is None else np.ascontiguousarray(W, dtype=np.float64)
+    t = _Targets(target_kind, target_scale, None if Wa is None else Wa.ctypes.data)
+    q = _Quad(quad_kind, nq)
+    return load().tmop_energy_noalloc(dim, order, st, C.byref(q), metric, C.byref(t), _ptr(x), _ptr(F),
+                                      _ptr(min_detA), _stream())
 
 
 @dataclass
