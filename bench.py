@@ -86,6 +86,20 @@ def kernel_src_hash() -> str:
     return h.hexdigest()
 
 
+def replica_value(t_local_s, units_per_step, steps, dist_mod=None, device="cpu"):
+    """Whole-job throughput of N independent replicas (one per rank, no data
+    exchange): every rank processed units_per_step * steps units, and the job
+    took as long as the slowest rank. Returns (value, job seconds)."""
+    import torch
+    ws, t = 1, t_local_s
+    if dist_mod is not None and dist_mod.is_initialized():
+        ws = dist_mod.get_world_size()
+        tt = torch.tensor([t_local_s], dtype=torch.float64, device=device)
+        dist_mod.all_reduce(tt, op=dist_mod.ReduceOp.MAX)
+        t = float(tt.item())
+    return ws * units_per_step * steps / t, t
+
+
 # ---------------------------------------------------------------- environment
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -306,12 +320,7 @@ def run_ours(args):
         dist.barrier()
     step_ms = [evs[k][0].elapsed_time(evs[k][3]) for k in range(args.steps)]
     hess_ms = [evs[k][1].elapsed_time(evs[k][2]) for k in range(args.steps)]
-    t_dev = sum(step_ms) * 1e-3
-    if ws > 1:
-        tt = torch.tensor([t_dev], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev = float(tt.item())
-    value = ws * m.n_qp * args.steps / t_dev
+    value, t_dev = replica_value(sum(step_ms) * 1e-3, m.n_qp, args.steps, dist if ws > 1 else None, dev)
 
     # ---- end to end through the public API from pinned host buffers
     xh = torch.tensor(m.x).pin_memory()
@@ -362,27 +371,19 @@ def run_ours(args):
             roofline["traffic"] = tr["dram_bytes_per_launch"]
 
     # ---- time to converged mesh, both precision forms (outside the timed region)
+    # ---- partial assembly: linearize once, then the stored-Hessian product
+    pa = None
+    if rank == 0 and args.pa:
+        pa = measure_pa(tm, m, x, v, y, flush, stream, args)
+
+    # ---- time to converged mesh, both precision forms (outside the timed region)
     converge = None
     if args.converge and rank == 0:
-        converge = {}
-        for name, pf in (("fp64", tm.FP64), ("mixed", tm.FP32_MIXED)):
-            c2 = ctx if pf == prec else tm.Context.from_mesh(m, precision=pf)
-            xc = torch.tensor(m.x, device=dev)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            res = c2.newton_solve(xc, max_newton=args.max_newton, krylov="cg" if args.krylov == "cg" else "minres",
-                                  rtol=1e-12 if pf == tm.FP64 else 1e-6)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            rep = res.report
-            converge[name] = {"seconds": dt, "status": tm.status_string(res.status), "newton": rep["iterations"],
-                              "krylov": rep["krylov_iterations"], "F0": None, "F": rep["F"],
-                              "grad_rel": rep["grad_norm"] / max(rep["grad_norm0"], 1e-300),
-                              "min_detA": rep["min_detA"]}
-        if "fp64" in converge and "mixed" in converge:
-            F64, F32 = converge["fp64"]["F"], converge["mixed"]["F"]
-            converge["mixed_vs_fp64_F_rel"] = abs(F32 - F64) / abs(F64)
-            converge["speedup_mixed_over_fp64"] = converge["fp64"]["seconds"] / converge["mixed"]["seconds"]
+        converge = time_to_converged(tm, m, dev, args)
+
+    learned = None
+    if args.learned and rank == 0:
+        learned = learned_proposal(tm, dev, args)
 
     if rank == 0:
         line = {
@@ -393,14 +394,152 @@ def run_ours(args):
             "e2e": e2e, "gpu_launches": 2 * args.steps, "roofline": roofline,
             "wall_s_timed_region": t_wall,
         }
+        if pa is not None:
+            line["partial_assembly"] = pa
         if converge is not None:
             line["time_to_converged"] = converge
+        if learned is not None:
+            line["learned_proposal"] = learned
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_block(m)
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def _event_ms(fn, reps, stream, flush=None):
+    """Average device time of fn over reps launches (L2 flushed before each)."""
+    import torch
+    tot = 0.0
+    for _ in range(reps):
+        if flush is not None:
+            flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / reps
+
+
+def measure_pa(tm, m, x, v, y, flush, stream, args):
+    """Linearize (once per Newton step) and the partially assembled Hessian
+    action (once per Krylov iteration), FP64 and FP32, with the HBM roofline
+    of the FP32 product: it reads the packed Hessians (dim^2 (dim^2+1)/2 FP32
+    per point) and v, and writes y."""
+    import torch
+    peaks = measured_peaks()
+    out = {}
+    for name, pf in (("fp64", tm.FP64), ("fp32", tm.FP32_MIXED)):
+        c = tm.Context.from_mesh(m, precision=pf)
+        c.linearize(x)
+        c.hess_apply_pa(v, out=y)
+        torch.cuda.synchronize()
+        lin_ms = _event_ms(lambda: c.linearize(x), 2, stream, flush)
+        hv_ms = _event_ms(lambda: c.hess_apply_pa(v, out=y), max(3, min(args.steps, 10)), stream, flush)
+        dd = m.dim * m.dim
+        ns = dd * (dd + 1) // 2
+        elt = 8 if pf == tm.FP64 else 4
+        nbytes = m.n_qp * ns * elt + 2 * x.numel() * 8 + x.numel() * 8   # Hessians + v read + y memset/write
+        n = m.order + 1
+        fwd, adj = contraction_fmas(m.dim, n, m.nq, m.dim)
+        flops = m.nelem * (2 * (fwd + adj) + 2 * dd * dd * m.Q)
+        ent = {"linearize_ms": lin_ms, "hess_pa_ms": hv_ms, "bytes_per_launch": nbytes,
+               "achieved_GBps": nbytes / (hv_ms * 1e-3) / 1e9, "achieved_TFLOPs": flops / (hv_ms * 1e-3) / 1e12}
+        if pf == tm.FP64:
+            ent["roofline"] = {"bound": "alu", "achieved": ent["achieved_TFLOPs"], "peak": FP64_PEAK_GFLOPS / 1e3,
+                               "unit": "TFLOP/s", "frac": ent["achieved_TFLOPs"] / (FP64_PEAK_GFLOPS / 1e3)}
+        else:
+            hbm = peaks.get("hbm_gbs", 6800.0)
+            ent["roofline"] = {"bound": "hbm", "achieved": ent["achieved_GBps"], "peak": hbm, "unit": "GB/s",
+                               "frac": ent["achieved_GBps"] / hbm,
+                               "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+        out[name] = ent
+        c.close()
+    return out
+
+
+def time_to_converged(tm, m, dev, args):
+    """Newton from the jittered mesh until |g| <= 1e-12 |g0| (Section 5
+    tolerance): plain FP64, and FP32 Hessian action with FP64 gradient, line
+    search and convergence test. Partially assembled Krylov operator."""
+    import torch
+    res_all = {}
+    for name, pf in (("fp64", tm.FP64), ("mixed", tm.FP32_MIXED)):
+        c = tm.Context.from_mesh(m, precision=pf)
+        xc = torch.tensor(m.x, device=dev)
+        F0 = c.energy(xc)[1]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = c.newton_solve(xc, max_newton=args.max_newton, krylov=args.krylov, rtol=1e-12)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        rep = res.report
+        res_all[name] = {"seconds": dt, "status": tm.status_string(res.status), "newton": rep["iterations"],
+                         "krylov": rep["krylov_iterations"], "F0": F0, "F": rep["F"],
+                         "grad_rel": rep["grad_norm"] / max(rep["grad_norm0"], 1e-300), "min_detA": rep["min_detA"]}
+        c.close()
+    F64, F32 = res_all["fp64"]["F"], res_all["mixed"]["F"]
+    res_all["mixed_vs_fp64_F_rel"] = abs(F32 - F64) / abs(F64)
+    res_all["speedup_mixed_over_fp64"] = res_all["fp64"]["seconds"] / res_all["mixed"]["seconds"]
+    return res_all
+
+
+def learned_proposal(tm, dev, args):
+    """Train the proposal MLP on Newton-converged displacements of seeded
+    32x32 order-3 meshes (mu2, jitter 0.15h), then on a 128x128 order-3 mesh
+    compare plain FP64 Newton from the jittered mesh with the FP32 form
+    started from the proposal (with its fallback). Same absolute target
+    |g| <= 1e-12 |g(x0)| for both."""
+    import torch
+    from paper_1807_09807_gb300 import learned as L
+    t0 = time.perf_counter()
+    ds = L.make_dataset(n_meshes=args.train_meshes, seed0=1000, chunk=250)
+    t_data = time.perf_counter() - t0
+    net = L.MLP(L.n_features(3), L.n_targets(3), 256, seed=0)
+    t0 = time.perf_counter()
+    hist = L.train(net, ds, epochs=args.train_epochs, batch=4096, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    out = {"train_meshes": args.train_meshes, "train_samples": int(ds.X.shape[0]), "data_seconds": t_data,
+           "train_seconds": t_train, "train_loss_first_last": [hist[0], hist[-1]], "apply": []}
+    for seed in (5000, 5001):
+        m = mg.make_mesh("c5apply", seed)
+        c64 = tm.Context.from_mesh(m)
+        c32 = tm.Context.from_mesh(m, precision=tm.FP32_MIXED)
+        x0 = torch.tensor(m.x, device=dev)
+        fx = torch.tensor(m.fixed, device=dev)
+        F0 = c64.energy(x0)[1]
+        g0 = float(torch.linalg.norm(c64.gradient(x0)))
+        atol = 1e-12 * g0
+        xa = x0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ra = c64.newton_solve(xa, max_newton=40, rtol=1e-30, atol=atol)
+        torch.cuda.synchronize()
+        ta = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        prop = L.propose(net, m, c32, x0, fx)
+        xb = prop.x.clone()
+        rb = c32.newton_solve(xb, max_newton=40, rtol=1e-30, atol=atol)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        out["apply"].append({
+            "mesh": f"128x128 order-3 quads, seed {seed}", "F0": F0,
+            "fp64_plain": {"seconds": ta, "status": tm.status_string(ra.status), "newton": ra.report["iterations"],
+                           "krylov": ra.report["krylov_iterations"], "F": ra.report["F"]},
+            "fp32_learned": {"seconds": tb, "status": tm.status_string(rb.status), "proposal_used": prop.used,
+                             "F_proposal": prop.F, "newton": rb.report["iterations"],
+                             "krylov": rb.report["krylov_iterations"], "F": rb.report["F"],
+                             "min_detA": rb.report["min_detA"]},
+            "F_diff_over_F0": abs(ra.report["F"] - rb.report["F"]) / F0,
+            "speedup": ta / tb})
+        c64.close()
+        c32.close()
+    net.close()
+    return out
 
 
 def main():
@@ -414,6 +553,10 @@ def main():
     ap.add_argument("--krylov", choices=["minres", "cg"], default="minres")
     ap.add_argument("--max-newton", type=int, default=12)
     ap.add_argument("--no-converge", dest="converge", action="store_false")
+    ap.add_argument("--no-pa", dest="pa", action="store_false")
+    ap.add_argument("--no-learned", dest="learned", action="store_false")
+    ap.add_argument("--train-meshes", type=int, default=2000)
+    ap.add_argument("--train-epochs", type=int, default=15)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels-only", action="store_true")
     args = ap.parse_args()

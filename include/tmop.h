@@ -134,6 +134,19 @@ int tmop_gradient(tmop_ctx* ctx, const double* x, double* g, void* stream);
  * y: DEVICE [d][nnode], overwritten. Asynchronous. */
 int tmop_hess_apply(tmop_ctx* ctx, const double* x, const double* v, double* y, void* stream);
 
+/* Partial assembly of the Hessian (Section 3.4: the Hessian from d^2mu/dT^2):
+ * stores, at every quadrature point of x, the symmetric A-space matrix
+ *   H_q = w_q det W (d^2mu/dT^2 composed with W^-1 on both sides)
+ * (dim^2 (dim^2 + 1) / 2 values per point, FP64 under TMOP_FP64 and FP32
+ * under the FP32 forms) in the context (allocated on first use:
+ * nelem * Q * 45 * 8 bytes for order-k hexes in FP64). Asynchronous. */
+int tmop_linearize(tmop_ctx* ctx, const double* x, void* stream);
+
+/* y = H(x) v with the Hessians stored by the last tmop_linearize(x): same
+ * result as tmop_hess_apply(ctx, x, v, y) up to rounding, without reading x.
+ * TMOP_ERR_ARG if the context holds no linearisation. Asynchronous. */
+int tmop_hess_apply_pa(tmop_ctx* ctx, const double* v, double* y, void* stream);
+
 /* Newton options (Section 3.4 and Section 5). Zero-initialised fields take
  * the defaults in brackets. */
 typedef struct {
@@ -146,6 +159,10 @@ typedef struct {
   int max_halvings;      /* [30] */
   double f_factor;       /* [1.2] accept only if F(x_new) < f_factor F(x) */
   double g_factor;       /* [1.2] accept only if |g(x_new)| < g_factor |g(x)| */
+  double atol;           /* [0 = off] also stop when |g| <= atol (an absolute target, e.g. to
+                            compare runs that start from different iterates) */
+  int matrix_free;       /* [0] 0: the Krylov operator is partially assembled once per Newton
+                            step (tmop_linearize), 1: recomputed from x at every product */
 } tmop_newton_opts;
 
 typedef struct {
@@ -170,7 +187,7 @@ typedef struct {
 int tmop_newton_step(tmop_ctx* ctx, double* x, const tmop_newton_opts* opts, tmop_newton_report* report,
                      void* stream);
 
-/* Newton iterations from x until |g| <= rtol |g(x0)| (TMOP_OK), no admissible
+/* Newton iterations from x until |g| <= rtol |g(x0)| or |g| <= atol (TMOP_OK), no admissible
  * step (TMOP_ERR_LINESEARCH, the termination rule of Section 3.4) or
  * max_newton steps (TMOP_ERR_NOT_CONVERGED). x: DEVICE, in/out. */
 int tmop_newton_solve(tmop_ctx* ctx, double* x, const tmop_newton_opts* opts, tmop_newton_report* report,

@@ -169,8 +169,8 @@ struct tmop_ctx {
   int dim, order, n, nq, Q, nelem, nnode, metric, precision;
   size_t ndof;
   KParams base;
-  const ElemEntry* ent[3];
-  int grid[3];
+  const ElemEntry* ent[OP_COUNT];
+  int grid[OP_COUNT];
   int32_t* d_elem_nodes = nullptr;
   uint8_t* d_fixed = nullptr;
   double* d_Winv_qp = nullptr;
@@ -180,6 +180,8 @@ struct tmop_ctx {
   double* h_res = nullptr;    // pinned mirror
   double* d_vec = nullptr;    // Krylov / Newton vectors, allocated on first use
   int nvec = 0;
+  void* d_pa = nullptr;       // packed per-point Hessians (partial assembly), allocated on first use
+  bool pa_valid = false;      // d_pa holds the linearisation of some x
 };
 
 namespace {
@@ -202,7 +204,9 @@ int launch_op(tmop_ctx* c, int op, const double* x, const double* v, double* y, 
   p.elem_min = elem_min;
   p.part_F = c->d_part;
   p.part_min = c->d_part + kMaxRedBlocks;
-  if (op != OP_ENERGY) CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * c->ndof, s));
+  p.pa = c->d_pa;
+  if (op == OP_GRADIENT || op == OP_HESS || op == OP_HESS_PA)
+    CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * c->ndof, s));
   if (c->ent[op]->launch(p, c->grid[op], s) != 0) return TMOP_ERR_CUDA;
   return TMOP_OK;
 }
@@ -250,6 +254,20 @@ int ensure_vectors(tmop_ctx* c) {
 
 double* vec(tmop_ctx* c, int i) { return c->d_vec + (size_t)i * c->ndof; }
 
+// Store the per-point A-space Hessians of x (partial assembly).
+int linearize(tmop_ctx* c, const double* x, cudaStream_t s) {
+  if (!c->d_pa) {
+    const size_t dd = (size_t)c->dim * c->dim, ns = dd * (dd + 1) / 2;
+    const size_t elt = c->precision == TMOP_FP64 ? sizeof(double) : sizeof(float);
+    CUDA_TRY(cudaMalloc(&c->d_pa, elt * ns * c->Q * (size_t)c->nelem));
+  }
+  c->pa_valid = false;
+  int rc = launch_op(c, OP_LINEARIZE, x, nullptr, nullptr, nullptr, s);
+  if (rc) return rc;
+  c->pa_valid = true;
+  return TMOP_OK;
+}
+
 // Vector slots
 enum { V_G = 0, V_P, V_XT, V_GT, V_K0, V_K1, V_K2, V_K3, V_K4, V_K5 };
 
@@ -266,6 +284,7 @@ tmop_newton_opts defaults(const tmop_ctx* c, const tmop_newton_opts* in) {
   if (o.max_halvings <= 0) o.max_halvings = 30;
   if (!(o.f_factor > 0.0)) o.f_factor = 1.2;
   if (!(o.g_factor > 0.0)) o.g_factor = 1.2;
+  if (!(o.atol > 0.0)) o.atol = 0.0;
   return o;
 }
 
@@ -274,6 +293,12 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
            cudaStream_t s) {
   int rc = ensure_vectors(c);
   if (rc) return rc;
+  // the Krylov operator: partially assembled at x (default) or recomputed from x
+  const int hop = o.matrix_free ? OP_HESS : OP_HESS_PA;
+  if (hop == OP_HESS_PA) {
+    rc = linearize(c, x, s);
+    if (rc) return rc;
+  }
   double* st = c->d_res + kResKrylov;
   double* part = c->d_part;
   const size_t n = c->ndof;
@@ -288,7 +313,7 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
     done = !(r0 > 0.0);
     while (!done && it < o.krylov_maxit) {
       ++it;
-      rc = launch_op(c, OP_HESS, x, d, Hd, nullptr, s);
+      rc = launch_op(c, hop, x, d, Hd, nullptr, s);
       if (rc) return rc;
       if (cg_after_hv(p, r, d, Hd, st, part, n, s)) return TMOP_ERR_CUDA;
       rc = read_res(c, kResKrylov, KS_COUNT, s);
@@ -307,7 +332,7 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
     done = !(beta1 > 0.0);
     while (!done && it < o.krylov_maxit) {
       ++it;
-      rc = launch_op(c, OP_HESS, x, v, Av, nullptr, s);
+      rc = launch_op(c, hop, x, v, Av, nullptr, s);
       if (rc) return rc;
       if (minres_after_hv(v, vprev, Av, w, wprev, p, st, part, n, s)) return TMOP_ERR_CUDA;
       rc = read_res(c, kResKrylov, KS_COUNT, s);
@@ -399,6 +424,7 @@ void tmop_destroy(tmop_ctx* c) {
   cudaFree(c->d_part);
   cudaFree(c->d_res);
   cudaFree(c->d_vec);
+  cudaFree(c->d_pa);
   cudaFreeHost(c->h_res);
   delete c;
 }
@@ -421,10 +447,12 @@ int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metr
   const int n = order + 1, nq = quad->npts1d;
   const int ndof_e = d == 2 ? n * n : n * n * n;
   const int Q = d == 2 ? nq * nq : nq * nq * nq;
-  const ElemEntry* ent[3];
-  for (int op = 0; op < 3; ++op) {
-    // FP32_MIXED: FP32 only for the Hessian action; FP32_BULK: every element kernel
-    const int fp32 = precision == TMOP_FP32_BULK || (precision == TMOP_FP32_MIXED && op == OP_HESS);
+  const ElemEntry* ent[OP_COUNT];
+  for (int op = 0; op < OP_COUNT; ++op) {
+    // FP32_MIXED: FP32 only for the Hessian action (and its partial assembly);
+    // FP32_BULK: every element kernel
+    const bool hess = op == OP_HESS || op == OP_LINEARIZE || op == OP_HESS_PA;
+    const int fp32 = precision == TMOP_FP32_BULK || (precision == TMOP_FP32_MIXED && hess);
     ent[op] = find_elem(d, n, nq, fp32, op);
     if (!ent[op]) return TMOP_ERR_ARG;  // unsupported (order, points) pair
   }
@@ -459,7 +487,7 @@ int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metr
   c->dim = d; c->order = order; c->n = n; c->nq = nq; c->Q = Q;
   c->nelem = mesh->nelem; c->nnode = mesh->nnode; c->metric = metric_id; c->precision = precision;
   c->ndof = (size_t)d * mesh->nnode;
-  for (int op = 0; op < 3; ++op) c->ent[op] = ent[op];
+  for (int op = 0; op < OP_COUNT; ++op) c->ent[op] = ent[op];
   KParams& p = c->base;
   memset(&p, 0, sizeof(p));
   p.dim = d; p.nelem = mesh->nelem; p.nnode = mesh->nnode; p.metric = metric_id;
@@ -538,7 +566,7 @@ int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metr
     p.fixed = c->d_fixed;
   }
   // launch shapes and workspace
-  for (int op = 0; op < 3 && rc == TMOP_OK; ++op) {
+  for (int op = 0; op < OP_COUNT && rc == TMOP_OK; ++op) {
     if (ent[op]->prepare(mesh->nelem, &c->grid[op]) != 0) rc = TMOP_ERR_CUDA;
     else if (c->grid[op] > kMaxRedBlocks) c->grid[op] = kMaxRedBlocks;
   }
@@ -590,6 +618,17 @@ int tmop_hess_apply(tmop_ctx* c, const double* x, const double* v, double* y, vo
   return launch_op(c, OP_HESS, x, v, y, nullptr, (cudaStream_t)stream);
 }
 
+int tmop_linearize(tmop_ctx* c, const double* x, void* stream) {
+  if (!c || !x) return TMOP_ERR_ARG;
+  return linearize(c, x, (cudaStream_t)stream);
+}
+
+int tmop_hess_apply_pa(tmop_ctx* c, const double* v, double* y, void* stream) {
+  if (!c || !v || !y) return TMOP_ERR_ARG;
+  if (!c->pa_valid) return TMOP_ERR_ARG;
+  return launch_op(c, OP_HESS_PA, nullptr, v, y, nullptr, (cudaStream_t)stream);
+}
+
 int tmop_element_min_detA(tmop_ctx* c, const double* x, double* out, void* stream) {
   if (!c || !x || !out) return TMOP_ERR_ARG;
   return launch_op(c, OP_ENERGY, x, nullptr, nullptr, out, (cudaStream_t)stream);
@@ -637,12 +676,12 @@ int tmop_newton_solve(tmop_ctx* c, double* x, const tmop_newton_opts* opts, tmop
     rep.grad_norm0 = ns.gnorm;
     rc = TMOP_ERR_NOT_CONVERGED;
     for (int it = 0; it < o.max_newton; ++it) {
-      if (ns.gnorm <= o.rtol * rep.grad_norm0) { rc = TMOP_OK; break; }
+      if (ns.gnorm <= o.rtol * rep.grad_norm0 || ns.gnorm <= o.atol) { rc = TMOP_OK; break; }
       int r = newton_iter(c, x, o, &ns, &rep, s);
       rep.iterations = it + 1;
       if (r != TMOP_OK) { rc = r; break; }
     }
-    if (rc == TMOP_ERR_NOT_CONVERGED && ns.gnorm <= o.rtol * rep.grad_norm0) rc = TMOP_OK;
+    if (rc == TMOP_ERR_NOT_CONVERGED && (ns.gnorm <= o.rtol * rep.grad_norm0 || ns.gnorm <= o.atol)) rc = TMOP_OK;
   }
   rep.status = rc;
   rep.F = ns.F;

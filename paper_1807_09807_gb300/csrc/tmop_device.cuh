@@ -196,6 +196,88 @@ __device__ __forceinline__ bool metric_P(int id, const S* T, S& mu, S* P) {
   return false;
 }
 
+// ---------------------------------------------------------------- linearised metric
+// For metrics written in I1 = |T|^2 and tau = det T (all but mu302), the
+// first derivative is P = 2 mu_1 T + mu_t C and, with dI1 = 2 T:dT and
+// dtau = C:dT (C = cof T, the derivative of det),
+//   dP = 2 mu_1 dT + 2 (mu_11 dI1 + mu_1t dtau) T + (mu_1t dI1 + mu_tt dtau) C + mu_t dC,
+// where dC is the directional derivative of the cofactor matrix (product rule
+// on its 2x2 minors in 3D; linear in 2D). MetricLin holds everything that
+// depends on T only, so one point can be differentiated in many directions.
+template <int D, class R>
+struct MetricLin {
+  static constexpr int DD = D * D;
+  R T[DD], C[DD];
+  R m1, mt, m11, m1t, mtt;
+  bool ok;
+
+  __device__ __forceinline__ bool init(int id, const R* Tin) {
+#pragma unroll
+    for (int i = 0; i < DD; ++i) T[i] = Tin[i];
+    R I1 = R(0);
+#pragma unroll
+    for (int i = 0; i < DD; ++i) I1 = fma(T[i], T[i], I1);
+    cof_m<D>(T, C);
+    R tau = R(0);
+#pragma unroll
+    for (int j = 0; j < D; ++j) tau = fma(T[j], C[j], tau);   // expansion along the first row
+    m1 = R(0); mt = R(0); m11 = R(0); m1t = R(0); mtt = R(0);
+    if (id == 1 || id == 14) { m1 = R(1); ok = true; return true; }
+    ok = tau > R(0);
+    if (!ok) return false;
+    const R it = R(1) / tau, it2 = it * it;
+    if (id == 2) {            // I1 / (2 tau) - 1
+      m1 = R(0.5) * it; mt = R(-0.5) * I1 * it2; m1t = R(-0.5) * it2; mtt = I1 * it2 * it;
+    } else if (id == 7) {     // I1 (1 + tau^-2) - 4 (2D)
+      m1 = R(1) + it2; mt = R(-2) * I1 * it2 * it; m1t = R(-2) * it2 * it; mtt = R(6) * I1 * it2 * it2;
+    } else if (id == 9) {     // tau I1 + I1 / tau - 4 tau (2D)
+      m1 = tau + it; mt = I1 - I1 * it2 - R(4); m1t = R(1) - it2; mtt = R(2) * I1 * it2 * it;
+    } else if (id == 77) {    // (tau - 1/tau)^2 / 2
+      const R sdiff = tau - it, ds = R(1) + it2;
+      mt = sdiff * ds; mtt = ds * ds - R(2) * sdiff * it2 * it;
+    } else if (id == 303) {   // I1 tau^{-2/3} / 3 - 1 (3D)
+      const R r = rcbrt_(tau), r2 = r * r, t53 = r2 * it;
+      m1 = r2 * R(1.0 / 3.0); mt = R(-2.0 / 9.0) * I1 * t53; m1t = R(-2.0 / 9.0) * t53;
+      mtt = R(10.0 / 27.0) * I1 * t53 * it;
+    } else {
+      ok = false;
+    }
+    return ok;
+  }
+
+  // dP for one direction dT
+  __device__ __forceinline__ void dP(const R* dT, R* out) const {
+    R dI1 = R(0), dtau = R(0);
+#pragma unroll
+    for (int i = 0; i < DD; ++i) {
+      dI1 = fma(T[i], dT[i], dI1);
+      dtau = fma(C[i], dT[i], dtau);
+    }
+    dI1 *= R(2);
+    const R a = R(2) * m1;
+    const R bT = R(2) * (m11 * dI1 + m1t * dtau);
+    const R bC = m1t * dI1 + mtt * dtau;
+    R dC[DD];
+    if constexpr (D == 2) {
+      dC[0] = dT[3]; dC[1] = -dT[2]; dC[2] = -dT[1]; dC[3] = dT[0];
+    } else {
+#define TMOP_DMINOR(a_, b_, c_, e_) (fma(dT[a_], T[b_], T[a_] * dT[b_]) - fma(dT[c_], T[e_], T[c_] * dT[e_]))
+      dC[0] = TMOP_DMINOR(4, 8, 5, 7);
+      dC[1] = TMOP_DMINOR(5, 6, 3, 8);
+      dC[2] = TMOP_DMINOR(3, 7, 4, 6);
+      dC[3] = TMOP_DMINOR(2, 7, 1, 8);
+      dC[4] = TMOP_DMINOR(0, 8, 2, 6);
+      dC[5] = TMOP_DMINOR(1, 6, 0, 7);
+      dC[6] = TMOP_DMINOR(1, 5, 2, 4);
+      dC[7] = TMOP_DMINOR(2, 3, 0, 5);
+      dC[8] = TMOP_DMINOR(0, 4, 1, 3);
+#undef TMOP_DMINOR
+    }
+#pragma unroll
+    for (int i = 0; i < DD; ++i) out[i] = fma(a, dT[i], fma(bT, T[i], fma(bC, C[i], mt * dC[i])));
+  }
+};
+
 // ---------------------------------------------------------------- contractions
 // Tables in shared memory: B[q][i] = phi_i(xi_q), G[q][i] = phi_i'(xi_q).
 

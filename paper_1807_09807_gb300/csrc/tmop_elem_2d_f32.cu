@@ -6,7 +6,9 @@ namespace tmop {
 #define TMOP_ENTRY(N, Q, OP) \
     {2, N, Q, 1, OP, launch_elem<2, N, Q, float, OP>, prepare_elem<2, N, Q, float, OP>, \
      ElemCfg<2, N, Q, float, OP>::WARPS}
-#define TMOP_ENTRIES(N, Q) TMOP_ENTRY(N, Q, OP_ENERGY), TMOP_ENTRY(N, Q, OP_GRADIENT), TMOP_ENTRY(N, Q, OP_HESS)
+#define TMOP_ENTRIES(N, Q)                                                                      \
+  TMOP_ENTRY(N, Q, OP_ENERGY), TMOP_ENTRY(N, Q, OP_GRADIENT), TMOP_ENTRY(N, Q, OP_HESS),         \
+      TMOP_ENTRY(N, Q, OP_LINEARIZE), TMOP_ENTRY(N, Q, OP_HESS_PA)
 
 extern const ElemEntry kElem_2d_f32[] = {
     TMOP_ENTRIES(2,2),

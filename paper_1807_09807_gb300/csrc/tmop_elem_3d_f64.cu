@@ -6,7 +6,9 @@ namespace tmop {
 #define TMOP_ENTRY(N, Q, OP) \
     {3, N, Q, 0, OP, launch_elem<3, N, Q, double, OP>, prepare_elem<3, N, Q, double, OP>, \
      ElemCfg<3, N, Q, double, OP>::WARPS}
-#define TMOP_ENTRIES(N, Q) TMOP_ENTRY(N, Q, OP_ENERGY), TMOP_ENTRY(N, Q, OP_GRADIENT), TMOP_ENTRY(N, Q, OP_HESS)
+#define TMOP_ENTRIES(N, Q)                                                                      \
+  TMOP_ENTRY(N, Q, OP_ENERGY), TMOP_ENTRY(N, Q, OP_GRADIENT), TMOP_ENTRY(N, Q, OP_HESS),         \
+      TMOP_ENTRY(N, Q, OP_LINEARIZE), TMOP_ENTRY(N, Q, OP_HESS_PA)
 
 extern const ElemEntry kElem_3d_f64[] = {
     TMOP_ENTRIES(2,2),

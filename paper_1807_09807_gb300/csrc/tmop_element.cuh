@@ -85,13 +85,23 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
     // (sum_i grad phi_i = 0), and this keeps the FP32 relative error of A at
     // the level of eps32 instead of eps32 |x| / h.
     double xref[D];
-    if constexpr (sizeof(R) == 4) {
+    if constexpr (sizeof(R) == 4 && OP != OP_HESS_PA) {
       const int g0 = node_id(p, e, 0, N);
 #pragma unroll
       for (int c = 0; c < D; ++c) xref[c] = __ldg(p.x + (size_t)c * p.nnode + g0);
     }
     for (int t = lane; t < NDOF; t += 32) {
       const int g = node_id(p, e, t, N);
+      if constexpr (OP == OP_HESS_PA) {
+        // the partially assembled product needs only the direction v
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const size_t dof = (size_t)c * p.nnode + g;
+          const bool fx = p.fixed && __ldg(p.fixed + dof);
+          P0[c * NDOF + t] = fx ? R(0) : R(__ldg(p.v + dof));
+        }
+        continue;
+      }
 #pragma unroll
       for (int c = 0; c < D; ++c) {
         const double xv = __ldg(p.x + (size_t)c * p.nnode + g);
@@ -114,7 +124,30 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
     R* Abuf = (D == 2) ? P0 : P1;  // [NC][D][QP]
     // ---- pointwise
     double emin = INFINITY;
+    constexpr int NS = DD * (DD + 1) / 2;
     for (int q = lane; q < QP; q += 32) {
+      if constexpr (OP == OP_HESS_PA) {
+        // y = H dA with the stored symmetric A-space Hessian (already scaled by w det W)
+        const R* H = static_cast<const R*>(p.pa) + (size_t)e * NS * QP + q;
+        R dA[DD], y[DD];
+#pragma unroll
+        for (int i = 0; i < DD; ++i) {
+          dA[i] = Abuf[i * QP + q];
+          y[i] = R(0);
+        }
+        int s = 0;
+#pragma unroll
+        for (int r = 0; r < DD; ++r)
+#pragma unroll
+          for (int c = r; c < DD; ++c, ++s) {
+            const R h = H[(size_t)s * QP];
+            y[r] = fma(h, dA[c], y[r]);
+            if (c != r) y[c] = fma(h, dA[r], y[c]);
+          }
+#pragma unroll
+        for (int i = 0; i < DD; ++i) Abuf[i * QP + q] = y[i];
+        continue;
+      }
       R A[DD];
 #pragma unroll
       for (int a = 0; a < D; ++a)
@@ -144,6 +177,51 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
             for (int c = 0; c < D; ++c) s = fma(A[a * D + c], Wi[c * D + b], s);
             T[a * D + b] = s;
           }
+      }
+      if constexpr (OP == OP_LINEARIZE) {
+        // column kl of the A-space Hessian: direction dA = E_kl, dT = E_kl W^-1,
+        // R = w det W (d^2mu/dT^2 : dT) W^-t; the upper triangle is stored
+        R* H = static_cast<R*>(p.pa) + (size_t)e * NS * QP + q;
+        const R s = wq * detW;
+        MetricLin<D, R> L;
+        const bool lin = p.metric != 302;
+        bool ok = lin ? L.init(p.metric, T) : true;
+        int off = 0;
+#pragma unroll 1
+        for (int kl = 0; kl < DD; ++kl) {
+          const int k = kl / D, l = kl % D;
+          R dT[DD], S[DD];
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = 0; b < D; ++b)
+              dT[a * D + b] = a == k ? (p.wkind == WK_IDENTITY ? R(l == b) : Wi[l * D + b]) : R(0);
+          if (lin) {
+            if (ok) L.dP(dT, S);
+          } else {
+            Dual<R> Td[DD], Pd[DD], mud;
+#pragma unroll
+            for (int i = 0; i < DD; ++i) Td[i] = Dual<R>{T[i], dT[i]};
+            ok = metric_P<D>(p.metric, Td, mud, Pd);
+#pragma unroll
+            for (int i = 0; i < DD; ++i) S[i] = Pd[i].d;
+          }
+#pragma unroll
+          for (int mn = 0; mn < DD; ++mn) {
+            if (mn < kl) continue;
+            const int m = mn / D, nn = mn % D;
+            R r = R(0);
+            if (p.wkind == WK_IDENTITY) {
+              r = S[mn];
+            } else {
+#pragma unroll
+              for (int c = 0; c < D; ++c) r = fma(S[m * D + c], Wi[nn * D + c], r);
+            }
+            H[(size_t)(off + mn - kl) * QP] = ok ? s * r : R(0);
+          }
+          off += DD - kl;
+        }
+        continue;
       }
       if constexpr (OP == OP_ENERGY) {
         double Ad[DD];
@@ -179,12 +257,19 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
                 dT[a * D + b] = s;
               }
           }
-          Dual<R> Td[DD], Pd[DD], mud;
+          if (p.metric == 302) {
+            // three invariants (I1, |cof T|^2, tau): forward-mode dual numbers
+            Dual<R> Td[DD], Pd[DD], mud;
 #pragma unroll
-          for (int i = 0; i < DD; ++i) Td[i] = Dual<R>{T[i], dT[i]};
-          ok = metric_P<D>(p.metric, Td, mud, Pd);
+            for (int i = 0; i < DD; ++i) Td[i] = Dual<R>{T[i], dT[i]};
+            ok = metric_P<D>(p.metric, Td, mud, Pd);
 #pragma unroll
-          for (int i = 0; i < DD; ++i) S[i] = Pd[i].d;
+            for (int i = 0; i < DD; ++i) S[i] = Pd[i].d;
+          } else {
+            MetricLin<D, R> L;
+            ok = L.init(p.metric, T);
+            if (ok) L.dP(dT, S);
+          }
         }
         const R s = wq * detW;
         // R = s * S W^-t, stored in place of A at this point
@@ -203,7 +288,9 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
           }
       }
     }
-    if constexpr (OP == OP_ENERGY) {
+    if constexpr (OP == OP_LINEARIZE) {
+      __syncwarp();
+    } else if constexpr (OP == OP_ENERGY) {
       accMin = fmin(accMin, emin);
       if (p.elem_min) {
 #pragma unroll

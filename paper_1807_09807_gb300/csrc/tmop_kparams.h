@@ -10,7 +10,9 @@ namespace tmop {
 constexpr int kMaxQ = 8;   // 1D quadrature points
 constexpr int kMaxN = 5;   // 1D nodes (order <= 4)
 
-enum { OP_ENERGY = 0, OP_GRADIENT = 1, OP_HESS = 2 };
+// OP_LINEARIZE stores the A-space Hessian of w det W mu at every point (once
+// per Newton step); OP_HESS_PA applies it (partial assembly).
+enum { OP_ENERGY = 0, OP_GRADIENT = 1, OP_HESS = 2, OP_LINEARIZE = 3, OP_HESS_PA = 4, OP_COUNT = 5 };
 enum { WK_IDENTITY = 0, WK_CONST = 1, WK_PER_QP = 2 };
 
 struct KParams {
@@ -26,6 +28,7 @@ struct KParams {
   double* part_F;                 // [grid] energy partials
   double* part_min;               // [grid] min det A partials
   double* elem_min;               // [nelem] per-element min det A, or null
+  void* pa;                       // [nelem][DD(DD+1)/2][Q] packed Hessians (float or double)
   double B[kMaxQ * kMaxN];              // B[q][i] = phi_i(xi_q)
   double G[kMaxQ * kMaxN];              // G[q][i] = phi_i'(xi_q)
   double w1[kMaxQ];                // 1D quadrature weights

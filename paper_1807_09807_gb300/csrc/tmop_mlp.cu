@@ -1,0 +1,538 @@
+// Learned initial-iterate proposal: patch features, targets, proposal
+// scatter, and a 3-layer MLP trained with hand-written bfloat16 tensor-core
+// GEMMs (mma.sync m16n8k16, FP32 accumulation) and Adam.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <random>
+#include <vector>
+
+#include "../../include/tmop.h"
+#include "../../include/tmop_mlp.h"
+#include "tmop_kparams.h"
+
+namespace tmop {
+namespace mlp {
+
+using bf16 = __nv_bfloat16;
+
+// ---------------------------------------------------------------- patches
+struct Grid2 {
+  int k, nx, ny, Nx, Ny, ldx;
+  const double* x;
+  double xi[6];  // Gauss-Lobatto node positions of one element on [0,1] (reference lattice)
+  __device__ __forceinline__ double at(int c, int gx, int gy) const { return x[(size_t)c * ldx + gy * Nx + gx]; }
+  // x-direction reflection, gy in range
+  __device__ __forceinline__ double qx(int c, int gx, int gy) const {
+    if (gx < 0) return 2.0 * at(c, 0, gy) - at(c, -gx, gy);
+    if (gx > Nx - 1) return 2.0 * at(c, Nx - 1, gy) - at(c, 2 * (Nx - 1) - gx, gy);
+    return at(c, gx, gy);
+  }
+  __device__ __forceinline__ double pos(int c, int gx, int gy) const {
+    if (gy < 0) return 2.0 * qx(c, gx, 0) - qx(c, gx, -gy);
+    if (gy > Ny - 1) return 2.0 * qx(c, gx, Ny - 1) - qx(c, gx, 2 * (Ny - 1) - gy);
+    return qx(c, gx, gy);
+  }
+};
+
+// one warp per patch
+__global__ void k_features(Grid2 G, int first, int count, bf16* feat, int ldf) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= count) return;
+  const int e = first + warp, ex = e % G.nx, ey = e / G.nx, k = G.k;
+  const int side = 3 * k + 1, nfeat = 2 * side * side;
+  double c[2];
+#pragma unroll
+  for (int d = 0; d < 2; ++d)
+    c[d] = 0.25 * (G.at(d, k * ex, k * ey) + G.at(d, k * ex + k, k * ey) + G.at(d, k * ex, k * ey + k) +
+                   G.at(d, k * ex + k, k * ey + k));
+  const double inv_h = (double)G.nx;
+  bf16* row = feat + (size_t)warp * ldf;
+  for (int f = lane; f < ldf; f += 32) {
+    float v = 0.0f;
+    if (f < nfeat) {
+      const int d = f & 1, node = f >> 1, a = node % side, b = node / side;
+      // position of this patch node in a uniform patch, relative to the centre
+      // element's centre, in units of h
+      const int ab = d == 0 ? a : b;
+      const double ref = (double)(ab / k - 1) + G.xi[ab % k] - 0.5;
+      v = (float)((G.pos(d, k * (ex - 1) + a, k * (ey - 1) + b) - c[d]) * inv_h - ref);
+    }
+    row[f] = __float2bfloat16_rn(v);
+  }
+}
+
+__global__ void k_targets(Grid2 G0, const double* x1, int first, int count, float* T, int ldt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = G0.k, per = 2 * k * k;
+  if (t >= count * per) return;
+  const int p = t / per, f = t % per, e = first + p;
+  const int d = f & 1, o = f >> 1, i = o % k, j = o / k;
+  const int ex = e % G0.nx, ey = e / G0.nx;
+  const size_t node = (size_t)(k * ey + j) * G0.Nx + k * ex + i;
+  T[(size_t)p * ldt + f] = (float)((x1[(size_t)d * G0.ldx + node] - G0.x[(size_t)d * G0.ldx + node]) * G0.nx);
+}
+
+__global__ void k_apply(Grid2 G0, const uint8_t* fixed, const float* Y, int ldy, double* xo) {
+  const size_t nn = (size_t)G0.Nx * G0.Ny;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= 2 * nn) return;
+  const int d = (int)(t / nn);
+  const size_t node = t % nn;
+  const int gx = (int)(node % G0.Nx), gy = (int)(node / G0.Nx), k = G0.k;
+  const size_t dof = (size_t)d * G0.ldx + node;
+  double v = G0.x[dof];
+  const bool owned = gx < k * G0.nx && gy < k * G0.ny;
+  if (owned && !(fixed && fixed[dof])) {
+    const int e = (gy / k) * G0.nx + gx / k, i = gx % k, j = gy % k;
+    v += (double)Y[(size_t)e * ldy + 2 * (j * k + i) + d] / G0.nx;
+  }
+  xo[dof] = v;
+}
+
+// ---------------------------------------------------------------- GEMM
+constexpr int BM = 64, BN = 64, BKT = 32, PADK = 8;
+enum { EPI_BIAS_RELU_BF16 = 0, EPI_BIAS_F32 = 1, EPI_MASK_BF16 = 2, EPI_F32 = 3 };
+
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// C[m][n] = sum_k A(m,k) B(n,k) with A(m,k) = AK ? A[m*lda+k] : A[k*lda+m] and
+// B(n,k) = BK ? B[n*ldb+k] : B[k*ldb+n]. M, N multiples of 64, K of 32, leading
+// dimensions multiples of 8 (16-byte rows). Block 64x64, 4 warps of 32x32.
+template <bool AK, bool BK, int EPI>
+__global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16* __restrict__ A, int lda,
+                                              const bf16* __restrict__ B, int ldb, void* __restrict__ C, int ldc,
+                                              const float* __restrict__ bias, const bf16* __restrict__ ref, int ldr) {
+  __shared__ __align__(16) bf16 As[BM][BKT + PADK];
+  __shared__ __align__(16) bf16 Bs[BN][BKT + PADK];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
+
+  for (int k0 = 0; k0 < K; k0 += BKT) {
+#pragma unroll
+    for (int c = tid; c < BM * BKT / 8; c += 128) {
+      if (AK) {
+        const int r = c / (BKT / 8), kc = (c % (BKT / 8)) * 8;
+        *reinterpret_cast<uint4*>(&As[r][kc]) =
+            *reinterpret_cast<const uint4*>(&A[(size_t)(m0 + r) * lda + k0 + kc]);
+      } else {
+        const int kk = c / (BM / 8), mc = (c % (BM / 8)) * 8;
+        const uint4 v = *reinterpret_cast<const uint4*>(&A[(size_t)(k0 + kk) * lda + m0 + mc]);
+        const bf16* e = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) As[mc + j][kk] = e[j];
+      }
+      if (BK) {
+        const int r = c / (BKT / 8), kc = (c % (BKT / 8)) * 8;
+        *reinterpret_cast<uint4*>(&Bs[r][kc]) =
+            *reinterpret_cast<const uint4*>(&B[(size_t)(n0 + r) * ldb + k0 + kc]);
+      } else {
+        const int kk = c / (BN / 8), nc = (c % (BN / 8)) * 8;
+        const uint4 v = *reinterpret_cast<const uint4*>(&B[(size_t)(k0 + kk) * ldb + n0 + nc]);
+        const bf16* e = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) Bs[nc + j][kk] = e[j];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BKT; kk += 16) {
+      uint32_t a[2][4], b[4][2];
+      const int g = lane >> 2, t2 = (lane & 3) * 2;
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + i * 16 + g;
+        a[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][kk + t2]);
+        a[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + t2]);
+        a[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][kk + t2 + 8]);
+        a[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + t2 + 8]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = wn + j * 8 + g;
+        b[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[r][kk + t2]);
+        b[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[r][kk + t2 + 8]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+  const int g = lane >> 2, t2 = (lane & 3) * 2;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int m = m0 + wm + i * 16 + g + h * 8, n = n0 + wn + j * 8 + t2;
+        float v0 = acc[i][j][2 * h], v1 = acc[i][j][2 * h + 1];
+        if (EPI == EPI_BIAS_RELU_BF16 || EPI == EPI_BIAS_F32) {
+          v0 += bias[n];
+          v1 += bias[n + 1];
+        }
+        if (EPI == EPI_BIAS_RELU_BF16) {
+          v0 = fmaxf(v0, 0.0f);
+          v1 = fmaxf(v1, 0.0f);
+        }
+        if (EPI == EPI_MASK_BF16) {
+          const __nv_bfloat162 rr = *reinterpret_cast<const __nv_bfloat162*>(&ref[(size_t)m * ldr + n]);
+          if (!(__bfloat162float(rr.x) > 0.0f)) v0 = 0.0f;
+          if (!(__bfloat162float(rr.y) > 0.0f)) v1 = 0.0f;
+        }
+        if (EPI == EPI_BIAS_RELU_BF16 || EPI == EPI_MASK_BF16) {
+          *reinterpret_cast<__nv_bfloat162*>(&reinterpret_cast<bf16*>(C)[(size_t)m * ldc + n]) =
+              __floats2bfloat162_rn(v0, v1);
+        } else {
+          *reinterpret_cast<float2*>(&reinterpret_cast<float*>(C)[(size_t)m * ldc + n]) = make_float2(v0, v1);
+        }
+      }
+}
+
+template <bool AK, bool BK, int EPI>
+int gemm(int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb, void* C, int ldc, const float* bias,
+         const bf16* ref, int ldr, cudaStream_t s) {
+  if (M % BM || N % BN || K % BKT || lda % 8 || ldb % 8 || ldc % 2 || M <= 0 || N <= 0 || K <= 0) return TMOP_ERR_ARG;
+  dim3 grid(N / BN, M / BM);
+  k_gemm<AK, BK, EPI><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, ref, ldr);
+  return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- loss, sums, Adam
+// dY = 2 (Y - T) / B on the n_out real columns (0 on the padding), as FP32
+// and as bf16; per-block partial sums of (Y - T)^2 / B.
+__global__ void k_loss_grad(const float* Y, int ldy, const float* T, int ldt, int batch, int n_out, int npad,
+                            float* dYf, bf16* dYb, double* part) {
+  __shared__ double red[256];
+  double s = 0.0;
+  const size_t tot = (size_t)batch * npad;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(t / npad), j = (int)(t % npad);
+    float g = 0.0f;
+    if (j < n_out) {
+      const float r = Y[(size_t)b * ldy + j] - T[(size_t)b * ldt + j];
+      g = 2.0f * r / (float)batch;
+      s += (double)r * (double)r / (double)batch;
+    }
+    dYf[t] = g;
+    dYb[t] = __float2bfloat16_rn(g);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum_parts(const double* part, int np, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < np; ++i) s += part[i];
+    *out = s;
+  }
+}
+
+// column sums of a [rows][ld] matrix (float or bf16) into out[ncol]
+template <class Tv>
+__global__ void k_colsum(const Tv* X, int rows, int ld, int ncol, float* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ncol) return;
+  float s = 0.0f;
+  for (int r = 0; r < rows; ++r) s += (float)X[(size_t)r * ld + j];
+  out[j] = s;
+}
+
+__global__ void k_adam(float* w, float* m, float* v, const float* g, size_t n, float lr, float b1t, float b2t,
+                       bf16* wb) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = 0.9f * m[i] + 0.1f * gi;
+    const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / (1.0f - b1t)) / (sqrtf(vi / (1.0f - b2t)) + 1e-8f);
+    w[i] = wi;
+    if (wb) wb[i] = __float2bfloat16_rn(wi);
+  }
+}
+
+__global__ void k_to_bf16(const float* a, bf16* b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = __float2bfloat16_rn(a[i]);
+}
+
+}  // namespace mlp
+}  // namespace tmop
+
+using namespace tmop::mlp;
+
+struct tmop_mlp {
+  int n_in, H, n_out, K1, N3;  // K1 = padded input, N3 = padded output (multiples of 64)
+  // FP32 masters (one allocation): W1 [H][K1], b1 [H], W2 [H][H], b2 [H], W3 [N3][H], b3 [N3]
+  size_t off[6], total;
+  float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+  bf16 *W1 = nullptr, *W2 = nullptr, *W3 = nullptr;  // bf16 copies of the weight matrices
+  int batch_cap = 0;
+  bf16 *H1 = nullptr, *H2 = nullptr, *dYb = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
+  float *Y = nullptr, *dYf = nullptr;
+  double* part = nullptr;
+  int t = 0;
+};
+
+namespace {
+
+int ensure_batch(tmop_mlp* n, int batch) {
+  if (batch <= n->batch_cap) return TMOP_OK;
+  cudaFree(n->H1); cudaFree(n->H2); cudaFree(n->dYb); cudaFree(n->dZ2); cudaFree(n->dZ1);
+  cudaFree(n->Y); cudaFree(n->dYf); cudaFree(n->part);
+  const size_t B = batch;
+  if (cudaMalloc(&n->H1, B * n->H * sizeof(bf16)) || cudaMalloc(&n->H2, B * n->H * sizeof(bf16)) ||
+      cudaMalloc(&n->dZ2, B * n->H * sizeof(bf16)) || cudaMalloc(&n->dZ1, B * n->H * sizeof(bf16)) ||
+      cudaMalloc(&n->dYb, B * n->N3 * sizeof(bf16)) || cudaMalloc(&n->Y, B * n->N3 * sizeof(float)) ||
+      cudaMalloc(&n->dYf, B * n->N3 * sizeof(float)) || cudaMalloc(&n->part, 1024 * sizeof(double))) {
+    n->batch_cap = 0;
+    return TMOP_ERR_CUDA;
+  }
+  n->batch_cap = batch;
+  return TMOP_OK;
+}
+
+float* P(tmop_mlp* n, float* base, int i) { return base + n->off[i]; }
+
+int refresh_bf16(tmop_mlp* n, cudaStream_t s) {
+  const size_t n1 = (size_t)n->H * n->K1, n2 = (size_t)n->H * n->H, n3 = (size_t)n->N3 * n->H;
+  k_to_bf16<<<256, 256, 0, s>>>(P(n, n->w, 0), n->W1, n1);
+  k_to_bf16<<<256, 256, 0, s>>>(P(n, n->w, 2), n->W2, n2);
+  k_to_bf16<<<64, 256, 0, s>>>(P(n, n->w, 4), n->W3, n3);
+  return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
+}
+
+int forward_impl(tmop_mlp* n, const bf16* X, int batch, float* Y, int ldy, cudaStream_t s) {
+  int rc = gemm<true, true, EPI_BIAS_RELU_BF16>(batch, n->H, n->K1, X, n->K1, n->W1, n->K1, n->H1, n->H,
+                                                P(n, n->w, 1), nullptr, 0, s);
+  if (!rc) rc = gemm<true, true, EPI_BIAS_RELU_BF16>(batch, n->H, n->H, n->H1, n->H, n->W2, n->H, n->H2, n->H,
+                                                     P(n, n->w, 3), nullptr, 0, s);
+  if (!rc) rc = gemm<true, true, EPI_BIAS_F32>(batch, n->N3, n->H, n->H2, n->H, n->W3, n->H, Y, ldy,
+                                               P(n, n->w, 5), nullptr, 0, s);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tmop_patch_features(int order, int nx, int ny, const double* x, int ldx, int first, int count, uint16_t* feat,
+                        int ldf, void* stream) {
+  if (order < 1 || order > 4 || nx < 1 || ny < 1 || !x || !feat || first < 0 || count < 0 ||
+      first + (long long)count > (long long)nx * ny)
+    return TMOP_ERR_ARG;
+  const int side = 3 * order + 1;
+  if (ldf < 2 * side * side || ldf % 8) return TMOP_ERR_ARG;
+  Grid2 G{order, nx, ny, order * nx + 1, order * ny + 1, ldx, x, {0}};
+  if (ldx < G.Nx * G.Ny) return TMOP_ERR_ARG;
+  double w[6];
+  tmop::rule_gll(order + 1, G.xi, w);
+  if (count == 0) return TMOP_OK;
+  const int threads = 256, blocks = (int)(((long long)count * 32 + threads - 1) / threads);
+  k_features<<<blocks, threads, 0, (cudaStream_t)stream>>>(G, first, count, reinterpret_cast<bf16*>(feat), ldf);
+  return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
+}
+
+int tmop_patch_targets(int order, int nx, int ny, const double* x0, const double* x1, int ldx, int first, int count,
+                       float* T, int ldt, void* stream) {
+  if (order < 1 || order > 4 || nx < 1 || ny < 1 || !x0 || !x1 || !T || first < 0 || count < 0 ||
+      first + (long long)count > (long long)nx * ny || ldt < 2 * order * order)
+    return TMOP_ERR_ARG;
+  Grid2 G{order, nx, ny, order * nx + 1, order * ny + 1, ldx, x0, {0}};
+  if (ldx < G.Nx * G.Ny) return TMOP_ERR_ARG;
+  const long long tot = (long long)count * 2 * order * order;
+  if (tot == 0) return TMOP_OK;
+  k_targets<<<(int)((tot + 255) / 256), 256, 0, (cudaStream_t)stream>>>(G, x1, first, count, T, ldt);
+  return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
+}
+
+int tmop_patch_apply(int order, int nx, int ny, const double* x0, const uint8_t* fixed, int ldx, const float* Y,
+                     int ldy, double* x_out, void* stream) {
+  if (order < 1 || order > 4 || nx < 1 || ny < 1 || !x0 || !Y || !x_out || x_out == x0 || ldy < 2 * order * order)
+    return TMOP_ERR_ARG;
+  Grid2 G{order, nx, ny, order * nx + 1, order * ny + 1, ldx, x0, {0}};
+  if (ldx < G.Nx * G.Ny) return TMOP_ERR_ARG;
+  const long long tot = 2LL * G.Nx * G.Ny;
+  k_apply<<<(int)((tot + 255) / 256), 256, 0, (cudaStream_t)stream>>>(G, fixed, Y, ldy, x_out);
+  return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
+}
+
+void tmop_mlp_destroy(tmop_mlp* n) {
+  if (!n) return;
+  cudaFree(n->w); cudaFree(n->g); cudaFree(n->m); cudaFree(n->v);
+  cudaFree(n->W1); cudaFree(n->W2); cudaFree(n->W3);
+  cudaFree(n->H1); cudaFree(n->H2); cudaFree(n->dYb); cudaFree(n->dZ2); cudaFree(n->dZ1);
+  cudaFree(n->Y); cudaFree(n->dYf); cudaFree(n->part);
+  delete n;
+}
+
+int tmop_mlp_create(int n_in, int n_hidden, int n_out, uint64_t seed, tmop_mlp** out) {
+  if (!out) return TMOP_ERR_ARG;
+  *out = nullptr;
+  if (n_in < 1 || n_in > 1024 || n_hidden < 64 || n_hidden % 64 || n_hidden > 4096 || n_out < 1 || n_out > 64)
+    return TMOP_ERR_ARG;
+  tmop_mlp* n = new tmop_mlp();
+  n->n_in = n_in; n->H = n_hidden; n->n_out = n_out;
+  n->K1 = (n_in + 63) / 64 * 64;
+  n->N3 = 64;
+  const size_t sz[6] = {(size_t)n->H * n->K1, (size_t)n->H, (size_t)n->H * n->H, (size_t)n->H,
+                        (size_t)n->N3 * n->H, (size_t)n->N3};
+  size_t acc = 0;
+  for (int i = 0; i < 6; ++i) { n->off[i] = acc; acc += (sz[i] + 63) / 64 * 64; }
+  n->total = acc;
+  std::vector<float> host(acc, 0.0f);
+  std::mt19937_64 gen(seed);
+  auto fill = [&](int i, int rows, int cols, int ld, float std) {
+    std::normal_distribution<float> nd(0.0f, std);
+    for (int r = 0; r < rows; ++r)
+      for (int c = 0; c < cols; ++c) host[n->off[i] + (size_t)r * ld + c] = nd(gen);
+  };
+  fill(0, n->H, n_in, n->K1, sqrtf(2.0f / n_in));
+  fill(2, n->H, n->H, n->H, sqrtf(2.0f / n->H));
+  fill(4, n_out, n->H, n->H, 0.1f * sqrtf(2.0f / n->H));
+  int rc = TMOP_OK;
+  if (cudaMalloc(&n->w, acc * 4) || cudaMalloc(&n->g, acc * 4) || cudaMalloc(&n->m, acc * 4) ||
+      cudaMalloc(&n->v, acc * 4) || cudaMalloc(&n->W1, sz[0] * 2) || cudaMalloc(&n->W2, sz[2] * 2) ||
+      cudaMalloc(&n->W3, sz[4] * 2) || cudaMemcpy(n->w, host.data(), acc * 4, cudaMemcpyHostToDevice) ||
+      cudaMemset(n->g, 0, acc * 4) || cudaMemset(n->m, 0, acc * 4) || cudaMemset(n->v, 0, acc * 4))
+    rc = TMOP_ERR_CUDA;
+  if (rc == TMOP_OK) rc = refresh_bf16(n, 0);
+  if (rc == TMOP_OK && cudaDeviceSynchronize() != cudaSuccess) rc = TMOP_ERR_CUDA;
+  if (rc != TMOP_OK) { tmop_mlp_destroy(n); return rc; }
+  *out = n;
+  return TMOP_OK;
+}
+
+int tmop_mlp_input_ld(const tmop_mlp* n) { return n ? n->K1 : 0; }
+
+size_t tmop_mlp_num_params(const tmop_mlp* n) {
+  if (!n) return 0;
+  return (size_t)n->H * n->n_in + n->H + (size_t)n->H * n->H + n->H + (size_t)n->n_out * n->H + n->n_out;
+}
+
+// Copy between the flat unpadded host layout and the padded device layout.
+static int copy_params(tmop_mlp* n, float* dev, float* host, bool to_host) {
+  std::vector<float> buf(n->total);
+  if (to_host) {
+    if (cudaDeviceSynchronize() || cudaMemcpy(buf.data(), dev, n->total * 4, cudaMemcpyDeviceToHost))
+      return TMOP_ERR_CUDA;
+  } else {
+    std::fill(buf.begin(), buf.end(), 0.0f);
+  }
+  const int rows[6] = {n->H, 1, n->H, 1, n->n_out, 1};
+  const int cols[6] = {n->n_in, n->H, n->H, n->H, n->H, n->n_out};
+  const int ld[6] = {n->K1, 0, n->H, 0, n->H, 0};
+  size_t h = 0;
+  for (int i = 0; i < 6; ++i)
+    for (int r = 0; r < rows[i]; ++r)
+      for (int c = 0; c < cols[i]; ++c, ++h) {
+        float& d = buf[n->off[i] + (size_t)r * ld[i] + c];
+        if (to_host) host[h] = d;
+        else d = host[h];
+      }
+  if (!to_host && cudaMemcpy(dev, buf.data(), n->total * 4, cudaMemcpyHostToDevice)) return TMOP_ERR_CUDA;
+  return TMOP_OK;
+}
+
+int tmop_mlp_get(tmop_mlp* n, int which, float* host, size_t cnt) {
+  if (!n || !host || cnt != tmop_mlp_num_params(n) || (which != 0 && which != 1)) return TMOP_ERR_ARG;
+  return copy_params(n, which == 0 ? n->w : n->g, host, true);
+}
+
+int tmop_mlp_set(tmop_mlp* n, const float* host, size_t cnt) {
+  if (!n || !host || cnt != tmop_mlp_num_params(n)) return TMOP_ERR_ARG;
+  int rc = copy_params(n, n->w, const_cast<float*>(host), false);
+  if (rc == TMOP_OK) rc = refresh_bf16(n, 0);
+  if (rc == TMOP_OK && cudaDeviceSynchronize() != cudaSuccess) rc = TMOP_ERR_CUDA;
+  return rc;
+}
+
+int tmop_mlp_forward(tmop_mlp* n, const uint16_t* X, int batch, float* Y, int ldy, void* stream) {
+  if (!n || !X || !Y || batch <= 0 || batch % 64 || ldy < n->n_out || ldy % 2) return TMOP_ERR_ARG;
+  int rc = ensure_batch(n, batch);
+  if (rc) return rc;
+  // the last GEMM writes all N3 padded columns
+  if (ldy < n->N3) {
+    rc = forward_impl(n, reinterpret_cast<const bf16*>(X), batch, n->Y, n->N3, (cudaStream_t)stream);
+    if (rc) return rc;
+    if (cudaMemcpy2DAsync(Y, (size_t)ldy * 4, n->Y, (size_t)n->N3 * 4, (size_t)ldy * 4, batch,
+                          cudaMemcpyDeviceToDevice, (cudaStream_t)stream))
+      return TMOP_ERR_CUDA;
+    return TMOP_OK;
+  }
+  return forward_impl(n, reinterpret_cast<const bf16*>(X), batch, Y, ldy, (cudaStream_t)stream);
+}
+
+int tmop_mlp_gradients(tmop_mlp* n, const uint16_t* Xu, const float* T, int ldt, int batch, double* loss,
+                       void* stream) {
+  if (!n || !Xu || !T || batch <= 0 || batch % 64 || ldt < n->n_out) return TMOP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = ensure_batch(n, batch);
+  if (rc) return rc;
+  const bf16* X = reinterpret_cast<const bf16*>(Xu);
+  rc = forward_impl(n, X, batch, n->Y, n->N3, s);
+  if (rc) return rc;
+  const int lblocks = 256;
+  k_loss_grad<<<lblocks, 256, 0, s>>>(n->Y, n->N3, T, ldt, batch, n->n_out, n->N3, n->dYf, n->dYb, n->part);
+  if (loss) k_sum_parts<<<1, 32, 0, s>>>(n->part, lblocks, loss);
+  // layer 3: dW3 = dY^T H2, db3 = colsum dY, dH2 = dY W3 masked by H2 > 0
+  rc = gemm<false, false, EPI_F32>(n->N3, n->H, batch, n->dYb, n->N3, n->H2, n->H, P(n, n->g, 4), n->H, nullptr,
+                                   nullptr, 0, s);
+  k_colsum<float><<<1, 64, 0, s>>>(n->dYf, batch, n->N3, n->N3, P(n, n->g, 5));
+  if (!rc) rc = gemm<true, false, EPI_MASK_BF16>(batch, n->H, n->N3, n->dYb, n->N3, n->W3, n->H, n->dZ2, n->H,
+                                                 nullptr, n->H2, n->H, s);
+  // layer 2
+  if (!rc) rc = gemm<false, false, EPI_F32>(n->H, n->H, batch, n->dZ2, n->H, n->H1, n->H, P(n, n->g, 2), n->H,
+                                            nullptr, nullptr, 0, s);
+  k_colsum<bf16><<<(n->H + 127) / 128, 128, 0, s>>>(n->dZ2, batch, n->H, n->H, P(n, n->g, 3));
+  if (!rc) rc = gemm<true, false, EPI_MASK_BF16>(batch, n->H, n->H, n->dZ2, n->H, n->W2, n->H, n->dZ1, n->H,
+                                                 nullptr, n->H1, n->H, s);
+  // layer 1
+  if (!rc) rc = gemm<false, false, EPI_F32>(n->H, n->K1, batch, n->dZ1, n->H, X, n->K1, P(n, n->g, 0), n->K1,
+                                            nullptr, nullptr, 0, s);
+  k_colsum<bf16><<<(n->H + 127) / 128, 128, 0, s>>>(n->dZ1, batch, n->H, n->H, P(n, n->g, 1));
+  if (rc) return rc;
+  return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
+}
+
+int tmop_mlp_adam(tmop_mlp* n, float lr, void* stream) {
+  if (!n || !(lr > 0.0f)) return TMOP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  n->t += 1;
+  const float b1t = powf(0.9f, (float)n->t), b2t = powf(0.999f, (float)n->t);
+  bf16* wb[6] = {n->W1, nullptr, n->W2, nullptr, n->W3, nullptr};
+  const size_t sz[6] = {(size_t)n->H * n->K1, (size_t)n->H, (size_t)n->H * n->H, (size_t)n->H,
+                        (size_t)n->N3 * n->H, (size_t)n->N3};
+  for (int i = 0; i < 6; ++i)
+    k_adam<<<128, 256, 0, s>>>(P(n, n->w, i), P(n, n->m, i), P(n, n->v, i), P(n, n->g, i), sz[i], lr, b1t, b2t,
+                               wb[i]);
+  return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
+}
+
+}  // extern "C"

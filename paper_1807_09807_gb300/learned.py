@@ -1,0 +1,265 @@
+"""Learned initial iterate for TMOP Newton on 2D structured order-k meshes.
+
+Pipeline (all arithmetic in libtmop_gb300.so; this module only sequences
+calls and marshals arguments):
+
+1. data:  many seeded jittered meshes are solved by plain Newton (Section 3.4
+   line search, MINRES) as ONE problem -- the meshes are disjoint, so the
+   Hessian is block diagonal and every block converges to its own minimiser;
+   features are the 3x3-element patches of the jittered meshes, targets the
+   Newton displacement of each centre element's owned nodes
+   (tmop_patch_features / tmop_patch_targets).
+2. train: MLP n_in -> 256 -> 256 -> 2k^2 on the GPU with the library's
+   bfloat16 tensor-core forward/backward kernels and Adam.
+3. propose: features of a new mesh -> MLP -> x0 + h * displacement at every
+   free owned node (tmop_patch_apply). The proposal is kept only if it is
+   valid (min det A > 0) and lowers F; otherwise Newton starts from x0.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import meshgen as mg
+from . import tmop as tm
+
+_MLP_SIGS = {
+    "tmop_patch_features": ([C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                             C.c_void_p], C.c_int),
+    "tmop_patch_targets": ([C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                            C.c_int, C.c_void_p], C.c_int),
+    "tmop_patch_apply": ([C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
+                          C.c_void_p], C.c_int),
+    "tmop_mlp_create": ([C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(C.c_void_p)], C.c_int),
+    "tmop_mlp_destroy": ([C.c_void_p], None),
+    "tmop_mlp_input_ld": ([C.c_void_p], C.c_int),
+    "tmop_mlp_forward": ([C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
+    "tmop_mlp_gradients": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+    "tmop_mlp_adam": ([C.c_void_p, C.c_float, C.c_void_p], C.c_int),
+    "tmop_mlp_num_params": ([C.c_void_p], C.c_size_t),
+    "tmop_mlp_get": ([C.c_void_p, C.c_int, C.c_void_p, C.c_size_t], C.c_int),
+    "tmop_mlp_set": ([C.c_void_p, C.c_void_p, C.c_size_t], C.c_int),
+}
+_loaded = False
+
+
+def lib():
+    global _loaded
+    L = tm.load()
+    if not _loaded:
+        for name, (args, res) in _MLP_SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _loaded = True
+    return L
+
+
+def _check(rc, what):
+    if rc != tm.OK:
+        raise tm.TmopError(rc, what)
+
+
+def _p(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _s():
+    return tm._stream()
+
+
+def n_features(order: int) -> int:
+    return 2 * (3 * order + 1) ** 2
+
+
+def n_targets(order: int) -> int:
+    return 2 * order * order
+
+
+class MLP:
+    """The proposal network (wraps tmop_mlp_*)."""
+
+    def __init__(self, n_in: int, n_out: int, hidden: int = 256, seed: int = 0):
+        h = C.c_void_p()
+        _check(lib().tmop_mlp_create(n_in, hidden, n_out, seed, C.byref(h)), "tmop_mlp_create")
+        self._h, self.n_in, self.n_out, self.hidden = h, n_in, n_out, hidden
+        self.ld = lib().tmop_mlp_input_ld(h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tmop_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_params(self):
+        return lib().tmop_mlp_num_params(self._h)
+
+    def get(self, which=0) -> np.ndarray:
+        out = np.zeros(self.num_params, dtype=np.float32)
+        _check(lib().tmop_mlp_get(self._h, which, out.ctypes.data, out.size), "tmop_mlp_get")
+        return out
+
+    def set(self, flat: np.ndarray):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        _check(lib().tmop_mlp_set(self._h, flat.ctypes.data, flat.size), "tmop_mlp_set")
+
+    def unflatten(self, flat):
+        h, i, o = self.hidden, self.n_in, self.n_out
+        sizes = [(h, i), (h,), (h, h), (h,), (o, h), (o,)]
+        out, k = [], 0
+        for s in sizes:
+            n = int(np.prod(s))
+            out.append(np.asarray(flat[k:k + n], dtype=np.float64).reshape(s))
+            k += n
+        return out
+
+    def forward(self, X, Y=None):
+        import torch
+        B = X.shape[0]
+        Y = torch.empty((B, 64), dtype=torch.float32, device=X.device) if Y is None else Y
+        _check(lib().tmop_mlp_forward(self._h, _p(X), B, _p(Y), Y.shape[1], _s()), "tmop_mlp_forward")
+        return Y
+
+    def gradients(self, X, T, loss=None):
+        _check(lib().tmop_mlp_gradients(self._h, _p(X), _p(T), T.shape[1], X.shape[0],
+                                        None if loss is None else _p(loss), _s()), "tmop_mlp_gradients")
+
+    def adam(self, lr: float):
+        _check(lib().tmop_mlp_adam(self._h, lr, _s()), "tmop_mlp_adam")
+
+
+def features(m: mg.Mesh, x, ldf: int, first: int = 0, count: int | None = None, ldx: int | None = None, out=None):
+    """bf16 patch features (as int16 tensor) of elements first..first+count-1."""
+    import torch
+    count = m.nelem if count is None else count
+    out = torch.zeros((count, ldf), dtype=torch.int16, device=x.device) if out is None else out
+    _check(lib().tmop_patch_features(m.order, m.nx[0], m.nx[1], _p(x), ldx or m.nnode, first, count, _p(out), ldf,
+                                     _s()), "tmop_patch_features")
+    return out
+
+
+def targets(m: mg.Mesh, x0, x1, first=0, count=None, ldx=None, out=None):
+    import torch
+    count = m.nelem if count is None else count
+    nt = n_targets(m.order)
+    out = torch.zeros((count, nt), dtype=torch.float32, device=x0.device) if out is None else out
+    _check(lib().tmop_patch_targets(m.order, m.nx[0], m.nx[1], _p(x0), _p(x1), ldx or m.nnode, first, count, _p(out),
+                                    out.shape[1], _s()), "tmop_patch_targets")
+    return out
+
+
+def apply(m: mg.Mesh, x0, fixed_dev, Y, out=None):
+    import torch
+    out = torch.empty_like(x0) if out is None else out
+    _check(lib().tmop_patch_apply(m.order, m.nx[0], m.nx[1], _p(x0), None if fixed_dev is None else _p(fixed_dev),
+                                  m.nnode, _p(Y), Y.shape[1], _p(out), _s()), "tmop_patch_apply")
+    return out
+
+
+def union_context(meshes, precision=tm.FP32_MIXED):
+    """One TMOP problem made of disjoint meshes (unstructured connectivity)."""
+    m0 = meshes[0]
+    N = m0.nnode
+    en = np.concatenate([m.elem_nodes + i * N for i, m in enumerate(meshes)]).astype(np.int32)
+    fixed = np.concatenate([m.fixed for m in meshes], axis=1)
+    x = np.concatenate([m.x for m in meshes], axis=1)
+    ctx = tm.Context(m0.dim, m0.order, N * len(meshes), en, fixed, m0.nq, m0.metric, quad_kind=m0.quad_kind,
+                     precision=precision)
+    return ctx, x
+
+
+@dataclass
+class Dataset:
+    X: object            # int16 (bf16 bits) [S, ld]
+    T: object            # float32 [S, n_targets]
+    meshes: int
+    newton: list = field(default_factory=list)   # per chunk (status, Newton its, Krylov its, seconds)
+    seconds: float = 0.0
+
+
+def make_dataset(n_meshes=2000, seed0=1000, nx=32, ldf=256, chunk=250, precision=tm.FP32_MIXED,
+                 preset="c5", max_newton=30) -> Dataset:
+    """Newton-converged displacement targets from n_meshes seeded meshes
+    (seeds seed0, seed0+1, ...), solved chunk meshes at a time as one
+    block-diagonal problem."""
+    import torch
+    t0 = time.perf_counter()
+    Xs, Ts, log = [], [], []
+    for c0 in range(0, n_meshes, chunk):
+        ms = [mg.make_mesh(preset, seed0 + i, nx=nx) for i in range(c0, min(c0 + chunk, n_meshes))]
+        ctx, xh = union_context(ms, precision)
+        x0 = torch.tensor(xh, device="cuda")
+        x1 = x0.clone()
+        r = ctx.newton_solve(x1, max_newton=max_newton)
+        log.append((r.status, r.report["iterations"], r.report["krylov_iterations"]))
+        if r.status != tm.OK:
+            raise RuntimeError(f"data generation: Newton failed on chunk {c0}: {tm.status_string(r.status)}")
+        N = ms[0].nnode
+        for i, m in enumerate(ms):
+            # component stride of the union positions is the union node count
+            xa, xb = x0[:, i * N:], x1[:, i * N:]
+            Xs.append(features(m, xa, ldf, ldx=x0.shape[1]))
+            Ts.append(targets(m, xa, xb, ldx=x0.shape[1]))
+        ctx.close()
+    torch.cuda.synchronize()
+    return Dataset(torch.cat(Xs), torch.cat(Ts), n_meshes, log, time.perf_counter() - t0)
+
+
+def train(net: MLP, ds: Dataset, epochs=20, batch=4096, lr=1e-3, seed=0, log_every=0):
+    """Adam on minibatches of the dataset (reshuffled every epoch)."""
+    import torch
+    S = ds.X.shape[0]
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    loss = torch.zeros((), dtype=torch.float64, device="cuda")
+    hist = []
+    nb = S // batch
+    for ep in range(epochs):
+        perm = torch.randperm(S, device="cuda", generator=g)
+        acc = 0.0
+        lr_ep = lr * 0.5 * (1 + np.cos(np.pi * ep / epochs))      # cosine decay
+        for b in range(nb):
+            idx = perm[b * batch:(b + 1) * batch]
+            X = ds.X.index_select(0, idx)
+            T = ds.T.index_select(0, idx)
+            net.gradients(X, T, loss)
+            net.adam(lr_ep)
+            if b % 50 == 0 or b == nb - 1:
+                acc = loss.item()
+        hist.append(acc)
+        if log_every and ep % log_every == 0:
+            print(f"epoch {ep} loss {acc:.4e}")
+    return hist
+
+
+@dataclass
+class Proposal:
+    x: object
+    used: bool
+    F0: float
+    F: float
+    min_detA: float
+
+
+def propose(net: MLP, m: mg.Mesh, ctx: tm.Context, x0, fixed_dev) -> Proposal:
+    """Proposal with fallback: kept only if min det A > 0 and F decreases."""
+    import torch
+    S = m.nelem
+    Sp = (S + 63) // 64 * 64
+    X = torch.zeros((Sp, net.ld), dtype=torch.int16, device=x0.device)
+    features(m, x0, net.ld, out=X[:S])
+    Y = net.forward(X)
+    xp = apply(m, x0, fixed_dev, Y[:S].contiguous())
+    _, F0, _ = ctx.energy(x0)
+    rc, F, md = ctx.energy(xp)
+    ok = rc == tm.OK and md > 0 and F < F0
+    return Proposal(xp if ok else x0, ok, F0, F, md)

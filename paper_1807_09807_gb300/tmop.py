@@ -46,7 +46,8 @@ class _Targets(C.Structure):
 class NewtonOpts(C.Structure):
     _fields_ = [("max_newton", C.c_int), ("rtol", C.c_double), ("krylov", C.c_int), ("krylov_rtol", C.c_double),
                 ("krylov_maxit", C.c_int), ("alpha_shrink", C.c_double), ("max_halvings", C.c_int),
-                ("f_factor", C.c_double), ("g_factor", C.c_double)]
+                ("f_factor", C.c_double), ("g_factor", C.c_double), ("atol", C.c_double),
+                ("matrix_free", C.c_int)]
 
 
 class NewtonReport(C.Structure):
@@ -75,6 +76,8 @@ _SIGNATURES = {
     "tmop_krylov_solve": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(NewtonOpts),
                            C.POINTER(C.c_int), C.c_void_p], C.c_int),
     "tmop_element_min_detA": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "tmop_linearize": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "tmop_hess_apply_pa": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_sizes": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
                    C.c_int),
     "tmop_energy_noalloc": ([C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(_Quad), C.c_int, C.POINTER(_Targets),
@@ -235,6 +238,24 @@ class Context:
         rc = load().tmop_hess_apply(self._h, _ptr(x), _ptr(v), _ptr(y), _stream())
         if rc != OK:
             raise TmopError(rc, "tmop_hess_apply")
+        return y
+
+    def linearize(self, x):
+        """Store the per-point Hessians at x (partial assembly)."""
+        _check_vec(x, self.shape, "x")
+        rc = load().tmop_linearize(self._h, _ptr(x), _stream())
+        if rc != OK:
+            raise TmopError(rc, "tmop_linearize")
+
+    def hess_apply_pa(self, v, out=None):
+        """y = H v with the Hessians of the last linearize()."""
+        import torch
+        _check_vec(v, self.shape, "v")
+        y = torch.empty_like(v) if out is None else out
+        _check_vec(y, self.shape, "y")
+        rc = load().tmop_hess_apply_pa(self._h, _ptr(v), _ptr(y), _stream())
+        if rc != OK:
+            raise TmopError(rc, "tmop_hess_apply_pa")
         return y
 
     def element_min_detA(self, x, out=None):

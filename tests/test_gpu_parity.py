@@ -203,6 +203,48 @@ def test_deterministic_energy(tm):
     assert len(vals) == 1
 
 
+# ---------------------------------------------------------------- partial assembly
+@pytest.mark.parametrize("name,kw,metric", [("c1", dict(nx=5), 2), ("c1", dict(nx=4), 77), ("c2", dict(nx=6), 9),
+                                            ("c3", dict(nx=3), 303), ("c3", dict(nx=3), 302), ("c4", dict(nx=2), 303),
+                                            ("c3", dict(nx=2, order=4, nq=6), 303)])
+def test_partial_assembly_matches_oracle(tm, name, kw, metric):
+    m = make(name, 2, **kw)
+    scale = 0.3 if metric in (7, 9, 77) else None
+    ctx = tm.Context.from_mesh(m, metric=metric, target_scale=scale)
+    orc = orc_for(m, metric=metric, W=None if scale is None else np.eye(m.dim) * scale)
+    x = dev(m.x)
+    ctx.linearize(x)
+    for seed in range(2):
+        v = np.random.default_rng(seed).standard_normal(m.x.shape)
+        y = host(ctx.hess_apply_pa(dev(v)))
+        yo = orc.hess_apply(m.x, v)
+        assert rel(y, yo) <= RTOL, rel(y, yo)
+        assert np.all(y[m.fixed == 1] == 0.0)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_partial_assembly_general_targets_and_fp32(tm, dim):
+    rng = np.random.default_rng(11)
+    m = make("c1" if dim == 2 else "c3", 5, nx=3 if dim == 2 else 2)
+    Wq = (np.eye(dim) + 0.15 * rng.standard_normal((m.nelem, m.Q, dim, dim))) / 6
+    Wq[np.linalg.det(Wq) < 0, :, 0] *= -1
+    v = rng.standard_normal(m.x.shape)
+    yo = orc_for(m, Wqp=Wq).hess_apply(m.x, v)
+    ctx = tm.Context.from_mesh(m, W_per_qp=Wq)
+    ctx.linearize(dev(m.x))
+    assert rel(host(ctx.hess_apply_pa(dev(v))), yo) <= RTOL
+    c32 = tm.Context.from_mesh(m, W_per_qp=Wq, precision=tm.FP32_MIXED)
+    c32.linearize(dev(m.x))
+    assert rel(host(c32.hess_apply_pa(dev(v))), yo) <= 1e-5
+
+
+def test_partial_assembly_requires_linearize(tm):
+    m = make("c1", 1, nx=2)
+    ctx = tm.Context.from_mesh(m)
+    with pytest.raises(tm.TmopError):
+        ctx.hess_apply_pa(dev(m.x))
+
+
 # ---------------------------------------------------------------- solvers
 @pytest.mark.parametrize("krylov", ["minres", "cg"])
 def test_krylov_matches_oracle(tm, krylov):
@@ -220,29 +262,37 @@ def test_krylov_matches_oracle(tm, krylov):
 
 @pytest.mark.parametrize("metric,scale", [(2, None), (7, 1.0 / 8)])
 def test_newton_matches_oracle_history(tm, metric, scale):
-    """Section 3.4 Newton on 8x8 order-2: same accepted steps and F history as
-    the oracle (to 1e-9 relative, Krylov rounding), convergence to the
-    uniform grid (F* = 0), det A > 0 throughout."""
+    """Section 3.4 Newton on 8x8 order-2: the same accepted step lengths and
+    F history as the oracle while F is above rounding level (F > 1e-8 F0;
+    below that the acceptance tests compare rounding noise, F* = 0 here), then
+    convergence to the uniform grid (F* = 0) with det A > 0 throughout."""
     m = make("c1", 1)
     ctx = tm.Context.from_mesh(m, metric=metric, target_scale=scale)
     orc = orc_for(m, metric=metric, W=None if scale is None else np.eye(2) * scale)
     rco, xo, hist = orc.newton(m.x, max_newton=20)
-    x = dev(m.x)
-    Fs = [ctx.energy(x)[1]]
-    for it in range(len(hist) - 1):
-        r = ctx.newton_step(x, max_newton=20)
-        assert r.status == tm.OK
-        assert r.report["alpha"] == hist[it + 1, 3]
-        Fs.append(r.report["F"])
-        assert r.report["min_detA"] > 0
-    Fs = np.array(Fs)
     F0 = hist[0, 0]
-    for k in range(len(Fs)):
-        assert abs(Fs[k] - hist[k, 0]) <= 1e-9 * hist[k, 0] + 1e-12 * F0, (k, Fs[k], hist[k, 0])
-    assert np.abs(host(x) - m.x_ideal).max() < 1e-11
+    x = dev(m.x)
+    assert abs(ctx.energy(x)[1] - F0) <= RTOL * F0
+    compared = 0
+    for it in range(len(hist) - 1):
+        if hist[it, 0] <= 1e-8 * F0:
+            break
+        r = ctx.newton_step(x, max_newton=20)
+        assert r.status == tm.OK and r.report["min_detA"] > 0
+        assert r.report["alpha"] == hist[it + 1, 3]
+        Fk, Fo = r.report["F"], hist[it + 1, 0]
+        assert abs(Fk - Fo) <= 1e-9 * Fo + 1e-12 * F0, (it, Fk, Fo)
+        compared += 1
+    assert compared >= 3
     x2 = dev(m.x)
     res = ctx.newton_solve(x2, max_newton=20)
-    assert res.status == tm.OK and res.report["F"] <= 1e-12 * F0
+    assert res.status == tm.OK and res.report["F"] <= 1e-12 * F0 and res.report["min_detA"] > 0
+    assert np.abs(host(x2) - m.x_ideal).max() < 1e-11
+    # the matrix-free Krylov operator converges to the same mesh
+    x3 = dev(m.x)
+    res3 = ctx.newton_solve(x3, max_newton=20, matrix_free=1)
+    assert res3.status == tm.OK
+    assert np.abs(host(x3) - host(x2)).max() < 1e-11
 
 
 def test_newton_strict_monotone_and_barrier(tm):
