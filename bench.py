@@ -15,7 +15,9 @@ MINRES inner solves) for the plain FP64 form and the FP32-bulk form.
 
 --impl reference times the plain FP64 CPU oracle (the reference for this
 path) on a bounded sample of the same workload, on the host cores.
---kernels-only runs warm-up plus K steps and nothing else (for profilers).
+--kernels-only runs warm-up plus K steps and nothing else (for profilers);
+with --profile pa it runs one linearisation and K+1 partially assembled
+Hessian actions instead.
 """
 from __future__ import annotations
 
@@ -295,9 +297,16 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
     if args.kernels_only:
-        for _ in range(args.steps):
-            flush.fill_(1.0)
-            step()
+        if args.profile == "pa":
+            # the partially assembled product alone: one linearisation, then K products
+            ctx.linearize(x)
+            for _ in range(args.steps + 1):
+                flush.fill_(1.0)
+                ctx.hess_apply_pa(v, out=y)
+        else:
+            for _ in range(args.steps):
+                flush.fill_(1.0)
+                step()
         torch.cuda.synchronize()
         return 0
 
@@ -559,6 +568,9 @@ def main():
     ap.add_argument("--train-epochs", type=int, default=15)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels-only", action="store_true")
+    ap.add_argument("--profile", choices=["step", "pa"], default="step",
+                    help="with --kernels-only: the timed step (gradient + Hessian action) or the partially "
+                         "assembled Hessian action alone")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if not args.kernels_only else args.warmup
     if args.impl == "reference":
