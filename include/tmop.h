@@ -49,6 +49,7 @@ enum { TMOP_GL = 0, TMOP_GLL = 1 };                                     /* quadr
 enum { TMOP_W_IDENTITY = 0, TMOP_W_CONST = 1, TMOP_W_SCALED = 2, TMOP_W_PER_QP = 3 }; /* target kind */
 enum { TMOP_FP64 = 0, TMOP_FP32_MIXED = 1, TMOP_FP32_BULK = 2 };        /* precision form */
 enum { TMOP_KRYLOV_MINRES = 0, TMOP_KRYLOV_CG = 1 };                     /* inner solver */
+enum { TMOP_WT_EQUAL_SIZE = 0, TMOP_WT_LOCAL_SIZE = 1, TMOP_WT_INITIAL = 2 }; /* targets from positions */
 
 typedef struct tmop_ctx tmop_ctx; /* opaque; owns device tables and workspace */
 
@@ -91,8 +92,10 @@ typedef struct {
  * targets, uploads everything and allocates the workspace (reduction
  * partials, Krylov vectors).
  *   order     1..4 (k of Q_k)
- *   metric_id 2D: 1, 2, 7, 9, 14, 77; 3D: 1, 14, 302, 303 (Table 3.1;
- *             mu302 = |T|^2 |T^-1|^2 / 9 - 1 is not in the paper)
+ *   metric_id 2D: 1, 2, 7, 9, 14, 77, 98; 3D: 1, 14, 98, 302, 303
+ *             (Table 3.1; mu98 = |T - I|^2 / det T is the replication
+ *             metric of Section 4.3.2; mu302 = |T|^2 |T^-1|^2 / 9 - 1 is not
+ *             in the paper)
  *   precision TMOP_FP64: every kernel in FP64.
  *             TMOP_FP32_MIXED: the Hessian action (the Krylov operator) in
  *             FP32; objective, det A, gradient, dot products, line search
@@ -147,6 +150,11 @@ int tmop_linearize(tmop_ctx* ctx, const double* x, void* stream);
  * TMOP_ERR_ARG if the context holds no linearisation. Asynchronous. */
 int tmop_hess_apply_pa(tmop_ctx* ctx, const double* v, double* y, void* stream);
 
+/* Diagonal of the Hessian stored by the last tmop_linearize (including the
+ * restricted-movement term), 1 at fixed dofs: out DEVICE [dim][nnode] FP64.
+ * TMOP_ERR_ARG if the context holds no linearisation. Asynchronous. */
+int tmop_hessian_diagonal(tmop_ctx* ctx, double* out, void* stream);
+
 /* Newton options (Section 3.4 and Section 5). Zero-initialised fields take
  * the defaults in brackets. */
 typedef struct {
@@ -163,6 +171,8 @@ typedef struct {
                             compare runs that start from different iterates) */
   int matrix_free;       /* [0] 0: the Krylov operator is partially assembled once per Newton
                             step (tmop_linearize), 1: recomputed from x at every product */
+  int precond;           /* [0] 0: none (the paper's standard MINRES), 1: Jacobi, the diagonal of the
+                            partially assembled Hessian (MINRES only; needs matrix_free = 0) */
 } tmop_newton_opts;
 
 typedef struct {
@@ -222,8 +232,8 @@ int tmop_element_min_detA(tmop_ctx* ctx, const double* x, double* out, void* str
  * Scratch: the per-block partial sums live in one file-scope device array of
  * 2 x 32768 doubles (512 KiB) that every GPU loading this library keeps until
  * the process exits. The launch uses one block per group of elements in
- * flight (4 for most kernels), so the limit is about 131 000 elements (at
- * least 32768 x the kernel's warps per block); larger grids return
+ * flight (4 to 8 per block, set by the kernel's shared memory), so the limit
+ * is 32768 x that many elements (131 072 to 262 144); larger grids return
  * TMOP_ERR_CAPACITY before anything is launched. The array is shared by every
  * call in the process and keeps the last call's contents (each call overwrites
  * the partials it reads, so nothing has to start at zero); calls that overlap
@@ -235,6 +245,48 @@ int tmop_element_min_detA(tmop_ctx* ctx, const double* x, double* out, void* str
  * it launches; make that first call before any stream capture. */
 int tmop_energy_noalloc(int dim, int order, const int structured[3], const tmop_quad* quad, int metric_id,
                         const tmop_targets* targets, const double* x, double* F, double* min_detA, void* stream);
+
+/* Composite metric (Section 4.2, eq. (4.1)): adds a second term so that the
+ * objective becomes sum_E sum_q w_q [ det W mu(A W^-1) + eta_q det W2 mu2(A W2^-1) ]
+ * in every call (energy, gradient, Hessian actions, linearisation, Newton).
+ * metric2 as for tmop_setup (0 removes the term); W2: HOST [dim][dim]
+ * constant target, det W2 > 0; eta2: HOST [nelem][Q] per-point weights
+ * (copied; held fixed during the optimisation), or NULL for 1 everywhere.
+ * Invalidates a stored linearisation. Errors: TMOP_ERR_ARG, TMOP_ERR_CUDA. */
+int tmop_set_composite(tmop_ctx* ctx, int metric2, const double* W2, const double* eta2);
+
+/* Restricted node movement (Section 4.3.1, eq. (4.2)): every call then
+ * evaluates F + sum_E int_{E_t} delta |x - x_init|^2 dx_t (weights w_q det W),
+ * with the matching gradient and Hessian-action terms (FP64, whatever the
+ * precision form). delta >= 0 (0 removes the term); x_init: DEVICE
+ * [dim][nnode] FP64, copied on the stream. Errors: TMOP_ERR_ARG,
+ * TMOP_ERR_CUDA. */
+int tmop_set_restricted_movement(tmop_ctx* ctx, double delta, const double* x_init, void* stream);
+
+/* Jacobians A(x_q) = sum_i x_i grad phi_i(xi_q) (eq. (2.2)) at every
+ * quadrature point: x DEVICE [dim][nnode], J DEVICE [nelem][Q][dim][dim]
+ * row-major (J[e][q][a][b] = d x_a / d xi_b), points ordered as the
+ * quadrature (first direction fastest). Asynchronous on the stream. Errors:
+ * TMOP_ERR_ARG, TMOP_ERR_CUDA. */
+int tmop_jacobians(tmop_ctx* ctx, const double* x, double* J, void* stream);
+
+/* Replace the context's targets by a set built from the positions x0
+ * (DEVICE [dim][nnode]):
+ *   TMOP_WT_EQUAL_SIZE  W2 = alpha^{1/d} I, alpha = (1/N_E) sum_E sum_q w_q
+ *                       det A(x0), the quadrature of eq. (3.1) (constant)
+ *   TMOP_WT_LOCAL_SIZE  W3 = det(A(x0))^{1/d} I at every point (Section 3.1)
+ *   TMOP_WT_INITIAL     W0 = A(x0) at every point: the target of the
+ *                       replication metric mu98 in the second restricted
+ *                       node movement algorithm (Section 4.3.2), where
+ *                       (1 - gamma) mu98(A W0^-1) + gamma mu(A W^-1) is a
+ *                       context with metric 98 and these targets plus
+ *                       tmop_set_composite(mu, W, eta2 = gamma / (1 - gamma))
+ *                       (the same objective times 1 / (1 - gamma)).
+ * Allocates temporaries, synchronises the stream, invalidates a stored
+ * linearisation. Errors: TMOP_ERR_INVERTED if det A(x0) <= 0 at some point
+ * (per-point kinds) or the measure is not positive (targets unchanged),
+ * TMOP_ERR_ARG, TMOP_ERR_CUDA. */
+int tmop_set_targets_from_positions(tmop_ctx* ctx, int kind, const double* x0, void* stream);
 
 /* Sizes of a context: Q (points per element), ndof = dim * nnode. */
 int tmop_sizes(const tmop_ctx* ctx, int* dim, int* nelem, int* nnode, int* Q);

@@ -51,6 +51,8 @@ class _Problem(C.Structure):
         ("elem_nodes", C.c_void_p), ("fixed", C.c_void_p),
         ("quad_kind", C.c_int), ("nq", C.c_int), ("metric", C.c_int),
         ("wkind", C.c_int), ("W", C.c_void_p),
+        ("metric2", C.c_int), ("W2", C.c_void_p), ("eta2", C.c_void_p),
+        ("delta", C.c_double), ("x_init", C.c_void_p),
     ]
 
 
@@ -138,6 +140,11 @@ class Problem:
     quad_kind: int = GL
     wkind: int = W_IDENTITY
     W: np.ndarray | None = None  # [d,d] (W_CONST) or [nelem, Q, d, d] (W_PER_QP)
+    metric2: int = 0             # composite second term (eq. (4.1)); 0 = none
+    W2: np.ndarray | None = None  # [d,d] constant target of the second term
+    eta2: np.ndarray | None = None  # [nelem, Q] weights of the second term (None = 1)
+    delta: float = 0.0           # restricted movement weight (eq. (4.2)); 0 = none
+    x_init: np.ndarray | None = None  # [dim, nnode] reference positions of that term
 
     def __post_init__(self):
         self.elem_nodes = np.ascontiguousarray(self.elem_nodes, dtype=np.int32)
@@ -145,9 +152,16 @@ class Problem:
             self.fixed = np.ascontiguousarray(self.fixed, dtype=np.uint8)
         if self.W is not None:
             self.W = np.ascontiguousarray(self.W, dtype=np.float64)
+        if self.metric2:
+            self.W2 = np.ascontiguousarray(np.eye(self.dim) if self.W2 is None else self.W2, dtype=np.float64)
+        if self.eta2 is not None:
+            self.eta2 = np.ascontiguousarray(self.eta2, dtype=np.float64)
+        if self.delta:
+            self.x_init = np.ascontiguousarray(self.x_init, dtype=np.float64)
         self._c = _Problem(self.dim, self.order, self.elem_nodes.shape[0], self.nnode,
                            _ptr(self.elem_nodes), _ptr(self.fixed), self.quad_kind, self.nq,
-                           self.metric, self.wkind, _ptr(self.W))
+                           self.metric, self.wkind, _ptr(self.W), self.metric2, _ptr(self.W2), _ptr(self.eta2),
+                           float(self.delta), _ptr(self.x_init))
 
     @property
     def nelem(self):

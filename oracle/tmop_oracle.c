@@ -46,6 +46,15 @@ typedef struct {
   int metric;                  /* 1, 2, 7, 9, 14, 77 (2D); 1, 14, 302, 303 (3D) */
   int wkind;                   /* ORC_W_* */
   const double* W;             /* CONST: [d][d] row-major; PER_QP: [nelem][Q][d][d] */
+  /* optional second term of a composite metric (Section 4.2, eq. (4.1)):
+   * mu = mu_metric(A W^-1) + eta_q mu_metric2(A W2^-1); metric2 = 0: none */
+  int metric2;
+  const double* W2;            /* [d][d] constant target of the second term */
+  const double* eta2;          /* [nelem][Q] weights of the second term, or NULL for 1 */
+  /* restricted node movement (Section 4.3.1, eq. (4.2)): adds
+   * sum_E int_{E_t} delta |x - x_init|^2 dx_t; delta = 0: none */
+  double delta;
+  const double* x_init;        /* [dim][nnode] */
 } orc_problem;
 
 /* ------------------------------------------------------------------------ */
@@ -214,7 +223,7 @@ static int inverse_d(int d, const double* M, double* Minv) {
 int orc_metric(int id, int d, const double* T, const double* dT, double* mu, double* P, double* dP) {
   const int dd = d * d;
   int ok2 = (id == 2 || id == 7 || id == 9 || id == 77), ok3 = (id == 302 || id == 303);
-  if (!(id == 1 || id == 14 || (d == 2 && ok2) || (d == 3 && ok3))) return ORC_ERR_ARG;
+  if (!(id == 1 || id == 14 || id == 98 || (d == 2 && ok2) || (d == 3 && ok3))) return ORC_ERR_ARG;
   double tau = det_d(d, T);
   double C[9], dC[9];
   double I1 = ddot_m(d, T, T);
@@ -247,6 +256,25 @@ int orc_metric(int id, int d, const double* T, const double* dT, double* mu, dou
   }
   if (!(tau > 0.0)) { *mu = INFINITY; return ORC_ERR_INVERTED; }
   switch (id) {
+    case 98: { /* mu98 = |T - I|^2 / tau, the replication barrier metric (Section 4.3.2), any d */
+      double E[9], s = 0.0;
+      for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+          E[i * d + j] = T[i * d + j] - (i == j ? 1.0 : 0.0);
+          s += E[i * d + j] * E[i * d + j];
+        }
+      *mu = s / tau;
+      /* P = (2 (T - I) - mu C) / tau */
+      double Pl[9];
+      for (int i = 0; i < dd; ++i) Pl[i] = (2.0 * E[i] - *mu * C[i]) / tau;
+      if (P) for (int i = 0; i < dd; ++i) P[i] = Pl[i];
+      if (dP) {
+        /* dP = (2 dT - dmu C - mu dC - P dtau) / tau, dmu = P : dT */
+        double dmu = ddot_m(d, Pl, dT);
+        for (int i = 0; i < dd; ++i) dP[i] = (2.0 * dT[i] - dmu * C[i] - *mu * dC[i] - Pl[i] * dtau) / tau;
+      }
+      return ORC_OK;
+    }
     case 2: { /* mu2 = |T|^2 / (2 tau) - 1, 2D shape */
       if (d != 2) return ORC_ERR_ARG;
       *mu = I1 / (2.0 * tau) - 1.0;
@@ -358,6 +386,7 @@ typedef struct {
   double gll[ORC_MAXN];
   double* w;      /* [Q] tensor weights */
   double* gradphi; /* [Q][ndof_e][d]: reference gradient of every local basis function */
+  double* phi;     /* [Q][ndof_e]: value of every local basis function */
 } orc_tables;
 
 static int ipow(int b, int e) { int r = 1; while (e--) r *= b; return r; }
@@ -377,6 +406,7 @@ static int tables_init(const orc_problem* p, orc_tables* t) {
   t->Q = ipow(t->nq, t->d);
   t->w = (double*)malloc(sizeof(double) * t->Q);
   t->gradphi = (double*)malloc(sizeof(double) * t->Q * t->ndof_e * t->d);
+  t->phi = (double*)malloc(sizeof(double) * t->Q * t->ndof_e);
   double phi[ORC_MAXQ][ORC_MAXN], dphi[ORC_MAXQ][ORC_MAXN];
   for (int a = 0; a < t->nq; ++a) orc_lagrange(t->n, t->gll, t->qp[a], phi[a], dphi[a]);
   for (int q = 0; q < t->Q; ++q) {
@@ -386,6 +416,9 @@ static int tables_init(const orc_problem* p, orc_tables* t) {
     t->w[q] = wq;
     for (int i = 0; i < t->ndof_e; ++i) {
       int ii[3] = {i % t->n, (i / t->n) % t->n, i / (t->n * t->n)};
+      double v = 1.0;
+      for (int c = 0; c < t->d; ++c) v *= phi[qi[c]][ii[c]];
+      t->phi[(size_t)q * t->ndof_e + i] = v;
       for (int b = 0; b < t->d; ++b) {
         /* d phi_i / d xi_b = phi'(xi_b) * prod_{c != b} phi(xi_c) */
         double g = 1.0;
@@ -397,7 +430,7 @@ static int tables_init(const orc_problem* p, orc_tables* t) {
   return ORC_OK;
 }
 
-static void tables_free(orc_tables* t) { free(t->w); free(t->gradphi); }
+static void tables_free(orc_tables* t) { free(t->w); free(t->gradphi); free(t->phi); }
 
 /* Target at (element, qp): W^{-1} and det W (Section 3.1; det W > 0 required). */
 static int target_at(const orc_problem* p, int e, int q, int Q, double* Winv, double* detW) {
@@ -487,6 +520,30 @@ int orc_energy(const orc_problem* p, const double* x, const int32_t* elems, int 
       if (mrc == ORC_ERR_ARG) { tables_free(&t); return ORC_ERR_ARG; }
       if (mrc == ORC_ERR_INVERTED) { barrier_hit = 1; continue; }
       kadd(&acc, t.w[q] * detW * mu);
+      if (p->metric2) {  /* eq. (4.1): second term with its own target and weight */
+        double W2inv[9], detW2, T2[9], mu2;
+        if (inverse_d(d, p->W2, W2inv) != ORC_OK) { tables_free(&t); return ORC_ERR_ARG; }
+        detW2 = det_d(d, p->W2);
+        matmul_d(d, A, W2inv, T2);
+        int m2 = orc_metric(p->metric2, d, T2, NULL, &mu2, NULL, NULL);
+        if (m2 == ORC_ERR_ARG) { tables_free(&t); return ORC_ERR_ARG; }
+        if (m2 == ORC_ERR_INVERTED) { barrier_hit = 1; continue; }
+        const double eta = p->eta2 ? p->eta2[(size_t)e * t.Q + q] : 1.0;
+        kadd(&acc, t.w[q] * detW2 * eta * mu2);
+      }
+      if (p->delta != 0.0) {  /* eq. (4.2): delta |x - x_init|^2 at the point */
+        const int32_t* en = p->elem_nodes + (size_t)e * t.ndof_e;
+        double u2 = 0.0;
+        for (int a = 0; a < d; ++a) {
+          double u = 0.0;
+          for (int i = 0; i < t.ndof_e; ++i) {
+            const size_t dof = (size_t)a * p->nnode + en[i];
+            u += (x[dof] - p->x_init[dof]) * t.phi[(size_t)q * t.ndof_e + i];
+          }
+          u2 += u * u;
+        }
+        kadd(&acc, t.w[q] * detW * p->delta * u2);
+      }
     }
   }
   *F = barrier_hit ? INFINITY : acc.s + acc.c;
@@ -542,6 +599,43 @@ static int nodal_op(const orc_problem* p, const double* x, const double* v, cons
           double s = 0.0;
           for (int b = 0; b < d; ++b) s += G[a * d + b] * gp[b];
           out[(size_t)a * p->nnode + en[i]] += wdet * s;
+        }
+      }
+      if (p->metric2) {  /* eq. (4.1): the second term, same formulas with W2 and eta */
+        double W2inv[9], W2invT[9], T2[9], dT2[9], P2[9], dP2[9], G2[9], mu2;
+        if (inverse_d(d, p->W2, W2inv) != ORC_OK) { tables_free(&t); return ORC_ERR_ARG; }
+        const double detW2 = det_d(d, p->W2);
+        matmul_d(d, A, W2inv, T2);
+        if (v) matmul_d(d, dA, W2inv, dT2);
+        int m2 = orc_metric(p->metric2, d, T2, v ? dT2 : NULL, &mu2, v ? NULL : P2, v ? dP2 : NULL);
+        if (m2 == ORC_ERR_ARG) { tables_free(&t); return ORC_ERR_ARG; }
+        if (m2 == ORC_ERR_INVERTED) { status = ORC_ERR_INVERTED; continue; }
+        const double eta = p->eta2 ? p->eta2[(size_t)e * t.Q + q] : 1.0;
+        transpose_d(d, W2inv, W2invT);
+        matmul_d(d, v ? dP2 : P2, W2invT, G2);
+        const double wdet2 = t.w[q] * detW2 * eta;
+        for (int i = 0; i < t.ndof_e; ++i) {
+          const double* gp = t.gradphi + ((size_t)q * t.ndof_e + i) * d;
+          for (int a = 0; a < d; ++a) {
+            double s = 0.0;
+            for (int b = 0; b < d; ++b) s += G2[a * d + b] * gp[b];
+            out[(size_t)a * p->nnode + en[i]] += wdet2 * s;
+          }
+        }
+      }
+      if (p->delta != 0.0) {
+        /* eq. (4.2): gradient 2 delta (x - x_init)(x_q) phi_i, Hessian action
+         * 2 delta v(x_q) phi_i (a mass matrix) */
+        const double* ph = t.phi + (size_t)q * t.ndof_e;
+        for (int a = 0; a < d; ++a) {
+          double u = 0.0;
+          for (int i = 0; i < t.ndof_e; ++i) {
+            const size_t dof = (size_t)a * p->nnode + en[i];
+            if (v) u += ((p->fixed && p->fixed[dof]) ? 0.0 : v[dof]) * ph[i];
+            else u += (x[dof] - p->x_init[dof]) * ph[i];
+          }
+          const double c = 2.0 * p->delta * wdet * u;
+          for (int i = 0; i < t.ndof_e; ++i) out[(size_t)a * p->nnode + en[i]] += c * ph[i];
         }
       }
     }

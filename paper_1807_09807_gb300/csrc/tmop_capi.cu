@@ -14,7 +14,10 @@
 #include <vector>
 
 #include "../../include/tmop.h"
+#include "tmop_diag.h"
+#include "tmop_targets.h"
 #include "tmop_kparams.h"
+#include "tmop_mass.h"
 #include "tmop_vec.h"
 
 namespace tmop {
@@ -182,6 +185,14 @@ struct tmop_ctx {
   int nvec = 0;
   void* d_pa = nullptr;       // packed per-point Hessians (partial assembly), allocated on first use
   bool pa_valid = false;      // d_pa holds the linearisation of some x
+  double* d_eta2 = nullptr;   // per-point weights of the composite second term
+  double delta = 0.0;         // restricted-movement weight (0: term off)
+  double* d_x_init = nullptr; // its reference positions [d][nnode]
+  mass_launch_fn mass[3] = {nullptr, nullptr, nullptr};
+  int mass_grid = 1;
+  double* d_diag = nullptr;   // Hessian diagonal [d][nnode] and its floored inverse [d][nnode]
+  cudaStream_t cap = nullptr; // internal stream for capturing Krylov iterations into a graph
+  cudaEvent_t ev = nullptr;   // orders the internal stream after / before the caller's stream
 };
 
 namespace {
@@ -194,6 +205,39 @@ constexpr int kNumVec = 10;
     cudaError_t e_ = (call);                        \
     if (e_ != cudaSuccess) return TMOP_ERR_CUDA;    \
   } while (0)
+
+MassParams mass_params(const tmop_ctx* c) {
+  MassParams mp;
+  memset(&mp, 0, sizeof(mp));
+  const KParams& b = c->base;
+  mp.dim = b.dim; mp.nelem = b.nelem; mp.nnode = b.nnode;
+  mp.sx = b.sx; mp.sy = b.sy; mp.sz = b.sz;
+  mp.elem_nodes = b.elem_nodes;
+  mp.fixed = b.fixed;
+  mp.x0 = c->d_x_init;
+  memcpy(mp.B, b.B, sizeof(mp.B));
+  memcpy(mp.w1, b.w1, sizeof(mp.w1));
+  mp.delta = c->delta;
+  mp.detW = b.detW;
+  mp.detW_qp = b.wkind == WK_PER_QP ? b.detW_qp : nullptr;
+  mp.part = c->d_part + 2 * kMaxRedBlocks;
+  return mp;
+}
+
+JacParams jac_params(const tmop_ctx* c, const double* x, double* J) {
+  JacParams jp;
+  memset(&jp, 0, sizeof(jp));
+  const KParams& b = c->base;
+  jp.dim = b.dim; jp.nelem = b.nelem; jp.nnode = b.nnode; jp.n = c->n; jp.q1 = c->nq;
+  jp.sx = b.sx; jp.sy = b.sy; jp.sz = b.sz;
+  jp.elem_nodes = b.elem_nodes;
+  jp.x = x;
+  jp.J = J;
+  memcpy(jp.B, b.B, sizeof(jp.B));
+  memcpy(jp.G, b.G, sizeof(jp.G));
+  memcpy(jp.w1, b.w1, sizeof(jp.w1));
+  return jp;
+}
 
 int launch_op(tmop_ctx* c, int op, const double* x, const double* v, double* y, double* elem_min,
               cudaStream_t s) {
@@ -208,6 +252,14 @@ int launch_op(tmop_ctx* c, int op, const double* x, const double* v, double* y, 
   if (op == OP_GRADIENT || op == OP_HESS || op == OP_HESS_PA)
     CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * c->ndof, s));
   if (c->ent[op]->launch(p, c->grid[op], s) != 0) return TMOP_ERR_CUDA;
+  if (c->delta != 0.0 && op != OP_ENERGY && op != OP_LINEARIZE) {
+    // restricted movement (eq. (4.2)): its gradient (from x) or Hessian action (from v)
+    MassParams mp = mass_params(c);
+    mp.x = x;
+    mp.v = v;
+    mp.y = y;
+    if (c->mass[op == OP_GRADIENT ? 1 : 2](mp, c->mass_grid, s) != 0) return TMOP_ERR_CUDA;
+  }
   return TMOP_OK;
 }
 
@@ -215,8 +267,15 @@ int launch_op(tmop_ctx* c, int op, const double* x, const double* v, double* y, 
 int energy_async(tmop_ctx* c, const double* x, cudaStream_t s, double* outF = nullptr, double* outMin = nullptr) {
   int rc = launch_op(c, OP_ENERGY, x, nullptr, nullptr, nullptr, s);
   if (rc) return rc;
-  if (energy_final(c->d_part, c->d_part + kMaxRedBlocks, c->grid[OP_ENERGY], outF ? outF : c->d_res,
-                   outMin ? outMin : c->d_res + 1, s))
+  const double* extra = nullptr;
+  if (c->delta != 0.0) {  // restricted movement: its own block partials of F
+    MassParams mp = mass_params(c);
+    mp.x = x;
+    if (c->mass[0](mp, c->mass_grid, s) != 0) return TMOP_ERR_CUDA;
+    extra = mp.part;
+  }
+  if (energy_final(c->d_part, c->d_part + kMaxRedBlocks, c->grid[OP_ENERGY], extra, c->mass_grid,
+                   outF ? outF : c->d_res, outMin ? outMin : c->d_res + 1, s))
     return TMOP_ERR_CUDA;
   return TMOP_OK;
 }
@@ -257,9 +316,9 @@ double* vec(tmop_ctx* c, int i) { return c->d_vec + (size_t)i * c->ndof; }
 // Store the per-point A-space Hessians of x (partial assembly).
 int linearize(tmop_ctx* c, const double* x, cudaStream_t s) {
   if (!c->d_pa) {
-    const size_t dd = (size_t)c->dim * c->dim, ns = dd * (dd + 1) / 2;
-    const size_t elt = c->precision == TMOP_FP64 ? sizeof(double) : sizeof(float);
-    CUDA_TRY(cudaMalloc(&c->d_pa, elt * ns * c->Q * (size_t)c->nelem));
+    const int elt = c->precision == TMOP_FP64 ? (int)sizeof(double) : (int)sizeof(float);
+    c->base.pa_stride = pa_stride_for(c->dim, c->Q, elt);
+    CUDA_TRY(cudaMalloc(&c->d_pa, (size_t)elt * c->base.pa_stride * (size_t)c->nelem));
   }
   c->pa_valid = false;
   int rc = launch_op(c, OP_LINEARIZE, x, nullptr, nullptr, nullptr, s);
@@ -288,6 +347,44 @@ tmop_newton_opts defaults(const tmop_ctx* c, const tmop_newton_opts* in) {
   return o;
 }
 
+// Diagonal of the stored linearisation (+ the restricted-movement mass term),
+// fixed dofs 1, into d_diag[0..ndof); with `inverse`, also the Jacobi
+// inverse 1 / max(|diag|, 1e-8 rms|diag|) into d_diag[ndof..2 ndof).
+int hessian_diagonal(tmop_ctx* c, bool inverse, cudaStream_t s) {
+  if (!c->pa_valid) return TMOP_ERR_ARG;
+  const int fp32 = c->precision != TMOP_FP64;
+  diag_launch_fn f = find_diag(c->dim, c->n, c->nq, fp32);
+  if (!f) return TMOP_ERR_ARG;
+  if (!c->d_diag) CUDA_TRY(cudaMalloc(&c->d_diag, sizeof(double) * 2 * c->ndof));
+  CUDA_TRY(cudaMemsetAsync(c->d_diag, 0, sizeof(double) * c->ndof, s));
+  DiagParams dp;
+  memset(&dp, 0, sizeof(dp));
+  const KParams& b = c->base;
+  dp.dim = b.dim; dp.nelem = b.nelem; dp.nnode = b.nnode; dp.sx = b.sx; dp.sy = b.sy; dp.sz = b.sz;
+  dp.elem_nodes = b.elem_nodes;
+  dp.pa = c->d_pa;
+  dp.pa_stride = b.pa_stride;
+  dp.diag = c->d_diag;
+  memcpy(dp.B, b.B, sizeof(dp.B));
+  memcpy(dp.G, b.G, sizeof(dp.G));
+  memcpy(dp.w1, b.w1, sizeof(dp.w1));
+  dp.delta = c->delta;
+  dp.detW = b.detW;
+  dp.detW_qp = b.wkind == WK_PER_QP ? b.detW_qp : nullptr;
+  if (f(dp, diag_grid(c->nelem), s) != 0) return TMOP_ERR_CUDA;
+  if (diag_finish(c->d_diag, b.fixed, c->ndof, s) != 0) return TMOP_ERR_CUDA;
+  if (inverse) {
+    double rms2;
+    if (dot(c->d_diag, c->d_diag, c->ndof, c->d_part, c->d_res + 2, s)) return TMOP_ERR_CUDA;
+    int rc = read_res(c, 2, 1, s);
+    if (rc) return rc;
+    rms2 = c->h_res[2] / (double)c->ndof;
+    const double floor_abs = 1e-8 * sqrt(rms2) + 1e-300;
+    if (diag_inverse(c->d_diag, c->d_diag + c->ndof, c->ndof, floor_abs, s) != 0) return TMOP_ERR_CUDA;
+  }
+  return TMOP_OK;
+}
+
 // Krylov solve H(x) p = b; returns iterations (negative if the cap was hit).
 int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_newton_opts& o, int* iters,
            cudaStream_t s) {
@@ -295,53 +392,103 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
   if (rc) return rc;
   // the Krylov operator: partially assembled at x (default) or recomputed from x
   const int hop = o.matrix_free ? OP_HESS : OP_HESS_PA;
+  if (o.precond && (hop != OP_HESS_PA || o.krylov == TMOP_KRYLOV_CG)) return TMOP_ERR_ARG;
   if (hop == OP_HESS_PA) {
     rc = linearize(c, x, s);
     if (rc) return rc;
   }
+  const double* minv = nullptr;
+  if (o.precond) {  // Jacobi: the diagonal of the linearisation just stored
+    rc = hessian_diagonal(c, true, s);
+    if (rc) return rc;
+    minv = c->d_diag + c->ndof;
+  }
   double* st = c->d_res + kResKrylov;
   double* part = c->d_part;
   const size_t n = c->ndof;
-  int it = 0;
-  bool done = false;
-  if (o.krylov == TMOP_KRYLOV_CG) {
-    double *r = vec(c, V_K0), *d = vec(c, V_K1), *Hd = vec(c, V_K2);
-    if (cg_init(b, r, d, p, st, part, n, s)) return TMOP_ERR_CUDA;
-    rc = read_res(c, kResKrylov, KS_COUNT, s);
-    if (rc) return rc;
-    const double r0 = c->h_res[kResKrylov + KS_BETA1];
-    done = !(r0 > 0.0);
-    while (!done && it < o.krylov_maxit) {
-      ++it;
-      rc = launch_op(c, hop, x, d, Hd, nullptr, s);
-      if (rc) return rc;
-      if (cg_after_hv(p, r, d, Hd, st, part, n, s)) return TMOP_ERR_CUDA;
-      rc = read_res(c, kResKrylov, KS_COUNT, s);
-      if (rc) return rc;
-      const double* h = c->h_res + kResKrylov;
-      if (h[KS_BREAKDOWN] != 0.0) break;
-      if (h[KS_RESID] <= o.krylov_rtol * r0) done = true;
-    }
+  // The device records convergence (KS_DONE, KS_CONV_IT) and freezes the
+  // iterate from then on (also at the iteration cap), so the host reads the
+  // state only every kCheck iterations: the result is the same as stopping at
+  // the converged iteration. The kCheck iterations are captured once into a
+  // CUDA graph on an internal stream and replayed (direct launches if capture
+  // is not possible).
+  constexpr int kCheck = 8;
+  const bool cg = o.krylov == TMOP_KRYLOV_CG;
+  double *k0 = vec(c, V_K0), *k1 = vec(c, V_K1), *k2 = vec(c, V_K2), *k3 = vec(c, V_K3), *k4 = vec(c, V_K4);
+  double* k5 = vec(c, V_K5);
+  if (cg) {
+    if (cg_init(b, k0, k1, p, st, part, n, o.krylov_rtol, o.krylov_maxit, s)) return TMOP_ERR_CUDA;
+  } else if (minv) {  // r1 = k0, r2 = k1, y = k2, v = k3, w = k4, wprev = k5
+    if (pminres_init(b, minv, k0, k1, k2, k4, k5, p, st, part, n, o.krylov_rtol, o.krylov_maxit, s))
+      return TMOP_ERR_CUDA;
   } else {
-    double *v = vec(c, V_K0), *vprev = vec(c, V_K1), *Av = vec(c, V_K2), *w = vec(c, V_K3),
-           *wprev = vec(c, V_K4);
-    if (minres_init(b, v, vprev, w, wprev, p, st, part, n, s)) return TMOP_ERR_CUDA;
-    rc = read_res(c, kResKrylov, KS_COUNT, s);
-    if (rc) return rc;
-    const double beta1 = c->h_res[kResKrylov + KS_BETA1];
-    done = !(beta1 > 0.0);
-    while (!done && it < o.krylov_maxit) {
-      ++it;
-      rc = launch_op(c, hop, x, v, Av, nullptr, s);
-      if (rc) return rc;
-      if (minres_after_hv(v, vprev, Av, w, wprev, p, st, part, n, s)) return TMOP_ERR_CUDA;
-      rc = read_res(c, kResKrylov, KS_COUNT, s);
-      if (rc) return rc;
-      const double* h = c->h_res + kResKrylov;
-      if (h[KS_RESID] <= o.krylov_rtol * beta1 || h[KS_BETA_NEXT] == 0.0) done = true;
-    }
+    if (minres_init(b, k0, k1, k3, k4, p, st, part, n, o.krylov_rtol, o.krylov_maxit, s)) return TMOP_ERR_CUDA;
   }
-  *iters = done ? it : -it;
+  auto enqueue_batch = [&](cudaStream_t q) -> int {
+    for (int j = 0; j < kCheck; ++j) {
+      int r;
+      if (minv) {
+        if (pminres_v(k3, k2, st, n, q)) return TMOP_ERR_CUDA;
+        r = launch_op(c, hop, x, k3, k2, nullptr, q);
+        if (r) return r;
+        if (pminres_after_hv(minv, k0, k1, k2, k3, k4, k5, p, st, part, n, q)) return TMOP_ERR_CUDA;
+        continue;
+      }
+      if (cg) {  // r = k0, d = k1, Hd = k2
+        r = launch_op(c, hop, x, k1, k2, nullptr, q);
+        if (r) return r;
+        if (cg_after_hv(p, k0, k1, k2, st, part, n, q)) return TMOP_ERR_CUDA;
+      } else {   // v = k0, vprev = k1, Av = k2, w = k3, wprev = k4
+        r = launch_op(c, hop, x, k0, k2, nullptr, q);
+        if (r) return r;
+        if (minres_after_hv(k0, k1, k2, k3, k4, p, st, part, n, q)) return TMOP_ERR_CUDA;
+      }
+    }
+    return TMOP_OK;
+  };
+  // try to capture one batch on the internal stream
+  cudaGraphExec_t exec = nullptr;
+  if (!c->cap) {
+    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) c->cap = nullptr;
+    if (cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess) c->ev = nullptr;
+  }
+  cudaStream_t q = s;
+  if (c->cap && c->ev && cudaEventRecord(c->ev, s) == cudaSuccess && cudaStreamWaitEvent(c->cap, c->ev, 0) == cudaSuccess) {
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const int r = enqueue_batch(c->cap);
+      const cudaError_t ec = cudaStreamEndCapture(c->cap, &graph);
+      if (r == TMOP_OK && ec == cudaSuccess && graph &&
+          cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+        exec = nullptr;
+      if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();  // a failed capture leaves no sticky error; fall back below
+    q = c->cap;
+  }
+  const double* h = c->h_res + kResKrylov;
+  rc = read_res(c, kResKrylov, KS_COUNT, q);
+  if (rc) { if (exec) cudaGraphExecDestroy(exec); return rc; }
+  int enqueued = 0;
+  while (h[KS_DONE] == 0.0 && enqueued < o.krylov_maxit) {
+    if (exec) {
+      if (cudaGraphLaunch(exec, q) != cudaSuccess) { cudaGraphExecDestroy(exec); return TMOP_ERR_CUDA; }
+    } else {
+      rc = enqueue_batch(q);
+      if (rc) return rc;
+    }
+    enqueued += kCheck;
+    rc = read_res(c, kResKrylov, KS_COUNT, q);
+    if (rc) { if (exec) cudaGraphExecDestroy(exec); return rc; }
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (q != s) {  // the caller's stream continues after the internal one
+    if (cudaEventRecord(c->ev, q) != cudaSuccess || cudaStreamWaitEvent(s, c->ev, 0) != cudaSuccess)
+      return TMOP_ERR_CUDA;
+  }
+  const int it = h[KS_DONE] != 0.0 ? (int)h[KS_CONV_IT] : (int)h[KS_ITER];
+  const bool converged = h[KS_DONE] != 0.0 && h[KS_BREAKDOWN] == 0.0 && h[KS_HITMAX] == 0.0;
+  *iters = converged ? it : -it;
   return TMOP_OK;
 }
 
@@ -425,7 +572,12 @@ void tmop_destroy(tmop_ctx* c) {
   cudaFree(c->d_res);
   cudaFree(c->d_vec);
   cudaFree(c->d_pa);
+  cudaFree(c->d_eta2);
+  cudaFree(c->d_x_init);
+  cudaFree(c->d_diag);
   cudaFreeHost(c->h_res);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->ev) cudaEventDestroy(c->ev);
   delete c;
 }
 
@@ -440,9 +592,7 @@ int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metr
   if (quad->kind != TMOP_GL && quad->kind != TMOP_GLL) return TMOP_ERR_ARG;
   if (quad->npts1d < 2 || quad->npts1d > kMaxQ) return TMOP_ERR_ARG;
   if (precision != TMOP_FP64 && precision != TMOP_FP32_MIXED && precision != TMOP_FP32_BULK) return TMOP_ERR_ARG;
-  const bool ok_metric = (metric_id == 1 || metric_id == 14) ||
-                         (d == 2 && (metric_id == 2 || metric_id == 7 || metric_id == 9 || metric_id == 77)) ||
-                         (d == 3 && (metric_id == 302 || metric_id == 303));
+  const bool ok_metric = metric_supported(d, metric_id);
   if (!ok_metric) return TMOP_ERR_ARG;
   const int n = order + 1, nq = quad->npts1d;
   const int ndof_e = d == 2 ? n * n : n * n * n;
@@ -571,8 +721,9 @@ int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metr
     else if (c->grid[op] > kMaxRedBlocks) c->grid[op] = kMaxRedBlocks;
   }
   if (rc == TMOP_OK) {
-    if (cudaMalloc(&c->d_part, sizeof(double) * 2 * kMaxRedBlocks) != cudaSuccess ||
+    if (cudaMalloc(&c->d_part, sizeof(double) * 3 * kMaxRedBlocks) != cudaSuccess ||
         cudaMalloc(&c->d_res, sizeof(double) * (kResKrylov + KS_COUNT)) != cudaSuccess ||
+        cudaMemset(c->d_res, 0, sizeof(double) * (kResKrylov + KS_COUNT)) != cudaSuccess ||
         cudaMallocHost(&c->h_res, sizeof(double) * (kResKrylov + KS_COUNT)) != cudaSuccess)
       rc = TMOP_ERR_CUDA;
   }
@@ -582,6 +733,126 @@ int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metr
   }
   *out = c;
   return TMOP_OK;
+}
+
+int tmop_set_composite(tmop_ctx* c, int metric2, const double* W2, const double* eta2) {
+  if (!c) return TMOP_ERR_ARG;
+  const int d = c->dim;
+  if (metric2 == 0) {
+    c->base.metric2 = 0;
+    c->base.eta2 = nullptr;
+    c->pa_valid = false;
+    return TMOP_OK;
+  }
+  const bool ok_metric = metric_supported(d, metric2);
+  if (!ok_metric || !W2) return TMOP_ERR_ARG;
+  double Wi[9], det;
+  if (!inv_h(d, W2, Wi, &det)) return TMOP_ERR_ARG;
+  if (eta2) {
+    const size_t cnt = (size_t)c->nelem * c->Q;
+    for (size_t i = 0; i < cnt; ++i)
+      if (!isfinite(eta2[i])) return TMOP_ERR_ARG;
+    if (!c->d_eta2 && cudaMalloc(&c->d_eta2, sizeof(double) * cnt) != cudaSuccess) return TMOP_ERR_CUDA;
+    if (cudaMemcpy(c->d_eta2, eta2, sizeof(double) * cnt, cudaMemcpyHostToDevice) != cudaSuccess)
+      return TMOP_ERR_CUDA;
+  }
+  c->base.metric2 = metric2;
+  memcpy(c->base.Winv2, Wi, sizeof(Wi));
+  c->base.detW2 = det;
+  c->base.eta2 = eta2 ? c->d_eta2 : nullptr;
+  c->pa_valid = false;
+  return TMOP_OK;
+}
+
+int tmop_set_restricted_movement(tmop_ctx* c, double delta, const double* x_init, void* stream) {
+  if (!c || !(delta >= 0.0) || !isfinite(delta) || (delta > 0.0 && !x_init)) return TMOP_ERR_ARG;
+  if (delta == 0.0) {
+    c->delta = 0.0;
+    return TMOP_OK;
+  }
+  for (int mode = 0; mode < 3; ++mode) {
+    c->mass[mode] = find_mass(c->dim, c->n, c->nq, mode);
+    if (!c->mass[mode]) return TMOP_ERR_ARG;
+  }
+  if (!c->d_x_init) CUDA_TRY(cudaMalloc(&c->d_x_init, sizeof(double) * c->ndof));
+  CUDA_TRY(cudaMemcpyAsync(c->d_x_init, x_init, sizeof(double) * c->ndof, cudaMemcpyDeviceToDevice,
+                           (cudaStream_t)stream));
+  c->mass_grid = mass_grid(c->nelem);
+  if (c->mass_grid > kMaxRedBlocks) c->mass_grid = kMaxRedBlocks;
+  c->delta = delta;
+  return TMOP_OK;
+}
+
+int tmop_jacobians(tmop_ctx* c, const double* x, double* J, void* stream) {
+  if (!c || !x || !J) return TMOP_ERR_ARG;
+  JacParams jp = jac_params(c, x, J);
+  return jacobians(jp, (cudaStream_t)stream) == 0 ? TMOP_OK : TMOP_ERR_CUDA;
+}
+
+int tmop_set_targets_from_positions(tmop_ctx* c, int kind, const double* x0, void* stream) {
+  if (!c || !x0) return TMOP_ERR_ARG;
+  if (kind != TMOP_WT_EQUAL_SIZE && kind != TMOP_WT_LOCAL_SIZE && kind != TMOP_WT_INITIAL) return TMOP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int d = c->dim, dd = d * d;
+  const size_t cnt = (size_t)c->nelem * c->Q;
+  double *J = nullptr, *Wi = nullptr, *dW = nullptr;
+  int* bad = nullptr;
+  int rc = TMOP_OK;
+  if (cudaMalloc(&J, sizeof(double) * cnt * dd) != cudaSuccess) return TMOP_ERR_CUDA;
+  JacParams jp = jac_params(c, x0, J);
+  if (jacobians(jp, s) != 0) rc = TMOP_ERR_CUDA;
+  if (rc == TMOP_OK && kind == TMOP_WT_EQUAL_SIZE) {
+    // W2 = alpha^{1/d} I, alpha = (mesh measure) / N_E (eq. (3.1))
+    if (mesh_measure(d, c->nq, J, (size_t)c->nelem, c->base.w1, c->d_res + 2, s) != 0) rc = TMOP_ERR_CUDA;
+    if (rc == TMOP_OK) rc = read_res(c, 2, 1, s);
+    const double alpha = rc == TMOP_OK ? c->h_res[2] / c->nelem : 0.0;
+    if (rc == TMOP_OK && !(alpha > 0.0 && isfinite(alpha))) rc = TMOP_ERR_INVERTED;
+    if (rc == TMOP_OK) {
+      const double scale = d == 2 ? sqrt(alpha) : cbrt(alpha);
+      for (int k = 0; k < 9; ++k) c->base.Winv[k] = 0.0;
+      for (int a = 0; a < d; ++a) c->base.Winv[a * d + a] = 1.0 / scale;
+      c->base.detW = alpha;
+      c->base.wkind = WK_CONST;
+      c->base.Winv_qp = nullptr;
+      c->base.detW_qp = nullptr;
+      cudaFree(c->d_Winv_qp);
+      cudaFree(c->d_detW_qp);
+      c->d_Winv_qp = c->d_detW_qp = nullptr;
+    }
+  } else if (rc == TMOP_OK) {
+    // per point: W0 = A(x0) (Section 4.3.2) or W3 = det(A(x0))^{1/d} I (Section 3.1)
+    if (cudaMalloc(&Wi, sizeof(double) * cnt * dd) != cudaSuccess || cudaMalloc(&dW, sizeof(double) * cnt) != cudaSuccess ||
+        cudaMalloc(&bad, sizeof(int)) != cudaSuccess || cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess)
+      rc = TMOP_ERR_CUDA;
+    if (rc == TMOP_OK &&
+        targets_from_jacobians(d, kind == TMOP_WT_INITIAL ? 0 : 1, J, cnt, Wi, dW, bad, s) != 0)
+      rc = TMOP_ERR_CUDA;
+    int h_bad = 0;
+    if (rc == TMOP_OK && (cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                          cudaStreamSynchronize(s) != cudaSuccess))
+      rc = TMOP_ERR_CUDA;
+    if (rc == TMOP_OK && h_bad > 0) rc = TMOP_ERR_INVERTED;
+    if (rc == TMOP_OK) {
+      cudaFree(c->d_Winv_qp);
+      cudaFree(c->d_detW_qp);
+      c->d_Winv_qp = Wi;
+      c->d_detW_qp = dW;
+      Wi = dW = nullptr;
+      for (int k = 0; k < 9; ++k) c->base.Winv[k] = 0.0;
+      for (int a = 0; a < d; ++a) c->base.Winv[a * d + a] = 1.0;
+      c->base.detW = 1.0;
+      c->base.wkind = WK_PER_QP;
+      c->base.Winv_qp = c->d_Winv_qp;
+      c->base.detW_qp = c->d_detW_qp;
+    }
+  }
+  cudaStreamSynchronize(s);  // the temporaries are in use until here
+  cudaFree(J);
+  cudaFree(Wi);
+  cudaFree(dW);
+  cudaFree(bad);
+  if (rc == TMOP_OK) c->pa_valid = false;
+  return rc;
 }
 
 int tmop_sizes(const tmop_ctx* c, int* dim, int* nelem, int* nnode, int* Q) {
@@ -627,6 +898,15 @@ int tmop_hess_apply_pa(tmop_ctx* c, const double* v, double* y, void* stream) {
   if (!c || !v || !y) return TMOP_ERR_ARG;
   if (!c->pa_valid) return TMOP_ERR_ARG;
   return launch_op(c, OP_HESS_PA, nullptr, v, y, nullptr, (cudaStream_t)stream);
+}
+
+int tmop_hessian_diagonal(tmop_ctx* c, double* out, void* stream) {
+  if (!c || !out) return TMOP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = hessian_diagonal(c, false, s);
+  if (rc) return rc;
+  CUDA_TRY(cudaMemcpyAsync(out, c->d_diag, sizeof(double) * c->ndof, cudaMemcpyDeviceToDevice, s));
+  return TMOP_OK;
 }
 
 int tmop_element_min_detA(tmop_ctx* c, const double* x, double* out, void* stream) {

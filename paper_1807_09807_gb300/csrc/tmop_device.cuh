@@ -128,6 +128,18 @@ __device__ __forceinline__ bool metric_P(int id, const S* T, S& mu, S* P) {
   S C[DD];
   cof_m<D>(T, C);
   S it = recip(tau);
+  if (id == 98) {  // |T - I|^2 / tau (Section 4.3.2); P = (2 (T - I) - mu C) / tau
+    S E[DD];
+#pragma unroll
+    for (int i = 0; i < DD; ++i) E[i] = (i % (D + 1) == 0) ? T[i] - sc<S>(1.0) : T[i];
+    S s = E[0] * E[0];
+#pragma unroll
+    for (int i = 1; i < DD; ++i) s = s + E[i] * E[i];
+    mu = s * it;
+#pragma unroll
+    for (int i = 0; i < DD; ++i) P[i] = it * (sc<S>(2.0) * E[i] - mu * C[i]);
+    return true;
+  }
   if constexpr (D == 2) {
     if (id == 2) {  // |T|^2 / (2 tau) - 1
       mu = sc<S>(0.5) * I1 * it - sc<S>(1.0);
@@ -450,6 +462,154 @@ __device__ __forceinline__ void adj3(const R* __restrict__ B, const R* __restric
 #pragma unroll
     for (int q0 = 0; q0 < Q1; ++q0) y = fma(vg[q0], G[q0 * N + i], fma(vb[q0], B[q0 * N + i], y));
     P0[(c * N * N + lj) * N + i] = y;
+  }
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------- register-blocked 3D contractions
+// Same maps as fwd3/adj3 with the same buffer layouts, but each lane owns a
+// whole row of outputs: it loads the row's inputs once into registers and
+// takes the 1D tables from registers (tB/tG: [Q1][N], compile-time indexed),
+// so a stage issues ~4x fewer shared-memory instructions. Used by the FP32
+// kernels, whose throughput the shared-memory pipe otherwise bounds.
+template <int N, int Q1, int NC, class R>
+__device__ __forceinline__ void fwd3_rb(const R (&tB)[Q1 * N], const R (&tG)[Q1 * N], R* P0, R* P1, int lane) {
+  constexpr int NNQ = N * N * Q1, NQQ = N * Q1 * Q1, QQ = Q1 * Q1, QQQ = Q1 * Q1 * Q1;
+  for (int t = lane; t < NC * N * N; t += 32) {           // (c, l, j) rows of x
+    const int c = t / (N * N), lj = t % (N * N);
+    R xv[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) xv[i] = P0[t * N + i];
+#pragma unroll
+    for (int q0 = 0; q0 < Q1; ++q0) {
+      R sb = R(0), sg = R(0);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        sb = fma(xv[i], tB[q0 * N + i], sb);
+        sg = fma(xv[i], tG[q0 * N + i], sg);
+      }
+      P1[(c * 2 + 0) * NNQ + lj * Q1 + q0] = sb;
+      P1[(c * 2 + 1) * NNQ + lj * Q1 + q0] = sg;
+    }
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * N * Q1; t += 32) {          // (c, l, q0)
+    const int q0 = t % Q1, l = (t / Q1) % N, c = t / (Q1 * N);
+    R xb[N], xg[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      xb[j] = P1[(c * 2 + 0) * NNQ + (l * N + j) * Q1 + q0];
+      xg[j] = P1[(c * 2 + 1) * NNQ + (l * N + j) * Q1 + q0];
+    }
+#pragma unroll
+    for (int q1 = 0; q1 < Q1; ++q1) {
+      R bb = R(0), bg = R(0), gb = R(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        bb = fma(xb[j], tB[q1 * N + j], bb);
+        bg = fma(xb[j], tG[q1 * N + j], bg);
+        gb = fma(xg[j], tB[q1 * N + j], gb);
+      }
+      const int o = l * QQ + q1 * Q1 + q0;
+      P0[(c * 3 + 0) * NQQ + o] = bb;
+      P0[(c * 3 + 1) * NQQ + o] = bg;
+      P0[(c * 3 + 2) * NQQ + o] = gb;
+    }
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * QQ; t += 32) {              // (c, q1, q0) columns
+    const int c = t / QQ, q01 = t % QQ;
+    R sbb[N], sbg[N], sgb[N];
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      sbb[l] = P0[(c * 3 + 0) * NQQ + l * QQ + q01];
+      sbg[l] = P0[(c * 3 + 1) * NQQ + l * QQ + q01];
+      sgb[l] = P0[(c * 3 + 2) * NQQ + l * QQ + q01];
+    }
+#pragma unroll
+    for (int q2 = 0; q2 < Q1; ++q2) {
+      R a0 = R(0), a1 = R(0), a2 = R(0);
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        a0 = fma(sgb[l], tB[q2 * N + l], a0);
+        a1 = fma(sbg[l], tB[q2 * N + l], a1);
+        a2 = fma(sbb[l], tG[q2 * N + l], a2);
+      }
+      const int o = q2 * QQ + q01;
+      P1[(c * 3 + 0) * QQQ + o] = a0;
+      P1[(c * 3 + 1) * QQQ + o] = a1;
+      P1[(c * 3 + 2) * QQQ + o] = a2;
+    }
+  }
+  __syncwarp();
+}
+
+template <int N, int Q1, int NC, class R>
+__device__ __forceinline__ void adj3_rb(const R (&tB)[Q1 * N], const R (&tG)[Q1 * N], R* P0, R* P1, int lane) {
+  constexpr int NNQ = N * N * Q1, NQQ = N * Q1 * Q1, QQ = Q1 * Q1, QQQ = Q1 * Q1 * Q1;
+  for (int t = lane; t < NC * QQ; t += 32) {              // (c, q1, q0) columns of R
+    const int c = t / QQ, q01 = t % QQ;
+    R r0[Q1], r1[Q1], r2[Q1];
+#pragma unroll
+    for (int q2 = 0; q2 < Q1; ++q2) {
+      r0[q2] = P1[(c * 3 + 0) * QQQ + q2 * QQ + q01];
+      r1[q2] = P1[(c * 3 + 1) * QQQ + q2 * QQ + q01];
+      r2[q2] = P1[(c * 3 + 2) * QQQ + q2 * QQ + q01];
+    }
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      R u0 = R(0), u1 = R(0), u2 = R(0);
+#pragma unroll
+      for (int q2 = 0; q2 < Q1; ++q2) {
+        u0 = fma(r0[q2], tB[q2 * N + l], u0);
+        u1 = fma(r1[q2], tB[q2 * N + l], u1);
+        u2 = fma(r2[q2], tG[q2 * N + l], u2);
+      }
+      const int o = l * QQ + q01;
+      P0[(c * 3 + 0) * NQQ + o] = u0;
+      P0[(c * 3 + 1) * NQQ + o] = u1;
+      P0[(c * 3 + 2) * NQQ + o] = u2;
+    }
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * N * Q1; t += 32) {          // (c, l, q0)
+    const int q0 = t % Q1, l = (t / Q1) % N, c = t / (Q1 * N);
+    R u0[Q1], u1[Q1], u2[Q1];
+#pragma unroll
+    for (int q1 = 0; q1 < Q1; ++q1) {
+      u0[q1] = P0[(c * 3 + 0) * NQQ + l * QQ + q1 * Q1 + q0];
+      u1[q1] = P0[(c * 3 + 1) * NQQ + l * QQ + q1 * Q1 + q0];
+      u2[q1] = P0[(c * 3 + 2) * NQQ + l * QQ + q1 * Q1 + q0];
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      R vg = R(0), vb = R(0);
+#pragma unroll
+      for (int q1 = 0; q1 < Q1; ++q1) {
+        vg = fma(u0[q1], tB[q1 * N + j], vg);
+        vb = fma(u1[q1], tG[q1 * N + j], fma(u2[q1], tB[q1 * N + j], vb));
+      }
+      const int o = (l * N + j) * Q1 + q0;
+      P1[(c * 2 + 0) * NNQ + o] = vg;
+      P1[(c * 2 + 1) * NNQ + o] = vb;
+    }
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * N * N; t += 32) {           // (c, l, j) rows of y
+    const int c = t / (N * N), lj = t % (N * N);
+    R vg[Q1], vb[Q1];
+#pragma unroll
+    for (int q0 = 0; q0 < Q1; ++q0) {
+      vg[q0] = P1[(c * 2 + 0) * NNQ + lj * Q1 + q0];
+      vb[q0] = P1[(c * 2 + 1) * NNQ + lj * Q1 + q0];
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      R y = R(0);
+#pragma unroll
+      for (int q0 = 0; q0 < Q1; ++q0) y = fma(vg[q0], tG[q0 * N + i], fma(vb[q0], tB[q0 * N + i], y));
+      P0[t * N + i] = y;
+    }
   }
   __syncwarp();
 }

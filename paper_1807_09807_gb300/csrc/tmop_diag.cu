@@ -1,0 +1,202 @@
+// Diagonal of the partially assembled Hessian (for Jacobi preconditioning of
+// the Newton systems of Section 3.4):
+//   diag_{i,a} = sum_E sum_q sum_{b,c} H_q[(a,b),(a,c)] d_b phi_i(x_q) d_c phi_i(x_q)
+// (+ 2 delta w_q det W phi_i(x_q)^2 for the restricted-movement term). The
+// product d_b phi_i d_c phi_i is separable: in direction d it is the 1D
+// product of (G if d == b else B) and (G if d == c else B), so every (a, b, c)
+// term is one sum-factorised contraction of a per-point scalar with three
+// per-direction tables. One warp per element, FP64 accumulation into diag.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "tmop_diag.h"
+#include "tmop_kparams.h"
+
+namespace tmop {
+
+namespace {
+
+constexpr int kDiagWarps = 4;
+
+__device__ __forceinline__ int dnode(const DiagParams& p, int e, int t, int N) {
+  if (p.sx > 0) {
+    const int k = N - 1, Nx = k * p.sx + 1, Ny = k * p.sy + 1;
+    const int ex = e % p.sx, ey = (e / p.sx) % p.sy, ez = e / (p.sx * p.sy);
+    const int i = t % N, j = (t / N) % N, l = t / (N * N);
+    return ((ez * k + l) * Ny + ey * k + j) * Nx + ex * k + i;
+  }
+  return __ldg(p.elem_nodes + (size_t)e * (p.dim == 2 ? N * N : N * N * N) + t);
+}
+
+// Y[n^DIM] += sum_q R[q] prod_d T_d[q_d][i_d]; R in `r` (QP values), tables T0,
+// T1, T2 ([Q1][N]), scratch U, V.
+template <int DIM, int N, int Q1>
+__device__ void contract_add(const double* r, const double* T0, const double* T1, const double* T2, double* U,
+                             double* V, double* Y, int lane) {
+  if constexpr (DIM == 2) {
+    for (int t = lane; t < N * Q1; t += 32) {  // U[j][q0] = sum_q1 R[q1][q0] T1[q1][j]
+      const int q0 = t % Q1, j = t / Q1;
+      double s = 0.0;
+#pragma unroll
+      for (int q1 = 0; q1 < Q1; ++q1) s = fma(r[q1 * Q1 + q0], T1[q1 * N + j], s);
+      U[j * Q1 + q0] = s;
+    }
+    __syncwarp();
+    for (int t = lane; t < N * N; t += 32) {  // Y[j][i] += sum_q0 U[j][q0] T0[q0][i]
+      const int i = t % N, j = t / N;
+      double s = 0.0;
+#pragma unroll
+      for (int q0 = 0; q0 < Q1; ++q0) s = fma(U[j * Q1 + q0], T0[q0 * N + i], s);
+      Y[t] += s;
+    }
+    __syncwarp();
+  } else {
+    constexpr int QQ = Q1 * Q1;
+    for (int t = lane; t < N * QQ; t += 32) {  // U[l][q1][q0] = sum_q2 R[q2][q1][q0] T2[q2][l]
+      const int q01 = t % QQ, l = t / QQ;
+      double s = 0.0;
+#pragma unroll
+      for (int q2 = 0; q2 < Q1; ++q2) s = fma(r[q2 * QQ + q01], T2[q2 * N + l], s);
+      U[l * QQ + q01] = s;
+    }
+    __syncwarp();
+    for (int t = lane; t < N * N * Q1; t += 32) {  // V[l][j][q0] = sum_q1 U[l][q1][q0] T1[q1][j]
+      const int q0 = t % Q1, j = (t / Q1) % N, l = t / (Q1 * N);
+      double s = 0.0;
+#pragma unroll
+      for (int q1 = 0; q1 < Q1; ++q1) s = fma(U[l * QQ + q1 * Q1 + q0], T1[q1 * N + j], s);
+      V[(l * N + j) * Q1 + q0] = s;
+    }
+    __syncwarp();
+    for (int t = lane; t < N * N * N; t += 32) {  // Y[l][j][i] += sum_q0 V[l][j][q0] T0[q0][i]
+      const int i = t % N, lj = t / N;
+      double s = 0.0;
+#pragma unroll
+      for (int q0 = 0; q0 < Q1; ++q0) s = fma(V[lj * Q1 + q0], T0[q0 * N + i], s);
+      Y[t] += s;
+    }
+    __syncwarp();
+  }
+}
+
+template <int DIM, int N, int Q1, class R>
+__global__ void __launch_bounds__(kDiagWarps * 32) diag_kernel(const DiagParams p) {
+  constexpr int NDOF = DIM == 2 ? N * N : N * N * N, QP = DIM == 2 ? Q1 * Q1 : Q1 * Q1 * Q1;
+  constexpr int DD = DIM * DIM, NS = DD * (DD + 1) / 2;
+  constexpr int UQ = DIM == 2 ? N * Q1 : N * Q1 * Q1, VQ = DIM == 2 ? 1 : N * N * Q1;
+  // tables: B, G and the three products BB, BG, GG ([Q1][N] each)
+  __shared__ double tab[5][kMaxQ * kMaxN];
+  __shared__ double sw[kMaxQ];
+  __shared__ double wr[kDiagWarps][QP], wu[kDiagWarps][UQ], wv[kDiagWarps][VQ], wy[kDiagWarps][NDOF];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int t = threadIdx.x; t < Q1 * N; t += blockDim.x) {
+    const double b = p.B[t], g = p.G[t];
+    tab[0][t] = b * b;
+    tab[1][t] = b * g;
+    tab[2][t] = g * g;
+  }
+  for (int t = threadIdx.x; t < Q1; t += blockDim.x) sw[t] = p.w1[t];
+  __syncthreads();
+  double *r = wr[warp], *U = wu[warp], *V = wv[warp], *Y = wy[warp];
+  const R* H = static_cast<const R*>(p.pa);
+  for (int e = blockIdx.x * kDiagWarps + warp; e < p.nelem; e += gridDim.x * kDiagWarps) {
+    const R* He = H + (size_t)e * p.pa_stride;
+    for (int a = 0; a < DIM; ++a) {
+      for (int t = lane; t < NDOF; t += 32) Y[t] = 0.0;
+      __syncwarp();
+      for (int b = 0; b < DIM; ++b)
+        for (int c = b; c < DIM; ++c) {
+          // packed index of (row a*DIM+b, column a*DIM+c), row <= column
+          const int rr = a * DIM + b, cc = a * DIM + c;
+          const int s = rr * DD - rr * (rr - 1) / 2 + (cc - rr);
+          const double m = b == c ? 1.0 : 2.0;
+          for (int q = lane; q < QP; q += 32) r[q] = m * (double)He[(size_t)s * QP + q];
+          __syncwarp();
+          // direction d uses tab[(d == b) + (d == c)]: BB, BG or GG
+          const double* T0 = tab[(b == 0) + (c == 0)];
+          const double* T1 = tab[(b == 1) + (c == 1)];
+          const double* T2 = tab[(b == 2) + (c == 2)];
+          contract_add<DIM, N, Q1>(r, T0, T1, T2, U, V, Y, lane);
+        }
+      if (p.delta != 0.0) {  // restricted movement: 2 delta w det W phi_i^2 (B^2 in every direction)
+        for (int q = lane; q < QP; q += 32) {
+          const int q0 = q % Q1, q1 = (q / Q1) % Q1;
+          double wq = sw[q0] * sw[q1];
+          if (DIM == 3) wq *= sw[q / (Q1 * Q1)];
+          const double dw = p.detW_qp ? __ldg(p.detW_qp + (size_t)e * QP + q) : p.detW;
+          r[q] = 2.0 * p.delta * wq * dw;
+        }
+        __syncwarp();
+        contract_add<DIM, N, Q1>(r, tab[0], tab[0], tab[0], U, V, Y, lane);
+      }
+      for (int t = lane; t < NDOF; t += 32) {
+        const int g = dnode(p, e, t, N);
+        atomicAdd(p.diag + (size_t)a * p.nnode + g, Y[t]);
+      }
+      __syncwarp();
+    }
+  }
+}
+
+template <int DIM, int N, int Q1, class R>
+int launch_diag(const DiagParams& p, int grid, void* stream) {
+  diag_kernel<DIM, N, Q1, R><<<grid, kDiagWarps * 32, 0, (cudaStream_t)stream>>>(p);
+  return (int)cudaGetLastError();
+}
+
+struct DiagEntry {
+  int dim, n, q;
+  diag_launch_fn f64, f32;
+};
+
+#define TMOP_DIAG(DIM, N, Q) {DIM, N, Q, launch_diag<DIM, N, Q, double>, launch_diag<DIM, N, Q, float>}
+
+const DiagEntry kDiag[] = {
+    TMOP_DIAG(2, 2, 2), TMOP_DIAG(2, 2, 3), TMOP_DIAG(2, 3, 3), TMOP_DIAG(2, 3, 4), TMOP_DIAG(2, 3, 5),
+    TMOP_DIAG(2, 4, 4), TMOP_DIAG(2, 4, 5), TMOP_DIAG(2, 4, 6), TMOP_DIAG(2, 5, 5), TMOP_DIAG(2, 5, 6),
+    TMOP_DIAG(3, 2, 2), TMOP_DIAG(3, 2, 3), TMOP_DIAG(3, 3, 3), TMOP_DIAG(3, 3, 4), TMOP_DIAG(3, 4, 4),
+    TMOP_DIAG(3, 4, 5), TMOP_DIAG(3, 5, 5), TMOP_DIAG(3, 5, 6),
+};
+
+// fixed dofs: diagonal 1 (the operator is the identity there in the masked system)
+__global__ void k_diag_fix(double* diag, const uint8_t* fixed, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    if (fixed && fixed[i]) diag[i] = 1.0;
+}
+
+// Jacobi inverse with a floor: minv = 1 / max(|diag|, floor * mean |diag|)
+__global__ void k_diag_inverse(const double* diag, double* minv, size_t n, double floor_abs) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    minv[i] = 1.0 / fmax(fabs(diag[i]), floor_abs);
+}
+
+}  // namespace
+
+diag_launch_fn find_diag(int dim, int n, int q, int fp32) {
+  for (const DiagEntry& d : kDiag)
+    if (d.dim == dim && d.n == n && d.q == q) return fp32 ? d.f32 : d.f64;
+  return nullptr;
+}
+
+int diag_grid(int nelem) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int need = (nelem + kDiagWarps - 1) / kDiagWarps;
+  const int full = 4 * (sms > 0 ? sms : 1);
+  const int g = need < full ? need : full;
+  return g < 1 ? 1 : g;
+}
+
+int diag_finish(double* diag, const uint8_t* fixed, size_t n, cudaStream_t s) {
+  k_diag_fix<<<256, 256, 0, s>>>(diag, fixed, n);
+  return (int)cudaGetLastError();
+}
+
+int diag_inverse(const double* diag, double* minv, size_t n, double floor_abs, cudaStream_t s) {
+  k_diag_inverse<<<256, 256, 0, s>>>(diag, minv, n, floor_abs);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace tmop

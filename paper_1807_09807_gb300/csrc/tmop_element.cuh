@@ -31,16 +31,29 @@ struct Buf {
                                      : cmax<2 * NC * N * N * Q1, 3 * NC * Q1 * Q1 * Q1>::value;
 };
 
+// Words of type R rounded up to a whole number of 16-byte units, so every
+// per-warp buffer starts on a 16-byte boundary (bulk-copy destinations).
+template <class R>
+constexpr int round16(int words) {
+  return ((words * (int)sizeof(R) + 15) / 16) * 16 / (int)sizeof(R);
+}
+
 template <int D, int N, int Q1, class R, int OP>
 struct ElemCfg {
-  static constexpr int NC = (OP == OP_HESS) ? 2 * D : D;
-  static constexpr int B0 = Buf<D, N, Q1, NC>::B0;
-  static constexpr int B1 = Buf<D, N, Q1, NC>::B1;
-  static constexpr int PER_WARP = (int)sizeof(R) * (B0 + B1);
-  // up to 4 warps per block within ~200 KB of shared memory
-  static constexpr int WARPS = (200 * 1024 / PER_WARP) >= 4 ? 4 : ((200 * 1024 / PER_WARP) < 1 ? 1 : 200 * 1024 / PER_WARP);
-  static constexpr int TABLE = 2 * kMaxQ * kMaxN + kMaxQ;
-  static constexpr size_t smem_bytes() { return sizeof(R) * (TABLE + WARPS * (B0 + B1)); }
+  // 3D Hessian action: x and v are contracted one after the other and only
+  // A(x) is kept (buffer B2) while v runs through the stage buffers, so the
+  // stage buffers hold D components; 2D contracts both at once (2D
+  // components, no B2).
+  static constexpr bool SPLIT = (OP == OP_HESS) && D == 3;
+  static constexpr int NC = (OP == OP_HESS && !SPLIT) ? 2 * D : D;
+  static constexpr int B0 = round16<R>(Buf<D, N, Q1, NC>::B0);
+  static constexpr int B1 = round16<R>(Buf<D, N, Q1, NC>::B1);
+  static constexpr int B2 = SPLIT ? round16<R>(D * D * Shape<D, N, Q1>::QP) : 0;
+  static constexpr int PER_WARP = (int)sizeof(R) * (B0 + B1 + B2);
+  // up to 8 warps (elements in flight) per block within ~200 KB of shared memory
+  static constexpr int WARPS = (200 * 1024 / PER_WARP) >= 8 ? 8 : ((200 * 1024 / PER_WARP) < 1 ? 1 : 200 * 1024 / PER_WARP);
+  static constexpr int TABLE = round16<R>(2 * kMaxQ * kMaxN + kMaxQ);
+  static constexpr size_t smem_bytes() { return sizeof(R) * (TABLE + WARPS * (B0 + B1 + B2)); }
 };
 
 __device__ __forceinline__ int node_id(const KParams& p, int e, int t, int N) {
@@ -54,6 +67,45 @@ __device__ __forceinline__ int node_id(const KParams& p, int e, int t, int N) {
   return __ldg(p.elem_nodes + (size_t)e * (p.dim == 2 ? N * N : N * N * N) + t);
 }
 
+// Second term of a composite metric at one point: T2 = A W2^-1 and, for a
+// direction dA, dT2 = dA W2^-1 (Section 4.2, eq. (4.1)).
+template <int D, class R>
+__device__ __forceinline__ void times_w2(const KParams& p, const R* M, R* out) {
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      R s = R(0);
+#pragma unroll
+      for (int c = 0; c < D; ++c) s = fma(M[a * D + c], R(p.Winv2[c * D + b]), s);
+      out[a * D + b] = s;
+    }
+}
+
+// Metrics not written in I1 = |T|^2 and tau = det T alone (mu302 also needs
+// |cof T|^2, mu98 needs T - I): their second derivative comes from
+// forward-mode dual numbers instead of MetricLin.
+__device__ __forceinline__ bool metric_dual(int id) { return id == 302 || id == 98; }
+
+// dP of metric `id` at T in direction dT (closed form, or dual numbers)
+template <int D, class R>
+__device__ __forceinline__ bool metric_dP(int id, const R* T, const R* dT, R* S) {
+  constexpr int DD = D * D;
+  if (metric_dual(id)) {
+    Dual<R> Td[DD], Pd[DD], mud;
+#pragma unroll
+    for (int i = 0; i < DD; ++i) Td[i] = Dual<R>{T[i], dT[i]};
+    const bool ok = metric_P<D>(id, Td, mud, Pd);
+#pragma unroll
+    for (int i = 0; i < DD; ++i) S[i] = Pd[i].d;
+    return ok;
+  }
+  MetricLin<D, R> L;
+  const bool ok = L.init(id, T);
+  if (ok) L.dP(dT, S);
+  return ok;
+}
+
 template <int D, int N, int Q1, class R, int OP>
 __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
     elem_kernel(const KParams p) {
@@ -65,8 +117,10 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
   R* sG = sB + kMaxQ * kMaxN;
   R* sw = sG + kMaxQ * kMaxN;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  R* P0 = sB + Cfg::TABLE + warp * (Cfg::B0 + Cfg::B1);
+  R* P0 = sB + Cfg::TABLE + warp * (Cfg::B0 + Cfg::B1 + Cfg::B2);
   R* P1 = P0 + Cfg::B0;
+  R* P2 = P1 + Cfg::B1;  // A(x) of the split 3D Hessian action
+
   for (int t = threadIdx.x; t < Q1 * N; t += blockDim.x) {
     sB[t] = R(p.B[t]);
     sG[t] = R(p.G[t]);
@@ -75,11 +129,32 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
   R Wi[DD];
 #pragma unroll
   for (int i = 0; i < DD; ++i) Wi[i] = R(p.Winv[i]);
+  // FP32 3D kernels: the 1D tables in registers for the register-blocked stages
+  constexpr bool RB = (D == 3) && sizeof(R) == 4;
+  R tB[Q1 * N], tG[Q1 * N];
+  if constexpr (RB) {
+#pragma unroll
+    for (int t = 0; t < Q1 * N; ++t) {
+      tB[t] = R(p.B[t]);
+      tG[t] = R(p.G[t]);
+    }
+  }
   __syncthreads();
 
   double accF = 0.0, accMin = INFINITY;
   const int nwarps_total = gridDim.x * WARPS;
+  constexpr int NSH = (OP == OP_HESS_PA) ? D * D * (D * D + 1) / 2 : 1;
   for (int e = blockIdx.x * WARPS + warp; e < p.nelem; e += nwarps_total) {
+    // Partially assembled product: the Hessians of this lane's first point are
+    // loaded now, so their latency overlaps the gather and the v-contraction.
+    R hpre[NSH];
+    if constexpr (OP == OP_HESS_PA) {
+      if (lane < Shape<D, N, Q1>::QP) {
+        const R* H0 = static_cast<const R*>(p.pa) + (size_t)e * p.pa_stride + lane;
+#pragma unroll
+        for (int t = 0; t < NSH; ++t) hpre[t] = __ldg(H0 + (size_t)t * Shape<D, N, Q1>::QP);
+      }
+    }
     // ---- gather. In FP32 the coordinates are taken relative to the element's
     // first node (in FP64) before rounding: A is translation invariant
     // (sum_i grad phi_i = 0), and this keeps the FP32 relative error of A at
@@ -108,7 +183,7 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
         if constexpr (sizeof(R) == 4) P0[c * NDOF + t] = R(xv - xref[c]);
         else P0[c * NDOF + t] = R(xv);
       }
-      if constexpr (OP == OP_HESS) {
+      if constexpr (OP == OP_HESS && !Cfg::SPLIT) {
 #pragma unroll
         for (int c = 0; c < D; ++c) {
           const size_t dof = (size_t)c * p.nnode + g;
@@ -119,16 +194,48 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
     }
     __syncwarp();
     // ---- forward contraction: A (and dA) at every point
-    if constexpr (D == 2) fwd2<N, Q1, Cfg::NC, R>(sB, sG, P0, P1, lane);
-    else fwd3<N, Q1, Cfg::NC, R>(sB, sG, P0, P1, lane);
-    R* Abuf = (D == 2) ? P0 : P1;  // [NC][D][QP]
+    if constexpr (Cfg::SPLIT) {
+      // A(x) into P2 (P2 also serves as the first stage buffer), then v
+      if constexpr (RB) fwd3_rb<N, Q1, D, R>(tB, tG, P0, P2, lane);
+      else fwd3<N, Q1, D, R>(sB, sG, P0, P2, lane);
+      for (int t = lane; t < NDOF; t += 32) {
+        const int g = node_id(p, e, t, N);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const size_t dof = (size_t)c * p.nnode + g;
+          const bool fx = p.fixed && __ldg(p.fixed + dof);
+          P0[c * NDOF + t] = fx ? R(0) : R(__ldg(p.v + dof));
+        }
+      }
+      __syncwarp();
+      if constexpr (RB) fwd3_rb<N, Q1, D, R>(tB, tG, P0, P1, lane);
+      else fwd3<N, Q1, D, R>(sB, sG, P0, P1, lane);
+    } else if constexpr (D == 2) {
+      fwd2<N, Q1, Cfg::NC, R>(sB, sG, P0, P1, lane);
+    } else if constexpr (RB) {
+      fwd3_rb<N, Q1, Cfg::NC, R>(tB, tG, P0, P1, lane);
+    } else {
+      fwd3<N, Q1, Cfg::NC, R>(sB, sG, P0, P1, lane);
+    }
+    R* Abuf = Cfg::SPLIT ? P2 : ((D == 2) ? P0 : P1);     // A: [D][D][QP]
+    R* dAbuf = Cfg::SPLIT ? P1 : Abuf + DD * QP;         // dA (Hessian action)
+    R* Rbuf = Cfg::SPLIT ? P1 : Abuf;                    // per-point output of the adjoint
     // ---- pointwise
     double emin = INFINITY;
     constexpr int NS = DD * (DD + 1) / 2;
     for (int q = lane; q < QP; q += 32) {
       if constexpr (OP == OP_HESS_PA) {
         // y = H dA with the stored symmetric A-space Hessian (already scaled by w det W)
-        const R* H = static_cast<const R*>(p.pa) + (size_t)e * NS * QP + q;
+        const R* H = static_cast<const R*>(p.pa) + (size_t)e * p.pa_stride + q;
+        // all NS loads are issued before the first use, so their latencies overlap
+        R h[NS];
+        if (q == lane) {
+#pragma unroll
+          for (int t = 0; t < NS; ++t) h[t] = hpre[t];
+        } else {
+#pragma unroll
+          for (int t = 0; t < NS; ++t) h[t] = __ldg(H + (size_t)t * QP);
+        }
         R dA[DD], y[DD];
 #pragma unroll
         for (int i = 0; i < DD; ++i) {
@@ -140,9 +247,8 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
         for (int r = 0; r < DD; ++r)
 #pragma unroll
           for (int c = r; c < DD; ++c, ++s) {
-            const R h = H[(size_t)s * QP];
-            y[r] = fma(h, dA[c], y[r]);
-            if (c != r) y[c] = fma(h, dA[r], y[c]);
+            y[r] = fma(h[s], dA[c], y[r]);
+            if (c != r) y[c] = fma(h[s], dA[r], y[c]);
           }
 #pragma unroll
         for (int i = 0; i < DD; ++i) Abuf[i * QP + q] = y[i];
@@ -181,10 +287,10 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
       if constexpr (OP == OP_LINEARIZE) {
         // column kl of the A-space Hessian: direction dA = E_kl, dT = E_kl W^-1,
         // R = w det W (d^2mu/dT^2 : dT) W^-t; the upper triangle is stored
-        R* H = static_cast<R*>(p.pa) + (size_t)e * NS * QP + q;
+        R* H = static_cast<R*>(p.pa) + (size_t)e * p.pa_stride + q;
         const R s = wq * detW;
         MetricLin<D, R> L;
-        const bool lin = p.metric != 302;
+        const bool lin = !metric_dual(p.metric);
         bool ok = lin ? L.init(p.metric, T) : true;
         int off = 0;
 #pragma unroll 1
@@ -206,6 +312,20 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
 #pragma unroll
             for (int i = 0; i < DD; ++i) S[i] = Pd[i].d;
           }
+          // second term: dT2 = E_kl W2^-1
+          R S2[DD];
+          bool ok2 = false;
+          R s2 = R(0);
+          if (p.metric2) {
+            R T2[DD], dT2[DD];
+            times_w2<D>(p, A, T2);
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+              for (int b = 0; b < D; ++b) dT2[a * D + b] = a == k ? R(p.Winv2[l * D + b]) : R(0);
+            ok2 = metric_dP<D>(p.metric2, T2, dT2, S2);
+            s2 = wq * R(p.detW2) * (p.eta2 ? R(__ldg(p.eta2 + (size_t)e * QP + q)) : R(1));
+          }
 #pragma unroll
           for (int mn = 0; mn < DD; ++mn) {
             if (mn < kl) continue;
@@ -217,7 +337,14 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
 #pragma unroll
               for (int c = 0; c < D; ++c) r = fma(S[m * D + c], Wi[nn * D + c], r);
             }
-            H[(size_t)(off + mn - kl) * QP] = ok ? s * r : R(0);
+            R val = ok ? s * r : R(0);
+            if (ok2) {
+              R r2 = R(0);
+#pragma unroll
+              for (int c = 0; c < D; ++c) r2 = fma(S2[m * D + c], R(p.Winv2[nn * D + c]), r2);
+              val = fma(s2, r2, val);
+            }
+            H[(size_t)(off + mn - kl) * QP] = val;
           }
           off += DD - kl;
         }
@@ -233,16 +360,23 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
         R Pd[DD];
         if (metric_P<D>(p.metric, T, mu, Pd)) accF += double(wq * detW) * double(mu);
         else accF = INFINITY;
+        if (p.metric2) {
+          R T2[DD], mu2;
+          times_w2<D>(p, A, T2);
+          const double eta = p.eta2 ? __ldg(p.eta2 + (size_t)e * QP + q) : 1.0;
+          if (metric_P<D>(p.metric2, T2, mu2, Pd)) accF += double(wq) * p.detW2 * eta * double(mu2);
+          else accF = INFINITY;
+        }
       } else {
-        R S[DD];
+        R S[DD], dA[DD];
         bool ok;
         if constexpr (OP == OP_GRADIENT) {
           R mu;
           ok = metric_P<D>(p.metric, T, mu, S);
         } else {
-          R dA[DD], dT[DD];
+          R dT[DD];
 #pragma unroll
-          for (int i = 0; i < DD; ++i) dA[i] = Abuf[(DD + i) * QP + q];
+          for (int i = 0; i < DD; ++i) dA[i] = dAbuf[i * QP + q];
           if (p.wkind == WK_IDENTITY) {
 #pragma unroll
             for (int i = 0; i < DD; ++i) dT[i] = dA[i];
@@ -257,8 +391,8 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
                 dT[a * D + b] = s;
               }
           }
-          if (p.metric == 302) {
-            // three invariants (I1, |cof T|^2, tau): forward-mode dual numbers
+          if (metric_dual(p.metric)) {
+            // not an (I1, tau) metric: forward-mode dual numbers
             Dual<R> Td[DD], Pd[DD], mud;
 #pragma unroll
             for (int i = 0; i < DD; ++i) Td[i] = Dual<R>{T[i], dT[i]};
@@ -284,8 +418,34 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
 #pragma unroll
               for (int c = 0; c < D; ++c) r = fma(S[a * D + c], Wi[b * D + c], r);
             }
-            Abuf[(a * D + b) * QP + q] = ok ? s * r : R(0);
+            Rbuf[(a * D + b) * QP + q] = ok ? s * r : R(0);
           }
+        if (p.metric2) {
+          // + eta w det W2 S2 W2^-t (S2 = P2 or dP2 at T2 = A W2^-1)
+          R T2[DD], S2[DD];
+          times_w2<D>(p, A, T2);
+          bool ok2;
+          if constexpr (OP == OP_GRADIENT) {
+            R mu2;
+            ok2 = metric_P<D>(p.metric2, T2, mu2, S2);
+          } else {
+            R dT2[DD];
+            times_w2<D>(p, dA, dT2);
+            ok2 = metric_dP<D>(p.metric2, T2, dT2, S2);
+          }
+          if (ok2) {
+            const R s2 = wq * R(p.detW2) * (p.eta2 ? R(__ldg(p.eta2 + (size_t)e * QP + q)) : R(1));
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+              for (int b = 0; b < D; ++b) {
+                R r2 = R(0);
+#pragma unroll
+                for (int c = 0; c < D; ++c) r2 = fma(S2[a * D + c], R(p.Winv2[b * D + c]), r2);
+                Rbuf[(a * D + b) * QP + q] = fma(s2, r2, Rbuf[(a * D + b) * QP + q]);
+              }
+          }
+        }
       }
     }
     if constexpr (OP == OP_LINEARIZE) {
@@ -301,6 +461,7 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
       __syncwarp();
       // ---- adjoint contraction and scatter
       if constexpr (D == 2) adj2<N, Q1, D, R>(sB, sG, P0, P1, lane);
+      else if constexpr (RB) adj3_rb<N, Q1, D, R>(tB, tG, P0, P1, lane);
       else adj3<N, Q1, D, R>(sB, sG, P0, P1, lane);
       for (int t = lane; t < NDOF; t += 32) {
         const int g = node_id(p, e, t, N);

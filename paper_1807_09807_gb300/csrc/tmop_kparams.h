@@ -28,13 +28,34 @@ struct KParams {
   double* part_F;                 // [grid] energy partials
   double* part_min;               // [grid] min det A partials
   double* elem_min;               // [nelem] per-element min det A, or null
-  void* pa;                       // [nelem][DD(DD+1)/2][Q] packed Hessians (float or double)
+  void* pa;                       // [nelem][pa_stride] packed Hessians [DD(DD+1)/2][Q] (float or double)
+  int pa_stride;                  // elements per element block, padded to 16 bytes
   double B[kMaxQ * kMaxN];              // B[q][i] = phi_i(xi_q)
   double G[kMaxQ * kMaxN];              // G[q][i] = phi_i'(xi_q)
   double w1[kMaxQ];                // 1D quadrature weights
   double Winv[9];                 // constant W^-1 (row-major)
   double detW;                    // constant det W
+  // optional second term of a composite metric (eq. (4.1)): + eta_q mu2(A W2^-1)
+  int metric2;                    // 0 = no second term
+  double Winv2[9];                // constant W2^-1
+  double detW2;                   // det W2
+  const double* eta2;             // [nelem][Q] weights of the second term, or null (= 1)
 };
+
+// Metrics of Table 3.1 (and mu98 of Section 4.3.2, mu302) available in
+// dimension d.
+inline bool metric_supported(int d, int id) {
+  return id == 1 || id == 14 || id == 98 || (d == 2 && (id == 2 || id == 7 || id == 9 || id == 77)) ||
+         (d == 3 && (id == 302 || id == 303));
+}
+
+// Per-element block of packed Hessians, in elements of `elt` bytes, padded so
+// that every block starts on a 16-byte boundary (bulk-copy granularity).
+inline int pa_stride_for(int dim, int Q, int elt) {
+  const int dd = dim * dim, ns = dd * (dd + 1) / 2;
+  const int bytes = ((ns * Q * elt + 15) / 16) * 16;
+  return bytes / elt;
+}
 
 typedef int (*elem_launch_fn)(const KParams& p, int grid, void* stream);
 typedef int (*elem_prepare_fn)(int nelem, int* grid);

@@ -13,8 +13,8 @@
 // The element kernel is the same one tmop_energy launches (one warp per
 // element); only its scratch differs: the per-block partial sums of F and of
 // min det A go into the file-scope array below instead of a context's
-// workspace, and the launch uses one block per group of `warps` elements, so
-// the number of partials is ceil(nelem / warps).
+// workspace, and the launch uses one block per group of `warps` elements
+// (4 to 8), so the number of partials is ceil(nelem / warps).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <mutex>
@@ -65,9 +65,7 @@ extern "C" int tmop_energy_noalloc(int dim, int order, const int structured[3], 
   if (order < 1 || order > 4) return TMOP_ERR_ARG;
   if (quad->kind != TMOP_GL && quad->kind != TMOP_GLL) return TMOP_ERR_ARG;
   if (quad->npts1d < 2 || quad->npts1d > kMaxQ) return TMOP_ERR_ARG;
-  const bool ok_metric = (metric_id == 1 || metric_id == 14) ||
-                         (dim == 2 && (metric_id == 2 || metric_id == 7 || metric_id == 9 || metric_id == 77)) ||
-                         (dim == 3 && (metric_id == 302 || metric_id == 303));
+  const bool ok_metric = metric_supported(dim, metric_id);
   if (!ok_metric) return TMOP_ERR_ARG;
   const int nx = structured[0], ny = structured[1], nz = dim == 3 ? structured[2] : 1;
   if (nx < 1 || ny < 1 || nz < 1) return TMOP_ERR_ARG;
@@ -133,6 +131,6 @@ extern "C" int tmop_energy_noalloc(int dim, int order, const int structured[3], 
   if (ent->prepare((int)nelem, &grid) != 0) return TMOP_ERR_CUDA;  // shared-memory opt-in only
   cudaStream_t s = (cudaStream_t)stream;
   if (ent->launch(p, (int)blocks, s) != 0) return TMOP_ERR_CUDA;
-  if (energy_final(p.part_F, p.part_min, (int)blocks, F, min_detA, s) != 0) return TMOP_ERR_CUDA;
+  if (energy_final(p.part_F, p.part_min, (int)blocks, nullptr, 0, F, min_detA, s) != 0) return TMOP_ERR_CUDA;
   return TMOP_OK;
 }

@@ -66,13 +66,15 @@ __global__ void k_sum_final(const double* __restrict__ part, int np, double* __r
 }
 
 __global__ void k_energy_final(const double* __restrict__ pf, const double* __restrict__ pm, int np,
-                               double* __restrict__ outF, double* __restrict__ outMin) {
+                               const double* __restrict__ pf2, int np2, double* __restrict__ outF,
+                               double* __restrict__ outMin) {
   __shared__ double mins[kThreads];
   double s = 0.0, m = INFINITY;
   for (int i = threadIdx.x; i < np; i += blockDim.x) {
     s += pf[i];
     m = fmin(m, pm[i]);
   }
+  for (int i = threadIdx.x; i < np2; i += blockDim.x) s += pf2[i];  // extra terms of F (eq. (4.2))
   mins[threadIdx.x] = m;
   s = block_sum(s);
   __syncthreads();
@@ -90,8 +92,9 @@ int dot(const double* a, const double* b, size_t n, double* part, double* out, c
   return (int)cudaGetLastError();
 }
 
-int energy_final(const double* pf, const double* pm, int np, double* outF, double* outMin, cudaStream_t s) {
-  k_energy_final<<<1, kThreads, 0, s>>>(pf, pm, np, outF, outMin);
+int energy_final(const double* pf, const double* pm, int np, const double* pf2, int np2, double* outF,
+                 double* outMin, cudaStream_t s) {
+  k_energy_final<<<1, kThreads, 0, s>>>(pf, pm, np, pf2, pf2 ? np2 : 0, outF, outMin);
   return (int)cudaGetLastError();
 }
 
@@ -110,7 +113,7 @@ int step(const double* x, const double* p, double alpha, double* y, size_t n, cu
 // ---------------------------------------------------------------- MINRES
 // v = b / beta1, vprev = w = wprev = sol = 0 and the rotation state.
 __global__ void k_minres_init(const double* __restrict__ b, double* v, double* vprev, double* w, double* wprev,
-                              double* sol, double* st, size_t n) {
+                              double* sol, double* st, size_t n, double rtol, int maxit) {
   const double beta1 = sqrt(st[KS_BETA_NEXT2]);
   const double inv = beta1 > 0.0 ? 1.0 / beta1 : 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -126,6 +129,12 @@ __global__ void k_minres_init(const double* __restrict__ b, double* v, double* v
     st[KS_ETA] = beta1;
     st[KS_RESID] = beta1;
     st[KS_C_OLD] = 1.0; st[KS_S_OLD] = 0.0; st[KS_C] = 1.0; st[KS_S] = 0.0;
+    st[KS_TOL] = rtol * beta1;
+    st[KS_ITER] = 0.0;
+    st[KS_DONE] = beta1 > 0.0 ? 0.0 : 1.0;
+    st[KS_CONV_IT] = 0.0;
+    st[KS_MAXIT] = (double)maxit;
+    st[KS_HITMAX] = 0.0;
   }
 }
 
@@ -146,6 +155,20 @@ __global__ void k_lanczos(double* __restrict__ Av, const double* __restrict__ v,
 // Apply the two previous rotations to the new tridiagonal column
 // (beta_k, alpha_k, beta_{k+1}), form the new rotation, update eta.
 __global__ void k_minres_scalar(double* st) {
+  if (st[KS_DONE] == 0.0 && st[KS_ITER] >= st[KS_MAXIT]) {  // the cap: freeze, not converged
+    st[KS_DONE] = 1.0;
+    st[KS_HITMAX] = 1.0;
+    st[KS_CONV_IT] = st[KS_ITER];
+  }
+  if (st[KS_DONE] != 0.0) {  // converged earlier: this iteration leaves the solution unchanged
+    st[KS_PHI] = 0.0;
+    st[KS_R1] = 0.0;
+    st[KS_R2] = 0.0;
+    st[KS_INV_RHO] = 0.0;
+    st[KS_INV_BETA_NEXT] = 0.0;
+    return;
+  }
+  st[KS_ITER] += 1.0;
   const double beta = st[KS_BETA], alpha = st[KS_ALPHA];
   const double beta_next = sqrt(fmax(st[KS_BETA_NEXT2], 0.0));
   const double c_old = st[KS_C_OLD], s_old = st[KS_S_OLD], c = st[KS_C], s = st[KS_S];
@@ -166,6 +189,10 @@ __global__ void k_minres_scalar(double* st) {
   st[KS_BETA_NEXT] = beta_next;
   st[KS_C_OLD] = c; st[KS_S_OLD] = s; st[KS_C] = c_new; st[KS_S] = s_new;
   st[KS_BETA] = beta_next;
+  if (fabs(s_new * eta) <= st[KS_TOL] || beta_next == 0.0) {
+    st[KS_DONE] = 1.0;
+    st[KS_CONV_IT] = st[KS_ITER];
+  }
 }
 
 // New search direction w_k = (v_k - r1 w_{k-2} - r2 w_{k-1}) / rho, solution
@@ -184,13 +211,15 @@ __global__ void k_minres_vec(double* __restrict__ v, double* __restrict__ vprev,
     v[i] = Av[i] * ib;
   }
 }
+// (once KS_DONE is set, phi = 0 keeps sol fixed and v becomes 0, so every
+// later product is zero)
 
 int minres_init(const double* b, double* v, double* vprev, double* w, double* wprev, double* sol, double* st,
-                double* part, size_t n, cudaStream_t s) {
+                double* part, size_t n, double rtol, int maxit, cudaStream_t s) {
   int g = red_grid(n);
   k_dot_part<<<g, kThreads, 0, s>>>(b, b, n, part);
   k_sum_final<<<1, kThreads, 0, s>>>(part, g, st + KS_BETA_NEXT2);
-  k_minres_init<<<g, kThreads, 0, s>>>(b, v, vprev, w, wprev, sol, st, n);
+  k_minres_init<<<g, kThreads, 0, s>>>(b, v, vprev, w, wprev, sol, st, n, rtol, maxit);
   return (int)cudaGetLastError();
 }
 
@@ -206,8 +235,176 @@ int minres_after_hv(double* v, double* vprev, double* Av, double* w, double* wpr
   return (int)cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- preconditioned MINRES
+// Lanczos in the M^-1 inner product with the residual minimised through
+// Givens rotations (Paige and Saunders), M = diag(1 / minv). The residual
+// estimate phibar is the M^-1-norm of the residual; the solve stops when it
+// falls to rtol times its initial value.
+__global__ void k_pm_init(const double* __restrict__ b, const double* __restrict__ minv, double* r1, double* r2,
+                          double* y, double* w, double* wprev, double* sol, size_t n, double* __restrict__ part) {
+  double s = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double bi = b[i], yi = minv[i] * bi;
+    r1[i] = bi;
+    r2[i] = bi;
+    y[i] = yi;
+    w[i] = 0.0;
+    wprev[i] = 0.0;
+    sol[i] = 0.0;
+    s = fma(bi, yi, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_pm_init_scalar(double* st, double rtol, int maxit) {
+  const double beta1 = sqrt(fmax(st[KS_BETA_NEXT2], 0.0));
+  st[KS_BETA1] = beta1;
+  st[KS_BETA] = beta1;
+  st[KS_OLDB] = 0.0;
+  st[KS_DBAR] = 0.0;
+  st[KS_EPSLN] = 0.0;
+  st[KS_OLDEPS] = 0.0;
+  st[KS_PHIBAR] = beta1;
+  st[KS_RESID] = beta1;
+  st[KS_CS] = -1.0;
+  st[KS_SN] = 0.0;
+  st[KS_DELTA] = 0.0;
+  st[KS_INV_GAMMA] = 0.0;
+  st[KS_PHI] = 0.0;
+  st[KS_INV_BETA] = beta1 > 0.0 ? 1.0 / beta1 : 0.0;
+  st[KS_TOL] = rtol * beta1;
+  st[KS_ITER] = 0.0;
+  st[KS_DONE] = beta1 > 0.0 ? 0.0 : 1.0;
+  st[KS_CONV_IT] = 0.0;
+  st[KS_MAXIT] = (double)maxit;
+  st[KS_HITMAX] = 0.0;
+  st[KS_BREAKDOWN] = 0.0;
+}
+
+__global__ void k_pm_v(double* __restrict__ v, const double* __restrict__ y, const double* __restrict__ st, size_t n) {
+  const double ib = st[KS_INV_BETA];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    v[i] = y[i] * ib;
+}
+
+// y <- y - (beta / oldb) r1 (from the second iteration on), partials of v . y
+__global__ void k_pm_a(double* __restrict__ y, const double* __restrict__ r1, const double* __restrict__ v,
+                       const double* __restrict__ st, size_t n, double* __restrict__ part) {
+  const double oldb = st[KS_OLDB];
+  const double c = oldb > 0.0 ? st[KS_BETA] / oldb : 0.0;
+  double s = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double yi = fma(-c, r1[i], y[i]);
+    y[i] = yi;
+    s = fma(v[i], yi, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// y <- y - (alpha / beta) r2; r1 <- r2; r2 <- y; y <- M^-1 r2; partials of r2 . y
+__global__ void k_pm_b(const double* __restrict__ minv, double* __restrict__ r1, double* __restrict__ r2,
+                       double* __restrict__ y, const double* __restrict__ st, size_t n, double* __restrict__ part) {
+  const double beta = st[KS_BETA];
+  const double c = beta > 0.0 ? st[KS_ALPHA] / beta : 0.0;
+  double s = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double t = fma(-c, r2[i], y[i]);
+    r1[i] = r2[i];
+    r2[i] = t;
+    const double yi = minv[i] * t;
+    y[i] = yi;
+    s = fma(t, yi, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_pm_scalar(double* st) {
+  if (st[KS_DONE] == 0.0 && st[KS_ITER] >= st[KS_MAXIT]) {
+    st[KS_DONE] = 1.0;
+    st[KS_HITMAX] = 1.0;
+    st[KS_CONV_IT] = st[KS_ITER];
+  }
+  if (st[KS_DONE] != 0.0) {  // frozen: later iterations leave the solution unchanged
+    st[KS_PHI] = 0.0;
+    st[KS_INV_GAMMA] = 0.0;
+    st[KS_OLDEPS] = 0.0;
+    st[KS_DELTA] = 0.0;
+    st[KS_INV_BETA] = 0.0;
+    return;
+  }
+  st[KS_ITER] += 1.0;
+  const double alpha = st[KS_ALPHA];
+  const double beta = sqrt(fmax(st[KS_BETA_NEXT2], 0.0));
+  st[KS_OLDB] = st[KS_BETA];
+  st[KS_BETA] = beta;
+  const double cs = st[KS_CS], sn = st[KS_SN], dbar = st[KS_DBAR];
+  st[KS_OLDEPS] = st[KS_EPSLN];
+  st[KS_DELTA] = cs * dbar + sn * alpha;
+  const double gbar = sn * dbar - cs * alpha;
+  st[KS_EPSLN] = sn * beta;
+  st[KS_DBAR] = -cs * beta;
+  double gamma = hypot(gbar, beta);
+  if (!(gamma > 0.0)) gamma = 1e-300;
+  const double cs_new = gbar / gamma, sn_new = beta / gamma;
+  st[KS_CS] = cs_new;
+  st[KS_SN] = sn_new;
+  const double phibar = st[KS_PHIBAR];
+  st[KS_PHI] = cs_new * phibar;
+  st[KS_PHIBAR] = sn_new * phibar;
+  st[KS_RESID] = fabs(sn_new * phibar);
+  st[KS_INV_GAMMA] = 1.0 / gamma;
+  st[KS_INV_BETA] = beta > 0.0 ? 1.0 / beta : 0.0;
+  if (fabs(sn_new * phibar) <= st[KS_TOL] || beta == 0.0) {
+    st[KS_DONE] = 1.0;
+    st[KS_CONV_IT] = st[KS_ITER];
+  }
+}
+
+// w_k = (v - oldeps w_{k-2} - delta w_{k-1}) / gamma, x += phi w_k
+__global__ void k_pm_w(const double* __restrict__ v, double* __restrict__ w, double* __restrict__ wprev,
+                       double* __restrict__ sol, const double* __restrict__ st, size_t n) {
+  const double oe = st[KS_OLDEPS], dl = st[KS_DELTA], ig = st[KS_INV_GAMMA], phi = st[KS_PHI];
+  if (phi == 0.0 && ig == 0.0) return;  // frozen
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double wn = (v[i] - oe * wprev[i] - dl * w[i]) * ig;
+    wprev[i] = w[i];
+    w[i] = wn;
+    sol[i] = fma(phi, wn, sol[i]);
+  }
+}
+
+int pminres_init(const double* b, const double* minv, double* r1, double* r2, double* y, double* w, double* wprev,
+                 double* sol, double* st, double* part, size_t n, double rtol, int maxit, cudaStream_t s) {
+  const int g = red_grid(n);
+  k_pm_init<<<g, kThreads, 0, s>>>(b, minv, r1, r2, y, w, wprev, sol, n, part);
+  k_sum_final<<<1, kThreads, 0, s>>>(part, g, st + KS_BETA_NEXT2);
+  k_pm_init_scalar<<<1, 1, 0, s>>>(st, rtol, maxit);
+  return (int)cudaGetLastError();
+}
+
+int pminres_v(double* v, const double* y, const double* st, size_t n, cudaStream_t s) {
+  k_pm_v<<<red_grid(n), kThreads, 0, s>>>(v, y, st, n);
+  return (int)cudaGetLastError();
+}
+
+int pminres_after_hv(const double* minv, double* r1, double* r2, double* y, const double* v, double* w,
+                     double* wprev, double* sol, double* st, double* part, size_t n, cudaStream_t s) {
+  const int g = red_grid(n);
+  k_pm_a<<<g, kThreads, 0, s>>>(y, r1, v, st, n, part);
+  k_sum_final<<<1, kThreads, 0, s>>>(part, g, st + KS_ALPHA);
+  k_pm_b<<<g, kThreads, 0, s>>>(minv, r1, r2, y, st, n, part);
+  k_sum_final<<<1, kThreads, 0, s>>>(part, g, st + KS_BETA_NEXT2);
+  k_pm_scalar<<<1, 1, 0, s>>>(st);
+  k_pm_w<<<g, kThreads, 0, s>>>(v, w, wprev, sol, st, n);
+  return (int)cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- CG
-__global__ void k_cg_init(const double* __restrict__ b, double* r, double* d, double* sol, double* st, size_t n) {
+__global__ void k_cg_init(const double* __restrict__ b, double* r, double* d, double* sol, double* st, size_t n,
+                          double rtol, int maxit) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     r[i] = b[i];
     d[i] = b[i];
@@ -218,12 +415,30 @@ __global__ void k_cg_init(const double* __restrict__ b, double* r, double* d, do
     st[KS_BETA1] = sqrt(st[KS_BETA_NEXT2]);
     st[KS_RESID] = st[KS_BETA1];
     st[KS_BREAKDOWN] = 0.0;
+    st[KS_TOL] = rtol * st[KS_BETA1];
+    st[KS_ITER] = 0.0;
+    st[KS_DONE] = st[KS_BETA1] > 0.0 ? 0.0 : 1.0;
+    st[KS_CONV_IT] = 0.0;
+    st[KS_MAXIT] = (double)maxit;
+    st[KS_HITMAX] = 0.0;
   }
 }
 
 __global__ void k_cg_a(double* st) {
   const double dHd = st[KS_ALPHA];
+  if (st[KS_DONE] == 0.0 && st[KS_ITER] >= st[KS_MAXIT]) {  // the cap: freeze, not converged
+    st[KS_DONE] = 1.0;
+    st[KS_HITMAX] = 1.0;
+    st[KS_CONV_IT] = st[KS_ITER];
+  }
+  if (st[KS_DONE] != 0.0) {  // converged or broken down earlier: no further update
+    st[KS_A] = 0.0;
+    return;
+  }
+  st[KS_ITER] += 1.0;
   if (!(dHd > 0.0)) {
+    st[KS_DONE] = 1.0;
+    st[KS_CONV_IT] = st[KS_ITER];
     st[KS_BREAKDOWN] = 1.0;
     st[KS_A] = 0.0;
   } else {
@@ -247,10 +462,18 @@ __global__ void k_cg_update(double* __restrict__ sol, double* __restrict__ r, co
 }
 
 __global__ void k_cg_b(double* st) {
+  if (st[KS_DONE] != 0.0) {
+    st[KS_B] = 0.0;
+    return;
+  }
   const double rr_new = st[KS_BETA_NEXT2];
   st[KS_B] = st[KS_RR] > 0.0 ? rr_new / st[KS_RR] : 0.0;
   st[KS_RR] = rr_new;
   st[KS_RESID] = sqrt(fmax(rr_new, 0.0));
+  if (st[KS_RESID] <= st[KS_TOL]) {
+    st[KS_DONE] = 1.0;
+    st[KS_CONV_IT] = st[KS_ITER];
+  }
 }
 
 __global__ void k_cg_dir(double* __restrict__ d, const double* __restrict__ r, const double* __restrict__ st,
@@ -260,12 +483,12 @@ __global__ void k_cg_dir(double* __restrict__ d, const double* __restrict__ r, c
     d[i] = fma(b, d[i], r[i]);
 }
 
-int cg_init(const double* b, double* r, double* d, double* sol, double* st, double* part, size_t n,
-            cudaStream_t s) {
+int cg_init(const double* b, double* r, double* d, double* sol, double* st, double* part, size_t n, double rtol,
+            int maxit, cudaStream_t s) {
   int g = red_grid(n);
   k_dot_part<<<g, kThreads, 0, s>>>(b, b, n, part);
   k_sum_final<<<1, kThreads, 0, s>>>(part, g, st + KS_BETA_NEXT2);
-  k_cg_init<<<g, kThreads, 0, s>>>(b, r, d, sol, st, n);
+  k_cg_init<<<g, kThreads, 0, s>>>(b, r, d, sol, st, n, rtol, maxit);
   return (int)cudaGetLastError();
 }
 

@@ -12,19 +12,36 @@ enum {
   KS_ALPHA = 0, KS_BETA, KS_BETA_NEXT2, KS_BETA_NEXT, KS_BETA1, KS_ETA, KS_C_OLD, KS_S_OLD, KS_C, KS_S,
   KS_R1, KS_R2, KS_INV_RHO, KS_PHI, KS_INV_BETA_NEXT, KS_RESID,
   KS_RR, KS_A, KS_B, KS_BREAKDOWN,
+  KS_TOL,      // absolute residual target (rtol * |b|)
+  KS_ITER,     // iterations executed on the device
+  KS_DONE,     // 1 once the target is met (or a breakdown): later iterations change nothing
+  KS_CONV_IT,  // the iteration at which KS_DONE was set
+  KS_MAXIT,    // iteration cap: reaching it freezes the iterate (not converged)
+  KS_HITMAX,   // 1 when KS_DONE was set by the cap
+  // preconditioned MINRES
+  KS_OLDB, KS_DBAR, KS_EPSLN, KS_OLDEPS, KS_PHIBAR, KS_CS, KS_SN, KS_DELTA, KS_INV_GAMMA, KS_INV_BETA,
   KS_COUNT
 };
 
 int red_grid(size_t n);
 int dot(const double* a, const double* b, size_t n, double* part, double* out, cudaStream_t s);
-int energy_final(const double* pf, const double* pm, int np, double* outF, double* outMin, cudaStream_t s);
+int energy_final(const double* pf, const double* pm, int np, const double* pf2, int np2, double* outF,
+                 double* outMin, cudaStream_t s);
 int step(const double* x, const double* p, double alpha, double* y, size_t n, cudaStream_t s);
 int minres_init(const double* b, double* v, double* vprev, double* w, double* wprev, double* sol, double* st,
-                double* part, size_t n, cudaStream_t s);
+                double* part, size_t n, double rtol, int maxit, cudaStream_t s);
 int minres_after_hv(double* v, double* vprev, double* Av, double* w, double* wprev, double* sol, double* st,
                     double* part, size_t n, cudaStream_t s);
-int cg_init(const double* b, double* r, double* d, double* sol, double* st, double* part, size_t n,
-            cudaStream_t s);
+// Preconditioned MINRES (M^-1 = minv, a diagonal): r1, r2, y, v, w, wprev, sol
+int pminres_init(const double* b, const double* minv, double* r1, double* r2, double* y, double* w, double* wprev,
+                 double* sol, double* st, double* part, size_t n, double rtol, int maxit, cudaStream_t s);
+// before the product: v = y / beta
+int pminres_v(double* v, const double* y, const double* st, size_t n, cudaStream_t s);
+// after the product y = H v
+int pminres_after_hv(const double* minv, double* r1, double* r2, double* y, const double* v, double* w,
+                     double* wprev, double* sol, double* st, double* part, size_t n, cudaStream_t s);
+int cg_init(const double* b, double* r, double* d, double* sol, double* st, double* part, size_t n, double rtol,
+            int maxit, cudaStream_t s);
 int cg_after_hv(double* sol, double* r, double* d, const double* Hd, double* st, double* part, size_t n,
                 cudaStream_t s);
 

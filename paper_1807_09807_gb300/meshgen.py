@@ -146,6 +146,22 @@ def structured(dim: int, order: int, nx) -> tuple:
     return np.ascontiguousarray(x), np.ascontiguousarray(elem_nodes.astype(np.int32)), fixed
 
 
+def tangential_mask(x_lattice_shape: tuple, dim: int) -> np.ndarray:
+    """Fixed-dof mask for boundary nodes that may slide along the axis-parallel
+    faces of the unit square/cube (Section 4.1: boundary motion allowed only
+    on boundaries parallel to the coordinate axes, imposed as Dirichlet
+    conditions on the displacement): component c of a node is fixed iff the
+    node lies on a face normal to axis c. Corners and edges therefore fix
+    every component normal to one of their faces."""
+    Nax = x_lattice_shape
+    idx = np.indices(tuple(reversed(Nax)))          # (z,) y, x index grids
+    comp = list(reversed([i.ravel() for i in idx]))  # x index first
+    fixed = np.zeros((dim, int(np.prod(Nax))), dtype=np.uint8)
+    for c in range(dim):
+        fixed[c] = ((comp[c] == 0) | (comp[c] == Nax[c] - 1)).astype(np.uint8)
+    return fixed
+
+
 def jitter(x: np.ndarray, fixed: np.ndarray, amplitude: float, seed: int) -> np.ndarray:
     """Add U(-amplitude, amplitude) to every free coordinate. The draw index is
     node * d + component (node-major), drawn for every node."""
@@ -193,6 +209,9 @@ def make_mesh(name: str = "c1", seed: int = 1, accept: Optional[Callable[["Mesh"
     dim, order, nx = cfg["dim"], cfg["order"], cfg["nx"]
     x0, en, fixed = structured(dim, order, nx)
     nxt = tuple(nx if np.ndim(nx) else (nx,) * dim)
+    if cfg.get("tangential"):
+        # boundary nodes keep their normal coordinate and slide along the face
+        fixed = tangential_mask(tuple(order * v + 1 for v in nxt), dim)
     if cfg.get("deform") == "sine" and dim == 2:
         # only the x-component; sin(2 pi x) sin(2 pi y) vanishes on the boundary
         x0 = x0.copy()

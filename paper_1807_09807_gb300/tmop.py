@@ -22,6 +22,7 @@ GL, GLL = 0, 1
 W_IDENTITY, W_CONST, W_SCALED, W_PER_QP = 0, 1, 2, 3
 FP64, FP32_MIXED, FP32_BULK = 0, 1, 2
 MINRES, CG = 0, 1
+WT_EQUAL_SIZE, WT_LOCAL_SIZE, WT_INITIAL = 0, 1, 2
 
 
 class TmopError(RuntimeError):
@@ -47,7 +48,7 @@ class NewtonOpts(C.Structure):
     _fields_ = [("max_newton", C.c_int), ("rtol", C.c_double), ("krylov", C.c_int), ("krylov_rtol", C.c_double),
                 ("krylov_maxit", C.c_int), ("alpha_shrink", C.c_double), ("max_halvings", C.c_int),
                 ("f_factor", C.c_double), ("g_factor", C.c_double), ("atol", C.c_double),
-                ("matrix_free", C.c_int)]
+                ("matrix_free", C.c_int), ("precond", C.c_int)]
 
 
 class NewtonReport(C.Structure):
@@ -78,10 +79,15 @@ _SIGNATURES = {
     "tmop_element_min_detA": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_linearize": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_hess_apply_pa": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "tmop_hessian_diagonal": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_sizes": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
                    C.c_int),
     "tmop_energy_noalloc": ([C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(_Quad), C.c_int, C.POINTER(_Targets),
                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "tmop_set_composite": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+    "tmop_set_restricted_movement": ([C.c_void_p, C.c_double, C.c_void_p, C.c_void_p], C.c_int),
+    "tmop_jacobians": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "tmop_set_targets_from_positions": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_destroy": ([C.c_void_p], None),
     "tmop_status_string": ([C.c_int], C.c_char_p),
 }
@@ -240,6 +246,48 @@ class Context:
             raise TmopError(rc, "tmop_hess_apply")
         return y
 
+    def set_composite(self, metric2: int, W2=None, eta2=None):
+        """Second metric term eta_q mu2(A W2^-1) (eq. (4.1)); metric2 = 0 removes it."""
+        W2a = None if W2 is None else np.ascontiguousarray(W2, dtype=np.float64)
+        eta = None if eta2 is None else np.ascontiguousarray(eta2, dtype=np.float64)
+        if metric2 and W2a is None:
+            W2a = np.eye(self.dim)
+        rc = load().tmop_set_composite(self._h, metric2, None if W2a is None else W2a.ctypes.data,
+                                       None if eta is None else eta.ctypes.data)
+        if rc != OK:
+            raise TmopError(rc, "tmop_set_composite")
+
+    def set_restricted_movement(self, delta: float, x_init=None):
+        """Add delta |x - x_init|^2 integrated over the target elements (eq. (4.2))."""
+        if x_init is not None:
+            _check_vec(x_init, self.shape, "x_init")
+        rc = load().tmop_set_restricted_movement(self._h, float(delta), None if x_init is None else _ptr(x_init),
+                                                 _stream())
+        if rc != OK:
+            raise TmopError(rc, "tmop_set_restricted_movement")
+
+    def jacobians(self, x, out=None):
+        """A(x) at every quadrature point, [nelem, Q, dim, dim] (eq. (2.2))."""
+        import torch
+        _check_vec(x, self.shape, "x")
+        J = torch.empty((self.nelem, self.Q, self.dim, self.dim), dtype=torch.float64, device=x.device) \
+            if out is None else out
+        if not (J.is_cuda and J.dtype == torch.float64 and J.is_contiguous()
+                and tuple(J.shape) == (self.nelem, self.Q, self.dim, self.dim)):
+            raise ValueError("out must be a contiguous float64 CUDA tensor [nelem, Q, dim, dim]")
+        rc = load().tmop_jacobians(self._h, _ptr(x), _ptr(J), _stream())
+        if rc != OK:
+            raise TmopError(rc, "tmop_jacobians")
+        return J
+
+    def set_targets_from_positions(self, kind: int, x0):
+        """Targets built from positions x0: WT_EQUAL_SIZE (W2, eq. (3.1)),
+        WT_LOCAL_SIZE (W3, Section 3.1) or WT_INITIAL (W0 = A(x0), Section 4.3.2)."""
+        _check_vec(x0, self.shape, "x0")
+        rc = load().tmop_set_targets_from_positions(self._h, int(kind), _ptr(x0), _stream())
+        if rc != OK:
+            raise TmopError(rc, "tmop_set_targets_from_positions")
+
     def linearize(self, x):
         """Store the per-point Hessians at x (partial assembly)."""
         _check_vec(x, self.shape, "x")
@@ -257,6 +305,16 @@ class Context:
         if rc != OK:
             raise TmopError(rc, "tmop_hess_apply_pa")
         return y
+
+    def hessian_diagonal(self, out=None):
+        """Diagonal of the Hessian stored by the last linearize() (1 at fixed dofs)."""
+        import torch
+        d = torch.empty(self.shape, dtype=torch.float64, device="cuda") if out is None else out
+        _check_vec(d, self.shape, "out")
+        rc = load().tmop_hessian_diagonal(self._h, _ptr(d), _stream())
+        if rc != OK:
+            raise TmopError(rc, "tmop_hessian_diagonal")
+        return d
 
     def element_min_detA(self, x, out=None):
         import torch

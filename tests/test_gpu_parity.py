@@ -8,6 +8,8 @@ Tolerances (FP64 path, relative):
 FP32-mixed path: bounds derived from eps32 = 6e-8 times the conditioning of
 each result; see test_fp32_mixed_bounds.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -84,8 +86,8 @@ def test_fp64_small_configs(tm, name, kw, structured):
     check_all(tm, m, tm.Context.from_mesh(m, structured=structured), orc_for(m))
 
 
-@pytest.mark.parametrize("dim,metric", [(2, 1), (2, 2), (2, 7), (2, 9), (2, 14), (2, 77),
-                                        (3, 1), (3, 14), (3, 302), (3, 303)])
+@pytest.mark.parametrize("dim,metric", [(2, 1), (2, 2), (2, 7), (2, 9), (2, 14), (2, 77), (2, 98),
+                                        (3, 1), (3, 14), (3, 98), (3, 302), (3, 303)])
 def test_fp64_every_metric(tm, dim, metric):
     m = make("c1" if dim == 2 else "c3", 2, nx=4 if dim == 2 else 2)
     scale = 1.0 / 4 if metric in (7, 9, 77) else None      # element size: W2 of eq. (3.1)
@@ -122,6 +124,81 @@ def test_fp64_general_and_per_point_targets(tm, dim):
     check_all(tm, m, tm.Context.from_mesh(m, W_per_qp=Wq), orc_for(m, Wqp=Wq))
 
 
+@pytest.mark.parametrize("dim,structured", [(2, True), (2, False), (3, True), (3, False)])
+def test_jacobians_match_oracle(tm, dim, structured):
+    """A(x) at every quadrature point (eq. (2.2)) against the oracle's."""
+    m = make("c1" if dim == 2 else "c3", 5, nx=(3, 2) if dim == 2 else (2, 3, 1))
+    J = host(tm.Context.from_mesh(m, structured=structured).jacobians(dev(m.x)))
+    Jo = orc_for(m).jacobians(m.x)
+    assert np.abs(J - Jo).max() <= 1e-13 * np.abs(Jo).max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_targets_from_positions_match_oracle(tm, dim):
+    """W2 (eq. (3.1)), W3 (Section 3.1) and W0 (Section 4.3.2) built on the
+    GPU from x0, against the oracle run with the same targets written out
+    from its own Jacobians of x0."""
+    m = make("c1" if dim == 2 else "c3", 6, nx=3 if dim == 2 else 2)
+    Jo = orc_for(m).jacobians(m.x)
+    w, _ = orc_for(m).tables()
+    dets = np.linalg.det(Jo)
+    alpha = float(np.sum(dets * w[None, :])) / m.nelem
+    cases = [
+        (tm.WT_EQUAL_SIZE, dict(W=alpha ** (1.0 / dim) * np.eye(dim))),
+        (tm.WT_LOCAL_SIZE, dict(Wqp=(dets ** (1.0 / dim))[:, :, None, None] * np.eye(dim))),
+        (tm.WT_INITIAL, dict(Wqp=Jo)),
+    ]
+    x1 = m.x + 0.02 / (m.order * 3) * np.random.default_rng(1).uniform(-1, 1, m.x.shape) * (1 - m.fixed)
+    for kind, wk in cases:
+        for metric in ((2, 98) if dim == 2 else (303, 98)):
+            ctx = tm.Context.from_mesh(m, metric=metric)
+            ctx.set_targets_from_positions(kind, dev(m.x))
+            orc = orc_for(m, metric=metric, **wk)
+            check_all(tm, dataclasses.replace(m, x=x1), ctx, orc)
+
+
+def test_replication_metric_on_gpu(tm):
+    """Section 4.3.2 on the GPU: mu98 with W0 = A(x_init) gives F = 0, g = 0
+    at x_init, and Newton from a perturbed mesh returns to x_init; the gamma
+    blend mu98(A W0^-1) + (gamma / (1 - gamma)) mu2(A) converges to the
+    oracle's minimiser."""
+    m = make("c1", 1, nx=4)
+    ctx = tm.Context.from_mesh(m, metric=98)
+    x0 = dev(m.x)
+    ctx.set_targets_from_positions(tm.WT_INITIAL, x0)
+    rc, F, md = ctx.energy(x0)
+    assert rc == tm.OK and abs(F) < 1e-13
+    assert np.abs(host(ctx.gradient(x0))).max() < 1e-12
+    x1 = m.x + 0.05 / (m.order * 4) * np.random.default_rng(2).uniform(-1, 1, m.x.shape) * (1 - m.fixed)
+    x = dev(x1)
+    res = ctx.newton_solve(x, max_newton=20)
+    assert res.status == tm.OK and np.abs(host(x) - m.x).max() < 1e-10
+    gamma = 0.3
+    eta = np.full((m.nelem, m.Q), gamma / (1 - gamma))
+    ctx.set_composite(2, np.eye(2), eta)
+    x = dev(m.x)
+    res = ctx.newton_solve(x, max_newton=30)
+    orc = oracle.Problem(m.dim, m.order, m.elem_nodes, m.nnode, m.fixed, m.nq, 98, wkind=oracle.W_PER_QP,
+                         W=orc_for(m).jacobians(m.x), metric2=2, eta2=eta)
+    rco, xo, _ = orc.newton(m.x, max_newton=30)
+    assert res.status == tm.OK and rco == oracle.OK
+    assert np.abs(host(x) - xo).max() < 1e-10 * np.abs(xo).max()
+    assert np.linalg.norm(xo - m.x) > 1e-3
+
+
+def test_targets_from_inverted_positions_are_rejected(tm):
+    m = make("c1", 1, nx=3)
+    ctx = tm.Context.from_mesh(m, metric=98)
+    xb = m.x.copy()
+    xb[0] = -xb[0]                         # mirrored mesh: det A < 0 everywhere
+    for kind in (tm.WT_LOCAL_SIZE, tm.WT_INITIAL, tm.WT_EQUAL_SIZE):
+        with pytest.raises(tm.TmopError) as ei:
+            ctx.set_targets_from_positions(kind, dev(xb))
+        assert ei.value.status == tm.ERR_INVERTED
+    # targets unchanged: still W = I
+    check_all(tm, m, ctx, orc_for(m, metric=98))
+
+
 def test_fp64_ragged_and_single_element(tm):
     # one element, and a 5x3 (non-square, element count not a multiple of a block)
     for nx in [1, (5, 3)]:
@@ -129,6 +206,20 @@ def test_fp64_ragged_and_single_element(tm):
         check_all(tm, m, tm.Context.from_mesh(m), orc_for(m))
     m = make("c3", 1, nx=(3, 2, 1))
     check_all(tm, m, tm.Context.from_mesh(m), orc_for(m))
+
+
+def test_fp64_tangential_relaxation(tm):
+    """Per-component fixed mask: boundary nodes slide along axis-parallel faces
+    (Section 4.1); parity, and Newton keeps them on their faces."""
+    for name, kw in [("c1", dict(nx=4)), ("c3", dict(nx=3))]:
+        m = make(name, 3, tangential=True, **kw)
+        ctx = tm.Context.from_mesh(m)
+        check_all(tm, m, ctx, orc_for(m))
+        x = dev(m.x)
+        r = ctx.newton_solve(x, max_newton=20)
+        assert r.status == tm.OK
+        xf = host(x)
+        assert np.array_equal(xf[m.fixed == 1], m.x[m.fixed == 1])
 
 
 def test_fp64_no_fixed_dofs(tm):
@@ -203,6 +294,74 @@ def test_deterministic_energy(tm):
     assert len(vals) == 1
 
 
+# ---------------------------------------------------------------- composite metrics
+@pytest.mark.parametrize("dim,ma,mb,prec", [(2, 1, 77, "fp64"), (2, 2, 7, "fp64"), (3, 303, 14, "fp64"),
+                                            (3, 303, 302, "fp64"), (3, 303, 14, "fp32")])
+def test_composite_metric_matches_oracle(tm, dim, ma, mb, prec):
+    """eq. (4.1): mu_a(A W^-1) + eta_q mu_b(A W2^-1) with per-point weights and
+    a non-symmetric W2: energy, gradient, recompute and partially assembled
+    Hessian actions against the oracle."""
+    rng = np.random.default_rng(dim * 100 + mb)
+    m = make("c1" if dim == 2 else "c3", 4, nx=4 if dim == 2 else 3)
+    W2 = (np.eye(dim) + 0.15 * rng.standard_normal((dim, dim))) * 0.3
+    if np.linalg.det(W2) < 0:
+        W2[:, 0] *= -1
+    eta = 0.5 + rng.random((m.nelem, m.Q))
+    ctx = tm.Context.from_mesh(m, metric=ma, precision=tm.FP64 if prec == "fp64" else tm.FP32_BULK)
+    ctx.set_composite(mb, W2, eta)
+    orc = oracle.Problem(m.dim, m.order, m.elem_nodes, m.nnode, m.fixed, m.nq, ma, metric2=mb, W2=W2, eta2=eta)
+    tol_F, tol_v = (RTOL, RTOL) if prec == "fp64" else (1e-6, 1e-5)
+    check_all(tm, m, ctx, orc, rtol_F=tol_F, rtol_vec=tol_v)
+    x = dev(m.x)
+    ctx.linearize(x)
+    v = rng.standard_normal(m.x.shape)
+    assert rel(host(ctx.hess_apply_pa(dev(v))), orc.hess_apply(m.x, v)) <= tol_v
+    ctx.set_composite(0)
+    assert abs(ctx.energy(x)[1] - _single(m, ma).energy(m.x)[1]) <= tol_F * _single(m, ma).energy(m.x)[1]
+
+
+def _single(m, metric):
+    return oracle.Problem(m.dim, m.order, m.elem_nodes, m.nnode, m.fixed, m.nq, metric)
+
+
+# ---------------------------------------------------------------- restricted movement
+@pytest.mark.parametrize("name,kw,metric,prec", [("c1", dict(nx=4), 2, "fp64"), ("c2", dict(nx=5), 2, "fp64"),
+                                                 ("c3", dict(nx=3), 303, "fp64"), ("c4", dict(nx=2), 303, "fp64"),
+                                                 ("c3", dict(nx=3), 303, "mixed")])
+def test_restricted_movement_matches_oracle(tm, name, kw, metric, prec):
+    """eq. (4.2): + sum_E int delta |x - x_init|^2: energy, gradient, recompute
+    and partially assembled Hessian actions against the oracle, and a Newton
+    solve that stays closer to x_init than without the term."""
+    m = make(name, 2, **kw)
+    rng = np.random.default_rng(7)
+    x_init = m.x + 0.02 / (m.order * m.nx[0]) * rng.standard_normal(m.x.shape) * (1 - m.fixed)
+    delta = 50.0
+    pf = tm.FP64 if prec == "fp64" else tm.FP32_MIXED
+    ctx = tm.Context.from_mesh(m, metric=metric, precision=pf)
+    ctx.set_restricted_movement(delta, dev(x_init))
+    orc = oracle.Problem(m.dim, m.order, m.elem_nodes, m.nnode, m.fixed, m.nq, metric, delta=delta, x_init=x_init)
+    tol_v = RTOL if prec == "fp64" else 1e-5
+    x = dev(m.x)
+    rc, F, _ = ctx.energy(x)
+    assert abs(F - orc.energy(m.x)[1]) <= RTOL * abs(F)
+    assert rel(host(ctx.gradient(x)), orc.gradient(m.x)) <= RTOL
+    v = rng.standard_normal(m.x.shape)
+    yo = orc.hess_apply(m.x, v)
+    assert rel(host(ctx.hess_apply(x, dev(v))), yo) <= tol_v
+    ctx.linearize(x)
+    assert rel(host(ctx.hess_apply_pa(dev(v))), yo) <= tol_v
+    if name == "c1":
+        xa = dev(m.x)
+        r = ctx.newton_solve(xa, max_newton=30)
+        assert r.status == tm.OK
+        free_ctx = tm.Context.from_mesh(m, metric=metric)
+        xb = dev(m.x)
+        assert free_ctx.newton_solve(xb, max_newton=30).status == tm.OK
+        assert np.linalg.norm(host(xa) - x_init) < np.linalg.norm(host(xb) - x_init)
+    ctx.set_restricted_movement(0.0)
+    assert abs(ctx.energy(x)[1] - _single(m, metric).energy(m.x)[1]) <= RTOL * F
+
+
 # ---------------------------------------------------------------- partial assembly
 @pytest.mark.parametrize("name,kw,metric", [("c1", dict(nx=5), 2), ("c1", dict(nx=4), 77), ("c2", dict(nx=6), 9),
                                             ("c3", dict(nx=3), 303), ("c3", dict(nx=3), 302), ("c4", dict(nx=2), 303),
@@ -243,6 +402,63 @@ def test_partial_assembly_requires_linearize(tm):
     ctx = tm.Context.from_mesh(m)
     with pytest.raises(tm.TmopError):
         ctx.hess_apply_pa(dev(m.x))
+
+
+# ---------------------------------------------------------------- Jacobi preconditioning
+@pytest.mark.parametrize("name,kw,extras", [("c1", dict(nx=4), ""), ("c3", dict(nx=2), ""),
+                                            ("c1", dict(nx=3), "composite+delta"), ("c3", dict(nx=2), "fp32")])
+def test_hessian_diagonal_matches_oracle(tm, name, kw, extras):
+    """Diagonal of the partially assembled Hessian against the oracle's
+    Hessian action on every unit vector (brute force), 1 at fixed dofs."""
+    m = make(name, 5, **kw)
+    prec = tm.FP32_MIXED if extras == "fp32" else tm.FP64
+    ctx = tm.Context.from_mesh(m, precision=prec)
+    okw = {}
+    if "composite" in extras:
+        W2 = np.eye(m.dim) * 0.4
+        eta = np.full((m.nelem, m.Q), 0.7)
+        ctx.set_composite(77 if m.dim == 2 else 14, W2, eta)
+        okw.update(metric2=77 if m.dim == 2 else 14, W2=W2, eta2=eta)
+    if "delta" in extras:
+        ctx.set_restricted_movement(3.0, dev(m.x_ideal))
+        okw.update(delta=3.0, x_init=m.x_ideal)
+    orc = oracle.Problem(m.dim, m.order, m.elem_nodes, m.nnode, m.fixed, m.nq, m.metric, **okw)
+    x = dev(m.x)
+    ctx.linearize(x)
+    d = host(ctx.hessian_diagonal())
+    ref = np.ones_like(m.x)
+    for a, i in np.argwhere(m.fixed == 0):
+        e = np.zeros_like(m.x)
+        e[a, i] = 1.0
+        ref[a, i] = orc.hess_apply(m.x, e)[a, i]
+    tol = RTOL if prec == tm.FP64 else 1e-5
+    assert np.abs(d - ref).max() <= tol * np.abs(ref).max()
+
+
+def test_jacobi_minres_solves_the_same_system(tm):
+    m = make("c2", 1, nx=12)
+    ctx = tm.Context.from_mesh(m)
+    orc = orc_for(m)
+    b = orc.gradient(m.x)
+    po, _ = orc.minres(m.x, b, rtol=1e-13, maxit=3000)
+    p1, it1 = ctx.krylov_solve(dev(m.x), dev(b), krylov_rtol=1e-12, krylov_maxit=3000)
+    p2, it2 = ctx.krylov_solve(dev(m.x), dev(b), krylov_rtol=1e-12, krylov_maxit=3000, precond=1)
+    assert it1 > 0 and it2 > 0
+    assert rel(host(p1), po) <= 1e-9 and rel(host(p2), po) <= 1e-9
+    assert it2 < it1
+
+
+def test_jacobi_newton_converges_with_fewer_iterations(tm):
+    m = make("c3", 2, nx=8)
+    ctx = tm.Context.from_mesh(m)
+    xa, xb = dev(m.x), dev(m.x)
+    ra = ctx.newton_solve(xa, max_newton=20)
+    rb = ctx.newton_solve(xb, max_newton=20, precond=1)
+    assert ra.status == tm.OK and rb.status == tm.OK
+    F0 = ctx.energy(dev(m.x))[1]
+    assert abs(ra.report["F"] - rb.report["F"]) <= 1e-12 * F0
+    assert rb.report["krylov_iterations"] < ra.report["krylov_iterations"]
+    assert np.abs(host(xa) - host(xb)).max() < 1e-9 / 16
 
 
 # ---------------------------------------------------------------- solvers

@@ -76,8 +76,8 @@ def test_lagrange_basis(k):
 
 
 # ---------------------------------------------------------------- metrics
-METRICS_2D = [1, 2, 7, 9, 14, 77]
-METRICS_3D = [1, 14, 302, 303]
+METRICS_2D = [1, 2, 7, 9, 14, 77, 98]
+METRICS_3D = [1, 14, 98, 302, 303]
 
 
 def _definition(mid, T):
@@ -94,6 +94,7 @@ def _definition(mid, T):
         9: tau * np.sum((T - Tinv.T) ** 2),
         14: np.sum((T - I) ** 2),
         77: 0.5 * (tau - 1 / tau) ** 2,
+        98: np.sum((T - I) ** 2) / tau,
         302: n2 * np.sum(Tinv ** 2) / 9 - 1,
         303: n2 / (3 * np.cbrt(tau) ** 2) - 1,
     }[mid]
@@ -140,7 +141,8 @@ def test_metric_derivatives_against_central_fd(d, mid):
         np.testing.assert_allclose(dP, (Pp - Pm) / (2 * h), rtol=1e-6, atol=1e-7 * np.abs(dP).max())
 
 
-@pytest.mark.parametrize("d,mid", [(2, 2), (2, 7), (2, 9), (2, 14), (2, 77), (3, 14), (3, 302), (3, 303)])
+@pytest.mark.parametrize("d,mid", [(2, 2), (2, 7), (2, 9), (2, 14), (2, 77), (2, 98), (3, 14), (3, 98), (3, 302),
+                                   (3, 303)])
 def test_metric_zero_at_identity(d, mid):
     rc, mu, P, _ = oracle.metric(mid, np.eye(d))
     assert abs(mu) < 1e-15 and np.abs(P).max() < 1e-15
@@ -160,11 +162,25 @@ def test_metric_invariances(d, mid, scale_inv):
 
 def test_barrier_metrics_reject_inverted():
     T = np.array([[1.0, 0.0], [0.0, -0.5]])
-    for mid in (2, 7, 9, 77):
+    for mid in (2, 7, 9, 77, 98):
         assert oracle.metric(mid, T)[0] == oracle.ERR_INVERTED
     T3 = np.diag([1.0, 1.0, -1.0])
-    for mid in (302, 303):
+    for mid in (98, 302, 303):
         assert oracle.metric(mid, T3)[0] == oracle.ERR_INVERTED
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_mu98_closed_forms(d):
+    """mu98 (Section 4.3.2) on T = s I is d (s - 1)^2 / s^d; it is not
+    rotation invariant: on a rotation R by angle t (2D) it is |R - I|^2 =
+    2 d_rot (1 - cos t) with det R = 1."""
+    for s_ in (0.5, 1.0, 1.7):
+        mu = oracle.metric(98, s_ * np.eye(d))[1]
+        assert abs(mu - d * (s_ - 1) ** 2 / s_ ** d) < 1e-14
+    t = 0.3
+    R = np.eye(d)
+    R[:2, :2] = [[np.cos(t), -np.sin(t)], [np.sin(t), np.cos(t)]]
+    assert abs(oracle.metric(98, R)[1] - 4 * (1 - np.cos(t))) < 1e-14
 
 
 # ---------------------------------------------------------------- mesh level
@@ -434,3 +450,173 @@ def test_per_point_target_fd(dim, mid):
         xp = xj.copy(); xp[a, i] += h
         xm = xj.copy(); xm[a, i] -= h
         assert abs((p.energy(xp)[1] - p.energy(xm)[1]) / (2 * h) - g[a, i]) < 1e-6 * np.abs(g).max()
+
+
+def test_tangential_relaxation_on_axis_parallel_boundaries():
+    """Section 4.1: boundary nodes slide along axis-parallel faces (only the
+    normal displacement is fixed). Boundary nodes stay on their faces exactly,
+    the gradient matches FD on the sliding dofs, and Newton still reaches the
+    uniform grid (F* = 0)."""
+    m = mg.make_mesh("c1", 3, nx=4, tangential=True)
+    p = _problem(m)
+    x0 = m.x
+    on_face = m.fixed == 1
+    assert np.array_equal(x0[on_face], m.x_ideal[on_face])           # normal coordinates untouched
+    slide = (m.fixed == 0) & (np.abs(x0 - m.x_ideal) > 0)
+    g = p.gradient(x0)
+    h = 1e-6
+    for a, i in np.argwhere(slide)[:10]:
+        xp = x0.copy(); xp[a, i] += h
+        xm = x0.copy(); xm[a, i] -= h
+        assert abs((p.energy(xp)[1] - p.energy(xm)[1]) / (2 * h) - g[a, i]) < 1e-6 * np.abs(g).max()
+    rc, x, hist = p.newton(x0, max_newton=20)
+    assert rc == oracle.OK
+    assert np.array_equal(x[on_face], x0[on_face])
+    assert np.abs(x - m.x_ideal).max() < 1e-11
+
+
+@pytest.mark.parametrize("dim,ma,mb", [(2, 1, 77), (2, 2, 7), (3, 303, 14)])
+def test_composite_metric(dim, ma, mb):
+    """Section 4.2, eq. (4.1): mu = mu_a(A W^-1) + eta_q mu_b(A W2^-1), with
+    point weights eta (the paper's ICF example combines mu1/W1 with
+    eta(r) mu77/W2). F against the literal sum evaluated with numpy.linalg at
+    the oracle's own Jacobians; gradient and Hessian action against FD."""
+    m = mg.make_mesh("c1" if dim == 2 else "c3", 2, nx=3 if dim == 2 else 2)
+    W2 = (np.eye(dim) + 0.2 * rng.standard_normal((dim, dim))) * (0.7 / 3)   # non-symmetric
+    if np.linalg.det(W2) < 0:
+        W2[:, 0] *= -1
+    eta = 0.5 + rng.random((m.nelem, m.Q))
+    p = oracle.Problem(m.dim, m.order, m.elem_nodes, m.nnode, m.fixed, m.nq, ma, metric2=mb, W2=W2, eta2=eta)
+    pa = _problem(m, metric=ma)
+    w, _ = pa.tables()
+    J = pa.jacobians(m.x)
+    W2i = np.linalg.inv(W2)
+    Fdef = sum(w[q] * (_definition(ma, J[e, q]) + np.linalg.det(W2) * eta[e, q] * _definition(mb, J[e, q] @ W2i))
+               for e in range(m.nelem) for q in range(m.Q))
+    rc, F, _ = p.energy(m.x)
+    assert rc == 0 and abs(F - Fdef) < 1e-12 * abs(Fdef)
+    g = p.gradient(m.x)
+    h = 1e-6
+    free = np.argwhere(m.fixed == 0)
+    for a, i in free[rng.choice(len(free), size=min(12, len(free)), replace=False)]:
+        xp = m.x.copy(); xp[a, i] += h
+        xm = m.x.copy(); xm[a, i] -= h
+        assert abs((p.energy(xp)[1] - p.energy(xm)[1]) / (2 * h) - g[a, i]) < 1e-6 * np.abs(g).max()
+    v = rng.standard_normal(m.x.shape) * (1 - m.fixed)
+    Hv = p.hess_apply(m.x, v)
+    fd = (p.gradient(m.x + h * v) - p.gradient(m.x - h * v)) / (2 * h)
+    assert np.linalg.norm(Hv - fd) < 1e-6 * np.linalg.norm(Hv)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_replication_metric_keeps_the_initial_mesh(dim):
+    """Section 4.3.2: with the per-point target W0 = A(x_init), mu98(A W0^-1)
+    = |T0 - I|^2 / det T0 vanishes exactly at x_init and is positive
+    elsewhere, so x_init is the minimiser: F = 0 and g = 0 there, and Newton
+    from a perturbed mesh goes back to it."""
+    m = mg.make_mesh("c1" if dim == 2 else "c3", 1, nx=4 if dim == 2 else 2)
+    A0 = _problem(m).jacobians(m.x)
+    p = oracle.Problem(m.dim, m.order, m.elem_nodes, m.nnode, m.fixed, m.nq, 98, wkind=oracle.W_PER_QP, W=A0)
+    rc, F, _ = p.energy(m.x)
+    assert rc == 0 and abs(F) < 1e-13
+    assert np.abs(p.gradient(m.x)).max() < 1e-12
+    x1 = m.x + 0.05 / (m.order * 4) * rng.uniform(-1, 1, m.x.shape) * (1 - m.fixed)
+    assert p.energy(x1)[1] > 1e-6
+    rc, x, hist = p.newton(x1, max_newton=20)
+    assert rc == 0 and np.abs(x - m.x).max() < 1e-10, (rc, np.abs(x - m.x).max(), hist[:, 0])
+
+
+def test_gamma_blend_restricts_movement():
+    """Section 4.3.2 second restricted-movement algorithm: mu' = (1 - gamma)
+    mu98(A W0^-1) + gamma mu2(A), W0 = A(x_init). Written as eq. (4.1) with
+    mu98 first and eta2 = gamma / (1 - gamma) (the same objective times
+    1 / (1 - gamma), so the same minimiser). The optimised mesh moves further
+    from x_init as gamma grows, and the unrestricted (mu2 alone) optimum moves
+    furthest."""
+    m = mg.make_mesh("c1", 1, nx=4)
+    A0 = _problem(m).jacobians(m.x)
+    moved = []
+    for gamma in (0.05, 0.3, 0.7):
+        eta = np.full((m.nelem, m.Q), gamma / (1 - gamma))
+        p = oracle.Problem(m.dim, m.order, m.elem_nodes, m.nnode, m.fixed, m.nq, 98, wkind=oracle.W_PER_QP,
+                           W=A0, metric2=2, eta2=eta)
+        rc, x, _ = p.newton(m.x, max_newton=30)
+        assert rc == 0
+        moved.append(np.linalg.norm(x - m.x))
+    rc, x, _ = _problem(m, metric=2).newton(m.x, max_newton=30)
+    assert rc == 0
+    moved.append(np.linalg.norm(x - m.x))
+    assert moved[0] > 0 and all(a < b for a, b in zip(moved, moved[1:])), moved
+
+
+def _textbook_mass(dim, order, nx):
+    """Reference-element Q_k mass matrix M_ij = int phi_i phi_j assembled over
+    the grid (exact 1D polynomial integrals, Kronecker products)."""
+    nodes, _ = oracle.gauss_lobatto(order + 1)
+    n = order + 1
+    polys = [np.polynomial.Polynomial.fit(nodes, np.eye(n)[i], order).convert() for i in range(n)]
+    M1 = np.array([[((polys[i] * polys[j]).integ()(1.0) - (polys[i] * polys[j]).integ()(0.0)) for j in range(n)]
+                   for i in range(n)])
+    Me = np.kron(M1, M1) if dim == 2 else np.kron(np.kron(M1, M1), M1)
+    _, en, _ = mg.structured(dim, order, nx)
+    N = en.max() + 1
+    M = np.zeros((N, N))
+    for e in range(en.shape[0]):
+        M[np.ix_(en[e], en[e])] += Me
+    return M
+
+
+def test_restricted_movement_closed_forms():
+    """Section 4.3.1, eq. (4.2): adds sum_E int delta |x - x_init|^2 dx_t.
+    (i) a rigid translation c of a free mesh adds delta |c|^2 N_E (the metric
+    part is translation invariant); (ii) with mu14 the Hessian is
+    2 (K + delta M) with the textbook stiffness K and mass M; (iii) FD."""
+    delta = 3.7
+    for dim, order, nq, nx in [(2, 2, 4, 3), (3, 2, 4, 2)]:
+        x0, en, fixed = mg.structured(dim, order, nx)
+        xi = x0 + 0.01 / nx * rng.standard_normal(x0.shape)
+        mid = 2 if dim == 2 else 303
+        p0 = oracle.Problem(dim, order, en, x0.shape[1], None, nq, mid)
+        pd = oracle.Problem(dim, order, en, x0.shape[1], None, nq, mid, delta=delta, x_init=xi)
+        c = rng.standard_normal((dim, 1)) * 0.05
+        F0 = p0.energy(xi)[1]
+        Fd = pd.energy(xi + c)[1]
+        assert abs(Fd - F0 - delta * np.sum(c * c) * en.shape[0]) < 1e-12 * max(1.0, Fd)
+        # (ii) mu14
+        K, _, _, _ = _textbook_stiffness(dim, order, nx)
+        M = _textbook_mass(dim, order, nx)
+        p14 = oracle.Problem(dim, order, en, x0.shape[1], fixed, nq, 14, delta=delta, x_init=xi)
+        v = rng.standard_normal(x0.shape) * (1 - fixed)
+        y = p14.hess_apply(xi, v)
+        ref = 2.0 * ((K + delta * M) @ v.T).T * (1 - fixed)
+        assert np.abs(y - ref).max() < 1e-12 * np.abs(ref).max()
+        # (iii) gradient and Hessian action against FD
+        pf = oracle.Problem(dim, order, en, x0.shape[1], fixed, nq, mid, delta=delta, x_init=xi)
+        x = xi + 0.02 / nx * rng.standard_normal(x0.shape) * (1 - fixed)
+        g = pf.gradient(x)
+        h = 1e-6
+        free = np.argwhere(fixed == 0)
+        for a, i in free[rng.choice(len(free), size=min(10, len(free)), replace=False)]:
+            xp = x.copy(); xp[a, i] += h
+            xm = x.copy(); xm[a, i] -= h
+            assert abs((pf.energy(xp)[1] - pf.energy(xm)[1]) / (2 * h) - g[a, i]) < 1e-6 * np.abs(g).max()
+        Hv = pf.hess_apply(x, v)
+        fd = (pf.gradient(x + h * v) - pf.gradient(x - h * v)) / (2 * h)
+        assert np.linalg.norm(Hv - fd) < 1e-6 * np.linalg.norm(Hv)
+
+
+def test_restricted_movement_scaled_target_and_masking():
+    """The penalty is integrated over the target element (weights w_q det W):
+    with W = s I a rigid translation adds delta |c|^2 N_E s^d; and fixed
+    entries of a Hessian-action direction are ignored by the penalty too."""
+    dim, order, nq, nx, s, delta = 2, 3, 5, 3, 0.4, 2.5
+    x0, en, fixed = mg.structured(dim, order, nx)
+    xi = x0 + 0.01 / nx * rng.standard_normal(x0.shape)
+    W = np.eye(dim) * s
+    p0 = oracle.Problem(dim, order, en, x0.shape[1], None, nq, 2, wkind=oracle.W_CONST, W=W)
+    pd = oracle.Problem(dim, order, en, x0.shape[1], None, nq, 2, wkind=oracle.W_CONST, W=W, delta=delta, x_init=xi)
+    c = np.array([[0.03], [-0.02]])
+    assert abs(pd.energy(xi + c)[1] - p0.energy(xi)[1] - delta * np.sum(c * c) * en.shape[0] * s ** dim) < 1e-12
+    pf = oracle.Problem(dim, order, en, x0.shape[1], fixed, nq, 2, delta=delta, x_init=xi)
+    v = rng.standard_normal(x0.shape)
+    np.testing.assert_array_equal(pf.hess_apply(xi, v), pf.hess_apply(xi, v * (1 - fixed)))

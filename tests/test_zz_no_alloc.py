@@ -72,12 +72,13 @@ def test_noalloc_smaller_call_after_larger_and_scaled_target(tm):
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch(tm):
-    # 400 x 400 quads need 40 000 blocks of partials > 32 768: refused on the
-    # host before anything is launched
+    # 1024 x 1024 order-1 quads need at least 131 072 blocks of partials (at
+    # most 8 elements per block) > 32 768: refused on the host before anything
+    # is launched
     F = torch.empty((), dtype=torch.float64, device="cuda")
     md = torch.empty((), dtype=torch.float64, device="cuda")
-    x = torch.zeros((2, (2 * 400 + 1) ** 2), dtype=torch.float64, device="cuda")
-    rc = tm.energy_noalloc(2, 2, [400, 400], 4, 2, x, F, md)
+    x = torch.zeros((2, 1025 * 1025), dtype=torch.float64, device="cuda")
+    rc = tm.energy_noalloc(2, 1, [1024, 1024], 2, 2, x, F, md)
     assert rc == tm.ERR_CAPACITY
     assert "scratch" in tm.status_string(rc)
-    assert tm.energy_noalloc(2, 2, [4, 4], 4, 2, x[:, :81].contiguous(), F, md, target_kind=tm.W_PER_QP) == tm.ERR_ARG
+    assert tm.energy_noalloc(2, 1, [4, 4], 2, 2, x[:, :25].contiguous(), F, md, target_kind=tm.W_PER_QP) == tm.ERR_ARG
