@@ -78,12 +78,15 @@ def grad_flops_per_element(dim, n, q, metric):
     return 2 * (fwd + adj) + (METRIC_DP_FLOPS[metric] // 2) * q ** dim
 
 
-def kernel_src_hash() -> str:
-    """Hash of the element-kernel sources; ncu counters are reused only when
-    it matches the hash recorded with them."""
+ELEM_SOURCES = ("tmop_device.cuh", "tmop_element.cuh", "tmop_kparams.h")
+
+
+def kernel_src_hash(files=ELEM_SOURCES) -> str:
+    """Hash of a kernel's sources; ncu counters are reused only when it
+    matches the hash recorded with them."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("tmop_device.cuh", "tmop_element.cuh", "tmop_kparams.h"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1807_09807_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -451,12 +454,12 @@ def measure_pa(tm, m, x, v, y, flush, stream, args):
         lin_ms = _event_ms(lambda: c.linearize(x), 2, stream, flush)
         hv_ms = _event_ms(lambda: c.hess_apply_pa(v, out=y), max(3, min(args.steps, 10)), stream, flush)
         dd = m.dim * m.dim
-        ns = dd * (dd + 1) // 2
-        elt = 8 if pf == tm.FP64 else 4
-        nbytes = m.n_qp * ns * elt + 2 * x.numel() * 8 + x.numel() * 8   # Hessians + v read + y memset/write
+        ns, _, elt = c.pa_layout()     # packed Hessian entries or compact record values per point
+        compact = ns != dd * (dd + 1) // 2
+        nbytes = m.n_qp * ns * elt + 2 * x.numel() * 8 + x.numel() * 8   # stored values + v read + y memset/write
         n = m.order + 1
         fwd, adj = contraction_fmas(m.dim, n, m.nq, m.dim)
-        flops = m.nelem * (2 * (fwd + adj) + 2 * dd * dd * m.Q)
+        flops = m.nelem * (2 * (fwd + adj) + 2 * dd * dd * m.Q)   # contractions + the d^2 x d^2 product
         ent = {"linearize_ms": lin_ms, "hess_pa_ms": hv_ms, "bytes_per_launch": nbytes,
                "achieved_GBps": nbytes / (hv_ms * 1e-3) / 1e9, "achieved_TFLOPs": flops / (hv_ms * 1e-3) / 1e12}
         if pf == tm.FP64:
@@ -466,7 +469,16 @@ def measure_pa(tm, m, x, v, y, flush, stream, args):
             hbm = peaks.get("hbm_gbs", 6800.0)
             ent["roofline"] = {"bound": "hbm", "achieved": ent["achieved_GBps"], "peak": hbm, "unit": "GB/s",
                                "frac": ent["achieved_GBps"] / hbm,
-                               "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+                               "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                               "kernel": f"elem_kernel<{m.dim},{n},{m.nq},float,"
+                                         f"{'OP_HESS_PA_C' if compact else 'OP_HESS_PA'}>", "traffic": None}
+            ent["values_per_point"] = ns
+            tfile = os.path.join(ROOT, "profiles", "traffic.json")
+            if os.path.exists(tfile):
+                with open(tfile) as f:
+                    tr = json.load(f).get(f"{args.workload}:pa_fp32")
+                if tr and tr.get("kernel_src_sha256") == kernel_src_hash():
+                    ent["roofline"]["traffic"] = tr["dram_bytes_per_launch"]
         out[name] = ent
         c.close()
     return out

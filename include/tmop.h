@@ -142,13 +142,26 @@ int tmop_hess_apply(tmop_ctx* ctx, const double* x, const double* v, double* y, 
  *   H_q = w_q det W (d^2mu/dT^2 composed with W^-1 on both sides)
  * (dim^2 (dim^2 + 1) / 2 values per point, FP64 under TMOP_FP64 and FP32
  * under the FP32 forms) in the context (allocated on first use:
- * nelem * Q * 45 * 8 bytes for order-k hexes in FP64). Asynchronous. */
+ * nelem * Q * 45 * 8 bytes for order-k hexes in FP64). A 3D FP32 context
+ * whose metric is written in |T|^2 and det T (1, 14, 303), with a constant
+ * target and no second term, stores instead 14 values per point from which
+ * the product rebuilds H_q (see tmop_pa_layout). Asynchronous. */
 int tmop_linearize(tmop_ctx* ctx, const double* x, void* stream);
 
 /* y = H(x) v with the Hessians stored by the last tmop_linearize(x): same
  * result as tmop_hess_apply(ctx, x, v, y) up to rounding, without reading x.
  * TMOP_ERR_ARG if the context holds no linearisation. Asynchronous. */
 int tmop_hess_apply_pa(tmop_ctx* ctx, const double* v, double* y, void* stream);
+
+/* Layout of the stored linearisation: values per quadrature point (the
+ * packed upper triangle of the d^2 x d^2 A-space Hessian, 10 in 2D and 45 in
+ * 3D; or, for a 3D FP32 context with an (|T|^2, det T) metric, a constant
+ * target and no second term, the 14-value record T, w det W (mu_1, mu_t,
+ * mu_11, mu_1t, mu_tt) the product rebuilds the Hessian from), the element
+ * stride in values (each element's block [value][point], padded to 16 bytes)
+ * and the bytes per value (8 FP64, 4 FP32). Any pointer may be NULL.
+ * Errors: TMOP_ERR_ARG if nothing is stored. */
+int tmop_pa_layout(const tmop_ctx* ctx, int* values_per_point, int* stride, int* elt_bytes);
 
 /* Diagonal of the Hessian stored by the last tmop_linearize (including the
  * restricted-movement term), 1 at fixed dofs: out DEVICE [dim][nnode] FP64.
@@ -287,6 +300,14 @@ int tmop_jacobians(tmop_ctx* ctx, const double* x, double* J, void* stream);
  * (per-point kinds) or the measure is not positive (targets unchanged),
  * TMOP_ERR_ARG, TMOP_ERR_CUDA. */
 int tmop_set_targets_from_positions(tmop_ctx* ctx, int kind, const double* x0, void* stream);
+
+/* Diagnostic: the FP64 -> FP32 -> FP64 conversions the FP32 kernels apply
+ * to gathered values and to their contributions (integer-pipe
+ * implementations: round to nearest even, results below 2^-126 in magnitude
+ * become a signed zero, FP32 -> FP64 exact). in DEVICE [n] FP64; f32 DEVICE
+ * [n] receives the converted values, back DEVICE [n] FP64 their exact
+ * widening. Asynchronous. Errors: TMOP_ERR_ARG, TMOP_ERR_CUDA. */
+int tmop_selftest_convert(const double* in, float* f32, double* back, size_t n, void* stream);
 
 /* Sizes of a context: Q (points per element), ndof = dim * nnode. */
 int tmop_sizes(const tmop_ctx* ctx, int* dim, int* nelem, int* nnode, int* Q);

@@ -185,6 +185,7 @@ struct tmop_ctx {
   int nvec = 0;
   void* d_pa = nullptr;       // packed per-point Hessians (partial assembly), allocated on first use
   bool pa_valid = false;      // d_pa holds the linearisation of some x
+  bool pa_compact = false;    // ... as compact records (OP_LINEARIZE_C / OP_HESS_PA_C)
   double* d_eta2 = nullptr;   // per-point weights of the composite second term
   double delta = 0.0;         // restricted-movement weight (0: term off)
   double* d_x_init = nullptr; // its reference positions [d][nnode]
@@ -251,7 +252,10 @@ int launch_op(tmop_ctx* c, int op, const double* x, const double* v, double* y, 
   p.pa = c->d_pa;
   if (op == OP_GRADIENT || op == OP_HESS || op == OP_HESS_PA)
     CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * c->ndof, s));
-  if (c->ent[op]->launch(p, c->grid[op], s) != 0) return TMOP_ERR_CUDA;
+  int kop = op;  // the stored linearisation decides which form of the pair runs
+  if (c->pa_compact && op == OP_LINEARIZE) kop = OP_LINEARIZE_C;
+  if (c->pa_compact && op == OP_HESS_PA) kop = OP_HESS_PA_C;
+  if (c->ent[kop]->launch(p, c->grid[kop], s) != 0) return TMOP_ERR_CUDA;
   if (c->delta != 0.0 && op != OP_ENERGY && op != OP_LINEARIZE) {
     // restricted movement (eq. (4.2)): its gradient (from x) or Hessian action (from v)
     MassParams mp = mass_params(c);
@@ -313,13 +317,19 @@ int ensure_vectors(tmop_ctx* c) {
 
 double* vec(tmop_ctx* c, int i) { return c->d_vec + (size_t)i * c->ndof; }
 
-// Store the per-point A-space Hessians of x (partial assembly).
+// Store the per-point A-space Hessians of x (partial assembly): the 45 (3D)
+// or 10 (2D) packed entries, or, for a 3D FP32 context with an (|T|^2, det T)
+// metric, one constant target and no second term, the 14-value compact
+// record the product rebuilds them from.
 int linearize(tmop_ctx* c, const double* x, cudaStream_t s) {
-  if (!c->d_pa) {
-    const int elt = c->precision == TMOP_FP64 ? (int)sizeof(double) : (int)sizeof(float);
-    c->base.pa_stride = pa_stride_for(c->dim, c->Q, elt);
-    CUDA_TRY(cudaMalloc(&c->d_pa, (size_t)elt * c->base.pa_stride * (size_t)c->nelem));
+  const int elt = c->precision == TMOP_FP64 ? (int)sizeof(double) : (int)sizeof(float);
+  if (!c->d_pa) {  // sized for the packed form, which is never smaller than the compact one
+    const size_t stride = (size_t)pa_stride_for(c->dim, c->Q, elt);
+    CUDA_TRY(cudaMalloc(&c->d_pa, (size_t)elt * stride * (size_t)c->nelem));
   }
+  c->pa_compact = c->ent[OP_LINEARIZE_C] && c->ent[OP_HESS_PA_C] && metric_is_lin(c->base.metric) &&
+                  c->base.metric2 == 0 && c->base.wkind != WK_PER_QP;
+  c->base.pa_stride = pa_stride_for(c->dim, c->Q, elt, c->pa_compact);
   c->pa_valid = false;
   int rc = launch_op(c, OP_LINEARIZE, x, nullptr, nullptr, nullptr, s);
   if (rc) return rc;
@@ -371,6 +381,9 @@ int hessian_diagonal(tmop_ctx* c, bool inverse, cudaStream_t s) {
   dp.delta = c->delta;
   dp.detW = b.detW;
   dp.detW_qp = b.wkind == WK_PER_QP ? b.detW_qp : nullptr;
+  dp.compact = c->pa_compact ? 1 : 0;
+  dp.identity = b.wkind == WK_IDENTITY ? 1 : 0;
+  memcpy(dp.Winv, b.Winv, sizeof(dp.Winv));
   if (f(dp, diag_grid(c->nelem), s) != 0) return TMOP_ERR_CUDA;
   if (diag_finish(c->d_diag, b.fixed, c->ndof, s) != 0) return TMOP_ERR_CUDA;
   if (inverse) {
@@ -601,10 +614,12 @@ int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metr
   for (int op = 0; op < OP_COUNT; ++op) {
     // FP32_MIXED: FP32 only for the Hessian action (and its partial assembly);
     // FP32_BULK: every element kernel
-    const bool hess = op == OP_HESS || op == OP_LINEARIZE || op == OP_HESS_PA;
+    const bool hess = op == OP_HESS || op == OP_LINEARIZE || op == OP_HESS_PA || op == OP_LINEARIZE_C ||
+                      op == OP_HESS_PA_C;
     const int fp32 = precision == TMOP_FP32_BULK || (precision == TMOP_FP32_MIXED && hess);
     ent[op] = find_elem(d, n, nq, fp32, op);
-    if (!ent[op]) return TMOP_ERR_ARG;  // unsupported (order, points) pair
+    // unsupported (order, points) pair; the compact pair exists for 3D FP32 only
+    if (!ent[op] && op < OP_LINEARIZE_C) return TMOP_ERR_ARG;
   }
   // structured grid: sizes must match, and elem_nodes (if given) must agree
   const int* sd = mesh->structured;
@@ -717,6 +732,7 @@ int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metr
   }
   // launch shapes and workspace
   for (int op = 0; op < OP_COUNT && rc == TMOP_OK; ++op) {
+    if (!ent[op]) continue;
     if (ent[op]->prepare(mesh->nelem, &c->grid[op]) != 0) rc = TMOP_ERR_CUDA;
     else if (c->grid[op] > kMaxRedBlocks) c->grid[op] = kMaxRedBlocks;
   }
@@ -898,6 +914,15 @@ int tmop_hess_apply_pa(tmop_ctx* c, const double* v, double* y, void* stream) {
   if (!c || !v || !y) return TMOP_ERR_ARG;
   if (!c->pa_valid) return TMOP_ERR_ARG;
   return launch_op(c, OP_HESS_PA, nullptr, v, y, nullptr, (cudaStream_t)stream);
+}
+
+int tmop_pa_layout(const tmop_ctx* c, int* values_per_point, int* stride, int* elt_bytes) {
+  if (!c || !c->pa_valid) return TMOP_ERR_ARG;
+  const int dd = c->dim * c->dim;
+  if (values_per_point) *values_per_point = c->pa_compact ? kCompactRec : dd * (dd + 1) / 2;
+  if (stride) *stride = c->base.pa_stride;
+  if (elt_bytes) *elt_bytes = c->precision == TMOP_FP64 ? 8 : 4;
+  return TMOP_OK;
 }
 
 int tmop_hessian_diagonal(tmop_ctx* c, double* out, void* stream) {

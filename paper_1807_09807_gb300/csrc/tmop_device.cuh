@@ -66,6 +66,78 @@ template <class S> __device__ __forceinline__ typename base_of<S>::type sc(doubl
   return typename base_of<S>::type(c);
 }
 
+// ---------------------------------------------------------------- node numbering
+// Global node ids of the nodes of an element. A structured order-(N-1) grid
+// of sx x sy (x sz) elements is numbered lexicographically, x fastest, on a
+// (k sx + 1) x (k sy + 1) (x (k sz + 1)) node lattice: the first node of
+// element e is found once per element (the divisions by the run-time grid
+// sizes are the costly part; GB300 runs their conversions on its narrow FP64
+// pipe), and local node t = i + N j + N^2 l adds compile-time digits times
+// the lattice strides. Unstructured meshes read the connectivity table.
+template <int N>
+struct NodeMap {
+  const int32_t* conn;
+  int sx, sy, Nx, NxNy, base;
+  const int32_t* row;
+  __device__ __forceinline__ NodeMap(const int32_t* elem_nodes, int sx_, int sy_)
+      : conn(elem_nodes), sx(sx_), sy(sy_), Nx((N - 1) * sx_ + 1), NxNy(((N - 1) * sx_ + 1) * ((N - 1) * sy_ + 1)),
+        base(0), row(nullptr) {}
+  __device__ __forceinline__ void element(int e, int ndof) {
+    if (sx > 0) {
+      const int exy = sx * sy, ez = e / exy, r = e - ez * exy, ey = r / sx, ex = r - ey * sx;
+      base = (N - 1) * (ez * NxNy + ey * Nx + ex);
+    } else {
+      row = conn + (size_t)e * ndof;
+    }
+  }
+  __device__ __forceinline__ int operator()(int t) const {
+    if (sx > 0) {
+      const int i = t % N, j = (t / N) % N, l = t / (N * N);
+      return base + l * NxNy + j * Nx + i;
+    }
+    return __ldg(row + t);
+  }
+};
+
+// ---------------------------------------------------------------- precision conversions
+// IEEE binary64 <-> binary32 with integer operations. The FP32 kernels
+// convert every gathered FP64 value of v (and x) and every FP32 contribution
+// they add into an FP64 output; done with F2F instructions these run on
+// GB300's narrow FP64 pipe, here on the integer pipes. f64_to_f32 rounds to
+// nearest even, as a cast does, except that results below the smallest
+// normal float (|d| < 2^-126) become a signed zero; f32_to_f64 is exact, with
+// subnormal inputs read as zero. Infinities and NaNs are kept.
+__device__ __forceinline__ float f64_to_f32(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (((hi & 0xFFFFFu) | lo) ? 0x400000u : 0u));
+  const int fe = e - 1023 + 127;
+  if (fe <= 0) return __uint_as_float(sign);
+  unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);   // the top 23 of the 52 mantissa bits
+  const unsigned rem = lo & 0x1FFFFFFFu, half = 0x10000000u;
+  m += (rem > half || (rem == half && (m & 1u))) ? 1u : 0u;
+  unsigned r = ((unsigned)fe << 23) + m;              // a carry out of m steps the exponent
+  if (fe >= 255 || r >= 0x7F800000u) r = 0x7F800000u;
+  return __uint_as_float(sign | r);
+}
+
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  if (e == 0) return __longlong_as_double((long long)((unsigned long long)sign << 32));
+  const unsigned hi = sign | (e == 0xFFu ? 0x7FF00000u : ((e + (1023u - 127u)) << 20)) | (m >> 3);
+  const unsigned lo = m << 29;
+  return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+
+// FP64 value -> the kernel's arithmetic type, and back
+template <class R> __device__ __forceinline__ R from_f64(double d) { return R(d); }
+template <> __device__ __forceinline__ float from_f64<float>(double d) { return f64_to_f32(d); }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float v) { return f32_to_f64(v); }
+
 // ---------------------------------------------------------------- matrices
 template <int D, class S>
 __device__ __forceinline__ S det_m(const S* M) {

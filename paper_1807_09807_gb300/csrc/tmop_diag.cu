@@ -1,5 +1,6 @@
 // Diagonal of the partially assembled Hessian (for Jacobi preconditioning of
-// the Newton systems of Section 3.4):
+// the Newton systems of Section 3.4), from the packed per-point Hessians or,
+// in 3D, from the compact records the entries are rebuilt from:
 //   diag_{i,a} = sum_E sum_q sum_{b,c} H_q[(a,b),(a,c)] d_b phi_i(x_q) d_c phi_i(x_q)
 // (+ 2 delta w_q det W phi_i(x_q)^2 for the restricted-movement term). The
 // product d_b phi_i d_c phi_i is separable: in direction d it is the 1D
@@ -10,6 +11,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "tmop_device.cuh"
 #include "tmop_diag.h"
 #include "tmop_kparams.h"
 
@@ -18,16 +20,6 @@ namespace tmop {
 namespace {
 
 constexpr int kDiagWarps = 4;
-
-__device__ __forceinline__ int dnode(const DiagParams& p, int e, int t, int N) {
-  if (p.sx > 0) {
-    const int k = N - 1, Nx = k * p.sx + 1, Ny = k * p.sy + 1;
-    const int ex = e % p.sx, ey = (e / p.sx) % p.sy, ez = e / (p.sx * p.sy);
-    const int i = t % N, j = (t / N) % N, l = t / (N * N);
-    return ((ez * k + l) * Ny + ey * k + j) * Nx + ex * k + i;
-  }
-  return __ldg(p.elem_nodes + (size_t)e * (p.dim == 2 ? N * N : N * N * N) + t);
-}
 
 // Y[n^DIM] += sum_q R[q] prod_d T_d[q_d][i_d]; R in `r` (QP values), tables T0,
 // T1, T2 ([Q1][N]), scratch U, V.
@@ -80,6 +72,45 @@ __device__ void contract_add(const double* r, const double* T0, const double* T1
   }
 }
 
+// Row a of the response to dA = E_ac at point q from a 3D compact record
+// (T, then w det W times mu_1, mu_t, mu_11, mu_1t, mu_tt), in FP32 like the
+// record: out[b] = H[(a,b),(a,c)] = [w det W (d^2mu/dT^2 : E_ac W^-1) W^-t]_ab.
+template <class R>
+__device__ void compact_row(const DiagParams& p, const R* He, int QP, int q, int a, int c, float out[3]) {
+  MetricLin<3, float> L;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) L.T[i] = (float)He[(size_t)i * QP + q];
+  cof_m<3>(L.T, L.C);
+  L.m1 = (float)He[(size_t)9 * QP + q];
+  L.mt = (float)He[(size_t)10 * QP + q];
+  L.m11 = (float)He[(size_t)11 * QP + q];
+  L.m1t = (float)He[(size_t)12 * QP + q];
+  L.mtt = (float)He[(size_t)13 * QP + q];
+  // (a, c) are run-time values: every index below is a compile-time one
+  // with a select, so the small arrays stay in registers
+  float w[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) w[k] = p.identity ? (k == c ? 1.0f : 0.0f) : (float)p.Winv[c * 3 + k];
+  float dT[9], S[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) dT[i] = (i / 3 == a) ? w[i % 3] : 0.0f;
+  L.dP(dT, S);
+  float Sa[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) Sa[k] = a == 0 ? S[k] : (a == 1 ? S[3 + k] : S[6 + k]);
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    float v = 0.0f;
+    if (p.identity) {
+      v = Sa[b];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) v = fmaf(Sa[k], (float)p.Winv[b * 3 + k], v);
+    }
+    out[b] = v;
+  }
+}
+
 template <int DIM, int N, int Q1, class R>
 __global__ void __launch_bounds__(kDiagWarps * 32) diag_kernel(const DiagParams p) {
   constexpr int NDOF = DIM == 2 ? N * N : N * N * N, QP = DIM == 2 ? Q1 * Q1 : Q1 * Q1 * Q1;
@@ -89,6 +120,8 @@ __global__ void __launch_bounds__(kDiagWarps * 32) diag_kernel(const DiagParams 
   __shared__ double tab[5][kMaxQ * kMaxN];
   __shared__ double sw[kMaxQ];
   __shared__ double wr[kDiagWarps][QP], wu[kDiagWarps][UQ], wv[kDiagWarps][VQ], wy[kDiagWarps][NDOF];
+  // compact records (3D): entries b = 0..2 of row a of the response to E_ac
+  __shared__ float whh[kDiagWarps][DIM == 3 ? 3 * QP : 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < Q1 * N; t += blockDim.x) {
     const double b = p.B[t], g = p.G[t];
@@ -100,25 +133,43 @@ __global__ void __launch_bounds__(kDiagWarps * 32) diag_kernel(const DiagParams 
   __syncthreads();
   double *r = wr[warp], *U = wu[warp], *V = wv[warp], *Y = wy[warp];
   const R* H = static_cast<const R*>(p.pa);
+  NodeMap<N> nodes(p.elem_nodes, p.sx, p.sy);
   for (int e = blockIdx.x * kDiagWarps + warp; e < p.nelem; e += gridDim.x * kDiagWarps) {
+    nodes.element(e, NDOF);
     const R* He = H + (size_t)e * p.pa_stride;
     for (int a = 0; a < DIM; ++a) {
       for (int t = lane; t < NDOF; t += 32) Y[t] = 0.0;
       __syncwarp();
-      for (int b = 0; b < DIM; ++b)
-        for (int c = b; c < DIM; ++c) {
-          // packed index of (row a*DIM+b, column a*DIM+c), row <= column
-          const int rr = a * DIM + b, cc = a * DIM + c;
-          const int s = rr * DD - rr * (rr - 1) / 2 + (cc - rr);
-          const double m = b == c ? 1.0 : 2.0;
-          for (int q = lane; q < QP; q += 32) r[q] = m * (double)He[(size_t)s * QP + q];
+      // terms (b <= c): H[(a,b),(a,c)] (twice for b != c) against the 1D
+      // table products; direction d uses tab[(d == b) + (d == c)]: BB, BG or GG
+      for (int c = 0; c < DIM; ++c) {
+        float* hh = whh[warp];
+        if (DIM == 3 && p.compact) {  // the whole row of the response to E_ac at once
+          for (int q = lane; q < QP; q += 32) {
+            float row[3];
+            compact_row(p, He, QP, q, a, c, row);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) hh[b * QP + q] = row[b];
+          }
           __syncwarp();
-          // direction d uses tab[(d == b) + (d == c)]: BB, BG or GG
+        }
+        for (int b = 0; b <= c; ++b) {
+          const double m = b == c ? 1.0 : 2.0;
+          if (DIM == 3 && p.compact) {
+            for (int q = lane; q < QP; q += 32) r[q] = m * (double)hh[b * QP + q];
+          } else {
+            // packed index of (row a*DIM+b, column a*DIM+c), row <= column
+            const int rr = a * DIM + b, cc = a * DIM + c;
+            const int s = rr * DD - rr * (rr - 1) / 2 + (cc - rr);
+            for (int q = lane; q < QP; q += 32) r[q] = m * (double)He[(size_t)s * QP + q];
+          }
+          __syncwarp();
           const double* T0 = tab[(b == 0) + (c == 0)];
           const double* T1 = tab[(b == 1) + (c == 1)];
           const double* T2 = tab[(b == 2) + (c == 2)];
           contract_add<DIM, N, Q1>(r, T0, T1, T2, U, V, Y, lane);
         }
+      }
       if (p.delta != 0.0) {  // restricted movement: 2 delta w det W phi_i^2 (B^2 in every direction)
         for (int q = lane; q < QP; q += 32) {
           const int q0 = q % Q1, q1 = (q / Q1) % Q1;
@@ -131,7 +182,7 @@ __global__ void __launch_bounds__(kDiagWarps * 32) diag_kernel(const DiagParams 
         contract_add<DIM, N, Q1>(r, tab[0], tab[0], tab[0], U, V, Y, lane);
       }
       for (int t = lane; t < NDOF; t += 32) {
-        const int g = dnode(p, e, t, N);
+        const int g = nodes(t);
         atomicAdd(p.diag + (size_t)a * p.nnode + g, Y[t]);
       }
       __syncwarp();

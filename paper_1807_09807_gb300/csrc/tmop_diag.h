@@ -17,6 +17,9 @@ struct DiagParams {
   double B[kMaxQ * kMaxN], G[kMaxQ * kMaxN], w1[kMaxQ];
   double delta, detW;         // restricted-movement term (delta = 0: none)
   const double* detW_qp;
+  int compact;                // pa holds 3D compact records (T, scaled partials of mu)
+  int identity;               // W = I (else the constant Winv)
+  double Winv[9];
 };
 
 typedef int (*diag_launch_fn)(const DiagParams& p, int grid, void* stream);

@@ -1,4 +1,5 @@
-// Element-kernel instantiations: dim 3, float arithmetic, (n = order+1, q) pairs.
+// Element-kernel instantiations: dim 3, float arithmetic, (n = order+1, q)
+// pairs, including the compact partially assembled pair.
 #include "tmop_element.cuh"
 
 namespace tmop {
@@ -8,7 +9,8 @@ namespace tmop {
      ElemCfg<3, N, Q, float, OP>::WARPS}
 #define TMOP_ENTRIES(N, Q)                                                                      \
   TMOP_ENTRY(N, Q, OP_ENERGY), TMOP_ENTRY(N, Q, OP_GRADIENT), TMOP_ENTRY(N, Q, OP_HESS),         \
-      TMOP_ENTRY(N, Q, OP_LINEARIZE), TMOP_ENTRY(N, Q, OP_HESS_PA)
+      TMOP_ENTRY(N, Q, OP_LINEARIZE), TMOP_ENTRY(N, Q, OP_HESS_PA), TMOP_ENTRY(N, Q, OP_LINEARIZE_C), \
+      TMOP_ENTRY(N, Q, OP_HESS_PA_C)
 
 extern const ElemEntry kElem_3d_f32[] = {
     TMOP_ENTRIES(2,2),

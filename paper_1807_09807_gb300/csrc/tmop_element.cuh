@@ -56,17 +56,6 @@ struct ElemCfg {
   static constexpr size_t smem_bytes() { return sizeof(R) * (TABLE + WARPS * (B0 + B1 + B2)); }
 };
 
-__device__ __forceinline__ int node_id(const KParams& p, int e, int t, int N) {
-  if (p.sx > 0) {
-    const int k = N - 1;
-    const int Nx = k * p.sx + 1, Ny = k * p.sy + 1;
-    const int ex = e % p.sx, ey = (e / p.sx) % p.sy, ez = e / (p.sx * p.sy);
-    const int i = t % N, j = (t / N) % N, l = t / (N * N);
-    return ((ez * k + l) * Ny + ey * k + j) * Nx + ex * k + i;
-  }
-  return __ldg(p.elem_nodes + (size_t)e * (p.dim == 2 ? N * N : N * N * N) + t);
-}
-
 // Second term of a composite metric at one point: T2 = A W2^-1 and, for a
 // direction dA, dT2 = dA W2^-1 (Section 4.2, eq. (4.1)).
 template <int D, class R>
@@ -143,12 +132,17 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
 
   double accF = 0.0, accMin = INFINITY;
   const int nwarps_total = gridDim.x * WARPS;
-  constexpr int NSH = (OP == OP_HESS_PA) ? D * D * (D * D + 1) / 2 : 1;
+  constexpr bool PA_APPLY = OP == OP_HESS_PA || OP == OP_HESS_PA_C;
+  constexpr int NSH = (OP == OP_HESS_PA) ? D * D * (D * D + 1) / 2 : (OP == OP_HESS_PA_C ? kCompactRec : 1);
+  static_assert(!(OP == OP_LINEARIZE_C || OP == OP_HESS_PA_C) || D == 3, "compact records are 3D");
+  NodeMap<N> nodes(p.elem_nodes, p.sx, p.sy);
   for (int e = blockIdx.x * WARPS + warp; e < p.nelem; e += nwarps_total) {
-    // Partially assembled product: the Hessians of this lane's first point are
-    // loaded now, so their latency overlaps the gather and the v-contraction.
+    nodes.element(e, NDOF);
+    // Partially assembled product: the stored values of this lane's first
+    // point are loaded now, so their latency overlaps the gather and the
+    // v-contraction.
     R hpre[NSH];
-    if constexpr (OP == OP_HESS_PA) {
+    if constexpr (PA_APPLY) {
       if (lane < Shape<D, N, Q1>::QP) {
         const R* H0 = static_cast<const R*>(p.pa) + (size_t)e * p.pa_stride + lane;
 #pragma unroll
@@ -160,27 +154,27 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
     // (sum_i grad phi_i = 0), and this keeps the FP32 relative error of A at
     // the level of eps32 instead of eps32 |x| / h.
     double xref[D];
-    if constexpr (sizeof(R) == 4 && OP != OP_HESS_PA) {
-      const int g0 = node_id(p, e, 0, N);
+    if constexpr (sizeof(R) == 4 && !PA_APPLY) {
+      const int g0 = nodes(0);
 #pragma unroll
       for (int c = 0; c < D; ++c) xref[c] = __ldg(p.x + (size_t)c * p.nnode + g0);
     }
     for (int t = lane; t < NDOF; t += 32) {
-      const int g = node_id(p, e, t, N);
-      if constexpr (OP == OP_HESS_PA) {
+      const int g = nodes(t);
+      if constexpr (PA_APPLY) {
         // the partially assembled product needs only the direction v
 #pragma unroll
         for (int c = 0; c < D; ++c) {
           const size_t dof = (size_t)c * p.nnode + g;
           const bool fx = p.fixed && __ldg(p.fixed + dof);
-          P0[c * NDOF + t] = fx ? R(0) : R(__ldg(p.v + dof));
+          P0[c * NDOF + t] = fx ? R(0) : from_f64<R>(__ldg(p.v + dof));
         }
         continue;
       }
 #pragma unroll
       for (int c = 0; c < D; ++c) {
         const double xv = __ldg(p.x + (size_t)c * p.nnode + g);
-        if constexpr (sizeof(R) == 4) P0[c * NDOF + t] = R(xv - xref[c]);
+        if constexpr (sizeof(R) == 4) P0[c * NDOF + t] = from_f64<R>(xv - xref[c]);
         else P0[c * NDOF + t] = R(xv);
       }
       if constexpr (OP == OP_HESS && !Cfg::SPLIT) {
@@ -188,7 +182,7 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
         for (int c = 0; c < D; ++c) {
           const size_t dof = (size_t)c * p.nnode + g;
           const bool fx = p.fixed && __ldg(p.fixed + dof);
-          P0[(D + c) * NDOF + t] = fx ? R(0) : R(__ldg(p.v + dof));
+          P0[(D + c) * NDOF + t] = fx ? R(0) : from_f64<R>(__ldg(p.v + dof));
         }
       }
     }
@@ -199,12 +193,12 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
       if constexpr (RB) fwd3_rb<N, Q1, D, R>(tB, tG, P0, P2, lane);
       else fwd3<N, Q1, D, R>(sB, sG, P0, P2, lane);
       for (int t = lane; t < NDOF; t += 32) {
-        const int g = node_id(p, e, t, N);
+        const int g = nodes(t);
 #pragma unroll
         for (int c = 0; c < D; ++c) {
           const size_t dof = (size_t)c * p.nnode + g;
           const bool fx = p.fixed && __ldg(p.fixed + dof);
-          P0[c * NDOF + t] = fx ? R(0) : R(__ldg(p.v + dof));
+          P0[c * NDOF + t] = fx ? R(0) : from_f64<R>(__ldg(p.v + dof));
         }
       }
       __syncwarp();
@@ -224,6 +218,57 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
     double emin = INFINITY;
     constexpr int NS = DD * (DD + 1) / 2;
     for (int q = lane; q < QP; q += 32) {
+      if constexpr (OP == OP_HESS_PA_C) {
+        // y = w det W (d^2mu/dT^2 : dA W^-1) W^-t rebuilt from the compact
+        // record: T, then the scaled partials (mu_1, mu_t, mu_11, mu_1t, mu_tt)
+        const R* H = static_cast<const R*>(p.pa) + (size_t)e * p.pa_stride + q;
+        R h[kCompactRec];
+        if (q == lane) {
+#pragma unroll
+          for (int t = 0; t < kCompactRec; ++t) h[t] = hpre[t];
+        } else {
+#pragma unroll
+          for (int t = 0; t < kCompactRec; ++t) h[t] = __ldg(H + (size_t)t * QP);
+        }
+        MetricLin<D, R> L;
+#pragma unroll
+        for (int i = 0; i < DD; ++i) L.T[i] = h[i];
+        cof_m<D>(L.T, L.C);
+        L.m1 = h[DD]; L.mt = h[DD + 1]; L.m11 = h[DD + 2]; L.m1t = h[DD + 3]; L.mtt = h[DD + 4];
+        R dA[DD], dT[DD], S[DD];
+#pragma unroll
+        for (int i = 0; i < DD; ++i) dA[i] = Abuf[i * QP + q];
+        if (p.wkind == WK_IDENTITY) {
+#pragma unroll
+          for (int i = 0; i < DD; ++i) dT[i] = dA[i];
+        } else {
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = 0; b < D; ++b) {
+              R t = R(0);
+#pragma unroll
+              for (int c = 0; c < D; ++c) t = fma(dA[a * D + c], Wi[c * D + b], t);
+              dT[a * D + b] = t;
+            }
+        }
+        L.dP(dT, S);
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int b = 0; b < D; ++b) {
+            R r;
+            if (p.wkind == WK_IDENTITY) {
+              r = S[a * D + b];
+            } else {
+              r = R(0);
+#pragma unroll
+              for (int c = 0; c < D; ++c) r = fma(S[a * D + c], Wi[b * D + c], r);
+            }
+            Abuf[(a * D + b) * QP + q] = r;
+          }
+        continue;
+      }
       if constexpr (OP == OP_HESS_PA) {
         // y = H dA with the stored symmetric A-space Hessian (already scaled by w det W)
         const R* H = static_cast<const R*>(p.pa) + (size_t)e * p.pa_stride + q;
@@ -283,6 +328,21 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
             for (int c = 0; c < D; ++c) s = fma(A[a * D + c], Wi[c * D + b], s);
             T[a * D + b] = s;
           }
+      }
+      if constexpr (OP == OP_LINEARIZE_C) {
+        // compact record: T and w det W times the partials of mu in (|T|^2, det T)
+        R* H = static_cast<R*>(p.pa) + (size_t)e * p.pa_stride + q;
+        const R s = wq * detW;
+        MetricLin<D, R> L;
+        const bool ok = L.init(p.metric, T);
+#pragma unroll
+        for (int i = 0; i < DD; ++i) H[(size_t)i * QP] = T[i];
+        H[(size_t)(DD + 0) * QP] = ok ? s * L.m1 : R(0);
+        H[(size_t)(DD + 1) * QP] = ok ? s * L.mt : R(0);
+        H[(size_t)(DD + 2) * QP] = ok ? s * L.m11 : R(0);
+        H[(size_t)(DD + 3) * QP] = ok ? s * L.m1t : R(0);
+        H[(size_t)(DD + 4) * QP] = ok ? s * L.mtt : R(0);
+        continue;
       }
       if constexpr (OP == OP_LINEARIZE) {
         // column kl of the A-space Hessian: direction dA = E_kl, dT = E_kl W^-1,
@@ -448,7 +508,7 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
         }
       }
     }
-    if constexpr (OP == OP_LINEARIZE) {
+    if constexpr (OP == OP_LINEARIZE || OP == OP_LINEARIZE_C) {
       __syncwarp();
     } else if constexpr (OP == OP_ENERGY) {
       accMin = fmin(accMin, emin);
@@ -464,12 +524,12 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
       else if constexpr (RB) adj3_rb<N, Q1, D, R>(tB, tG, P0, P1, lane);
       else adj3<N, Q1, D, R>(sB, sG, P0, P1, lane);
       for (int t = lane; t < NDOF; t += 32) {
-        const int g = node_id(p, e, t, N);
+        const int g = nodes(t);
 #pragma unroll
         for (int c = 0; c < D; ++c) {
           const size_t dof = (size_t)c * p.nnode + g;
           if (p.fixed && __ldg(p.fixed + dof)) continue;
-          atomicAdd(p.y + dof, double(P0[c * NDOF + t]));
+          atomicAdd(p.y + dof, to_f64(P0[c * NDOF + t]));
         }
       }
     }

@@ -11,8 +11,16 @@ constexpr int kMaxQ = 8;   // 1D quadrature points
 constexpr int kMaxN = 5;   // 1D nodes (order <= 4)
 
 // OP_LINEARIZE stores the A-space Hessian of w det W mu at every point (once
-// per Newton step); OP_HESS_PA applies it (partial assembly).
-enum { OP_ENERGY = 0, OP_GRADIENT = 1, OP_HESS = 2, OP_LINEARIZE = 3, OP_HESS_PA = 4, OP_COUNT = 5 };
+// per Newton step); OP_HESS_PA applies it (partial assembly). The compact
+// pair (3D FP32 only) stores instead what the second derivative of an
+// (|T|^2, det T) metric is made of: T and the five scaled partials
+// w det W (mu_1, mu_t, mu_11, mu_1t, mu_tt), 14 values per point instead of
+// 45, and OP_HESS_PA_C rebuilds dP from them.
+enum {
+  OP_ENERGY = 0, OP_GRADIENT = 1, OP_HESS = 2, OP_LINEARIZE = 3, OP_HESS_PA = 4,
+  OP_LINEARIZE_C = 5, OP_HESS_PA_C = 6, OP_COUNT = 7
+};
+constexpr int kCompactRec = 14;  // values per point of the compact record (3D)
 enum { WK_IDENTITY = 0, WK_CONST = 1, WK_PER_QP = 2 };
 
 struct KParams {
@@ -49,13 +57,16 @@ inline bool metric_supported(int d, int id) {
          (d == 3 && (id == 302 || id == 303));
 }
 
-// Per-element block of packed Hessians, in elements of `elt` bytes, padded so
-// that every block starts on a 16-byte boundary (bulk-copy granularity).
-inline int pa_stride_for(int dim, int Q, int elt) {
-  const int dd = dim * dim, ns = dd * (dd + 1) / 2;
+// Per-element block of packed Hessians (or compact records), in elements of
+// `elt` bytes, padded so that every block starts on a 16-byte boundary.
+inline int pa_stride_for(int dim, int Q, int elt, bool compact = false) {
+  const int dd = dim * dim, ns = compact ? kCompactRec : dd * (dd + 1) / 2;
   const int bytes = ((ns * Q * elt + 15) / 16) * 16;
   return bytes / elt;
 }
+
+// Metrics whose second derivative MetricLin writes in (|T|^2, det T).
+inline bool metric_is_lin(int id) { return id != 302 && id != 98; }
 
 typedef int (*elem_launch_fn)(const KParams& p, int grid, void* stream);
 typedef int (*elem_prepare_fn)(int nelem, int* grid);

@@ -9,22 +9,13 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "tmop_device.cuh"
 #include "tmop_kparams.h"
 #include "tmop_mass.h"
 
 namespace tmop {
 
 namespace {
-
-__device__ __forceinline__ int mnode(const MassParams& p, int e, int t, int N) {
-  if (p.sx > 0) {
-    const int k = N - 1, Nx = k * p.sx + 1, Ny = k * p.sy + 1;
-    const int ex = e % p.sx, ey = (e / p.sx) % p.sy, ez = e / (p.sx * p.sy);
-    const int i = t % N, j = (t / N) % N, l = t / (N * N);
-    return ((ez * k + l) * Ny + ey * k + j) * Nx + ex * k + i;
-  }
-  return __ldg(p.elem_nodes + (size_t)e * (p.dim == 2 ? N * N : N * N * N) + t);
-}
 
 // forward value contraction: X[D][N^d] -> V[D][Q^d] (tensor product of B);
 // in place between two buffers, result in the returned one
@@ -153,9 +144,11 @@ __global__ void __launch_bounds__(kMassWarps * 32) mass_kernel(const MassParams 
   double* P0 = buf[warp][0];
   double* P1 = buf[warp][1];
   double acc = 0.0;
+  NodeMap<N> nodes(p.elem_nodes, p.sx, p.sy);
   for (int e = blockIdx.x * kMassWarps + warp; e < p.nelem; e += gridDim.x * kMassWarps) {
+    nodes.element(e, NDOF);
     for (int t = lane; t < NDOF; t += 32) {
-      const int g = mnode(p, e, t, N);
+      const int g = nodes(t);
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
         const size_t dof = (size_t)c * p.nnode + g;
@@ -188,7 +181,7 @@ __global__ void __launch_bounds__(kMassWarps * 32) mass_kernel(const MassParams 
     if (MODE != 0) {
       double* Y = adj_val<DIM, N, Q1, DIM>(sB, V, O, lane);
       for (int t = lane; t < NDOF; t += 32) {
-        const int g = mnode(p, e, t, N);
+        const int g = nodes(t);
 #pragma unroll
         for (int c = 0; c < DIM; ++c) {
           const size_t dof = (size_t)c * p.nnode + g;

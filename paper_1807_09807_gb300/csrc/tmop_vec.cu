@@ -12,6 +12,8 @@
 #include <math.h>
 #include <stddef.h>
 
+#include "../../include/tmop.h"
+#include "tmop_device.cuh"
 #include "tmop_vec.h"
 
 namespace tmop {
@@ -506,3 +508,21 @@ int cg_after_hv(double* sol, double* r, double* d, const double* Hd, double* st,
 }
 
 }  // namespace tmop
+
+namespace {
+__global__ void k_selftest_convert(const double* __restrict__ in, float* __restrict__ f32, double* __restrict__ back,
+                                   size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float f = tmop::f64_to_f32(in[i]);
+    f32[i] = f;
+    back[i] = tmop::f32_to_f64(f);
+  }
+}
+}  // namespace
+
+extern "C" int tmop_selftest_convert(const double* in, float* f32, double* back, size_t n, void* stream) {
+  if (n == 0) return TMOP_OK;
+  if (!in || !f32 || !back) return TMOP_ERR_ARG;
+  k_selftest_convert<<<256, 256, 0, (cudaStream_t)stream>>>(in, f32, back, n);
+  return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
+}

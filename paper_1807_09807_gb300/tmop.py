@@ -80,6 +80,7 @@ _SIGNATURES = {
     "tmop_linearize": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_hess_apply_pa": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_hessian_diagonal": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "tmop_pa_layout": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "tmop_sizes": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
                    C.c_int),
     "tmop_energy_noalloc": ([C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(_Quad), C.c_int, C.POINTER(_Targets),
@@ -88,6 +89,7 @@ _SIGNATURES = {
     "tmop_set_restricted_movement": ([C.c_void_p, C.c_double, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_jacobians": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_set_targets_from_positions": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+    "tmop_selftest_convert": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p], C.c_int),
     "tmop_destroy": ([C.c_void_p], None),
     "tmop_status_string": ([C.c_int], C.c_char_p),
 }
@@ -127,6 +129,19 @@ def _check_vec(t, shape, what):
         raise TypeError(f"{what} must be a contiguous float64 CUDA tensor")
     if tuple(t.shape) != tuple(shape):
         raise ValueError(f"{what} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+def selftest_convert(x):
+    """(f32, back): the FP64 -> FP32 -> FP64 conversions of the FP32 kernels on x."""
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+        raise TypeError("x must be a contiguous float64 CUDA tensor")
+    f32 = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    back = torch.empty_like(x)
+    rc = load().tmop_selftest_convert(_ptr(x), _ptr(f32), _ptr(back), x.numel(), _stream())
+    if rc != OK:
+        raise TmopError(rc, "tmop_selftest_convert")
+    return f32, back
 
 
 def energy_noalloc(dim, order, structured, nq, metric, x, F, min_detA, quad_kind=GL, target_kind=W_IDENTITY,
@@ -305,6 +320,14 @@ class Context:
         if rc != OK:
             raise TmopError(rc, "tmop_hess_apply_pa")
         return y
+
+    def pa_layout(self):
+        """(values per point, element stride, bytes per value) of the stored linearisation."""
+        v, st, b = C.c_int(0), C.c_int(0), C.c_int(0)
+        rc = load().tmop_pa_layout(self._h, C.byref(v), C.byref(st), C.byref(b))
+        if rc != OK:
+            raise TmopError(rc, "tmop_pa_layout")
+        return v.value, st.value, b.value
 
     def hessian_diagonal(self, out=None):
         """Diagonal of the Hessian stored by the last linearize() (1 at fixed dofs)."""

@@ -397,6 +397,102 @@ def test_partial_assembly_general_targets_and_fp32(tm, dim):
     assert rel(host(c32.hess_apply_pa(dev(v))), yo) <= 1e-5
 
 
+@pytest.mark.parametrize("order,nq,nx,structured", [(1, 2, (3, 3, 2), True), (2, 3, (3, 2, 1), True),
+                                                    (2, 4, (5, 4, 3), False), (3, 4, (4, 3, 2), True),
+                                                    (3, 5, (12, 12, 12), True), (3, 5, (7, 5, 3), False),
+                                                    (4, 5, (3, 2, 2), False), (4, 6, (3, 3, 3), True)])
+def test_fp32_stored_hessian_product_3d(tm, order, nq, nx, structured):
+    """The 3D FP32 stored-Hessian product from compact records (mu303, W = I:
+    T and the five scaled partials of mu per point) against the oracle's
+    FP64 Hessian action, for every order, ragged grids, more elements than
+    resident warps, both node-numbering paths, with the boundary fixed. The
+    FP32 bound is that of the other FP32 products."""
+    m = make("c4", 2, order=order, nq=nq, nx=nx)
+    rng = np.random.default_rng(order * 10 + nq)
+    v = rng.standard_normal(m.x.shape)
+    yo = orc_for(m).hess_apply(m.x, v)
+    c32 = tm.Context.from_mesh(m, precision=tm.FP32_MIXED, structured=structured)
+    c32.linearize(dev(m.x))
+    assert c32.pa_layout()[0] == 14
+    y = host(c32.hess_apply_pa(dev(v)))
+    assert rel(y, yo) <= 1e-5, rel(y, yo)
+    assert np.all(y[m.fixed == 1] == 0.0)
+
+
+@pytest.mark.parametrize("case", ["mu14", "mu1", "W", "mu302", "mu98", "composite", "per_point_W", "bulk"])
+def test_fp32_compact_and_packed_records_3d(tm, case):
+    """Which record a 3D FP32 linearisation stores, and that the product
+    from it matches the oracle: compact (14 values) for mu1, mu14, mu303 with
+    a constant target (also non-symmetric, and in the FP32-bulk form);
+    packed (45) for mu302 and mu98 (not (|T|^2, det T) metrics), for a
+    composite metric and for per-point targets."""
+    m = make("c3", 4, nx=(3, 2, 2))
+    metric = {"mu14": 14, "mu1": 1, "mu302": 302, "mu98": 98}.get(case, 303)
+    rng = np.random.default_rng(5)
+    okw, ckw = {}, {}
+    if case == "W":
+        W = (np.eye(3) + 0.2 * rng.standard_normal((3, 3))) / 4
+        if np.linalg.det(W) < 0:
+            W[:, 0] *= -1
+        m.W = W
+        okw.update(wkind=oracle.W_CONST, W=W)
+    if case == "per_point_W":
+        Wq = (np.eye(3) + 0.1 * rng.standard_normal((m.nelem, m.Q, 3, 3))) / 4
+        Wq[np.linalg.det(Wq) < 0, :, 0] *= -1
+        okw.update(wkind=oracle.W_PER_QP, W=Wq)
+        ckw.update(W_per_qp=Wq)
+    prec = tm.FP32_BULK if case == "bulk" else tm.FP32_MIXED
+    ctx = tm.Context.from_mesh(m, metric=metric, precision=prec, **ckw)
+    if case == "composite":
+        eta = 0.5 + rng.random((m.nelem, m.Q))
+        ctx.set_composite(14, np.eye(3) * 0.3, eta)
+        okw.update(metric2=14, W2=np.eye(3) * 0.3, eta2=eta)
+    orc = oracle.Problem(m.dim, m.order, m.elem_nodes, m.nnode, m.fixed, m.nq, metric, **okw)
+    ctx.linearize(dev(m.x))
+    packed = case in ("mu302", "mu98", "composite", "per_point_W")
+    assert ctx.pa_layout() == ((45, 45 * m.Q, 4) if packed else (14, 14 * m.Q + (-14 * m.Q) % 4, 4))
+    v = rng.standard_normal(m.x.shape)
+    yo = orc.hess_apply(m.x, v)
+    assert rel(host(ctx.hess_apply_pa(dev(v))), yo) <= 1e-5
+
+
+def test_fp32_conversions_round_like_a_cast(tm):
+    """The integer-pipe FP64 -> FP32 conversion of the FP32 kernels against
+    numpy's IEEE cast (round to nearest even) on random values over the
+    whole normal float range, exact ties (both parities), values that round
+    up across a binade, the largest finite float and overflow, zeros,
+    infinities and NaN; results below 2^-126 become signed zeros. The FP32 ->
+    FP64 widening must be exact."""
+    rng = np.random.default_rng(17)
+    n = 20000
+    sign = np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    f = (sign * (1.0 + rng.random(n)) * 2.0 ** rng.integers(-100, 100, n)).astype(np.float32)   # normal floats
+    ulp32 = np.abs(np.spacing(f)).astype(np.float64)
+    base = f.astype(np.float64)
+    vals = np.concatenate([
+        sign * (1.0 + rng.random(n)) * 2.0 ** rng.integers(-100, 100, n),
+        base + 0.5 * ulp32 * np.sign(base),          # exact ties
+        base + 0.5000001 * ulp32 * np.sign(base),    # just above a tie
+        base + 0.4999999 * ulp32 * np.sign(base),    # just below a tie
+        np.nextafter(np.float64(1.0), 2.0) * np.array([1.0, -1.0]),
+        np.array([2.0 - 2.0 ** -25, 2.0 ** -126, -(2.0 ** -126), 3.4028234663852886e38, 0.0, -0.0]),
+    ])
+    x = dev(vals)
+    f32, back = tm.selftest_convert(x)
+    ref = vals.astype(np.float32)
+    got = f32.cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+    assert np.array_equal(back.cpu().numpy(), got.astype(np.float64))
+    special = np.array([np.inf, -np.inf, np.nan, 1e39, -1e39, 1e-39, -1e-39, 1e-300])
+    f32, back = tm.selftest_convert(dev(special))
+    got = f32.cpu().numpy()
+    assert got[0] == np.inf and got[1] == -np.inf and np.isnan(got[2])
+    assert got[3] == np.inf and got[4] == -np.inf
+    assert np.array_equal(got[5:], np.array([0.0, -0.0, 0.0], np.float32)) and np.signbit(got[6])
+    b = back.cpu().numpy()
+    assert b[0] == np.inf and b[1] == -np.inf and np.isnan(b[2])
+
+
 def test_partial_assembly_requires_linearize(tm):
     m = make("c1", 1, nx=2)
     ctx = tm.Context.from_mesh(m)
@@ -406,14 +502,23 @@ def test_partial_assembly_requires_linearize(tm):
 
 # ---------------------------------------------------------------- Jacobi preconditioning
 @pytest.mark.parametrize("name,kw,extras", [("c1", dict(nx=4), ""), ("c3", dict(nx=2), ""),
-                                            ("c1", dict(nx=3), "composite+delta"), ("c3", dict(nx=2), "fp32")])
+                                            ("c1", dict(nx=3), "composite+delta"), ("c3", dict(nx=2), "fp32"),
+                                            ("c3", dict(nx=2), "fp32+W"), ("c3", dict(nx=2), "fp32+composite")])
 def test_hessian_diagonal_matches_oracle(tm, name, kw, extras):
     """Diagonal of the partially assembled Hessian against the oracle's
-    Hessian action on every unit vector (brute force), 1 at fixed dofs."""
+    Hessian action on every unit vector (brute force), 1 at fixed dofs; in
+    3D FP32 both from compact records (W = I and a constant non-symmetric W)
+    and from packed Hessians (a composite metric)."""
     m = make(name, 5, **kw)
-    prec = tm.FP32_MIXED if extras == "fp32" else tm.FP64
-    ctx = tm.Context.from_mesh(m, precision=prec)
+    prec = tm.FP32_MIXED if "fp32" in extras else tm.FP64
     okw = {}
+    if "W" in extras.split("+"):
+        W = (np.eye(m.dim) + 0.2 * np.random.default_rng(3).standard_normal((m.dim, m.dim))) / 4
+        if np.linalg.det(W) < 0:
+            W[:, 0] *= -1
+        m.W = W
+        okw.update(wkind=oracle.W_CONST, W=W)
+    ctx = tm.Context.from_mesh(m, precision=prec)
     if "composite" in extras:
         W2 = np.eye(m.dim) * 0.4
         eta = np.full((m.nelem, m.Q), 0.7)
@@ -425,6 +530,8 @@ def test_hessian_diagonal_matches_oracle(tm, name, kw, extras):
     orc = oracle.Problem(m.dim, m.order, m.elem_nodes, m.nnode, m.fixed, m.nq, m.metric, **okw)
     x = dev(m.x)
     ctx.linearize(x)
+    if prec != tm.FP64 and m.dim == 3:
+        assert ctx.pa_layout()[0] == (45 if "composite" in extras else 14)
     d = host(ctx.hessian_diagonal())
     ref = np.ones_like(m.x)
     for a, i in np.argwhere(m.fixed == 0):
