@@ -79,6 +79,7 @@ def grad_flops_per_element(dim, n, q, metric):
 
 
 ELEM_SOURCES = ("tmop_device.cuh", "tmop_element.cuh", "tmop_kparams.h")
+PAC_SOURCES = ("tmop_device.cuh", "tmop_pa_compact.cu", "tmop_pa_compact.h", "tmop_kparams.h")
 
 
 def kernel_src_hash(files=ELEM_SOURCES) -> str:
@@ -470,14 +471,14 @@ def measure_pa(tm, m, x, v, y, flush, stream, args):
             ent["roofline"] = {"bound": "hbm", "achieved": ent["achieved_GBps"], "peak": hbm, "unit": "GB/s",
                                "frac": ent["achieved_GBps"] / hbm,
                                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-                               "kernel": f"elem_kernel<{m.dim},{n},{m.nq},float,"
-                                         f"{'OP_HESS_PA_C' if compact else 'OP_HESS_PA'}>", "traffic": None}
+                               "kernel": f"pac_kernel<{n},{m.nq}> (compact records)" if compact
+                               else f"elem_kernel<{m.dim},{n},{m.nq},float,OP_HESS_PA>", "traffic": None}
             ent["values_per_point"] = ns
             tfile = os.path.join(ROOT, "profiles", "traffic.json")
             if os.path.exists(tfile):
                 with open(tfile) as f:
                     tr = json.load(f).get(f"{args.workload}:pa_fp32")
-                if tr and tr.get("kernel_src_sha256") == kernel_src_hash():
+                if tr and tr.get("kernel_src_sha256") == kernel_src_hash(PAC_SOURCES if compact else ELEM_SOURCES):
                     ent["roofline"]["traffic"] = tr["dram_bytes_per_launch"]
         out[name] = ent
         c.close()

@@ -1,6 +1,8 @@
 // Element-kernel instantiations: dim 3, float arithmetic, (n = order+1, q)
-// pairs, including the compact partially assembled pair.
+// pairs, including the compact partially assembled pair (its product is the
+// software-pipelined kernel of tmop_pa_compact.cu).
 #include "tmop_element.cuh"
+#include "tmop_pa_compact.h"
 
 namespace tmop {
 
@@ -10,7 +12,7 @@ namespace tmop {
 #define TMOP_ENTRIES(N, Q)                                                                      \
   TMOP_ENTRY(N, Q, OP_ENERGY), TMOP_ENTRY(N, Q, OP_GRADIENT), TMOP_ENTRY(N, Q, OP_HESS),         \
       TMOP_ENTRY(N, Q, OP_LINEARIZE), TMOP_ENTRY(N, Q, OP_HESS_PA), TMOP_ENTRY(N, Q, OP_LINEARIZE_C), \
-      TMOP_ENTRY(N, Q, OP_HESS_PA_C)
+      {3, N, Q, 1, OP_HESS_PA_C, launch_pac<N, Q>, prepare_pac<N, Q>, kPacWarps}
 
 extern const ElemEntry kElem_3d_f32[] = {
     TMOP_ENTRIES(2,2),

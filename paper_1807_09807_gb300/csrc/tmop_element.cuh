@@ -132,9 +132,11 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
 
   double accF = 0.0, accMin = INFINITY;
   const int nwarps_total = gridDim.x * WARPS;
-  constexpr bool PA_APPLY = OP == OP_HESS_PA || OP == OP_HESS_PA_C;
-  constexpr int NSH = (OP == OP_HESS_PA) ? D * D * (D * D + 1) / 2 : (OP == OP_HESS_PA_C ? kCompactRec : 1);
-  static_assert(!(OP == OP_LINEARIZE_C || OP == OP_HESS_PA_C) || D == 3, "compact records are 3D");
+  // (the product from compact records, OP_HESS_PA_C, is pac_kernel in tmop_pa_compact.cu)
+  constexpr bool PA_APPLY = OP == OP_HESS_PA;
+  constexpr int NSH = PA_APPLY ? D * D * (D * D + 1) / 2 : 1;
+  static_assert(OP != OP_HESS_PA_C, "OP_HESS_PA_C runs in pac_kernel");
+  static_assert(OP != OP_LINEARIZE_C || D == 3, "compact records are 3D");
   NodeMap<N> nodes(p.elem_nodes, p.sx, p.sy);
   for (int e = blockIdx.x * WARPS + warp; e < p.nelem; e += nwarps_total) {
     nodes.element(e, NDOF);
@@ -218,57 +220,6 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
     double emin = INFINITY;
     constexpr int NS = DD * (DD + 1) / 2;
     for (int q = lane; q < QP; q += 32) {
-      if constexpr (OP == OP_HESS_PA_C) {
-        // y = w det W (d^2mu/dT^2 : dA W^-1) W^-t rebuilt from the compact
-        // record: T, then the scaled partials (mu_1, mu_t, mu_11, mu_1t, mu_tt)
-        const R* H = static_cast<const R*>(p.pa) + (size_t)e * p.pa_stride + q;
-        R h[kCompactRec];
-        if (q == lane) {
-#pragma unroll
-          for (int t = 0; t < kCompactRec; ++t) h[t] = hpre[t];
-        } else {
-#pragma unroll
-          for (int t = 0; t < kCompactRec; ++t) h[t] = __ldg(H + (size_t)t * QP);
-        }
-        MetricLin<D, R> L;
-#pragma unroll
-        for (int i = 0; i < DD; ++i) L.T[i] = h[i];
-        cof_m<D>(L.T, L.C);
-        L.m1 = h[DD]; L.mt = h[DD + 1]; L.m11 = h[DD + 2]; L.m1t = h[DD + 3]; L.mtt = h[DD + 4];
-        R dA[DD], dT[DD], S[DD];
-#pragma unroll
-        for (int i = 0; i < DD; ++i) dA[i] = Abuf[i * QP + q];
-        if (p.wkind == WK_IDENTITY) {
-#pragma unroll
-          for (int i = 0; i < DD; ++i) dT[i] = dA[i];
-        } else {
-#pragma unroll
-          for (int a = 0; a < D; ++a)
-#pragma unroll
-            for (int b = 0; b < D; ++b) {
-              R t = R(0);
-#pragma unroll
-              for (int c = 0; c < D; ++c) t = fma(dA[a * D + c], Wi[c * D + b], t);
-              dT[a * D + b] = t;
-            }
-        }
-        L.dP(dT, S);
-#pragma unroll
-        for (int a = 0; a < D; ++a)
-#pragma unroll
-          for (int b = 0; b < D; ++b) {
-            R r;
-            if (p.wkind == WK_IDENTITY) {
-              r = S[a * D + b];
-            } else {
-              r = R(0);
-#pragma unroll
-              for (int c = 0; c < D; ++c) r = fma(S[a * D + c], Wi[b * D + c], r);
-            }
-            Abuf[(a * D + b) * QP + q] = r;
-          }
-        continue;
-      }
       if constexpr (OP == OP_HESS_PA) {
         // y = H dA with the stored symmetric A-space Hessian (already scaled by w det W)
         const R* H = static_cast<const R*>(p.pa) + (size_t)e * p.pa_stride + q;
