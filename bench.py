@@ -18,7 +18,8 @@ path) on a bounded sample of the same workload, on the host cores.
 --kernels-only runs warm-up plus K steps and nothing else (for profilers);
 with --profile pa it runs one linearisation and W+K partially assembled
 Hessian actions instead (the linearisation is the second element-kernel
-launch, after the validity check of the mesh).
+launch, after the validity check of the mesh); with --profile mlp, W+K
+training steps (gradients + Adam) of the proposal MLP at batch 4096.
 """
 from __future__ import annotations
 
@@ -297,6 +298,21 @@ def run_ours(args):
         if ev is not None:
             ev[1].record(stream)
 
+    if args.kernels_only and args.profile == "mlp":
+        # W + K training steps of the proposal MLP on random bf16 inputs (batch 4096)
+        from paper_1807_09807_gb300 import learned as L
+        net = L.MLP(L.n_features(3), L.n_targets(3), 256, seed=0)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(3)
+        X = (torch.randn((4096, net.ld), device=dev, generator=gen) * 0.5).to(torch.bfloat16).view(torch.int16)
+        T = torch.randn((4096, L.n_targets(3)), device=dev, generator=gen) * 0.1
+        loss = torch.zeros((), dtype=torch.float64, device=dev)
+        for _ in range(args.warmup + args.steps):
+            net.gradients(X, T, loss)
+            net.adam(1e-4)
+        torch.cuda.synchronize()
+        net.close()
+        return 0
     if args.kernels_only and args.profile == "pa":
         # the partially assembled product alone: one linearisation, then W + K products
         ctx.linearize(x)
@@ -399,6 +415,7 @@ def run_ours(args):
     learned = None
     if args.learned and rank == 0:
         learned = learned_proposal(tm, dev, args)
+        learned["curved_boundary"] = learned_proposal(tm, dev, args, "c5curved", "c5curved", measure_step=False)
 
     if rank == 0:
         line = {
@@ -515,16 +532,55 @@ def time_to_converged(tm, m, dev, args):
     return res_all
 
 
-def learned_proposal(tm, dev, args):
+def mlp_gemm_flops(net, batch):
+    """Tensor-core FLOPs of one training step (forward + backward GEMMs) on
+    the padded shapes the kernels run: input K1, hidden H, output N3."""
+    K1, H, N3 = net.ld, net.hidden, 64
+    fwd = K1 * H + H * H + H * N3
+    bwd = N3 * H + H * N3 + H * H + H * H + H * K1   # dW3, dH2, dW2, dH1, dW1
+    return 2 * batch * (fwd + bwd)
+
+
+def mlp_step_roofline(L, net, X, T, reps=20):
+    """One training step (loss gradients + Adam) of the proposal MLP at batch
+    4096, CUDA-event timed, against the measured dense bf16 tensor peak. The
+    GEMMs are small (K <= 4096), so the step is bound by latency and launches,
+    not by the tensor cores; the fraction says how far."""
+    import torch
+    loss = torch.zeros((), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        net.gradients(X, T, loss)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        net.gradients(X, T, loss)
+        net.adam(1e-12)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    flops = mlp_gemm_flops(net, X.shape[0])
+    peak = measured_peaks().get("bf16_tflops", 1877.0)
+    tf = flops / (ms * 1e-3) / 1e12
+    return {"batch": int(X.shape[0]), "ms": ms, "gemm_flops": flops,
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                         "kernel": "k_gemm_tc (tcgen05.mma kind::f16, 128x64 tiles, split-K for weight gradients)",
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured)"}}
+
+
+def learned_proposal(tm, dev, args, train_preset="c5", apply_preset="c5apply", measure_step=True):
     """Train the proposal MLP on Newton-converged displacements of seeded
-    32x32 order-3 meshes (mu2, jitter 0.15h), then on a 128x128 order-3 mesh
-    compare plain FP64 Newton from the jittered mesh with the FP32 form
-    started from the proposal (with its fallback). Same absolute target
-    |g| <= 1e-12 |g(x0)| for both."""
+    32x32 order-3 meshes (mu2, jitter 0.15h), then on unseen meshes compare
+    plain FP64 Newton from the jittered mesh with the FP32 form started from
+    the proposal (with its fallback). Same absolute target |g| <= 1e-12
+    |g(x0)| for both. Presets: the unit square (c5 / 128x128 c5apply, the
+    optimum is the uniform grid) or the curved top boundary (c5curved, train
+    and apply at 32x32: the optimum moves ~6 h from the mapped lattice)."""
     import torch
     from paper_1807_09807_gb300 import learned as L
     t0 = time.perf_counter()
-    ds = L.make_dataset(n_meshes=args.train_meshes, seed0=1000, chunk=250)
+    ds = L.make_dataset(n_meshes=args.train_meshes, seed0=1000, chunk=250, preset=train_preset)
     t_data = time.perf_counter() - t0
     net = L.MLP(L.n_features(3), L.n_targets(3), 256, seed=0)
     t0 = time.perf_counter()
@@ -534,7 +590,7 @@ def learned_proposal(tm, dev, args):
     out = {"train_meshes": args.train_meshes, "train_samples": int(ds.X.shape[0]), "data_seconds": t_data,
            "train_seconds": t_train, "train_loss_first_last": [hist[0], hist[-1]], "apply": []}
     for seed in (5000, 5001):
-        m = mg.make_mesh("c5apply", seed)
+        m = mg.make_mesh(apply_preset, seed)
         c64 = tm.Context.from_mesh(m)
         c32 = tm.Context.from_mesh(m, precision=tm.FP32_MIXED)
         x0 = torch.tensor(m.x, device=dev)
@@ -555,7 +611,7 @@ def learned_proposal(tm, dev, args):
         torch.cuda.synchronize()
         tb = time.perf_counter() - t0
         out["apply"].append({
-            "mesh": f"128x128 order-3 quads, seed {seed}", "F0": F0,
+            "mesh": f"{m.nx[0]}x{m.nx[1]} order-3 quads ({apply_preset}), seed {seed}", "F0": F0,
             "fp64_plain": {"seconds": ta, "status": tm.status_string(ra.status), "newton": ra.report["iterations"],
                            "krylov": ra.report["krylov_iterations"], "F": ra.report["F"]},
             "fp32_learned": {"seconds": tb, "status": tm.status_string(rb.status), "proposal_used": prop.used,
@@ -566,6 +622,8 @@ def learned_proposal(tm, dev, args):
             "speedup": ta / tb})
         c64.close()
         c32.close()
+    if measure_step:
+        out["mlp_step"] = mlp_step_roofline(L, net, ds.X[:4096], ds.T[:4096])   # after the proposals: it steps Adam
     net.close()
     return out
 
@@ -587,9 +645,9 @@ def main():
     ap.add_argument("--train-epochs", type=int, default=15)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels-only", action="store_true")
-    ap.add_argument("--profile", choices=["step", "pa"], default="step",
-                    help="with --kernels-only: the timed step (gradient + Hessian action) or the partially "
-                         "assembled Hessian action alone")
+    ap.add_argument("--profile", choices=["step", "pa", "mlp"], default="step",
+                    help="with --kernels-only: the timed step (gradient + Hessian action), the partially "
+                         "assembled Hessian action alone, or training steps of the proposal MLP")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if not args.kernels_only else args.warmup
     if args.impl == "reference":

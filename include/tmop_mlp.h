@@ -56,8 +56,11 @@ int tmop_patch_apply(int order, int nx, int ny, const double* x0, const uint8_t*
                      int ldy, double* x_out, void* stream);
 
 /* The network: n_in -> n_hidden -> n_hidden -> n_out, ReLU between layers,
- * bfloat16 weights and activations with FP32 accumulation on the tensor
- * cores (mma.sync m16n8k16), FP32 master weights and Adam state.
+ * bfloat16 weights and activations with FP32 accumulation on the
+ * fifth-generation tensor cores (tcgen05.mma, accumulators in tensor
+ * memory), FP32 master weights and Adam state. A GEMM whose bounded wait for
+ * its tensor-core work gives up is reported as TMOP_ERR_CUDA by the next
+ * tmop_mlp_get.
  * n_hidden must be a multiple of 64; n_in <= 1024, n_out <= 64. Weights are
  * initialised He-normal from seed (the last layer scaled by 0.1), biases 0. */
 typedef struct tmop_mlp tmop_mlp;

@@ -1,12 +1,13 @@
 // Learned initial-iterate proposal: patch features, targets, proposal
 // scatter, and a 3-layer MLP trained with hand-written bfloat16 tensor-core
-// GEMMs (mma.sync m16n8k16, FP32 accumulation) and Adam.
+// GEMMs (tcgen05.mma, FP32 accumulation in tensor memory) and Adam.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <random>
 #include <vector>
 
@@ -93,127 +94,235 @@ __global__ void k_apply(Grid2 G0, const uint8_t* fixed, const float* Y, int ldy,
   xo[dof] = v;
 }
 
-// ---------------------------------------------------------------- GEMM
-constexpr int BM = 64, BN = 64, BKT = 32, PADK = 8;
+// ---------------------------------------------------------------- GEMM (tcgen05)
+// C[m][n] = sum_k A(m,k) B(n,k) with A(m,k) = AK ? A[m*lda+k] : A[k*lda+m] and
+// B(n,k) = BK ? B[n*ldb+k] : B[k*ldb+n], on the fifth-generation tensor cores.
+// One CTA of 4 warps per 128 x 64 tile of C. K goes in chunks of 64: the
+// threads stage the A and B chunks in shared memory in the K-major,
+// unswizzled operand layout of tcgen05 (8-row x 16-byte core matrices,
+// transposing operands that are stored MN-major), one thread issues four
+// tcgen05.mma (kind::f16: bf16 inputs, FP32 accumulator in tensor memory,
+// 128 lanes x 64 columns) and tcgen05.commit, which signals an mbarrier; at
+// the end each warp reads its 32 accumulator lanes with tcgen05.ld for the
+// epilogue. blockIdx.z splits K for the weight gradients (a small M x N grid
+// over K = batch): each split writes its FP32 partial tile to a slice of a
+// workspace, and k_splitk_sum adds the slices in split order.
+// Requirements (checked by gemm()): M, N multiples of 64, K of 64, leading
+// dimensions multiples of 8 (16-byte rows); rows of the last 128-row tile
+// beyond M read as zero and are not stored.
+constexpr int TM = 128, TN = 64, TK = 64;
+constexpr uint32_t kTmemCols = 64;                    // FP32 accumulator columns (power of 2, >= 32)
+constexpr long kMmaSpin = 1L << 20;                   // bound on the wait for one chunk's MMAs
 enum { EPI_BIAS_RELU_BF16 = 0, EPI_BIAS_F32 = 1, EPI_MASK_BF16 = 2, EPI_F32 = 3 };
 
-__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of element (r, k) of a [rows][TK] tile in the core-matrix layout:
+// core matrix (r / 8, k / 8) is 128 contiguous bytes, K-adjacent core matrices
+// 128 B apart (leading byte offset), row-adjacent ones TK / 8 * 128 B apart
+// (stride byte offset)
+__device__ __forceinline__ int cm_off(int r, int k) {
+  return ((r >> 3) * (TK >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
-// C[m][n] = sum_k A(m,k) B(n,k) with A(m,k) = AK ? A[m*lda+k] : A[k*lda+m] and
-// B(n,k) = BK ? B[n*ldb+k] : B[k*ldb+n]. M, N multiples of 64, K of 32, leading
-// dimensions multiples of 8 (16-byte rows). Block 64x64, 4 warps of 32x32.
-template <bool AK, bool BK, int EPI>
-__global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16* __restrict__ A, int lda,
-                                              const bf16* __restrict__ B, int ldb, void* __restrict__ C, int ldc,
-                                              const float* __restrict__ bias, const bf16* __restrict__ ref, int ldr) {
-  __shared__ __align__(16) bf16 As[BM][BKT + PADK];
-  __shared__ __align__(16) bf16 Bs[BN][BKT + PADK];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
+// shared-memory matrix descriptor: start address, leading and stride byte
+// offsets (all >> 4), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
 
-  for (int k0 = 0; k0 < K; k0 += BKT) {
-#pragma unroll
-    for (int c = tid; c < BM * BKT / 8; c += 128) {
+// instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and
+// B bf16 (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 at bit
+// 17, M / 16 at bit 24
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                            ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(saddr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+template <bool AK, bool BK, int EPI>
+__global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int kper, const bf16* __restrict__ A, int lda,
+                                                 const bf16* __restrict__ B, int ldb, void* __restrict__ C, int ldc,
+                                                 size_t split_stride, const float* __restrict__ bias,
+                                                 const bf16* __restrict__ ref, int ldr, int* err) {
+  // 24 KB of operands, padded to 26 KB so that at most 8 CTAs share an SM:
+  // 8 x 64 accumulator columns = the SM's 512 columns of tensor memory
+  __shared__ __align__(128) unsigned char sA[TM * TK * 2 + 2048];
+  __shared__ __align__(128) unsigned char sB[TN * TK * 2];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  const int kb = blockIdx.z * kper, ke = min(K, kb + kper);
+
+  if (warp == 0) {  // the accumulator: 128 lanes x 64 FP32 columns of tensor memory
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  bool ok = true;
+  int chunk = 0;
+  for (int k0 = kb; k0 < ke; k0 += TK, ++chunk) {
+    // ---- stage the chunk (zero rows beyond M)
+    for (int c = tid; c < TM * TK / 8; c += 128) {
       if (AK) {
-        const int r = c / (BKT / 8), kc = (c % (BKT / 8)) * 8;
-        *reinterpret_cast<uint4*>(&As[r][kc]) =
-            *reinterpret_cast<const uint4*>(&A[(size_t)(m0 + r) * lda + k0 + kc]);
+        const int r = c / (TK / 8), kc = (c % (TK / 8)) * 8;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (m0 + r < M) v = *reinterpret_cast<const uint4*>(&A[(size_t)(m0 + r) * lda + k0 + kc]);
+        *reinterpret_cast<uint4*>(sA + cm_off(r, kc)) = v;
       } else {
-        const int kk = c / (BM / 8), mc = (c % (BM / 8)) * 8;
-        const uint4 v = *reinterpret_cast<const uint4*>(&A[(size_t)(k0 + kk) * lda + m0 + mc]);
-        const bf16* e = reinterpret_cast<const bf16*>(&v);
+        const int kk = c / (TM / 8), mc = (c % (TM / 8)) * 8;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (m0 + mc < M) v = *reinterpret_cast<const uint4*>(&A[(size_t)(k0 + kk) * lda + m0 + mc]);
+        const unsigned short* e = reinterpret_cast<const unsigned short*>(&v);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) As[mc + j][kk] = e[j];
+        for (int j = 0; j < 8; ++j) *reinterpret_cast<unsigned short*>(sA + cm_off(mc + j, kk)) = e[j];
       }
+    }
+    for (int c = tid; c < TN * TK / 8; c += 128) {
       if (BK) {
-        const int r = c / (BKT / 8), kc = (c % (BKT / 8)) * 8;
-        *reinterpret_cast<uint4*>(&Bs[r][kc]) =
+        const int r = c / (TK / 8), kc = (c % (TK / 8)) * 8;
+        *reinterpret_cast<uint4*>(sB + cm_off(r, kc)) =
             *reinterpret_cast<const uint4*>(&B[(size_t)(n0 + r) * ldb + k0 + kc]);
       } else {
-        const int kk = c / (BN / 8), nc = (c % (BN / 8)) * 8;
+        const int kk = c / (TN / 8), nc = (c % (TN / 8)) * 8;
         const uint4 v = *reinterpret_cast<const uint4*>(&B[(size_t)(k0 + kk) * ldb + n0 + nc]);
-        const bf16* e = reinterpret_cast<const bf16*>(&v);
+        const unsigned short* e = reinterpret_cast<const unsigned short*>(&v);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) Bs[nc + j][kk] = e[j];
+        for (int j = 0; j < 8; ++j) *reinterpret_cast<unsigned short*>(sB + cm_off(nc + j, kk)) = e[j];
       }
     }
+    // generic-proxy stores -> visible to the tensor core's (async proxy) reads
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
 #pragma unroll
-    for (int kk = 0; kk < BKT; kk += 16) {
-      uint32_t a[2][4], b[4][2];
-      const int g = lane >> 2, t2 = (lane & 3) * 2;
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm + i * 16 + g;
-        a[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][kk + t2]);
-        a[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + t2]);
-        a[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][kk + t2 + 8]);
-        a[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + t2 + 8]);
+      for (int s = 0; s < TK / 16; ++s) {  // K = 16 per instruction: two core matrices along K
+        const uint64_t ad = umma_desc(saddr(sA) + s * 256, 128, (TK / 8) * 128);
+        const uint64_t bd = umma_desc(saddr(sB) + s * 256, 128, (TK / 8) * 128);
+        const uint32_t acc = (chunk > 0 || s > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+            : "memory");
       }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int r = wn + j * 8 + g;
-        b[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[r][kk + t2]);
-        b[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[r][kk + t2 + 8]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i], b[j]);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(&bar))
+                   : "memory");
     }
-    __syncthreads();
+    // the chunk's MMAs have read the staged operands (and written the accumulator)
+    bool done = false;
+    for (long i = 0; i < kMmaSpin && !done; ++i) done = mbar_try(&bar, (uint32_t)(chunk & 1));
+    if (!done) ok = false;
+    if (__syncthreads_or(!ok)) {
+      ok = false;
+      break;
+    }
   }
-  const int g = lane >> 2, t2 = (lane & 3) * 2;
+  tc_fence_after();
+  if (ok && chunk > 0) {
+    // ---- epilogue: warp w owns accumulator lanes (rows) 32 w .. 32 w + 31
+    const int m = m0 + warp * 32 + lane;
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+    for (int cb = 0; cb < TN / 16; ++cb) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 16)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (m < M) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int m = m0 + wm + i * 16 + g + h * 8, n = n0 + wn + j * 8 + t2;
-        float v0 = acc[i][j][2 * h], v1 = acc[i][j][2 * h + 1];
-        if (EPI == EPI_BIAS_RELU_BF16 || EPI == EPI_BIAS_F32) {
-          v0 += bias[n];
-          v1 += bias[n + 1];
-        }
-        if (EPI == EPI_BIAS_RELU_BF16) {
-          v0 = fmaxf(v0, 0.0f);
-          v1 = fmaxf(v1, 0.0f);
-        }
-        if (EPI == EPI_MASK_BF16) {
-          const __nv_bfloat162 rr = *reinterpret_cast<const __nv_bfloat162*>(&ref[(size_t)m * ldr + n]);
-          if (!(__bfloat162float(rr.x) > 0.0f)) v0 = 0.0f;
-          if (!(__bfloat162float(rr.y) > 0.0f)) v1 = 0.0f;
-        }
-        if (EPI == EPI_BIAS_RELU_BF16 || EPI == EPI_MASK_BF16) {
-          *reinterpret_cast<__nv_bfloat162*>(&reinterpret_cast<bf16*>(C)[(size_t)m * ldc + n]) =
-              __floats2bfloat162_rn(v0, v1);
-        } else {
-          *reinterpret_cast<float2*>(&reinterpret_cast<float*>(C)[(size_t)m * ldc + n]) = make_float2(v0, v1);
+        for (int j = 0; j < 16; j += 2) {
+          const int n = n0 + cb * 16 + j;
+          float v0 = __uint_as_float(r[j]), v1 = __uint_as_float(r[j + 1]);
+          if (EPI == EPI_BIAS_RELU_BF16 || EPI == EPI_BIAS_F32) {
+            v0 += bias[n];
+            v1 += bias[n + 1];
+          }
+          if (EPI == EPI_BIAS_RELU_BF16) {
+            v0 = fmaxf(v0, 0.0f);
+            v1 = fmaxf(v1, 0.0f);
+          }
+          if (EPI == EPI_MASK_BF16) {
+            const __nv_bfloat162 rr = *reinterpret_cast<const __nv_bfloat162*>(&ref[(size_t)m * ldr + n]);
+            if (!(__bfloat162float(rr.x) > 0.0f)) v0 = 0.0f;
+            if (!(__bfloat162float(rr.y) > 0.0f)) v1 = 0.0f;
+          }
+          if (EPI == EPI_BIAS_RELU_BF16 || EPI == EPI_MASK_BF16) {
+            *reinterpret_cast<__nv_bfloat162*>(&reinterpret_cast<bf16*>(C)[(size_t)m * ldc + n]) =
+                __floats2bfloat162_rn(v0, v1);
+          } else {
+            float* Cf = reinterpret_cast<float*>(C) + blockIdx.z * split_stride;
+            *reinterpret_cast<float2*>(&Cf[(size_t)m * ldc + n]) = make_float2(v0, v1);
+          }
         }
       }
+    }
+  }
+  if (!ok && tid == 0) atomicExch(err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
+// C[i] = sum over splits z (in order) of W[z][i], i < count
+__global__ void k_splitk_sum(const float* __restrict__ W, int splits, size_t stride, size_t count, float* C) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    float s = 0.0f;
+    for (int z = 0; z < splits; ++z) s += W[z * stride + i];
+    C[i] = s;
+  }
+}
+
+// Launch; FP32 outputs with a small tile grid and a long K are split along K
+// through the workspace ws (capacity ws_cap floats).
 template <bool AK, bool BK, int EPI>
 int gemm(int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb, void* C, int ldc, const float* bias,
-         const bf16* ref, int ldr, cudaStream_t s) {
-  if (M % BM || N % BN || K % BKT || lda % 8 || ldb % 8 || ldc % 2 || M <= 0 || N <= 0 || K <= 0) return TMOP_ERR_ARG;
-  dim3 grid(N / BN, M / BM);
-  k_gemm<AK, BK, EPI><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, ref, ldr);
+         const bf16* ref, int ldr, float* ws, size_t ws_cap, int* err, cudaStream_t s) {
+  if (M % 64 || N % TN || K % TK || lda % 8 || ldb % 8 || ldc % 2 || M <= 0 || N <= 0 || K <= 0) return TMOP_ERR_ARG;
+  const int mt = (M + TM - 1) / TM, nt = N / TN;
+  int splits = 1;
+  if (EPI == EPI_F32 && ws) {
+    while (splits < 64 && mt * nt * splits * 2 <= 512 && K % (splits * 2 * TK) == 0 &&
+           (size_t)(splits * 2) * M * ldc <= ws_cap)
+      splits *= 2;
+  }
+  const int kper = K / splits;
+  dim3 grid(nt, mt, splits);
+  if (splits == 1) {
+    k_gemm_tc<AK, BK, EPI><<<grid, 128, 0, s>>>(M, N, K, kper, A, lda, B, ldb, C, ldc, 0, bias, ref, ldr, err);
+  } else {
+    const size_t stride = (size_t)M * ldc;
+    k_gemm_tc<AK, BK, EPI><<<grid, 128, 0, s>>>(M, N, K, kper, A, lda, B, ldb, ws, ldc, stride, bias, ref, ldr, err);
+    k_splitk_sum<<<256, 256, 0, s>>>(ws, splits, stride, stride, reinterpret_cast<float*>(C));
+  }
   return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
 }
 
@@ -253,14 +362,41 @@ __global__ void k_sum_parts(const double* part, int np, double* out) {
   }
 }
 
-// column sums of a [rows][ld] matrix (float or bf16) into out[ncol]
+// Column sums of a [rows][ld] matrix (float or bf16) into out[ncol] (the
+// bias gradients), in two deterministic passes: block (x, y) sums rows
+// chunk y of columns x * 64 .. x * 64 + 63 (the 4 warps of a block split the
+// chunk's rows, consecutive lanes read consecutive columns), then one thread
+// per column adds the chunk partials in order.
+constexpr int kColChunks = 64;
 template <class Tv>
-__global__ void k_colsum(const Tv* X, int rows, int ld, int ncol, float* out) {
+__global__ void k_colsum_part(const Tv* X, int rows, int ld, int ncol, float* part) {
+  __shared__ float red[4][64];
+  const int lane = threadIdx.x & 63, q = threadIdx.x >> 6;   // 256 threads: 4 row quarters x 64 columns
+  const int j = blockIdx.x * 64 + lane;
+  const int per = (rows + kColChunks - 1) / kColChunks;
+  const int r0 = blockIdx.y * per, r1 = min(rows, r0 + per);
+  float s = 0.0f;
+  if (j < ncol)
+    for (int r = r0 + q; r < r1; r += 4) s += (float)X[(size_t)r * ld + j];
+  red[q][lane] = s;
+  __syncthreads();
+  if (q == 0 && j < ncol) part[(size_t)blockIdx.y * ncol + j] = ((red[0][lane] + red[1][lane]) + red[2][lane]) + red[3][lane];
+}
+
+__global__ void k_colsum_final(const float* part, int ncol, float* out) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= ncol) return;
   float s = 0.0f;
-  for (int r = 0; r < rows; ++r) s += (float)X[(size_t)r * ld + j];
+  for (int c = 0; c < kColChunks; ++c) s += part[(size_t)c * ncol + j];
   out[j] = s;
+}
+
+template <class Tv>
+int colsum(const Tv* X, int rows, int ld, int ncol, float* part, float* out, cudaStream_t s) {
+  dim3 grid((ncol + 63) / 64, kColChunks);
+  k_colsum_part<Tv><<<grid, 256, 0, s>>>(X, rows, ld, ncol, part);
+  k_colsum_final<<<(ncol + 127) / 128, 128, 0, s>>>(part, ncol, out);
+  return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
 }
 
 __global__ void k_adam(float* w, float* m, float* v, const float* g, size_t n, float lr, float b1t, float b2t,
@@ -297,6 +433,9 @@ struct tmop_mlp {
   bf16 *H1 = nullptr, *H2 = nullptr, *dYb = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
   float *Y = nullptr, *dYf = nullptr;
   double* part = nullptr;
+  float* ws = nullptr;   // split-K partial tiles of the weight-gradient GEMMs
+  size_t ws_cap = 0;     // in floats
+  int* d_err = nullptr;  // set when a GEMM's bounded wait for its MMAs gave up
   int t = 0;
 };
 
@@ -330,11 +469,11 @@ int refresh_bf16(tmop_mlp* n, cudaStream_t s) {
 
 int forward_impl(tmop_mlp* n, const bf16* X, int batch, float* Y, int ldy, cudaStream_t s) {
   int rc = gemm<true, true, EPI_BIAS_RELU_BF16>(batch, n->H, n->K1, X, n->K1, n->W1, n->K1, n->H1, n->H,
-                                                P(n, n->w, 1), nullptr, 0, s);
+                                                P(n, n->w, 1), nullptr, 0, n->ws, n->ws_cap, n->d_err, s);
   if (!rc) rc = gemm<true, true, EPI_BIAS_RELU_BF16>(batch, n->H, n->H, n->H1, n->H, n->W2, n->H, n->H2, n->H,
-                                                     P(n, n->w, 3), nullptr, 0, s);
+                                                     P(n, n->w, 3), nullptr, 0, n->ws, n->ws_cap, n->d_err, s);
   if (!rc) rc = gemm<true, true, EPI_BIAS_F32>(batch, n->N3, n->H, n->H2, n->H, n->W3, n->H, Y, ldy,
-                                               P(n, n->w, 5), nullptr, 0, s);
+                                               P(n, n->w, 5), nullptr, 0, n->ws, n->ws_cap, n->d_err, s);
   return rc;
 }
 
@@ -389,6 +528,7 @@ void tmop_mlp_destroy(tmop_mlp* n) {
   cudaFree(n->W1); cudaFree(n->W2); cudaFree(n->W3);
   cudaFree(n->H1); cudaFree(n->H2); cudaFree(n->dYb); cudaFree(n->dZ2); cudaFree(n->dZ1);
   cudaFree(n->Y); cudaFree(n->dYf); cudaFree(n->part);
+  cudaFree(n->ws); cudaFree(n->d_err);
   delete n;
 }
 
@@ -417,10 +557,14 @@ int tmop_mlp_create(int n_in, int n_hidden, int n_out, uint64_t seed, tmop_mlp**
   fill(2, n->H, n->H, n->H, sqrtf(2.0f / n->H));
   fill(4, n_out, n->H, n->H, 0.1f * sqrtf(2.0f / n->H));
   int rc = TMOP_OK;
-  if (cudaMalloc(&n->w, acc * 4) || cudaMalloc(&n->g, acc * 4) || cudaMalloc(&n->m, acc * 4) ||
+  // split-K workspace: up to 64 slices of the largest weight gradient (rows padded to 128)
+  n->ws_cap = (size_t)64 * ((std::max(n->H, n->N3) + 127) / 128 * 128) * std::max(n->H, n->K1);
+  if (cudaMalloc(&n->ws, n->ws_cap * 4) || cudaMalloc(&n->d_err, sizeof(int)) || cudaMemset(n->d_err, 0, sizeof(int)))
+    rc = TMOP_ERR_CUDA;
+  if (rc == TMOP_OK && (cudaMalloc(&n->w, acc * 4) || cudaMalloc(&n->g, acc * 4) || cudaMalloc(&n->m, acc * 4) ||
       cudaMalloc(&n->v, acc * 4) || cudaMalloc(&n->W1, sz[0] * 2) || cudaMalloc(&n->W2, sz[2] * 2) ||
       cudaMalloc(&n->W3, sz[4] * 2) || cudaMemcpy(n->w, host.data(), acc * 4, cudaMemcpyHostToDevice) ||
-      cudaMemset(n->g, 0, acc * 4) || cudaMemset(n->m, 0, acc * 4) || cudaMemset(n->v, 0, acc * 4))
+      cudaMemset(n->g, 0, acc * 4) || cudaMemset(n->m, 0, acc * 4) || cudaMemset(n->v, 0, acc * 4)))
     rc = TMOP_ERR_CUDA;
   if (rc == TMOP_OK) rc = refresh_bf16(n, 0);
   if (rc == TMOP_OK && cudaDeviceSynchronize() != cudaSuccess) rc = TMOP_ERR_CUDA;
@@ -462,7 +606,14 @@ static int copy_params(tmop_mlp* n, float* dev, float* host, bool to_host) {
 
 int tmop_mlp_get(tmop_mlp* n, int which, float* host, size_t cnt) {
   if (!n || !host || cnt != tmop_mlp_num_params(n) || (which != 0 && which != 1)) return TMOP_ERR_ARG;
-  return copy_params(n, which == 0 ? n->w : n->g, host, true);
+  int rc = copy_params(n, which == 0 ? n->w : n->g, host, true);
+  int e = 0;  // a GEMM whose bounded wait for its MMAs gave up since the last check
+  if (rc == TMOP_OK && cudaMemcpy(&e, n->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = TMOP_ERR_CUDA;
+  if (rc == TMOP_OK && e) {
+    cudaMemset(n->d_err, 0, sizeof(int));
+    rc = TMOP_ERR_CUDA;
+  }
+  return rc;
 }
 
 int tmop_mlp_set(tmop_mlp* n, const float* host, size_t cnt) {
@@ -503,20 +654,20 @@ int tmop_mlp_gradients(tmop_mlp* n, const uint16_t* Xu, const float* T, int ldt,
   if (loss) k_sum_parts<<<1, 32, 0, s>>>(n->part, lblocks, loss);
   // layer 3: dW3 = dY^T H2, db3 = colsum dY, dH2 = dY W3 masked by H2 > 0
   rc = gemm<false, false, EPI_F32>(n->N3, n->H, batch, n->dYb, n->N3, n->H2, n->H, P(n, n->g, 4), n->H, nullptr,
-                                   nullptr, 0, s);
-  k_colsum<float><<<1, 64, 0, s>>>(n->dYf, batch, n->N3, n->N3, P(n, n->g, 5));
+                                   nullptr, 0, n->ws, n->ws_cap, n->d_err, s);
+  if (!rc) rc = colsum<float>(n->dYf, batch, n->N3, n->N3, n->ws, P(n, n->g, 5), s);
   if (!rc) rc = gemm<true, false, EPI_MASK_BF16>(batch, n->H, n->N3, n->dYb, n->N3, n->W3, n->H, n->dZ2, n->H,
-                                                 nullptr, n->H2, n->H, s);
+                                                 nullptr, n->H2, n->H, n->ws, n->ws_cap, n->d_err, s);
   // layer 2
   if (!rc) rc = gemm<false, false, EPI_F32>(n->H, n->H, batch, n->dZ2, n->H, n->H1, n->H, P(n, n->g, 2), n->H,
-                                            nullptr, nullptr, 0, s);
-  k_colsum<bf16><<<(n->H + 127) / 128, 128, 0, s>>>(n->dZ2, batch, n->H, n->H, P(n, n->g, 3));
+                                            nullptr, nullptr, 0, n->ws, n->ws_cap, n->d_err, s);
+  if (!rc) rc = colsum<bf16>(n->dZ2, batch, n->H, n->H, n->ws, P(n, n->g, 3), s);
   if (!rc) rc = gemm<true, false, EPI_MASK_BF16>(batch, n->H, n->H, n->dZ2, n->H, n->W2, n->H, n->dZ1, n->H,
-                                                 nullptr, n->H1, n->H, s);
+                                                 nullptr, n->H1, n->H, n->ws, n->ws_cap, n->d_err, s);
   // layer 1
   if (!rc) rc = gemm<false, false, EPI_F32>(n->H, n->K1, batch, n->dZ1, n->H, X, n->K1, P(n, n->g, 0), n->K1,
-                                            nullptr, nullptr, 0, s);
-  k_colsum<bf16><<<(n->H + 127) / 128, 128, 0, s>>>(n->dZ1, batch, n->H, n->H, P(n, n->g, 1));
+                                            nullptr, nullptr, 0, n->ws, n->ws_cap, n->d_err, s);
+  if (!rc) rc = colsum<bf16>(n->dZ1, batch, n->H, n->H, n->ws, P(n, n->g, 1), s);
   if (rc) return rc;
   return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
 }

@@ -193,6 +193,10 @@ PRESETS = {
     # learned-proposal meshes: 2D order 3, jitter +-0.15h, mu2 (32x32 train, 128x128 apply)
     "c5": dict(dim=2, order=3, nx=32, nq=5, jitter=0.15, deform=None, metric=2),
     "c5apply": dict(dim=2, order=3, nx=128, nq=5, jitter=0.15, deform=None, metric=2),
+    # the same with a curved top boundary y = 1 + 0.15 sin(pi x) (all boundary
+    # nodes fixed on it): the minimiser is no longer the uniform grid
+    "c5curved": dict(dim=2, order=3, nx=32, nq=5, jitter=0.15, deform="bump", metric=2),
+    "c5curvedapply": dict(dim=2, order=3, nx=128, nq=5, jitter=0.15, deform="bump", metric=2),
 }
 
 REDRAW_STRIDE = 1_000_003
@@ -216,6 +220,10 @@ def make_mesh(name: str = "c1", seed: int = 1, accept: Optional[Callable[["Mesh"
         # only the x-component; sin(2 pi x) sin(2 pi y) vanishes on the boundary
         x0 = x0.copy()
         x0[0] += 0.05 * np.sin(2 * np.pi * x0[0]) * np.sin(2 * np.pi * x0[1])
+    if cfg.get("deform") == "bump" and dim == 2:
+        # y -> y (1 + a sin(pi x)): the top edge becomes the curve 1 + a sin(pi x)
+        x0 = x0.copy()
+        x0[1] *= 1.0 + float(cfg.get("bump", 0.15)) * np.sin(np.pi * x0[0])
     # h is the node spacing of the order-k lattice, 1 / (k * n_x): jitter is
     # measured against the distance between neighbouring nodes.
     h = 1.0 / (order * max(nxt))

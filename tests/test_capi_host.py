@@ -78,7 +78,23 @@ def test_structured_mismatch_with_table_is_rejected(lib):
 
 def test_null_arguments(lib):
     assert lib.tmop_energy(None, None, None, None, None) == tm.ERR_ARG
+    assert lib.tmop_energy_device(None, None, None, None, None) == tm.ERR_ARG
     assert lib.tmop_gradient(None, None, None, None) == tm.ERR_ARG
     assert lib.tmop_hess_apply(None, None, None, None, None) == tm.ERR_ARG
     assert lib.tmop_newton_step(None, None, None, None, None) == tm.ERR_ARG
+    assert lib.tmop_newton_solve(None, None, None, None, None) == tm.ERR_ARG
+    assert lib.tmop_krylov_solve(None, None, None, None, None, None, None) == tm.ERR_ARG
+    assert lib.tmop_linearize(None, None, None) == tm.ERR_ARG
+    assert lib.tmop_hess_apply_pa(None, None, None, None) == tm.ERR_ARG
+    assert lib.tmop_hessian_diagonal(None, None, None) == tm.ERR_ARG
+    assert lib.tmop_element_min_detA(None, None, None, None) == tm.ERR_ARG
+    assert lib.tmop_set_composite(None, 0, None, None) == tm.ERR_ARG
+    assert lib.tmop_set_restricted_movement(None, 0.0, None, None) == tm.ERR_ARG
+    assert lib.tmop_jacobians(None, None, None, None) == tm.ERR_ARG
+    assert lib.tmop_set_targets_from_positions(None, 0, None, None) == tm.ERR_ARG
+    assert lib.tmop_pa_layout(None, None, None, None) == tm.ERR_ARG
+    assert lib.tmop_sizes(None, None, None, None, None) == tm.ERR_ARG
+    # empty input: nothing to convert, no device work
+    assert lib.tmop_selftest_convert(None, None, None, 0, None) == tm.OK
+    assert lib.tmop_selftest_convert(None, None, None, 5, None) == tm.ERR_ARG
     lib.tmop_destroy(None)

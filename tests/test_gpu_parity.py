@@ -222,6 +222,31 @@ def test_fp64_tangential_relaxation(tm):
         assert np.array_equal(xf[m.fixed == 1], m.x[m.fixed == 1])
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_all_dofs_fixed_and_zero_rhs(tm, prec):
+    """Degenerate cases: a mesh whose nodes are all on the boundary (one
+    order-1 element, 2D and 3D) has no free dof, so the gradient and every
+    Hessian action vanish and Newton stops at once with x unchanged; a
+    Krylov solve with b = 0 returns p = 0."""
+    for name, nx in (("c1", 1), ("c3", (1, 1, 1))):
+        m = make(name, 1, order=1, nq=2, nx=nx)
+        assert np.all(m.fixed == 1)
+        ctx = tm.Context.from_mesh(m, precision=tm.FP64 if prec == "fp64" else tm.FP32_MIXED)
+        x = dev(m.x)
+        assert np.all(host(ctx.gradient(x)) == 0.0)
+        v = dev(np.random.default_rng(0).standard_normal(m.x.shape))
+        assert np.all(host(ctx.hess_apply(x, v)) == 0.0)
+        ctx.linearize(x)
+        assert np.all(host(ctx.hess_apply_pa(v)) == 0.0)
+        res = ctx.newton_solve(x, max_newton=5)
+        assert res.status == tm.OK and res.report["iterations"] == 0
+        assert np.array_equal(host(x), m.x)
+    m = make("c1", 1, nx=3)
+    ctx = tm.Context.from_mesh(m)
+    p, it = ctx.krylov_solve(dev(m.x), dev(np.zeros_like(m.x)))
+    assert np.all(host(p) == 0.0) and it >= 0
+
+
 def test_fp64_no_fixed_dofs(tm):
     m = make("c1", 1, nx=3)
     m.fixed = np.zeros_like(m.fixed)

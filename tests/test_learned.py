@@ -32,7 +32,7 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-@pytest.mark.parametrize("batch", [64, 192])
+@pytest.mark.parametrize("batch", [64, 192, 1024])
 def test_mlp_gradients_match_reference(L, batch):
     rng = np.random.default_rng(batch)
     net = L.MLP(200, 18, 256, seed=5)

@@ -452,6 +452,22 @@ def test_per_point_target_fd(dim, mid):
         assert abs((p.energy(xp)[1] - p.energy(xm)[1]) / (2 * h) - g[a, i]) < 1e-6 * np.abs(g).max()
 
 
+def test_curved_boundary_optimum_is_not_the_initial_lattice():
+    """The curved-boundary workload of the learned proposal: with the top
+    boundary on y = 1 + 0.15 sin(pi x) and every boundary node fixed, mu2
+    Newton converges to a mesh that differs from both the mapped lattice and
+    its jittered copy, so a proposal has more to predict than the jitter."""
+    m = mg.make_mesh("c5curved", 3, nx=4, order=2, nq=4)
+    top = m.fixed[1] == 1
+    on_curve = np.isclose(m.x[1], 1.0 + 0.15 * np.sin(np.pi * m.x[0])) & (m.x[1] > 1.0 - 1e-12)
+    assert np.any(on_curve) and np.all(m.fixed[:, on_curve] == 1) and np.any(top)
+    p = _problem(m)
+    rc, x, hist = p.newton(m.x, max_newton=30)
+    assert rc == oracle.OK and hist[-1, 1] <= 1e-12 * hist[0, 1]
+    assert np.abs(x - m.x_ideal).max() > 1e-3
+    assert np.array_equal(x[m.fixed == 1], m.x[m.fixed == 1])
+
+
 def test_tangential_relaxation_on_axis_parallel_boundaries():
     """Section 4.1: boundary nodes slide along axis-parallel faces (only the
     normal displacement is fixed). Boundary nodes stay on their faces exactly,
