@@ -415,7 +415,8 @@ def run_ours(args):
     learned = None
     if args.learned and rank == 0:
         learned = learned_proposal(tm, dev, args)
-        learned["curved_boundary"] = learned_proposal(tm, dev, args, "c5curved", "c5curved", measure_step=False)
+        learned["curved_boundary"] = learned_proposal(tm, dev, args, "c5curved", "c5curved", measure_step=False,
+                                                      train_meshes=args.train_meshes_curved)
 
     if rank == 0:
         line = {
@@ -569,7 +570,7 @@ def mlp_step_roofline(L, net, X, T, reps=20):
                          "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured)"}}
 
 
-def learned_proposal(tm, dev, args, train_preset="c5", apply_preset="c5apply", measure_step=True):
+def learned_proposal(tm, dev, args, train_preset="c5", apply_preset="c5apply", measure_step=True, train_meshes=None):
     """Train the proposal MLP on Newton-converged displacements of seeded
     32x32 order-3 meshes (mu2, jitter 0.15h), then on unseen meshes compare
     plain FP64 Newton from the jittered mesh with the FP32 form started from
@@ -580,14 +581,15 @@ def learned_proposal(tm, dev, args, train_preset="c5", apply_preset="c5apply", m
     import torch
     from paper_1807_09807_gb300 import learned as L
     t0 = time.perf_counter()
-    ds = L.make_dataset(n_meshes=args.train_meshes, seed0=1000, chunk=250, preset=train_preset)
+    train_meshes = args.train_meshes if train_meshes is None else train_meshes
+    ds = L.make_dataset(n_meshes=train_meshes, seed0=1000, chunk=250, preset=train_preset)
     t_data = time.perf_counter() - t0
     net = L.MLP(L.n_features(3), L.n_targets(3), 256, seed=0)
     t0 = time.perf_counter()
     hist = L.train(net, ds, epochs=args.train_epochs, batch=4096, lr=2e-3)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    out = {"train_meshes": args.train_meshes, "train_samples": int(ds.X.shape[0]), "data_seconds": t_data,
+    out = {"train_meshes": train_meshes, "train_samples": int(ds.X.shape[0]), "data_seconds": t_data,
            "train_seconds": t_train, "train_loss_first_last": [hist[0], hist[-1]], "apply": []}
     for seed in (5000, 5001):
         m = mg.make_mesh(apply_preset, seed)
@@ -615,7 +617,7 @@ def learned_proposal(tm, dev, args, train_preset="c5", apply_preset="c5apply", m
             "fp64_plain": {"seconds": ta, "status": tm.status_string(ra.status), "newton": ra.report["iterations"],
                            "krylov": ra.report["krylov_iterations"], "F": ra.report["F"]},
             "fp32_learned": {"seconds": tb, "status": tm.status_string(rb.status), "proposal_used": prop.used,
-                             "F_proposal": prop.F, "newton": rb.report["iterations"],
+                             "proposal_scale": prop.scale, "F_proposal": prop.F, "newton": rb.report["iterations"],
                              "krylov": rb.report["krylov_iterations"], "F": rb.report["F"],
                              "min_detA": rb.report["min_detA"]},
             "F_diff_over_F0": abs(ra.report["F"] - rb.report["F"]) / F0,
@@ -643,6 +645,7 @@ def main():
     ap.add_argument("--no-learned", dest="learned", action="store_false")
     ap.add_argument("--train-meshes", type=int, default=2000)
     ap.add_argument("--train-epochs", type=int, default=15)
+    ap.add_argument("--train-meshes-curved", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels-only", action="store_true")
     ap.add_argument("--profile", choices=["step", "pa", "mlp"], default="step",

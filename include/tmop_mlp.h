@@ -49,11 +49,12 @@ int tmop_patch_features(int order, int nx, int ny, const double* x, int ldx, int
 int tmop_patch_targets(int order, int nx, int ny, const double* x0, const double* x1, int ldx, int first, int count,
                        float* T, int ldt, void* stream);
 
-/* Proposal: x_out = x0 + h Y at every owned dof that is not fixed, x0
- * elsewhere. Y DEVICE float [nx*ny][ldy] in the target layout (all elements,
- * in order); fixed DEVICE uint8 [2][ldx] or NULL. x_out may not alias x0. */
+/* Proposal: x_out = x0 + scale h Y at every owned dof that is not fixed, x0
+ * elsewhere (scale 1 is the network's prediction; smaller scales damp it).
+ * Y DEVICE float [nx*ny][ldy] in the target layout (all elements, in
+ * order); fixed DEVICE uint8 [2][ldx] or NULL. x_out may not alias x0. */
 int tmop_patch_apply(int order, int nx, int ny, const double* x0, const uint8_t* fixed, int ldx, const float* Y,
-                     int ldy, double* x_out, void* stream);
+                     int ldy, double scale, double* x_out, void* stream);
 
 /* The network: n_in -> n_hidden -> n_hidden -> n_out, ReLU between layers,
  * bfloat16 weights and activations with FP32 accumulation on the

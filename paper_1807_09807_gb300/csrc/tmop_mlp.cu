@@ -77,7 +77,7 @@ __global__ void k_targets(Grid2 G0, const double* x1, int first, int count, floa
   T[(size_t)p * ldt + f] = (float)((x1[(size_t)d * G0.ldx + node] - G0.x[(size_t)d * G0.ldx + node]) * G0.nx);
 }
 
-__global__ void k_apply(Grid2 G0, const uint8_t* fixed, const float* Y, int ldy, double* xo) {
+__global__ void k_apply(Grid2 G0, const uint8_t* fixed, const float* Y, int ldy, double scale, double* xo) {
   const size_t nn = (size_t)G0.Nx * G0.Ny;
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= 2 * nn) return;
@@ -89,7 +89,7 @@ __global__ void k_apply(Grid2 G0, const uint8_t* fixed, const float* Y, int ldy,
   const bool owned = gx < k * G0.nx && gy < k * G0.ny;
   if (owned && !(fixed && fixed[dof])) {
     const int e = (gy / k) * G0.nx + gx / k, i = gx % k, j = gy % k;
-    v += (double)Y[(size_t)e * ldy + 2 * (j * k + i) + d] / G0.nx;
+    v += scale * (double)Y[(size_t)e * ldy + 2 * (j * k + i) + d] / G0.nx;
   }
   xo[dof] = v;
 }
@@ -512,13 +512,14 @@ int tmop_patch_targets(int order, int nx, int ny, const double* x0, const double
 }
 
 int tmop_patch_apply(int order, int nx, int ny, const double* x0, const uint8_t* fixed, int ldx, const float* Y,
-                     int ldy, double* x_out, void* stream) {
-  if (order < 1 || order > 4 || nx < 1 || ny < 1 || !x0 || !Y || !x_out || x_out == x0 || ldy < 2 * order * order)
+                     int ldy, double scale, double* x_out, void* stream) {
+  if (order < 1 || order > 4 || nx < 1 || ny < 1 || !x0 || !Y || !x_out || x_out == x0 || ldy < 2 * order * order ||
+      !isfinite(scale))
     return TMOP_ERR_ARG;
   Grid2 G{order, nx, ny, order * nx + 1, order * ny + 1, ldx, x0, {0}};
   if (ldx < G.Nx * G.Ny) return TMOP_ERR_ARG;
   const long long tot = 2LL * G.Nx * G.Ny;
-  k_apply<<<(int)((tot + 255) / 256), 256, 0, (cudaStream_t)stream>>>(G, fixed, Y, ldy, x_out);
+  k_apply<<<(int)((tot + 255) / 256), 256, 0, (cudaStream_t)stream>>>(G, fixed, Y, ldy, scale, x_out);
   return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
 }
 

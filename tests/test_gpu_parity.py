@@ -296,6 +296,31 @@ def test_fp64_full_c4_sampled(tm):
     assert abs(emin.min() - mdo) <= RTOL * abs(mdo)
 
 
+def test_fp32_compact_product_full_c4_sampled(tm):
+    """The benchmark's FP32 Krylov operator at full size (48^3 order-3 hexes,
+    compact records, the launch shape bench.py times): the stored-Hessian
+    product at 64 sampled free nodes against the oracle restricted to the
+    elements around them, within the FP32 bound of the other FP32 products;
+    and the same product from the FP64 context's packed Hessians at 1e-12."""
+    m = make("c4", 1)
+    orc = orc_for(m)
+    x = dev(m.x)
+    rng = np.random.default_rng(4)
+    free = np.nonzero(m.fixed[0] == 0)[0]
+    nodes = rng.choice(free, 64, replace=False)
+    els = _patch(m, nodes)
+    v = rng.standard_normal(m.x.shape)
+    yo = orc.hess_apply(m.x, v, elems=els)[:, nodes]
+    c32 = tm.Context.from_mesh(m, precision=tm.FP32_MIXED)
+    c32.linearize(x)
+    assert c32.pa_layout()[0] == 14
+    assert rel(host(c32.hess_apply_pa(dev(v)))[:, nodes], yo) <= 1e-5
+    c32.close()
+    c64 = tm.Context.from_mesh(m)
+    c64.linearize(x)
+    assert rel(host(c64.hess_apply_pa(dev(v)))[:, nodes], yo) <= RTOL
+
+
 def test_inverted_mesh(tm):
     m = make("c1", 1, nx=4)
     x = m.x_ideal.copy()

@@ -129,6 +129,9 @@ def test_patch_features_targets_apply(L):
     # every free node off the right/top boundary is owned by exactly one element
     assert np.abs(xp - x1).max() <= 1e-9
     assert np.array_equal(xp[m.fixed == 1], m.x[m.fixed == 1])
+    # a damped proposal moves each owned free node by the same fraction
+    xh = L.apply(m, x0, torch.tensor(m.fixed, device="cuda"), Y, scale=0.25).cpu().numpy()
+    assert np.abs(xh - (m.x + 0.25 * (x1 - m.x))).max() <= 1e-9
 
 
 def test_learned_proposal_gain(L):
