@@ -309,6 +309,12 @@ int tmop_set_targets_from_positions(tmop_ctx* ctx, int kind, const double* x0, v
  * widening. Asynchronous. Errors: TMOP_ERR_ARG, TMOP_ERR_CUDA. */
 int tmop_selftest_convert(const double* in, float* f32, double* back, size_t n, void* stream);
 
+/* Diagnostic: tau^{-1/3} as the FP64 kernels evaluate it (mu303 and its
+ * derivatives): Newton's method from an FP32 estimate on [2^-120, 2^120],
+ * the library cube root elsewhere. in, out DEVICE [n] FP64. Asynchronous.
+ * Errors: TMOP_ERR_ARG, TMOP_ERR_CUDA. */
+int tmop_selftest_rcbrt(const double* in, double* out, size_t n, void* stream);
+
 /* Sizes of a context: Q (points per element), ndof = dim * nnode. */
 int tmop_sizes(const tmop_ctx* ctx, int* dim, int* nelem, int* nnode, int* Q);
 

@@ -49,8 +49,14 @@ template <class R> __device__ __forceinline__ Dual<R> recip(Dual<R> a) {
   R r = R(1) / a.v;
   return {r, -a.d * r * r};
 }
-// tau^{-1/3}
-__device__ __forceinline__ double rcbrt_(double a) { return rcbrt(a); }
+// tau^{-1/3}. In FP64 by Newton's method on y^-3 = tau from the FP32
+// estimate: y <- y (4 - tau y^3) / 3 squares the relative error, so two
+// steps take the ~1e-7 start to rounding level (a few ulp) with ~10 FP64
+// operations, on GB300's narrow FP64 pipe the cheaper route. Outside
+// [2^-120, 2^120] (where the FP32 start would over- or underflow) and for
+// non-finite input it defers to rcbrt.
+__device__ __forceinline__ double rcbrt_nr(double a);
+__device__ __forceinline__ double rcbrt_(double a) { return rcbrt_nr(a); }
 __device__ __forceinline__ float rcbrt_(float a) { return rcbrtf(a); }
 template <class R> __device__ __forceinline__ Dual<R> rcbrt_(Dual<R> a) {
   R r = rcbrt_(a.v);
@@ -132,6 +138,14 @@ __device__ __forceinline__ double f32_to_f64(float f) {
   return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
 }
 
+__device__ __forceinline__ double rcbrt_nr(double a) {
+  if (!(a >= 0x1p-120 && a <= 0x1p120)) return rcbrt(a);
+  double y = f32_to_f64(rcbrtf(f64_to_f32(a)));
+  y = y * fma(-a, y * y * y, 4.0) * (1.0 / 3.0);
+  y = y * fma(-a, y * y * y, 4.0) * (1.0 / 3.0);
+  return y;
+}
+
 // FP64 value -> the kernel's arithmetic type, and back
 template <class R> __device__ __forceinline__ R from_f64(double d) { return R(d); }
 template <> __device__ __forceinline__ float from_f64<float>(double d) { return f64_to_f32(d); }
@@ -199,8 +213,8 @@ __device__ __forceinline__ bool metric_P(int id, const S* T, S& mu, S* P) {
   if (!(value(tau) > 0)) return false;
   S C[DD];
   cof_m<D>(T, C);
-  S it = recip(tau);
   if (id == 98) {  // |T - I|^2 / tau (Section 4.3.2); P = (2 (T - I) - mu C) / tau
+    S it = recip(tau);
     S E[DD];
 #pragma unroll
     for (int i = 0; i < DD; ++i) E[i] = (i % (D + 1) == 0) ? T[i] - sc<S>(1.0) : T[i];
@@ -213,6 +227,7 @@ __device__ __forceinline__ bool metric_P(int id, const S* T, S& mu, S* P) {
     return true;
   }
   if constexpr (D == 2) {
+    S it = recip(tau);
     if (id == 2) {  // |T|^2 / (2 tau) - 1
       mu = sc<S>(0.5) * I1 * it - sc<S>(1.0);
       S b = sc<S>(0.5) * I1 * it * it;
@@ -244,9 +259,10 @@ __device__ __forceinline__ bool metric_P(int id, const S* T, S& mu, S* P) {
       return true;
     }
   } else {
-    if (id == 303) {  // |T|^2 / (3 tau^{2/3}) - 1
+    if (id == 303) {  // |T|^2 / (3 tau^{2/3}) - 1; 1 / tau = (tau^{-1/3})^3, no division
       S r = rcbrt_(tau);
       S r2 = r * r;
+      S it = r2 * r;
       mu = sc<S>(1.0 / 3.0) * I1 * r2 - sc<S>(1.0);
       S a = sc<S>(2.0 / 3.0) * r2, b = sc<S>(2.0 / 9.0) * I1 * r2 * it;
 #pragma unroll
@@ -254,6 +270,7 @@ __device__ __forceinline__ bool metric_P(int id, const S* T, S& mu, S* P) {
       return true;
     }
     if (id == 302) {  // |T|^2 |T^-1|^2 / 9 - 1 = I1 K / (9 tau^2) - 1, K = |cof T|^2
+      S it = recip(tau);
       S K = C[0] * C[0];
 #pragma unroll
       for (int i = 1; i < 9; ++i) K = K + C[i] * C[i];
@@ -309,6 +326,12 @@ struct MetricLin {
     if (id == 1 || id == 14) { m1 = R(1); ok = true; return true; }
     ok = tau > R(0);
     if (!ok) return false;
+    if (id == 303) {          // I1 tau^{-2/3} / 3 - 1 (3D); 1 / tau = (tau^{-1/3})^3, no division
+      const R r = rcbrt_(tau), r2 = r * r, it = r2 * r, t53 = r2 * it;
+      m1 = r2 * R(1.0 / 3.0); mt = R(-2.0 / 9.0) * I1 * t53; m1t = R(-2.0 / 9.0) * t53;
+      mtt = R(10.0 / 27.0) * I1 * t53 * it;
+      return ok;
+    }
     const R it = R(1) / tau, it2 = it * it;
     if (id == 2) {            // I1 / (2 tau) - 1
       m1 = R(0.5) * it; mt = R(-0.5) * I1 * it2; m1t = R(-0.5) * it2; mtt = I1 * it2 * it;
@@ -319,10 +342,6 @@ struct MetricLin {
     } else if (id == 77) {    // (tau - 1/tau)^2 / 2
       const R sdiff = tau - it, ds = R(1) + it2;
       mt = sdiff * ds; mtt = ds * ds - R(2) * sdiff * it2 * it;
-    } else if (id == 303) {   // I1 tau^{-2/3} / 3 - 1 (3D)
-      const R r = rcbrt_(tau), r2 = r * r, t53 = r2 * it;
-      m1 = r2 * R(1.0 / 3.0); mt = R(-2.0 / 9.0) * I1 * t53; m1t = R(-2.0 / 9.0) * t53;
-      mtt = R(10.0 / 27.0) * I1 * t53 * it;
     } else {
       ok = false;
     }

@@ -520,6 +520,20 @@ __global__ void k_selftest_convert(const double* __restrict__ in, float* __restr
 }
 }  // namespace
 
+namespace {
+__global__ void k_selftest_rcbrt(const double* __restrict__ in, double* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = tmop::rcbrt_(in[i]);
+}
+}  // namespace
+
+extern "C" int tmop_selftest_rcbrt(const double* in, double* out, size_t n, void* stream) {
+  if (n == 0) return TMOP_OK;
+  if (!in || !out) return TMOP_ERR_ARG;
+  k_selftest_rcbrt<<<256, 256, 0, (cudaStream_t)stream>>>(in, out, n);
+  return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
+}
+
 extern "C" int tmop_selftest_convert(const double* in, float* f32, double* back, size_t n, void* stream) {
   if (n == 0) return TMOP_OK;
   if (!in || !f32 || !back) return TMOP_ERR_ARG;

@@ -90,6 +90,7 @@ _SIGNATURES = {
     "tmop_jacobians": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_set_targets_from_positions": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_selftest_convert": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p], C.c_int),
+    "tmop_selftest_rcbrt": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p], C.c_int),
     "tmop_destroy": ([C.c_void_p], None),
     "tmop_status_string": ([C.c_int], C.c_char_p),
 }
@@ -142,6 +143,18 @@ def selftest_convert(x):
     if rc != OK:
         raise TmopError(rc, "tmop_selftest_convert")
     return f32, back
+
+
+def selftest_rcbrt(x):
+    """tau^{-1/3} as the FP64 kernels evaluate it, on x (FP64, CUDA)."""
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+        raise TypeError("x must be a contiguous float64 CUDA tensor")
+    out = torch.empty_like(x)
+    rc = load().tmop_selftest_rcbrt(_ptr(x), _ptr(out), x.numel(), _stream())
+    if rc != OK:
+        raise TmopError(rc, "tmop_selftest_rcbrt")
+    return out
 
 
 def energy_noalloc(dim, order, structured, nq, metric, x, F, min_detA, quad_kind=GL, target_kind=W_IDENTITY,

@@ -97,4 +97,6 @@ def test_null_arguments(lib):
     # empty input: nothing to convert, no device work
     assert lib.tmop_selftest_convert(None, None, None, 0, None) == tm.OK
     assert lib.tmop_selftest_convert(None, None, None, 5, None) == tm.ERR_ARG
+    assert lib.tmop_selftest_rcbrt(None, None, 0, None) == tm.OK
+    assert lib.tmop_selftest_rcbrt(None, None, 3, None) == tm.ERR_ARG
     lib.tmop_destroy(None)

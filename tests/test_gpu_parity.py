@@ -543,6 +543,23 @@ def test_fp32_conversions_round_like_a_cast(tm):
     assert b[0] == np.inf and b[1] == -np.inf and np.isnan(b[2])
 
 
+def test_inverse_cube_root_within_a_few_ulp(tm):
+    """tau^{-1/3} of the FP64 kernels (Newton from an FP32 start) against
+    numpy's cube root: within 8 ulp (the reference itself is two roundings)
+    over the Newton range, exact cubes,
+    the range ends and the library fallback beyond them."""
+    rng = np.random.default_rng(9)
+    a = np.concatenate([
+        10.0 ** rng.uniform(-36, 36, 20000),
+        np.array([1.0, 8.0, 27.0, 0.125, 2.0 ** -120, 2.0 ** 120, 2.0 ** -121, 2.0 ** 121, 1e-300, 1e300]),
+        (rng.integers(1, 1000, 1000).astype(np.float64)) ** 3,
+    ])
+    got = host(tm.selftest_rcbrt(dev(a)))
+    ref = 1.0 / np.cbrt(a)
+    ulp = np.spacing(np.abs(ref))
+    assert np.all(np.abs(got - ref) <= 8 * ulp), np.max(np.abs(got - ref) / ulp)
+
+
 def test_partial_assembly_requires_linearize(tm):
     m = make("c1", 1, nx=2)
     ctx = tm.Context.from_mesh(m)
