@@ -298,6 +298,14 @@ def run_ours(args):
         if ev is not None:
             ev[1].record(stream)
 
+    if args.kernels_only and args.profile == "newton":
+        # one FP32-mixed Newton step of the workload (linearisation, MINRES with the stored-Hessian product)
+        c32 = tm.Context.from_mesh(m, precision=tm.FP32_MIXED)
+        xn = x.clone()
+        c32.newton_step(xn)
+        torch.cuda.synchronize()
+        c32.close()
+        return 0
     if args.kernels_only and args.profile == "mlp":
         # W + K training steps of the proposal MLP on random bf16 inputs (batch 4096)
         from paper_1807_09807_gb300 import learned as L
@@ -680,9 +688,10 @@ def main():
     ap.add_argument("--train-meshes-curved", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels-only", action="store_true")
-    ap.add_argument("--profile", choices=["step", "pa", "mlp"], default="step",
+    ap.add_argument("--profile", choices=["step", "pa", "mlp", "newton"], default="step",
                     help="with --kernels-only: the timed step (gradient + Hessian action), the partially "
-                         "assembled Hessian action alone, or training steps of the proposal MLP")
+                         "assembled Hessian action alone, training steps of the proposal MLP, or one "
+                         "FP32-mixed Newton step")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if not args.kernels_only else args.warmup
     if args.impl == "reference":

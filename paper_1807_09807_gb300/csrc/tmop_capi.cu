@@ -192,6 +192,7 @@ struct tmop_ctx {
   mass_launch_fn mass[3] = {nullptr, nullptr, nullptr};
   int mass_grid = 1;
   double* d_diag = nullptr;   // Hessian diagonal [d][nnode] and its floored inverse [d][nnode]
+  double* d_vdot = nullptr;   // per-warp partials of v . (H v) from the compact-record product
   cudaStream_t cap = nullptr; // internal stream for capturing Krylov iterations into a graph
   cudaEvent_t ev = nullptr;   // orders the internal stream after / before the caller's stream
 };
@@ -241,7 +242,7 @@ JacParams jac_params(const tmop_ctx* c, const double* x, double* J) {
 }
 
 int launch_op(tmop_ctx* c, int op, const double* x, const double* v, double* y, double* elem_min,
-              cudaStream_t s) {
+              cudaStream_t s, double* vdot = nullptr) {
   KParams p = c->base;
   p.x = x;
   p.v = v;
@@ -255,6 +256,7 @@ int launch_op(tmop_ctx* c, int op, const double* x, const double* v, double* y, 
   int kop = op;  // the stored linearisation decides which form of the pair runs
   if (c->pa_compact && op == OP_LINEARIZE) kop = OP_LINEARIZE_C;
   if (c->pa_compact && op == OP_HESS_PA) kop = OP_HESS_PA_C;
+  p.vdot = kop == OP_HESS_PA_C ? vdot : nullptr;
   if (c->ent[kop]->launch(p, c->grid[kop], s) != 0) return TMOP_ERR_CUDA;
   if (c->delta != 0.0 && op != OP_ENERGY && op != OP_LINEARIZE) {
     // restricted movement (eq. (4.2)): its gradient (from x) or Hessian action (from v)
@@ -425,7 +427,9 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
   // the converged iteration. The kCheck iterations are captured once into a
   // CUDA graph on an internal stream and replayed (direct launches if capture
   // is not possible).
-  constexpr int kCheck = 8;
+  // (6: plain MINRES renames its vectors with period 3 and 2, so a batch of
+  // 6 iterations starts and ends with the same assignment)
+  constexpr int kCheck = 6;
   const bool cg = o.krylov == TMOP_KRYLOV_CG;
   double *k0 = vec(c, V_K0), *k1 = vec(c, V_K1), *k2 = vec(c, V_K2), *k3 = vec(c, V_K3), *k4 = vec(c, V_K4);
   double* k5 = vec(c, V_K5);
@@ -436,6 +440,15 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
       return TMOP_ERR_CUDA;
   } else {
     if (minres_init(b, k0, k1, k3, k4, p, st, part, n, o.krylov_rtol, o.krylov_maxit, s)) return TMOP_ERR_CUDA;
+  }
+  // the compact-record product also returns v . (H v) (not with the restricted-movement term, whose
+  // contribution it does not see)
+  double* vdot = nullptr;
+  int vdot_np = 0;
+  if (!cg && !minv && hop == OP_HESS_PA && c->pa_compact && c->delta == 0.0) {
+    vdot_np = c->grid[OP_HESS_PA_C] * c->ent[OP_HESS_PA_C]->warps;
+    if (!c->d_vdot) CUDA_TRY(cudaMalloc(&c->d_vdot, sizeof(double) * vdot_np));
+    vdot = c->d_vdot;
   }
   auto enqueue_batch = [&](cudaStream_t q) -> int {
     for (int j = 0; j < kCheck; ++j) {
@@ -451,10 +464,15 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
         r = launch_op(c, hop, x, k1, k2, nullptr, q);
         if (r) return r;
         if (cg_after_hv(p, k0, k1, k2, st, part, n, q)) return TMOP_ERR_CUDA;
-      } else {   // v = k0, vprev = k1, Av = k2, w = k3, wprev = k4
-        r = launch_op(c, hop, x, k0, k2, nullptr, q);
+      } else {   // Lanczos vectors rotate over k0, k1, k2 (period 3), search directions over k3, k4
+        double* V[3] = {k0, k1, k2};
+        double* W[2] = {k3, k4};
+        const int iv = (3 - j % 3) % 3;
+        double *v = V[iv], *vprev = V[(iv + 1) % 3], *Av = V[(iv + 2) % 3];
+        double *w = W[j % 2], *wp = W[(j + 1) % 2];
+        r = launch_op(c, hop, x, v, Av, nullptr, q, vdot);
         if (r) return r;
-        if (minres_after_hv(k0, k1, k2, k3, k4, p, st, part, n, q)) return TMOP_ERR_CUDA;
+        if (minres_after_hv_rot(v, vprev, Av, w, wp, p, st, part, n, q, vdot, vdot_np)) return TMOP_ERR_CUDA;
       }
     }
     return TMOP_OK;
@@ -588,6 +606,7 @@ void tmop_destroy(tmop_ctx* c) {
   cudaFree(c->d_eta2);
   cudaFree(c->d_x_init);
   cudaFree(c->d_diag);
+  cudaFree(c->d_vdot);
   cudaFreeHost(c->h_res);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->ev) cudaEventDestroy(c->ev);

@@ -37,6 +37,7 @@ struct KParams {
   double* part_min;               // [grid] min det A partials
   double* elem_min;               // [nelem] per-element min det A, or null
   void* pa;                       // [nelem][pa_stride] packed Hessians [DD(DD+1)/2][Q] (float or double)
+  double* vdot;                   // product from compact records: per-warp partials of v . (H v), or null
   int pa_stride;                  // elements per element block, padded to 16 bytes
   double B[kMaxQ * kMaxN];              // B[q][i] = phi_i(xi_q)
   double G[kMaxQ * kMaxN];              // G[q][i] = phi_i'(xi_q)

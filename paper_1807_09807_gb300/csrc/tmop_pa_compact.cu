@@ -11,7 +11,10 @@
 // flight (its v and fixed flags, the record of each lane's first point), and
 // inside the pointwise stage the record of a lane's next point is loaded
 // before the current point is computed. Everything is warp-synchronous: no
-// block barriers after the prologue.
+// block barriers after the prologue. With p.vdot set, each warp also sums
+// v_E . (H_E v_E) over its elements, which is v . (H v) summed element by
+// element (v is read as zero at fixed dofs, where H v is zero): MINRES then
+// needs no separate dot-product pass over v and H v.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -119,13 +122,18 @@ __global__ void __launch_bounds__(kPacWarps * 32) pac_kernel(const KParams p) {
   const float* rec = static_cast<const float*>(p.pa);
   const int stride = gridDim.x * kPacWarps;
   int e = blockIdx.x * kPacWarps + warp;
-  if (e >= p.nelem) return;  // whole warps only; nothing below waits on other warps
+  const int gw = blockIdx.x * kPacWarps + warp;  // this warp's slot of the v . (H v) partials
+  if (e >= p.nelem) {  // whole warps only; nothing below waits on other warps
+    if (p.vdot && lane == 0) p.vdot[gw] = 0.0;
+    return;
+  }
 
   NodeMap<N> cur(p.elem_nodes, p.sx, p.sy), nxt(p.elem_nodes, p.sx, p.sy);
   cur.element(e, NDOF);
-  double v[NT][3];
+  double v[NT][3], vc[NT][3];
   unsigned fnext;
   float hq[kCompactRec];
+  double vdot = 0.0;  // sum over this warp's elements of v_E . (H_E v_E), FP64
   fetch_v<N, NT>(p, cur, lane, v, fnext);
   fetch_rec<QP>(rec, p.pa_stride, e, lane, hq);
   for (;;) {
@@ -136,7 +144,10 @@ __global__ void __launch_bounds__(kPacWarps * 32) pac_kernel(const KParams p) {
       const int t = lane + 32 * s;
       if (t < NDOF) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) P0[c * NDOF + t] = (fcur >> (s * 3 + c)) & 1u ? 0.0f : f64_to_f32(v[s][c]);
+        for (int c = 0; c < 3; ++c) {
+          vc[s][c] = (fcur >> (s * 3 + c)) & 1u ? 0.0 : v[s][c];
+          P0[c * NDOF + t] = f64_to_f32(vc[s][c]);
+        }
       }
     }
     __syncwarp();
@@ -171,14 +182,22 @@ __global__ void __launch_bounds__(kPacWarps * 32) pac_kernel(const KParams p) {
       if (t < NDOF) {
         const int g = cur(t);
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-          if (!((fcur >> (s * 3 + c)) & 1u)) atomicAdd(p.y + (size_t)c * p.nnode + g, f32_to_f64(P0[c * NDOF + t]));
+        for (int c = 0; c < 3; ++c) {
+          const double yc = f32_to_f64(P0[c * NDOF + t]);
+          vdot = fma(vc[s][c], yc, vdot);  // 0 at fixed dofs (vc = 0 there)
+          if (!((fcur >> (s * 3 + c)) & 1u)) atomicAdd(p.y + (size_t)c * p.nnode + g, yc);
+        }
       }
     }
     __syncwarp();
     if (!more) break;
     e = en;
     cur = nxt;
+  }
+  if (p.vdot) {  // fixed-order warp reduction; one partial per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vdot += __shfl_xor_sync(0xffffffffu, vdot, o);
+    if (lane == 0) p.vdot[gw] = vdot;
   }
 }
 

@@ -237,6 +237,38 @@ int minres_after_hv(double* v, double* vprev, double* Av, double* w, double* wpr
   return (int)cudaGetLastError();
 }
 
+// Rotating-buffer form of the update: the new search direction overwrites
+// w_{k-2} (wp) and the next Lanczos vector is Av scaled in place, so nothing
+// is copied (8 vector passes instead of 10); the caller then renames
+// (v, vprev, Av) -> (Av, v, vprev) and (w, wp) -> (wp, w).
+__global__ void k_minres_vec_rot(const double* __restrict__ v, double* __restrict__ Av, const double* __restrict__ w,
+                                 double* __restrict__ wp, double* __restrict__ sol, const double* __restrict__ st,
+                                 size_t n) {
+  const double r1 = st[KS_R1], r2 = st[KS_R2], ir = st[KS_INV_RHO], phi = st[KS_PHI], ib = st[KS_INV_BETA_NEXT];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double wn = (v[i] - r1 * wp[i] - r2 * w[i]) * ir;
+    wp[i] = wn;
+    sol[i] = fma(phi, wn, sol[i]);
+    Av[i] *= ib;
+  }
+}
+
+int minres_after_hv_rot(const double* v, const double* vprev, double* Av, const double* w, double* wp, double* sol,
+                        double* st, double* part, size_t n, cudaStream_t s, const double* vdot, int vdot_np) {
+  int g = red_grid(n);
+  if (vdot) {  // alpha = v . (H v) from the product kernel's own partials
+    k_sum_final<<<1, kThreads, 0, s>>>(vdot, vdot_np, st + KS_ALPHA);
+  } else {
+    k_dot_part<<<g, kThreads, 0, s>>>(v, Av, n, part);
+    k_sum_final<<<1, kThreads, 0, s>>>(part, g, st + KS_ALPHA);
+  }
+  k_lanczos<<<g, kThreads, 0, s>>>(Av, v, vprev, st, n, part);
+  k_sum_final<<<1, kThreads, 0, s>>>(part, g, st + KS_BETA_NEXT2);
+  k_minres_scalar<<<1, 1, 0, s>>>(st);
+  k_minres_vec_rot<<<g, kThreads, 0, s>>>(v, Av, w, wp, sol, st, n);
+  return (int)cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- preconditioned MINRES
 // Lanczos in the M^-1 inner product with the residual minimised through
 // Givens rotations (Paige and Saunders), M = diag(1 / minv). The residual

@@ -32,6 +32,11 @@ int minres_init(const double* b, double* v, double* vprev, double* w, double* wp
                 double* part, size_t n, double rtol, int maxit, cudaStream_t s);
 int minres_after_hv(double* v, double* vprev, double* Av, double* w, double* wprev, double* sol, double* st,
                     double* part, size_t n, cudaStream_t s);
+// the same step on rotating buffers: afterwards (v, vprev, Av) -> (Av, v, vprev), (w, wp) -> (wp, w);
+// vdot (vdot_np partials of v . Av from the product kernel) replaces the dot-product pass when given
+int minres_after_hv_rot(const double* v, const double* vprev, double* Av, const double* w, double* wp, double* sol,
+                        double* st, double* part, size_t n, cudaStream_t s, const double* vdot = nullptr,
+                        int vdot_np = 0);
 // Preconditioned MINRES (M^-1 = minv, a diagonal): r1, r2, y, v, w, wprev, sol
 int pminres_init(const double* b, const double* minv, double* r1, double* r2, double* y, double* w, double* wprev,
                  double* sol, double* st, double* part, size_t n, double rtol, int maxit, cudaStream_t s);
