@@ -29,8 +29,10 @@ int red_grid(size_t n) {
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
     if (g_sms <= 0) g_sms = 1;
   }
+  // up to 8 blocks of 256 threads per SM (full occupancy): the update kernels
+  // stream 4 to 8 vectors, and more loads in flight keep HBM busier
   size_t want = (n + kThreads * 4 - 1) / (kThreads * 4);
-  size_t cap = (size_t)g_sms * 4;
+  size_t cap = (size_t)g_sms * 8;
   if (want > cap) want = cap;
   if (want > (size_t)kMaxRedBlocks) want = kMaxRedBlocks;
   if (want < 1) want = 1;
