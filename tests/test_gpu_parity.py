@@ -650,6 +650,28 @@ def test_krylov_matches_oracle(tm, krylov):
     assert np.linalg.norm(r) <= 1e-11 * np.linalg.norm(b)
 
 
+@pytest.mark.parametrize("delta", [0.0, 2.0])
+def test_minres_with_compact_records_solves_the_fp64_system(tm, delta):
+    """MINRES with the 3D FP32 compact-record product (which returns v.(Hv)
+    itself, so the solver skips its dot pass; with the restricted-movement
+    term it does not, and the separate pass runs): the solution of H p = b
+    against the oracle's FP64 Hessian, to the FP32 operator's accuracy, and
+    against the oracle's MINRES solution."""
+    m = make("c3", 2, nx=(4, 3, 3))
+    okw = dict(delta=delta, x_init=m.x_ideal) if delta else {}
+    orc = oracle.Problem(m.dim, m.order, m.elem_nodes, m.nnode, m.fixed, m.nq, m.metric, **okw)
+    ctx = tm.Context.from_mesh(m, precision=tm.FP32_MIXED)
+    if delta:
+        ctx.set_restricted_movement(delta, dev(m.x_ideal))
+    b = orc.gradient(m.x)
+    p, it = ctx.krylov_solve(dev(m.x), dev(b), krylov_rtol=1e-9, krylov_maxit=3000)
+    assert it > 0
+    r = orc.hess_apply(m.x, host(p)) - b
+    assert np.linalg.norm(r) <= 1e-4 * np.linalg.norm(b), np.linalg.norm(r) / np.linalg.norm(b)
+    po, _ = orc.minres(m.x, b, rtol=1e-12, maxit=3000)
+    assert rel(host(p), po) <= 1e-3
+
+
 @pytest.mark.parametrize("metric,scale", [(2, None), (7, 1.0 / 8)])
 def test_newton_matches_oracle_history(tm, metric, scale):
     """Section 3.4 Newton on 8x8 order-2: the same accepted step lengths and
