@@ -199,24 +199,9 @@ __global__ void k_minres_scalar(double* st) {
   }
 }
 
-// New search direction w_k = (v_k - r1 w_{k-2} - r2 w_{k-1}) / rho, solution
-// update, and the next Lanczos vector.
-__global__ void k_minres_vec(double* __restrict__ v, double* __restrict__ vprev, const double* __restrict__ Av,
-                             double* __restrict__ w, double* __restrict__ wprev, double* __restrict__ sol,
-                             const double* __restrict__ st, size_t n) {
-  const double r1 = st[KS_R1], r2 = st[KS_R2], ir = st[KS_INV_RHO], phi = st[KS_PHI], ib = st[KS_INV_BETA_NEXT];
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double vi = v[i];
-    const double wn = (vi - r1 * wprev[i] - r2 * w[i]) * ir;
-    wprev[i] = w[i];
-    w[i] = wn;
-    sol[i] = fma(phi, wn, sol[i]);
-    vprev[i] = vi;
-    v[i] = Av[i] * ib;
-  }
-}
-// (once KS_DONE is set, phi = 0 keeps sol fixed and v becomes 0, so every
-// later product is zero)
+// The direction/solution update and the next Lanczos vector follow in
+// k_minres_vec_rot. (Once KS_DONE is set, phi = 0 keeps sol fixed and the
+// next Lanczos vector is 0, so every later product is zero.)
 
 int minres_init(const double* b, double* v, double* vprev, double* w, double* wprev, double* sol, double* st,
                 double* part, size_t n, double rtol, int maxit, cudaStream_t s) {
@@ -227,17 +212,6 @@ int minres_init(const double* b, double* v, double* vprev, double* w, double* wp
   return (int)cudaGetLastError();
 }
 
-int minres_after_hv(double* v, double* vprev, double* Av, double* w, double* wprev, double* sol, double* st,
-                    double* part, size_t n, cudaStream_t s) {
-  int g = red_grid(n);
-  k_dot_part<<<g, kThreads, 0, s>>>(v, Av, n, part);
-  k_sum_final<<<1, kThreads, 0, s>>>(part, g, st + KS_ALPHA);
-  k_lanczos<<<g, kThreads, 0, s>>>(Av, v, vprev, st, n, part);
-  k_sum_final<<<1, kThreads, 0, s>>>(part, g, st + KS_BETA_NEXT2);
-  k_minres_scalar<<<1, 1, 0, s>>>(st);
-  k_minres_vec<<<g, kThreads, 0, s>>>(v, vprev, Av, w, wprev, sol, st, n);
-  return (int)cudaGetLastError();
-}
 
 // Rotating-buffer form of the update: the new search direction overwrites
 // w_{k-2} (wp) and the next Lanczos vector is Av scaled in place, so nothing

@@ -30,9 +30,8 @@ int energy_final(const double* pf, const double* pm, int np, const double* pf2, 
 int step(const double* x, const double* p, double alpha, double* y, size_t n, cudaStream_t s);
 int minres_init(const double* b, double* v, double* vprev, double* w, double* wprev, double* sol, double* st,
                 double* part, size_t n, double rtol, int maxit, cudaStream_t s);
-int minres_after_hv(double* v, double* vprev, double* Av, double* w, double* wprev, double* sol, double* st,
-                    double* part, size_t n, cudaStream_t s);
-// the same step on rotating buffers: afterwards (v, vprev, Av) -> (Av, v, vprev), (w, wp) -> (wp, w);
+// one MINRES step after Av = H v, on rotating buffers: afterwards (v, vprev, Av) -> (Av, v, vprev),
+// (w, wp) -> (wp, w);
 // vdot (vdot_np partials of v . Av from the product kernel) replaces the dot-product pass when given
 int minres_after_hv_rot(const double* v, const double* vprev, double* Av, const double* w, double* wp, double* sol,
                         double* st, double* part, size_t n, cudaStream_t s, const double* vdot = nullptr,
