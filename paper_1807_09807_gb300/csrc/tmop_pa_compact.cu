@@ -29,15 +29,226 @@ namespace {
 constexpr int round4(int v) { return (v + 3) / 4 * 4; }
 constexpr int imax(int a, int b) { return a > b ? a : b; }
 
+// ---------------------------------------------------------------- packed-pair contractions
+// The forward map v -> dA at the points and its adjoint R -> y, the same
+// sum-factorised maps as the generic element kernel, written for the FP32
+// pair instructions of sm_100+: __ffma2_rn rounds each half as one fmaf, so a
+// pair does two independent multiply-adds in one issue slot. The 1D tables
+// are held as pairs tBG[q][i] = (B[q][i], G[q][i]) (B = phi_i(xi_q),
+// G = phi_i'(xi_q)), and every stage arranges its inputs so that one operand
+// pair meets (B, G): stage 1 of the forward map broadcasts x and gets
+// (x B, x G); the later stages read pairs stored in the order the next stage
+// multiplies them, with the one product that needs B alone kept scalar.
+//
+// Stage buffers (words; pairs on even words):
+//   x, y      [c][l*N+j][i]                    c*XC + (l*N+j)*XR + i
+//   A pairs   [c][l][j][q0]                    c*AC + l*AL + j*AR + 2*q0
+//   B pairs   [c][l][q1][q0]                   c*BC + l*BL + q1*BQ + 2*q0
+//   B scalars [c][l][q1][q0]                   BS + c*SC + l*SL + q1*SQ + q0
+//   Z pairs   [c][q] (components 1, 2)         c*ZC + 2*q
+//   Z scalars [c][q] (component 0)             ZS + c*ZT + q
+// x, y and B share the first buffer of a warp, A and Z the second; each
+// stage reads one and writes the other.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 bcast2(float x) { return make_float2(x, x); }
+
+// Strides per (N, Q1), chosen by counting, for each shared-memory access of
+// the stages, the distinct words one warp instruction puts on one bank (half
+// warps for 8-byte accesses) and taking the strides with the lowest total
+// (ties: the smallest buffers).
+template <int N, int Q1>
+struct PacLayout;
+#define TMOP_PAC_LAYOUT(N_, Q_, XR_, XC_, AR_, AL_, AC_, BQ_, BL_, BC_, SQ_, SL_, SC_, ZC_, ZT_) \
+  template <>                                                                                  \
+  struct PacLayout<N_, Q_> {                                                                   \
+    static constexpr int XR = XR_, XC = XC_, AR = AR_, AL = AL_, AC = AC_;                     \
+    static constexpr int BQ = BQ_, BL = BL_, BC = BC_, SQ = SQ_, SL = SL_, SC = SC_;           \
+    static constexpr int ZC = ZC_, ZT = ZT_;                                                   \
+    static constexpr int BS = 3 * BC, ZS = 3 * ZC;                                             \
+  };
+TMOP_PAC_LAYOUT(2, 2, 2, 8, 6, 12, 24, 4, 12, 24, 2, 4, 8, 20, 8)
+TMOP_PAC_LAYOUT(2, 3, 2, 8, 10, 38, 76, 12, 50, 102, 3, 15, 42, 82, 41)
+TMOP_PAC_LAYOUT(3, 3, 3, 27, 6, 18, 54, 6, 38, 114, 3, 14, 43, 82, 41)
+TMOP_PAC_LAYOUT(3, 4, 3, 27, 10, 40, 120, 8, 40, 120, 4, 20, 60, 128, 80)
+TMOP_PAC_LAYOUT(4, 4, 5, 80, 10, 40, 160, 8, 40, 160, 4, 20, 80, 128, 80)
+TMOP_PAC_LAYOUT(4, 5, 5, 80, 24, 106, 424, 10, 74, 296, 6, 37, 148, 274, 153)
+TMOP_PAC_LAYOUT(5, 5, 5, 125, 12, 74, 370, 10, 74, 370, 5, 25, 153, 274, 153)
+TMOP_PAC_LAYOUT(5, 6, 5, 125, 14, 70, 350, 12, 76, 380, 6, 38, 190, 456, 228)
+#undef TMOP_PAC_LAYOUT
+
 template <int N, int Q1>
 struct PacCfg {
+  using L = PacLayout<N, Q1>;
   static constexpr int NDOF = N * N * N, QP = Q1 * Q1 * Q1;
   static constexpr int NT = (NDOF + 31) / 32, NPL = (QP + 31) / 32;  // nodes and points per lane
-  // stage buffers of the register-blocked contractions (fwd3_rb / adj3_rb maps)
-  static constexpr int B0 = round4(imax(3 * NDOF, 9 * N * Q1 * Q1));
-  static constexpr int B1 = round4(imax(9 * QP, 6 * N * N * Q1));
+  // words each stage buffer spans
+  static constexpr int XN = 2 * L::XC + (N * N - 1) * L::XR + N;
+  static constexpr int BN = L::BS + 2 * L::SC + (N - 1) * L::SL + (Q1 - 1) * L::SQ + Q1;
+  static constexpr int AN = 2 * L::AC + (N - 1) * L::AL + (N - 1) * L::AR + 2 * Q1;
+  static constexpr int ZN = L::ZS + 2 * L::ZT + QP;
+  static constexpr int B0 = round4(imax(XN, BN));
+  static constexpr int B1 = round4(imax(AN, ZN));
+  static_assert(L::XR >= N && L::XC >= N * N * L::XR, "x rows overlap");
+  static_assert(L::AR >= 2 * Q1 && L::AL >= N * L::AR && L::AC >= N * L::AL, "A overlaps");
+  static_assert(L::BQ >= 2 * Q1 && L::BL >= Q1 * L::BQ && L::BC >= N * L::BL, "B pairs overlap");
+  static_assert(L::SQ >= Q1 && L::SL >= Q1 * L::SQ && L::SC >= N * L::SL, "B scalars overlap");
+  static_assert(L::ZC >= 2 * QP && L::ZT >= QP, "points overlap");
+  static_assert(L::AR % 2 == 0 && L::AL % 2 == 0 && L::AC % 2 == 0 && L::BQ % 2 == 0 && L::BL % 2 == 0 &&
+                    L::BC % 2 == 0 && L::ZC % 2 == 0,
+                "pairs must sit on even words");
   static constexpr size_t smem_bytes() { return sizeof(float) * kPacWarps * (B0 + B1); }
 };
+
+// x (buffer 0) -> dA at every point (Z, buffer 1)
+template <int N, int Q1, class L>
+__device__ __forceinline__ void pac_fwd(const float2 (&tBG)[Q1 * N], float* P0, float* P1, int lane) {
+  constexpr int NC = 3, QQ = Q1 * Q1;
+  for (int t = lane; t < NC * N * N; t += 32) {           // rows (c, l, j) of x -> A = (x B, x G) over q0
+    const int c = t / (N * N), lj = t % (N * N), l = lj / N, j = lj % N;
+    float2 xv[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) xv[i] = bcast2(P0[c * L::XC + lj * L::XR + i]);
+    float2* o = reinterpret_cast<float2*>(P1 + c * L::AC + l * L::AL + j * L::AR);
+#pragma unroll
+    for (int q0 = 0; q0 < Q1; ++q0) {
+      float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < N; ++i) s = ffma2(xv[i], tBG[q0 * N + i], s);
+      o[q0] = s;
+    }
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * N * Q1; t += 32) {          // rows (c, l, q0): A over j -> B
+    const int q0 = t % Q1, l = (t / Q1) % N, c = t / (Q1 * N);
+    const float* in = P1 + c * L::AC + l * L::AL + 2 * q0;
+    float2 xb[N];
+    float xg[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const float2 a = *reinterpret_cast<const float2*>(in + j * L::AR);
+      xb[j] = bcast2(a.x);
+      xg[j] = a.y;
+    }
+    float* op = P0 + c * L::BC + l * L::BL + 2 * q0;
+    float* os = P0 + L::BS + c * L::SC + l * L::SL + q0;
+#pragma unroll
+    for (int q1 = 0; q1 < Q1; ++q1) {
+      float2 s = make_float2(0.f, 0.f);  // (bb, bg)
+      float gb = 0.f;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        s = ffma2(xb[j], tBG[q1 * N + j], s);
+        gb = fmaf(xg[j], tBG[q1 * N + j].x, gb);
+      }
+      op[q1 * L::BQ] = s.y;      // the pair stage 3 multiplies by (B, G): (bg, bb)
+      op[q1 * L::BQ + 1] = s.x;
+      os[q1 * L::SQ] = gb;
+    }
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * QQ; t += 32) {              // columns (c, q1, q0): B over l -> dA
+    const int c = t / QQ, q01 = t % QQ, q1 = q01 / Q1, q0 = q01 % Q1;
+    const float* ip = P0 + c * L::BC + q1 * L::BQ + 2 * q0;
+    const float* is = P0 + L::BS + c * L::SC + q1 * L::SQ + q0;
+    float2 pb[N];
+    float gb[N];
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      pb[l] = *reinterpret_cast<const float2*>(ip + l * L::BL);
+      gb[l] = is[l * L::SL];
+    }
+    float2* zp = reinterpret_cast<float2*>(P1 + c * L::ZC) + q01;
+    float* zs = P1 + L::ZS + c * L::ZT + q01;
+#pragma unroll
+    for (int q2 = 0; q2 < Q1; ++q2) {
+      float2 a12 = make_float2(0.f, 0.f);  // dA components (c, 1), (c, 2)
+      float a0 = 0.f;                      // dA component (c, 0)
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        a12 = ffma2(pb[l], tBG[q2 * N + l], a12);
+        a0 = fmaf(gb[l], tBG[q2 * N + l].x, a0);
+      }
+      zp[q2 * QQ] = a12;
+      zs[q2 * QQ] = a0;
+    }
+  }
+  __syncwarp();
+}
+
+// R at every point (Z, buffer 1) -> y (buffer 0)
+template <int N, int Q1, class L>
+__device__ __forceinline__ void pac_adj(const float2 (&tBG)[Q1 * N], float* P0, float* P1, int lane) {
+  constexpr int NC = 3, QQ = Q1 * Q1;
+  for (int t = lane; t < NC * QQ; t += 32) {              // columns (c, q1, q0): Z over q2 -> B
+    const int c = t / QQ, q01 = t % QQ, q1 = q01 / Q1, q0 = q01 % Q1;
+    const float2* zp = reinterpret_cast<const float2*>(P1 + c * L::ZC) + q01;
+    const float* zs = P1 + L::ZS + c * L::ZT + q01;
+    float2 r12[Q1];
+    float r0[Q1];
+#pragma unroll
+    for (int q2 = 0; q2 < Q1; ++q2) {
+      r12[q2] = zp[q2 * QQ];
+      r0[q2] = zs[q2 * QQ];
+    }
+    float* op = P0 + c * L::BC + q1 * L::BQ + 2 * q0;
+    float* os = P0 + L::BS + c * L::SC + q1 * L::SQ + q0;
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      float2 u12 = make_float2(0.f, 0.f);
+      float u0 = 0.f;
+#pragma unroll
+      for (int q2 = 0; q2 < Q1; ++q2) {
+        u12 = ffma2(r12[q2], tBG[q2 * N + l], u12);
+        u0 = fmaf(r0[q2], tBG[q2 * N + l].x, u0);
+      }
+      op[l * L::BL] = u0;        // the pair stage 2 multiplies by (B, G): (u0, u1)
+      op[l * L::BL + 1] = u12.x;
+      os[l * L::SL] = u12.y;
+    }
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * N * Q1; t += 32) {          // rows (c, l, q0): B over q1 -> A
+    const int q0 = t % Q1, l = (t / Q1) % N, c = t / (Q1 * N);
+    const float* ip = P0 + c * L::BC + l * L::BL + 2 * q0;
+    const float* is = P0 + L::BS + c * L::SC + l * L::SL + q0;
+    float2 u01[Q1];
+    float u2[Q1];
+#pragma unroll
+    for (int q1 = 0; q1 < Q1; ++q1) {
+      u01[q1] = *reinterpret_cast<const float2*>(ip + q1 * L::BQ);
+      u2[q1] = is[q1 * L::SQ];
+    }
+    float* o = P1 + c * L::AC + l * L::AL + 2 * q0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      float2 s = make_float2(0.f, 0.f);  // (u0 B, u1 G)
+      float pb = 0.f;                    // u2 B
+#pragma unroll
+      for (int q1 = 0; q1 < Q1; ++q1) {
+        s = ffma2(u01[q1], tBG[q1 * N + j], s);
+        pb = fmaf(u2[q1], tBG[q1 * N + j].x, pb);
+      }
+      o[j * L::AR] = s.y + pb;   // the pair stage 3 multiplies by (B, G): (vb, vg)
+      o[j * L::AR + 1] = s.x;
+    }
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * N * N; t += 32) {           // rows (c, l, j): A over q0 -> y
+    const int c = t / (N * N), lj = t % (N * N), l = lj / N, j = lj % N;
+    const float2* in = reinterpret_cast<const float2*>(P1 + c * L::AC + l * L::AL + j * L::AR);
+    float2 w[Q1];
+#pragma unroll
+    for (int q0 = 0; q0 < Q1; ++q0) w[q0] = in[q0];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int q0 = 0; q0 < Q1; ++q0) s = ffma2(w[q0], tBG[q0 * N + i], s);
+      P0[c * L::XC + lj * L::XR + i] = s.x + s.y;
+    }
+  }
+  __syncwarp();
+}
 
 // v and the fixed flags at the nodes this lane gathers
 template <int N, int NT>
@@ -69,19 +280,26 @@ __device__ __forceinline__ void fetch_rec(const float* rec, int pa_stride, int e
   }
 }
 
-// dA at point q (buffer [9][QP]) -> R = w det W (d^2mu/dT^2 : dA W^-1) W^-t, in place
-template <int QP>
-__device__ __forceinline__ void pac_point(const float (&h)[kCompactRec], bool ident, const float (&Wi)[9], float* buf,
-                                          int q) {
-  MetricLin<3, float> L;
+// dA at point q (Z) -> R = w det W (d^2mu/dT^2 : dA W^-1) W^-t, in place
+// (IDENT: W = I, so dT = dA and R = S, and W^-1 is never read)
+template <class L, bool IDENT>
+__device__ __forceinline__ void pac_point(const float (&h)[kCompactRec], const float (&Wi)[9], float* buf, int q) {
+  MetricLin<3, float> M;
 #pragma unroll
-  for (int i = 0; i < 9; ++i) L.T[i] = h[i];
-  cof_m<3>(L.T, L.C);
-  L.m1 = h[9]; L.mt = h[10]; L.m11 = h[11]; L.m1t = h[12]; L.mtt = h[13];
+  for (int i = 0; i < 9; ++i) M.T[i] = h[i];
+  cof_m<3>(M.T, M.C);
+  M.m1 = h[9]; M.mt = h[10]; M.m11 = h[11]; M.m1t = h[12]; M.mtt = h[13];
+  float2* zp = reinterpret_cast<float2*>(buf) + q;
+  float* zs = buf + L::ZS + q;
   float dA[9], dT[9], S[9];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) dA[i] = buf[i * QP + q];
-  if (ident) {
+  for (int c = 0; c < 3; ++c) {
+    const float2 a = zp[c * (L::ZC / 2)];
+    dA[c * 3 + 0] = zs[c * L::ZT];
+    dA[c * 3 + 1] = a.x;
+    dA[c * 3 + 2] = a.y;
+  }
+  if constexpr (IDENT) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) dT[i] = dA[i];
   } else {
@@ -91,34 +309,38 @@ __device__ __forceinline__ void pac_point(const float (&h)[kCompactRec], bool id
       for (int b = 0; b < 3; ++b)
         dT[a * 3 + b] = fmaf(dA[a * 3 + 0], Wi[0 * 3 + b], fmaf(dA[a * 3 + 1], Wi[1 * 3 + b], dA[a * 3 + 2] * Wi[2 * 3 + b]));
   }
-  L.dP(dT, S);
+  M.dP(dT, S);
+  float r[9];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const float r = ident ? S[a * 3 + b]
-                            : fmaf(S[a * 3 + 0], Wi[b * 3 + 0], fmaf(S[a * 3 + 1], Wi[b * 3 + 1], S[a * 3 + 2] * Wi[b * 3 + 2]));
-      buf[(a * 3 + b) * QP + q] = r;
-    }
+    for (int b = 0; b < 3; ++b)
+      if constexpr (IDENT) r[a * 3 + b] = S[a * 3 + b];
+      else r[a * 3 + b] = fmaf(S[a * 3 + 0], Wi[b * 3 + 0], fmaf(S[a * 3 + 1], Wi[b * 3 + 1], S[a * 3 + 2] * Wi[b * 3 + 2]));
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    zs[c * L::ZT] = r[c * 3 + 0];
+    zp[c * (L::ZC / 2)] = make_float2(r[c * 3 + 1], r[c * 3 + 2]);
+  }
 }
 
-template <int N, int Q1>
-__global__ void __launch_bounds__(kPacWarps * 32) pac_kernel(const KParams p) {
+// IDENT: the target is W = I (p.wkind == WK_IDENTITY); otherwise one constant W^-1.
+// For n = 4 the kernel is held to 128 registers, two blocks per SM (0: no bound).
+template <int N, int Q1, bool IDENT>
+__global__ void __launch_bounds__(kPacWarps * 32, N == 4 ? 2 : 0) pac_kernel(const KParams p) {
   using Cfg = PacCfg<N, Q1>;
+  using L = typename Cfg::L;
   constexpr int NDOF = Cfg::NDOF, QP = Cfg::QP, NT = Cfg::NT, NPL = Cfg::NPL;
   extern __shared__ __align__(16) float pac_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float* P0 = pac_smem + warp * (Cfg::B0 + Cfg::B1);
   float* P1 = P0 + Cfg::B0;
-  float tB[Q1 * N], tG[Q1 * N], Wi[9];
+  float2 tBG[Q1 * N];
+  float Wi[9];
 #pragma unroll
-  for (int t = 0; t < Q1 * N; ++t) {
-    tB[t] = f64_to_f32(p.B[t]);
-    tG[t] = f64_to_f32(p.G[t]);
-  }
+  for (int t = 0; t < Q1 * N; ++t) tBG[t] = make_float2(f64_to_f32(p.B[t]), f64_to_f32(p.G[t]));
 #pragma unroll
-  for (int i = 0; i < 9; ++i) Wi[i] = f64_to_f32(p.Winv[i]);
-  const bool ident = p.wkind == WK_IDENTITY;
+  for (int i = 0; i < 9; ++i) Wi[i] = IDENT ? 0.f : f64_to_f32(p.Winv[i]);
   const float* rec = static_cast<const float*>(p.pa);
   const int stride = gridDim.x * kPacWarps;
   int e = blockIdx.x * kPacWarps + warp;
@@ -146,20 +368,20 @@ __global__ void __launch_bounds__(kPacWarps * 32) pac_kernel(const KParams p) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           vc[s][c] = (fcur >> (s * 3 + c)) & 1u ? 0.0 : v[s][c];
-          P0[c * NDOF + t] = f64_to_f32(vc[s][c]);
+          P0[c * L::XC + (t / N) * L::XR + t % N] = f64_to_f32(vc[s][c]);
         }
       }
     }
     __syncwarp();
-    // ---- dA at every point: P1 [3][3][QP]
-    fwd3_rb<N, Q1, 3, float>(tB, tG, P0, P1, lane);
+    // ---- dA at every point (Z)
+    pac_fwd<N, Q1, L>(tBG, P0, P1, lane);
     // ---- pointwise; the next point's record is requested before this point is computed
 #pragma unroll
     for (int k = 0; k < NPL; ++k) {
       const int q = lane + 32 * k;
       float hn[kCompactRec];
       if (k + 1 < NPL) fetch_rec<QP>(rec, p.pa_stride, e, q + 32, hn);
-      if (q < QP) pac_point<QP>(hq, ident, Wi, P1, q);
+      if (q < QP) pac_point<L, IDENT>(hq, Wi, P1, q);
       if (k + 1 < NPL) {
 #pragma unroll
         for (int i = 0; i < kCompactRec; ++i) hq[i] = hn[i];
@@ -174,8 +396,8 @@ __global__ void __launch_bounds__(kPacWarps * 32) pac_kernel(const KParams p) {
       fetch_rec<QP>(rec, p.pa_stride, en, lane, hq);
     }
     __syncwarp();
-    // ---- adjoint contraction into P0 [3][NDOF], scatter
-    adj3_rb<N, Q1, 3, float>(tB, tG, P0, P1, lane);
+    // ---- adjoint contraction into y (buffer 0), scatter
+    pac_adj<N, Q1, L>(tBG, P0, P1, lane);
 #pragma unroll
     for (int s = 0; s < NT; ++s) {
       const int t = lane + 32 * s;
@@ -183,7 +405,7 @@ __global__ void __launch_bounds__(kPacWarps * 32) pac_kernel(const KParams p) {
         const int g = cur(t);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const double yc = f32_to_f64(P0[c * NDOF + t]);
+          const double yc = f32_to_f64(P0[c * L::XC + (t / N) * L::XR + t % N]);
           vdot = fma(vc[s][c], yc, vdot);  // 0 at fixed dofs (vc = 0 there)
           if (!((fcur >> (s * 3 + c)) & 1u)) atomicAdd(p.y + (size_t)c * p.nnode + g, yc);
         }
@@ -205,19 +427,26 @@ __global__ void __launch_bounds__(kPacWarps * 32) pac_kernel(const KParams p) {
 
 template <int N, int Q1>
 int launch_pac(const KParams& p, int grid, void* stream) {
-  pac_kernel<N, Q1><<<grid, kPacWarps * 32, PacCfg<N, Q1>::smem_bytes(), (cudaStream_t)stream>>>(p);
+  const size_t smem = PacCfg<N, Q1>::smem_bytes();
+  if (p.wkind == WK_IDENTITY) pac_kernel<N, Q1, true><<<grid, kPacWarps * 32, smem, (cudaStream_t)stream>>>(p);
+  else pac_kernel<N, Q1, false><<<grid, kPacWarps * 32, smem, (cudaStream_t)stream>>>(p);
   return (int)cudaGetLastError();
 }
 
+// grid: the blocks both forms keep resident on every SM
 template <int N, int Q1>
 int prepare_pac(int nelem, int* grid) {
   const size_t smem = PacCfg<N, Q1>::smem_bytes();
-  cudaError_t err =
-      cudaFuncSetAttribute((const void*)pac_kernel<N, Q1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return (int)err;
-  int per_sm = 0, dev = 0, sms = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)pac_kernel<N, Q1>, kPacWarps * 32, smem);
-  if (err != cudaSuccess) return (int)err;
+  const void* fn[2] = {(const void*)pac_kernel<N, Q1, true>, (const void*)pac_kernel<N, Q1, false>};
+  int per_sm = 1 << 30, dev = 0, sms = 0;
+  for (const void* f : fn) {
+    cudaError_t err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return (int)err;
+    int b = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kPacWarps * 32, smem);
+    if (err != cudaSuccess) return (int)err;
+    per_sm = b < per_sm ? b : per_sm;
+  }
   if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

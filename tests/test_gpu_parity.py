@@ -447,7 +447,8 @@ def test_partial_assembly_general_targets_and_fp32(tm, dim):
     assert rel(host(c32.hess_apply_pa(dev(v))), yo) <= 1e-5
 
 
-@pytest.mark.parametrize("order,nq,nx,structured", [(1, 2, (3, 3, 2), True), (2, 3, (3, 2, 1), True),
+@pytest.mark.parametrize("order,nq,nx,structured", [(1, 2, (3, 3, 2), True), (1, 3, (2, 3, 4), False),
+                                                    (2, 3, (3, 2, 1), True),
                                                     (2, 4, (5, 4, 3), False), (3, 4, (4, 3, 2), True),
                                                     (3, 5, (12, 12, 12), True), (3, 5, (7, 5, 3), False),
                                                     (4, 5, (3, 2, 2), False), (4, 6, (3, 3, 3), True)])
