@@ -360,24 +360,30 @@ struct MetricLin {
     const R a = R(2) * m1;
     const R bT = R(2) * (m11 * dI1 + m1t * dtau);
     const R bC = m1t * dI1 + mtt * dtau;
-    R dC[DD];
+    R mdC[DD];  // mu_t dC
     if constexpr (D == 2) {
-      dC[0] = dT[3]; dC[1] = -dT[2]; dC[2] = -dT[1]; dC[3] = dT[0];
+      mdC[0] = mt * dT[3]; mdC[1] = -mt * dT[2]; mdC[2] = -mt * dT[1]; mdC[3] = mt * dT[0];
     } else {
-#define TMOP_DMINOR(a_, b_, c_, e_) (fma(dT[a_], T[b_], T[a_] * dT[b_]) - fma(dT[c_], T[e_], T[c_] * dT[e_]))
-      dC[0] = TMOP_DMINOR(4, 8, 5, 7);
-      dC[1] = TMOP_DMINOR(5, 6, 3, 8);
-      dC[2] = TMOP_DMINOR(3, 7, 4, 6);
-      dC[3] = TMOP_DMINOR(2, 7, 1, 8);
-      dC[4] = TMOP_DMINOR(0, 8, 2, 6);
-      dC[5] = TMOP_DMINOR(1, 6, 0, 7);
-      dC[6] = TMOP_DMINOR(1, 5, 2, 4);
-      dC[7] = TMOP_DMINOR(2, 3, 0, 5);
-      dC[8] = TMOP_DMINOR(0, 4, 1, 3);
+      // each entry of dC is the derivative of a 2x2 minor, dT_a T_b + T_a dT_b
+      // - dT_c T_e - T_c dT_e; with U = mu_t T the factor mu_t costs no
+      // multiply per entry
+      R U[DD];
+#pragma unroll
+      for (int i = 0; i < DD; ++i) U[i] = mt * T[i];
+#define TMOP_DMINOR(a_, b_, c_, e_) fma(dT[a_], U[b_], fma(U[a_], dT[b_], -fma(dT[c_], U[e_], U[c_] * dT[e_])))
+      mdC[0] = TMOP_DMINOR(4, 8, 5, 7);
+      mdC[1] = TMOP_DMINOR(5, 6, 3, 8);
+      mdC[2] = TMOP_DMINOR(3, 7, 4, 6);
+      mdC[3] = TMOP_DMINOR(2, 7, 1, 8);
+      mdC[4] = TMOP_DMINOR(0, 8, 2, 6);
+      mdC[5] = TMOP_DMINOR(1, 6, 0, 7);
+      mdC[6] = TMOP_DMINOR(1, 5, 2, 4);
+      mdC[7] = TMOP_DMINOR(2, 3, 0, 5);
+      mdC[8] = TMOP_DMINOR(0, 4, 1, 3);
 #undef TMOP_DMINOR
     }
 #pragma unroll
-    for (int i = 0; i < DD; ++i) out[i] = fma(a, dT[i], fma(bT, T[i], fma(bC, C[i], mt * dC[i])));
+    for (int i = 0; i < DD; ++i) out[i] = fma(a, dT[i], fma(bT, T[i], fma(bC, C[i], mdC[i])));
   }
 };
 

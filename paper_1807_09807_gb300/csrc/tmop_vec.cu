@@ -30,11 +30,14 @@ int red_grid(size_t n) {
     if (g_sms <= 0) g_sms = 1;
   }
   // up to 8 blocks of 256 threads per SM (full occupancy): the update kernels
-  // stream 4 to 8 vectors, and more loads in flight keep HBM busier
+  // stream 4 to 8 vectors, and more loads in flight keep HBM busier. A grid
+  // of at least one block per SM is a whole number of blocks per SM, so every
+  // SM streams the same share.
   size_t want = (n + kThreads * 4 - 1) / (kThreads * 4);
   size_t cap = (size_t)g_sms * 8;
+  if (cap > (size_t)kMaxRedBlocks) cap = kMaxRedBlocks;
   if (want > cap) want = cap;
-  if (want > (size_t)kMaxRedBlocks) want = kMaxRedBlocks;
+  if (want >= (size_t)g_sms) want -= want % (size_t)g_sms;
   if (want < 1) want = 1;
   return (int)want;
 }
@@ -139,16 +142,21 @@ __global__ void k_minres_init(const double* __restrict__ b, double* v, double* v
     st[KS_CONV_IT] = 0.0;
     st[KS_MAXIT] = (double)maxit;
     st[KS_HITMAX] = 0.0;
+    st[KS_SV] = 1.0; st[KS_SVP] = 1.0; st[KS_SW] = 1.0;
   }
 }
 
-// Av <- Av - alpha v - beta vprev, with per-block partials of |Av|^2
+// The next Lanczos vector, unnormalised, over Av, with per-block partials of
+// its squared norm. The arrays hold v / sv, vprev / svp and H (v / sv), so
+// H v - alpha v - beta vprev = sv Av - (alpha sv) v - (beta svp) vprev, and
+// alpha = v . H v = sv^2 (v array . Av) from the sum in st[KS_ALPHA].
 __global__ void k_lanczos(double* __restrict__ Av, const double* __restrict__ v, const double* __restrict__ vprev,
                           const double* __restrict__ st, size_t n, double* __restrict__ part) {
-  const double alpha = st[KS_ALPHA], beta = st[KS_BETA];
+  const double sv = st[KS_SV];
+  const double av = st[KS_ALPHA] * sv * sv * sv, bv = st[KS_BETA] * st[KS_SVP];
   double s = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double r = Av[i] - alpha * v[i] - beta * vprev[i];
+    const double r = fma(sv, Av[i], -av * v[i]) - bv * vprev[i];
     Av[i] = r;
     s = fma(r, r, s);
   }
@@ -158,7 +166,7 @@ __global__ void k_lanczos(double* __restrict__ Av, const double* __restrict__ v,
 
 // Apply the two previous rotations to the new tridiagonal column
 // (beta_k, alpha_k, beta_{k+1}), form the new rotation, update eta.
-__global__ void k_minres_scalar(double* st) {
+__device__ void minres_scalar_step(double* st) {
   if (st[KS_DONE] == 0.0 && st[KS_ITER] >= st[KS_MAXIT]) {  // the cap: freeze, not converged
     st[KS_DONE] = 1.0;
     st[KS_HITMAX] = 1.0;
@@ -173,7 +181,7 @@ __global__ void k_minres_scalar(double* st) {
     return;
   }
   st[KS_ITER] += 1.0;
-  const double beta = st[KS_BETA], alpha = st[KS_ALPHA];
+  const double beta = st[KS_BETA], alpha = st[KS_ALPHA] * st[KS_SV] * st[KS_SV];
   const double beta_next = sqrt(fmax(st[KS_BETA_NEXT2], 0.0));
   const double c_old = st[KS_C_OLD], s_old = st[KS_S_OLD], c = st[KS_C], s = st[KS_S];
   const double r1 = s_old * beta;
@@ -199,6 +207,16 @@ __global__ void k_minres_scalar(double* st) {
   }
 }
 
+__global__ void k_minres_scalar(double* st) {
+  minres_scalar_step(st);
+  // scales of the unnormalised Lanczos vectors: the direction update takes v
+  // at its present scale, then the arrays rotate and the next v is the new
+  // Lanczos array times 1 / beta_next (0 once done)
+  st[KS_SW] = st[KS_SV];
+  st[KS_SVP] = st[KS_SV];
+  st[KS_SV] = st[KS_INV_BETA_NEXT];
+}
+
 // The direction/solution update and the next Lanczos vector follow in
 // k_minres_vec_rot. (Once KS_DONE is set, phi = 0 keeps sol fixed and the
 // next Lanczos vector is 0, so every later product is zero.)
@@ -214,18 +232,16 @@ int minres_init(const double* b, double* v, double* vprev, double* w, double* wp
 
 
 // Rotating-buffer form of the update: the new search direction overwrites
-// w_{k-2} (wp) and the next Lanczos vector is Av scaled in place, so nothing
-// is copied (8 vector passes instead of 10); the caller then renames
-// (v, vprev, Av) -> (Av, v, vprev) and (w, wp) -> (wp, w).
-__global__ void k_minres_vec_rot(const double* __restrict__ v, double* __restrict__ Av, const double* __restrict__ w,
-                                 double* __restrict__ wp, double* __restrict__ sol, const double* __restrict__ st,
-                                 size_t n) {
-  const double r1 = st[KS_R1], r2 = st[KS_R2], ir = st[KS_INV_RHO], phi = st[KS_PHI], ib = st[KS_INV_BETA_NEXT];
+// w_{k-2} (wp) and the Lanczos vectors stay unnormalised (their scales are
+// device scalars), so nothing is copied or rescaled: 6 vector passes; the
+// caller then renames (v, vprev, Av) -> (Av, v, vprev) and (w, wp) -> (wp, w).
+__global__ void k_minres_vec_rot(const double* __restrict__ v, const double* __restrict__ w, double* __restrict__ wp,
+                                 double* __restrict__ sol, const double* __restrict__ st, size_t n) {
+  const double r1 = st[KS_R1], r2 = st[KS_R2], ir = st[KS_INV_RHO], phi = st[KS_PHI], sw = st[KS_SW];
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double wn = (v[i] - r1 * wp[i] - r2 * w[i]) * ir;
+    const double wn = (fma(sw, v[i], -r1 * wp[i]) - r2 * w[i]) * ir;
     wp[i] = wn;
     sol[i] = fma(phi, wn, sol[i]);
-    Av[i] *= ib;
   }
 }
 
@@ -241,7 +257,7 @@ int minres_after_hv_rot(const double* v, const double* vprev, double* Av, const 
   k_lanczos<<<g, kThreads, 0, s>>>(Av, v, vprev, st, n, part);
   k_sum_final<<<1, kThreads, 0, s>>>(part, g, st + KS_BETA_NEXT2);
   k_minres_scalar<<<1, 1, 0, s>>>(st);
-  k_minres_vec_rot<<<g, kThreads, 0, s>>>(v, Av, w, wp, sol, st, n);
+  k_minres_vec_rot<<<g, kThreads, 0, s>>>(v, w, wp, sol, st, n);
   return (int)cudaGetLastError();
 }
 

@@ -5,7 +5,7 @@
 
 namespace tmop {
 
-constexpr int kMaxRedBlocks = 1024;
+constexpr int kMaxRedBlocks = 2048;  // capacity of the per-block partial buffers
 
 // Device scalar slots of the Krylov state (an array of doubles).
 enum {
@@ -18,6 +18,10 @@ enum {
   KS_CONV_IT,  // the iteration at which KS_DONE was set
   KS_MAXIT,    // iteration cap: reaching it freezes the iterate (not converged)
   KS_HITMAX,   // 1 when KS_DONE was set by the cap
+  // MINRES keeps its Lanczos vectors unnormalised: v = st[KS_SV] * (the v
+  // array), vprev = st[KS_SVP] * (the vprev array), and the direction update
+  // reads v at st[KS_SW] (the scale before the rotation)
+  KS_SV, KS_SVP, KS_SW,
   // preconditioned MINRES
   KS_OLDB, KS_DBAR, KS_EPSLN, KS_OLDEPS, KS_PHIBAR, KS_CS, KS_SN, KS_DELTA, KS_INV_GAMMA, KS_INV_BETA,
   KS_COUNT
@@ -32,7 +36,9 @@ int minres_init(const double* b, double* v, double* vprev, double* w, double* wp
                 double* part, size_t n, double rtol, int maxit, cudaStream_t s);
 // one MINRES step after Av = H v, on rotating buffers: afterwards (v, vprev, Av) -> (Av, v, vprev),
 // (w, wp) -> (wp, w);
-// vdot (vdot_np partials of v . Av from the product kernel) replaces the dot-product pass when given
+// Av is the product of the stored v array (not of the scaled vector); vdot (vdot_np partials of
+// v array . Av from the product kernel) replaces the dot-product pass when given. The new Lanczos
+// vector is left in Av unnormalised, its scale in st[KS_SV].
 int minres_after_hv_rot(const double* v, const double* vprev, double* Av, const double* w, double* wp, double* sol,
                         double* st, double* part, size_t n, cudaStream_t s, const double* vdot = nullptr,
                         int vdot_np = 0);
