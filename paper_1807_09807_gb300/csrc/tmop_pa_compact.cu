@@ -103,7 +103,10 @@ struct PacCfg {
 template <int N, int Q1, class L>
 __device__ __forceinline__ void pac_fwd(const float2 (&tBG)[Q1 * N], float* P0, float* P1, int lane) {
   constexpr int NC = 3, QQ = Q1 * Q1;
-  for (int t = lane; t < NC * N * N; t += 32) {           // rows (c, l, j) of x -> A = (x B, x G) over q0
+#pragma unroll
+  for (int k = 0; k < (NC * N * N + 31) / 32; ++k) {           // rows (c, l, j) of x -> A = (x B, x G) over q0
+    const int t = lane + 32 * k;
+    if (t >= NC * N * N) break;
     const int c = t / (N * N), lj = t % (N * N), l = lj / N, j = lj % N;
     float2 xv[N];
 #pragma unroll
@@ -118,7 +121,10 @@ __device__ __forceinline__ void pac_fwd(const float2 (&tBG)[Q1 * N], float* P0, 
     }
   }
   __syncwarp();
-  for (int t = lane; t < NC * N * Q1; t += 32) {          // rows (c, l, q0): A over j -> B
+#pragma unroll
+  for (int k = 0; k < (NC * N * Q1 + 31) / 32; ++k) {          // rows (c, l, q0): A over j -> B
+    const int t = lane + 32 * k;
+    if (t >= NC * N * Q1) break;
     const int q0 = t % Q1, l = (t / Q1) % N, c = t / (Q1 * N);
     const float* in = P1 + c * L::AC + l * L::AL + 2 * q0;
     float2 xb[N];
@@ -146,7 +152,10 @@ __device__ __forceinline__ void pac_fwd(const float2 (&tBG)[Q1 * N], float* P0, 
     }
   }
   __syncwarp();
-  for (int t = lane; t < NC * QQ; t += 32) {              // columns (c, q1, q0): B over l -> dA
+#pragma unroll
+  for (int k = 0; k < (NC * QQ + 31) / 32; ++k) {              // columns (c, q1, q0): B over l -> dA
+    const int t = lane + 32 * k;
+    if (t >= NC * QQ) break;
     const int c = t / QQ, q01 = t % QQ, q1 = q01 / Q1, q0 = q01 % Q1;
     const float* ip = P0 + c * L::BC + q1 * L::BQ + 2 * q0;
     const float* is = P0 + L::BS + c * L::SC + q1 * L::SQ + q0;
@@ -179,7 +188,10 @@ __device__ __forceinline__ void pac_fwd(const float2 (&tBG)[Q1 * N], float* P0, 
 template <int N, int Q1, class L>
 __device__ __forceinline__ void pac_adj(const float2 (&tBG)[Q1 * N], float* P0, float* P1, int lane) {
   constexpr int NC = 3, QQ = Q1 * Q1;
-  for (int t = lane; t < NC * QQ; t += 32) {              // columns (c, q1, q0): Z over q2 -> B
+#pragma unroll
+  for (int k = 0; k < (NC * QQ + 31) / 32; ++k) {              // columns (c, q1, q0): Z over q2 -> B
+    const int t = lane + 32 * k;
+    if (t >= NC * QQ) break;
     const int c = t / QQ, q01 = t % QQ, q1 = q01 / Q1, q0 = q01 % Q1;
     const float2* zp = reinterpret_cast<const float2*>(P1 + c * L::ZC) + q01;
     const float* zs = P1 + L::ZS + c * L::ZT + q01;
@@ -207,7 +219,10 @@ __device__ __forceinline__ void pac_adj(const float2 (&tBG)[Q1 * N], float* P0, 
     }
   }
   __syncwarp();
-  for (int t = lane; t < NC * N * Q1; t += 32) {          // rows (c, l, q0): B over q1 -> A
+#pragma unroll
+  for (int k = 0; k < (NC * N * Q1 + 31) / 32; ++k) {          // rows (c, l, q0): B over q1 -> A
+    const int t = lane + 32 * k;
+    if (t >= NC * N * Q1) break;
     const int q0 = t % Q1, l = (t / Q1) % N, c = t / (Q1 * N);
     const float* ip = P0 + c * L::BC + l * L::BL + 2 * q0;
     const float* is = P0 + L::BS + c * L::SC + l * L::SL + q0;
@@ -233,7 +248,10 @@ __device__ __forceinline__ void pac_adj(const float2 (&tBG)[Q1 * N], float* P0, 
     }
   }
   __syncwarp();
-  for (int t = lane; t < NC * N * N; t += 32) {           // rows (c, l, j): A over q0 -> y
+#pragma unroll
+  for (int k = 0; k < (NC * N * N + 31) / 32; ++k) {           // rows (c, l, j): A over q0 -> y
+    const int t = lane + 32 * k;
+    if (t >= NC * N * N) break;
     const int c = t / (N * N), lj = t % (N * N), l = lj / N, j = lj % N;
     const float2* in = reinterpret_cast<const float2*>(P1 + c * L::AC + l * L::AL + j * L::AR);
     float2 w[Q1];
