@@ -568,11 +568,16 @@ __device__ __forceinline__ void adj3(const R* __restrict__ B, const R* __restric
 // whole row of outputs: it loads the row's inputs once into registers and
 // takes the 1D tables from registers (tB/tG: [Q1][N], compile-time indexed),
 // so a stage issues ~4x fewer shared-memory instructions. Used by the FP32
-// kernels, whose throughput the shared-memory pipe otherwise bounds.
+// kernels, whose throughput the shared-memory pipe otherwise bounds. Each
+// loop over lanes runs its compile-time number of passes, so the index
+// arithmetic folds into straight-line code.
 template <int N, int Q1, int NC, class R>
 __device__ __forceinline__ void fwd3_rb(const R (&tB)[Q1 * N], const R (&tG)[Q1 * N], R* P0, R* P1, int lane) {
   constexpr int NNQ = N * N * Q1, NQQ = N * Q1 * Q1, QQ = Q1 * Q1, QQQ = Q1 * Q1 * Q1;
-  for (int t = lane; t < NC * N * N; t += 32) {           // (c, l, j) rows of x
+  #pragma unroll
+  for (int k = 0; k < (NC * N * N + 31) / 32; ++k) {           // (c, l, j) rows of x
+    const int t = lane + 32 * k;
+    if (t >= NC * N * N) break;
     const int c = t / (N * N), lj = t % (N * N);
     R xv[N];
 #pragma unroll
@@ -590,7 +595,10 @@ __device__ __forceinline__ void fwd3_rb(const R (&tB)[Q1 * N], const R (&tG)[Q1 
     }
   }
   __syncwarp();
-  for (int t = lane; t < NC * N * Q1; t += 32) {          // (c, l, q0)
+  #pragma unroll
+  for (int k = 0; k < (NC * N * Q1 + 31) / 32; ++k) {          // (c, l, q0)
+    const int t = lane + 32 * k;
+    if (t >= NC * N * Q1) break;
     const int q0 = t % Q1, l = (t / Q1) % N, c = t / (Q1 * N);
     R xb[N], xg[N];
 #pragma unroll
@@ -614,7 +622,10 @@ __device__ __forceinline__ void fwd3_rb(const R (&tB)[Q1 * N], const R (&tG)[Q1 
     }
   }
   __syncwarp();
-  for (int t = lane; t < NC * QQ; t += 32) {              // (c, q1, q0) columns
+  #pragma unroll
+  for (int k = 0; k < (NC * QQ + 31) / 32; ++k) {              // (c, q1, q0) columns
+    const int t = lane + 32 * k;
+    if (t >= NC * QQ) break;
     const int c = t / QQ, q01 = t % QQ;
     R sbb[N], sbg[N], sgb[N];
 #pragma unroll
@@ -644,7 +655,10 @@ __device__ __forceinline__ void fwd3_rb(const R (&tB)[Q1 * N], const R (&tG)[Q1 
 template <int N, int Q1, int NC, class R>
 __device__ __forceinline__ void adj3_rb(const R (&tB)[Q1 * N], const R (&tG)[Q1 * N], R* P0, R* P1, int lane) {
   constexpr int NNQ = N * N * Q1, NQQ = N * Q1 * Q1, QQ = Q1 * Q1, QQQ = Q1 * Q1 * Q1;
-  for (int t = lane; t < NC * QQ; t += 32) {              // (c, q1, q0) columns of R
+  #pragma unroll
+  for (int k = 0; k < (NC * QQ + 31) / 32; ++k) {              // (c, q1, q0) columns of R
+    const int t = lane + 32 * k;
+    if (t >= NC * QQ) break;
     const int c = t / QQ, q01 = t % QQ;
     R r0[Q1], r1[Q1], r2[Q1];
 #pragma unroll
@@ -669,7 +683,10 @@ __device__ __forceinline__ void adj3_rb(const R (&tB)[Q1 * N], const R (&tG)[Q1 
     }
   }
   __syncwarp();
-  for (int t = lane; t < NC * N * Q1; t += 32) {          // (c, l, q0)
+  #pragma unroll
+  for (int k = 0; k < (NC * N * Q1 + 31) / 32; ++k) {          // (c, l, q0)
+    const int t = lane + 32 * k;
+    if (t >= NC * N * Q1) break;
     const int q0 = t % Q1, l = (t / Q1) % N, c = t / (Q1 * N);
     R u0[Q1], u1[Q1], u2[Q1];
 #pragma unroll
@@ -692,7 +709,10 @@ __device__ __forceinline__ void adj3_rb(const R (&tB)[Q1 * N], const R (&tG)[Q1 
     }
   }
   __syncwarp();
-  for (int t = lane; t < NC * N * N; t += 32) {           // (c, l, j) rows of y
+  #pragma unroll
+  for (int k = 0; k < (NC * N * N + 31) / 32; ++k) {           // (c, l, j) rows of y
+    const int t = lane + 32 * k;
+    if (t >= NC * N * N) break;
     const int c = t / (N * N), lj = t % (N * N);
     R vg[Q1], vb[Q1];
 #pragma unroll

@@ -10,7 +10,9 @@
 // contraction and scatter) the loads of element e + stride are already in
 // flight (its v and fixed flags, the record of each lane's first point), and
 // inside the pointwise stage the record of a lane's next point is loaded
-// before the current point is computed. Everything is warp-synchronous: no
+// before the current point is computed; when a warp starts an element, the
+// record block of its next element is prefetched into L2 in one bulk
+// request. Everything is warp-synchronous: no
 // block barriers after the prologue. With p.vdot set, each warp also sums
 // v_E . (H_E v_E) over its elements, which is v . (H v) summed element by
 // element (v is read as zero at fixed dofs, where H v is zero): MINRES then
@@ -289,6 +291,10 @@ __device__ __forceinline__ void fetch_v(const KParams& p, const NodeMap<N>& m, i
   }
 }
 
+__device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <int QP>
 __device__ __forceinline__ void fetch_rec(const float* rec, int pa_stride, int e, int q, float (&h)[kCompactRec]) {
   if (q < QP) {
@@ -377,6 +383,11 @@ __global__ void __launch_bounds__(kPacWarps * 32, N == 4 ? 2 : 0) pac_kernel(con
   fetch_v<N, NT>(p, cur, lane, v, fnext);
   fetch_rec<QP>(rec, p.pa_stride, e, lane, hq);
   for (;;) {
+    // ---- the record block of the next element goes to L2 ahead of its loads
+    // (one bulk prefetch: the block is contiguous, 16-byte aligned and padded
+    // to a multiple of 16 bytes)
+    if (lane == 0 && e + stride < p.nelem)
+      l2_prefetch(rec + (size_t)(e + stride) * p.pa_stride, (unsigned)(p.pa_stride * sizeof(float)));
     // ---- v of this element into the stage buffer (fixed dofs read as 0)
     const unsigned fcur = fnext;
 #pragma unroll
