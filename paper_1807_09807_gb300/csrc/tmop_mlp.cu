@@ -111,6 +111,7 @@ __global__ void k_apply(Grid2 G0, const uint8_t* fixed, const float* Y, int ldy,
 // dimensions multiples of 8 (16-byte rows); rows of the last 128-row tile
 // beyond M read as zero and are not stored.
 constexpr int TM = 128, TN = 64, TK = 64;
+static_assert((TM * TK / 8) % 128 == 0 && (TN * TK / 8) % 128 == 0, "chunk staging: whole passes of 128 threads");
 constexpr uint32_t kTmemCols = 64;                    // FP32 accumulator columns (power of 2, >= 32)
 constexpr long kMmaSpin = 1L << 20;                   // bound on the wait for one chunk's MMAs
 enum { EPI_BIAS_RELU_BF16 = 0, EPI_BIAS_F32 = 1, EPI_MASK_BF16 = 2, EPI_F32 = 3 };
@@ -187,7 +188,11 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int kper, 
   int chunk = 0;
   for (int k0 = kb; k0 < ke; k0 += TK, ++chunk) {
     // ---- stage the chunk (zero rows beyond M)
-    for (int c = tid; c < TM * TK / 8; c += 128) {
+    // (compile-time trip counts: every thread issues all its loads of the chunk
+    // before the stores that wait on them)
+#pragma unroll
+    for (int i = 0; i < TM * TK / 8 / 128; ++i) {
+      const int c = tid + 128 * i;
       if (AK) {
         const int r = c / (TK / 8), kc = (c % (TK / 8)) * 8;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
@@ -202,7 +207,9 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int kper, 
         for (int j = 0; j < 8; ++j) *reinterpret_cast<unsigned short*>(sA + cm_off(mc + j, kk)) = e[j];
       }
     }
-    for (int c = tid; c < TN * TK / 8; c += 128) {
+#pragma unroll
+    for (int i = 0; i < TN * TK / 8 / 128; ++i) {
+      const int c = tid + 128 * i;
       if (BK) {
         const int r = c / (TK / 8), kc = (c % (TK / 8)) * 8;
         *reinterpret_cast<uint4*>(sB + cm_off(r, kc)) =
@@ -399,9 +406,21 @@ int colsum(const Tv* X, int rows, int ld, int ncol, float* part, float* out, cud
   return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
 }
 
-__global__ void k_adam(float* w, float* m, float* v, const float* g, size_t n, float lr, float b1t, float b2t,
-                       bf16* wb) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+// Adam (beta1 0.9, beta2 0.999, eps 1e-8) on all six parameter blocks in one
+// launch (blocks start at off[b], sz[b] entries each; the padding between
+// blocks is left alone), refreshing the bf16 copies of the weights.
+struct AdamSegs {
+  size_t off[6], sz[6];
+  bf16* wb[6];
+};
+
+__global__ void k_adam_all(float* w, float* m, float* v, const float* g, size_t total, const AdamSegs sg, float lr,
+                           float b1t, float b2t) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    int b = 5;
+    while (b > 0 && i < sg.off[b]) --b;
+    const size_t j = i - sg.off[b];
+    if (j >= sg.sz[b]) continue;
     const float gi = g[i];
     const float mi = 0.9f * m[i] + 0.1f * gi;
     const float vi = 0.999f * v[i] + 0.001f * gi * gi;
@@ -409,7 +428,7 @@ __global__ void k_adam(float* w, float* m, float* v, const float* g, size_t n, f
     v[i] = vi;
     const float wi = w[i] - lr * (mi / (1.0f - b1t)) / (sqrtf(vi / (1.0f - b2t)) + 1e-8f);
     w[i] = wi;
-    if (wb) wb[i] = __float2bfloat16_rn(wi);
+    if (sg.wb[b]) sg.wb[b][j] = __float2bfloat16_rn(wi);
   }
 }
 
@@ -681,9 +700,13 @@ int tmop_mlp_adam(tmop_mlp* n, float lr, void* stream) {
   bf16* wb[6] = {n->W1, nullptr, n->W2, nullptr, n->W3, nullptr};
   const size_t sz[6] = {(size_t)n->H * n->K1, (size_t)n->H, (size_t)n->H * n->H, (size_t)n->H,
                         (size_t)n->N3 * n->H, (size_t)n->N3};
-  for (int i = 0; i < 6; ++i)
-    k_adam<<<128, 256, 0, s>>>(P(n, n->w, i), P(n, n->m, i), P(n, n->v, i), P(n, n->g, i), sz[i], lr, b1t, b2t,
-                               wb[i]);
+  AdamSegs sg;
+  for (int i = 0; i < 6; ++i) {
+    sg.off[i] = n->off[i];
+    sg.sz[i] = sz[i];
+    sg.wb[i] = wb[i];
+  }
+  k_adam_all<<<304, 256, 0, s>>>(n->w, n->m, n->v, n->g, n->total, sg, lr, b1t, b2t);
   return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
 }
 

@@ -80,6 +80,37 @@ def test_mlp_adam_training_fits_a_smooth_map(L):
     assert loss.item() < first / 20
 
 
+def test_mlp_adam_step_matches_the_update_rule(L):
+    """Two Adam steps on every parameter block (W1, b1, W2, b2, W3, b3) against
+    the update written out in numpy float32: m = 0.9 m + 0.1 g,
+    v = 0.999 v + 0.001 g^2, w -= lr (m / (1 - 0.9^t)) / (sqrt(v / (1 - 0.999^t)) + 1e-8)."""
+    rng = np.random.default_rng(3)
+    net = L.MLP(40, 6, 64, seed=2)
+    B = 256
+    bits, Xr = bf16_bits(rng.standard_normal((B, 40)))
+    Xd = torch.zeros((B, net.ld), dtype=torch.int16, device="cuda")
+    Xd[:, :40] = torch.tensor(bits, device="cuda")
+    Td = torch.tensor(rng.standard_normal((B, 6)).astype(np.float32), device="cuda")
+    w = net.get(0).astype(np.float32)
+    m = np.zeros_like(w)
+    v = np.zeros_like(w)
+    for t, lr in ((1, np.float32(1e-3)), (2, np.float32(5e-4))):
+        net.gradients(Xd, Td)
+        g = net.get(1).astype(np.float32)
+        net.adam(float(lr))
+        m = np.float32(0.9) * m + np.float32(0.1) * g
+        v = np.float32(0.999) * v + np.float32(0.001) * g * g
+        mh = m / (np.float32(1) - np.float32(0.9) ** t)
+        vh = v / (np.float32(1) - np.float32(0.999) ** t)
+        w = w - lr * mh / (np.sqrt(vh) + np.float32(1e-8))
+        got = net.get(0)
+        assert np.allclose(got, w, rtol=1e-5, atol=1e-7), np.abs(got - w).max()
+    # the next forward pass uses the updated weights (their bf16 copies)
+    Y = net.forward(Xd)[:, :6].cpu().numpy()
+    Yo, _ = omlp.forward(Xr, net.unflatten(w), bf16=True)
+    assert _rel(Y, Yo) <= 1e-3
+
+
 def _features_numpy(m, x, ex, ey):
     k, Nx, Ny = m.order, m.nx[0] * m.order + 1, m.nx[1] * m.order + 1
     P = x.reshape(2, Ny, Nx)
