@@ -577,13 +577,18 @@ def _event_ms(fn, reps, stream, flush=None):
 def measure_pa(tm, m, x, v, y, flush, stream, args):
     """Linearize (once per Newton step) and the partially assembled Hessian
     action (once per Krylov iteration), FP64 and FP32, with the HBM roofline
-    of the FP32 product: it reads the packed Hessians (dim^2 (dim^2+1)/2 FP32
-    per point) and v, and writes y."""
+    of the FP32 product: it reads the stored values (the 14-value compact
+    record or the dim^2 (dim^2+1)/2 packed Hessian entries, FP32, per point)
+    and v, and writes y. In 3D the packed form is also timed on the same mesh
+    with mu302, whose Hessian is not written in (|T|^2, det T)."""
     import torch
     peaks = measured_peaks()
     out = {}
-    for name, pf in (("fp64", tm.FP64), ("fp32", tm.FP32_MIXED)):
-        c = tm.Context.from_mesh(m, precision=pf)
+    forms = [("fp64", tm.FP64, None), ("fp32", tm.FP32_MIXED, None)]
+    if m.dim == 3:
+        forms.append(("fp32_packed_mu302", tm.FP32_MIXED, 302))
+    for name, pf, metric in forms:
+        c = tm.Context.from_mesh(m, precision=pf, metric=metric)
         c.linearize(x)
         c.hess_apply_pa(v, out=y)
         torch.cuda.synchronize()
@@ -609,10 +614,12 @@ def measure_pa(tm, m, x, v, y, flush, stream, args):
                                "kernel": f"pac_kernel<{n},{m.nq}> (compact records)" if compact
                                else f"elem_kernel<{m.dim},{n},{m.nq},float,OP_HESS_PA>", "traffic": None}
             ent["values_per_point"] = ns
+            if metric is not None:
+                ent["metric"] = metric
             tfile = os.path.join(ROOT, "profiles", "traffic.json")
             if os.path.exists(tfile):
                 with open(tfile) as f:
-                    tr = json.load(f).get(f"{args.workload}:pa_fp32")
+                    tr = json.load(f).get(f"{args.workload}:pa_fp32" + ("" if compact else "_packed"))
                 if tr and tr.get("kernel_src_sha256") == kernel_src_hash(PAC_SOURCES if compact else ELEM_SOURCES):
                     ent["roofline"]["traffic"] = tr["dram_bytes_per_launch"]
         out[name] = ent
