@@ -529,6 +529,12 @@ def run_ours(args):
     if args.converge and rank == 0:
         converge = time_to_converged(tm, m, dev, args)
 
+    configs = None
+    if args.configs and rank == 0:
+        if converge is not None:
+            args._c4_counts = (converge["fp64"]["newton"], converge["fp64"]["krylov"]) if args.workload == "c4" else None
+        configs = newton_configs(tm, dev, args)
+
     learned = None
     if args.learned and rank == 0:
         learned = learned_proposal(tm, dev, args)
@@ -548,6 +554,8 @@ def run_ours(args):
             line["partial_assembly"] = pa
         if converge is not None:
             line["time_to_converged"] = converge
+        if configs is not None:
+            line["newton_configs"] = configs
         if learned is not None:
             line["learned_proposal"] = learned
         if not args.no_cpu_baseline:
@@ -655,6 +663,77 @@ def time_to_converged(tm, m, dev, args):
         res_all[f"{k}_vs_fp64_F_rel"] = abs(res_all[k]["F"] - F64) / abs(F64)
         res_all[f"speedup_{k}_over_fp64"] = res_all["fp64"]["seconds"] / res_all[k]["seconds"]
     return res_all
+
+
+def oracle_call_seconds(m, budget_s=1.5):
+    """Single-thread seconds of one oracle gradient and one Hessian action on
+    the whole mesh, scaled from whole z-slabs (rows of elements in 2D) timed
+    for about budget_s each."""
+    import oracle
+    p = oracle.Problem(m.dim, m.order, m.elem_nodes, m.nnode, m.fixed, m.nq, m.metric, quad_kind=m.quad_kind)
+    v = np.random.default_rng(11).standard_normal(m.x.shape)
+    slab = m.nx[0] * m.nx[1] if m.dim == 3 else m.nx[0]
+    out = {}
+    for name, call in (("gradient", lambda els: p.gradient(m.x, elems=els)),
+                       ("hess_apply", lambda els: p.hess_apply(m.x, v, elems=els))):
+        call(np.arange(0, min(slab, m.nelem), dtype=np.int32))   # warm-up (tables, first touch)
+        done, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < budget_s and done < m.nelem:
+            els = np.arange(done, min(done + slab, m.nelem), dtype=np.int32)
+            call(els)
+            done += len(els)
+        out[name] = (time.perf_counter() - t0) * m.nelem / done
+    return out
+
+
+def newton_configs(tm, dev, args):
+    """Newton to |g| <= 1e-12 |g0| on the smaller configurations (C1-C3) on
+    the GPU, plain FP64 and the FP32 Hessian-action form, beside the CPU
+    oracle: its own Newton measured on C1 (single thread); for C2-C4 the CPU
+    time is extrapolated from single-thread per-call times of the oracle
+    (gradient, matrix-free Hessian action) times the GPU run's Newton and
+    MINRES counts, a lower bound (line-search energies not counted)."""
+    import torch
+    out = {}
+    for name in ("c1", "c2", "c3", "c4"):
+        m = mg.make_mesh(name, 1)
+        ent = {"elements": m.nelem, "quad_points": m.n_qp, "metric": m.metric}
+        forms = (("fp64", tm.FP64), ("mixed", tm.FP32_MIXED)) if name != "c4" else ()
+        for form, pf in forms:
+            c = tm.Context.from_mesh(m, precision=pf)
+            xc = torch.tensor(m.x, device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = c.newton_solve(xc, max_newton=args.max_newton, rtol=1e-12)
+            torch.cuda.synchronize()
+            rep = res.report
+            ent[f"gpu_{form}"] = {"seconds": time.perf_counter() - t0, "status": tm.status_string(res.status),
+                                  "newton": rep["iterations"], "krylov": rep["krylov_iterations"], "F": rep["F"]}
+            c.close()
+        calls = oracle_call_seconds(m)
+        ent["cpu_oracle_call_seconds"] = calls
+        counts = ent.get("gpu_fp64") or {"newton": None, "krylov": None}
+        if name == "c4":   # the main benchmark's FP64 Newton counts
+            counts = {"newton": args._c4_counts[0], "krylov": args._c4_counts[1]} if getattr(args, "_c4_counts", None) \
+                else counts
+        if counts["newton"] is not None:
+            est = counts["newton"] * calls["gradient"] + counts["krylov"] * calls["hess_apply"]
+            ent["cpu_oracle_newton_seconds_extrapolated"] = est
+            if "gpu_fp64" in ent:
+                ent["speedup_gpu_fp64_over_cpu_extrapolated"] = est / ent["gpu_fp64"]["seconds"]
+                ent["speedup_gpu_mixed_over_cpu_extrapolated"] = est / ent["gpu_mixed"]["seconds"]
+        if name == "c1":
+            import oracle
+            p = oracle.Problem(m.dim, m.order, m.elem_nodes, m.nnode, m.fixed, m.nq, m.metric,
+                               quad_kind=m.quad_kind)
+            t0 = time.perf_counter()
+            rc, xo, hist = p.newton(m.x, max_newton=args.max_newton, rtol=1e-12)
+            dt = time.perf_counter() - t0
+            ent["cpu_oracle_newton"] = {"seconds": dt, "status": int(rc), "newton": len(hist) - 1,
+                                        "krylov": int(hist[1:, 4].sum()), "F": float(hist[-1, 0])}
+            ent["speedup_gpu_fp64_over_cpu_measured"] = dt / ent["gpu_fp64"]["seconds"]
+        out[name] = ent
+    return out
 
 
 def mlp_gemm_flops(net, batch):
@@ -767,6 +846,8 @@ def main():
     ap.add_argument("--no-converge", dest="converge", action="store_false")
     ap.add_argument("--no-pa", dest="pa", action="store_false")
     ap.add_argument("--no-learned", dest="learned", action="store_false")
+    ap.add_argument("--no-configs", dest="configs", action="store_false",
+                    help="skip the Newton runs on C1-C3 and the oracle per-call timings")
     ap.add_argument("--train-meshes", type=int, default=2000)
     ap.add_argument("--train-epochs", type=int, default=15)
     ap.add_argument("--train-meshes-curved", type=int, default=500)
