@@ -7,14 +7,17 @@ points, 9.1 M dofs), interior nodes jittered, trilinear shear, boundary fixed.
 
 Metric: quadrature points per second of gradient + Hessian action
 (NE * Q / t(step)), plus time-to-converged Newton (Section 3.4 line search,
-MINRES inner solves) for the plain FP64 form and the FP32-bulk form.
+MINRES inner solves) for the plain FP64 form and the FP32-bulk form, on this
+workload and (newton_configs) on the smaller configurations beside the CPU
+oracle.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload c4] [--precision fp64|mixed] [--no-converge]
+                    [--no-pa] [--no-learned] [--no-configs] [--no-cpu-baseline]
                     [--kernels-only]
 
 --impl reference times the plain FP64 CPU oracle (the reference for this
-path) on a bounded sample of the same workload, on the host cores.
+path) on a bounded sample of the same workload, one process per host core.
 --kernels-only runs warm-up plus K steps and nothing else (for profilers);
 with --profile pa it runs one linearisation and W+K partially assembled
 Hessian actions instead (the linearisation is the second element-kernel
