@@ -321,6 +321,26 @@ def test_fp32_compact_product_full_c4_sampled(tm):
     assert rel(host(c64.hess_apply_pa(dev(v)))[:, nodes], yo) <= RTOL
 
 
+def test_fp32_packed_product_full_c4_sampled(tm):
+    """The 45-value FP32 product at full size, as bench.py times it: mu302
+    (not written in |T|^2 and det T, so the packed A-space Hessians are
+    stored) on the 48^3 order-3 mesh, at 64 sampled free nodes against the
+    oracle restricted to the elements around them, within the FP32 bound."""
+    m = make("c4", 1)
+    orc = orc_for(m, metric=302)
+    x = dev(m.x)
+    rng = np.random.default_rng(5)
+    free = np.nonzero(m.fixed[0] == 0)[0]
+    nodes = rng.choice(free, 64, replace=False)
+    els = _patch(m, nodes)
+    v = rng.standard_normal(m.x.shape)
+    yo = orc.hess_apply(m.x, v, elems=els)[:, nodes]
+    c32 = tm.Context.from_mesh(m, precision=tm.FP32_MIXED, metric=302)
+    c32.linearize(x)
+    assert c32.pa_layout()[0] == 45
+    assert rel(host(c32.hess_apply_pa(dev(v)))[:, nodes], yo) <= 1e-5
+
+
 def test_inverted_mesh(tm):
     m = make("c1", 1, nx=4)
     x = m.x_ideal.copy()
