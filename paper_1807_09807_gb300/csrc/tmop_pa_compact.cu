@@ -57,7 +57,8 @@ __device__ __forceinline__ float2 bcast2(float x) { return make_float2(x, x); }
 // Strides per (N, Q1), chosen by counting, for each shared-memory access of
 // the stages, the distinct words one warp instruction puts on one bank (half
 // warps for 8-byte accesses) and taking the strides with the lowest total
-// (ties: the smallest buffers).
+// (ties: the smallest buffers). pac_layout_search.py, beside this file,
+// regenerates the table.
 template <int N, int Q1>
 struct PacLayout;
 #define TMOP_PAC_LAYOUT(N_, Q_, XR_, XC_, AR_, AL_, AC_, BQ_, BL_, BC_, SQ_, SL_, SC_, ZC_, ZT_) \
