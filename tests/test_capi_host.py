@@ -100,3 +100,22 @@ def test_null_arguments(lib):
     assert lib.tmop_selftest_rcbrt(None, None, 0, None) == tm.OK
     assert lib.tmop_selftest_rcbrt(None, None, 3, None) == tm.ERR_ARG
     lib.tmop_destroy(None)
+
+
+def test_compact_product_strides_are_the_search_result():
+    """The padded stage-buffer strides compiled into the compact product
+    (PacLayout in tmop_pa_compact.cu) are what the bank-conflict search
+    returns, for the benchmark's n = 4, q = 5 and the smallest pair."""
+    import importlib.util
+    csrc = os.path.join(ROOT, "paper_1807_09807_gb300", "csrc")
+    spec = importlib.util.spec_from_file_location("pac_layout_search", os.path.join(csrc, "pac_layout_search.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    src = open(os.path.join(csrc, "tmop_pa_compact.cu")).read()
+    table = {}
+    for line in re.findall(r"^TMOP_PAC_LAYOUT\(([^)]*)\)", src, re.M):
+        v = tuple(int(x) for x in line.split(","))
+        table[v[:2]] = v[2:]
+    assert set(table) == set(mod.PAIRS)
+    for pair in ((4, 5), (2, 2)):
+        assert table[pair] == mod.search(*pair)
