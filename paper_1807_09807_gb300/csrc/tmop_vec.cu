@@ -207,7 +207,14 @@ __device__ void minres_scalar_step(double* st) {
   }
 }
 
-__global__ void k_minres_scalar(double* st) {
+// one block: |next Lanczos vector|^2 from the Lanczos step's per-block
+// partials (the same sum as k_sum_final), then the scalar step in thread 0
+__global__ void k_minres_scalar(const double* __restrict__ part, int np, double* st) {
+  double sum = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) sum += part[i];
+  sum = block_sum(sum);
+  if (threadIdx.x != 0) return;
+  st[KS_BETA_NEXT2] = sum;
   minres_scalar_step(st);
   // scales of the unnormalised Lanczos vectors: the direction update takes v
   // at its present scale, then the arrays rotate and the next v is the new
@@ -255,8 +262,7 @@ int minres_after_hv_rot(const double* v, const double* vprev, double* Av, const 
     k_sum_final<<<1, kThreads, 0, s>>>(part, g, st + KS_ALPHA);
   }
   k_lanczos<<<g, kThreads, 0, s>>>(Av, v, vprev, st, n, part);
-  k_sum_final<<<1, kThreads, 0, s>>>(part, g, st + KS_BETA_NEXT2);
-  k_minres_scalar<<<1, 1, 0, s>>>(st);
+  k_minres_scalar<<<1, kThreads, 0, s>>>(part, g, st);
   k_minres_vec_rot<<<g, kThreads, 0, s>>>(v, w, wp, sol, st, n);
   return (int)cudaGetLastError();
 }
