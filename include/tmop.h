@@ -113,7 +113,7 @@ int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metr
  * A = sum_i x_i grad w_i (eq. (2.2), eq. (2.4)), and min over all points of
  * det A. F and min_detA are HOST pointers written after the stream is
  * synchronised. If some det A <= 0, *F = +inf for barrier metrics (the
- * "big value" of Section 3.4) and TMOP_ERR_INVERTED is returned with
+ * large objective Section 3.4 asks for at inverted points) and TMOP_ERR_INVERTED is returned with
  * *min_detA set. */
 int tmop_energy(tmop_ctx* ctx, const double* x, double* F, double* min_detA, void* stream);
 
@@ -314,6 +314,21 @@ int tmop_selftest_convert(const double* in, float* f32, double* back, size_t n, 
  * the library cube root elsewhere. in, out DEVICE [n] FP64. Asynchronous.
  * Errors: TMOP_ERR_ARG, TMOP_ERR_CUDA. */
 int tmop_selftest_rcbrt(const double* in, double* out, size_t n, void* stream);
+
+/* Measured FMA throughput of the current GPU (not part of the method: the
+ * denominator of the rooflines of the FP64 and FP32 element kernels, which
+ * are bound by their arithmetic pipes, not by HBM). kind TMOP_PEAK_FP64
+ * (DFMA), TMOP_PEAK_FP32 (FFMA) or TMOP_PEAK_FP32X2 (the paired FP32
+ * instruction, two multiply-adds each). Every thread of a grid of 1024
+ * threads per SM runs 8 independent multiply-add chains for a fixed count
+ * (a few ms per launch); one untimed launch, then the best of 3 timed with
+ * CUDA events on the stream, which this call synchronises. scratch: DEVICE,
+ * at least SMs * 1024 * 8 bytes (each thread's sum, so that no work is dead
+ * code). *gflops = 2 * multiply-adds / best time (GFLOP/s); *ms = that time
+ * (may be NULL). Errors: TMOP_ERR_ARG, TMOP_ERR_CAPACITY (scratch too
+ * small), TMOP_ERR_CUDA. */
+enum { TMOP_PEAK_FP64 = 0, TMOP_PEAK_FP32 = 1, TMOP_PEAK_FP32X2 = 2 };
+int tmop_fma_peak(int kind, void* scratch, size_t scratch_bytes, double* gflops, double* ms, void* stream);
 
 /* Sizes of a context: Q (points per element), ndof = dim * nnode. */
 int tmop_sizes(const tmop_ctx* ctx, int* dim, int* nelem, int* nnode, int* Q);

@@ -60,8 +60,10 @@ int tmop_patch_apply(int order, int nx, int ny, const double* x0, const uint8_t*
  * bfloat16 weights and activations with FP32 accumulation on the
  * fifth-generation tensor cores (tcgen05.mma, accumulators in tensor
  * memory), FP32 master weights and Adam state. A GEMM whose bounded wait for
- * its tensor-core work gives up is reported as TMOP_ERR_CUDA by the next
- * tmop_mlp_get.
+ * its tensor-core work gives up (not expected) raises the network's fault
+ * flag and writes NaN into its output tile, so the loss and every later
+ * output are NaN; tmop_mlp_forward, tmop_mlp_check and tmop_mlp_get report
+ * the flag as TMOP_ERR_CUDA (and clear it).
  * n_hidden must be a multiple of 64; n_in <= 1024, n_out <= 64. Weights are
  * initialised He-normal from seed (the last layer scaled by 0.1), biases 0. */
 typedef struct tmop_mlp tmop_mlp;
@@ -72,8 +74,15 @@ void tmop_mlp_destroy(tmop_mlp* net);
 int tmop_mlp_input_ld(const tmop_mlp* net);
 
 /* Y = net(X): X DEVICE bf16 [batch][input_ld], Y DEVICE float [batch][ldy]
- * (ldy >= n_out). batch a multiple of 64. */
+ * (ldy >= n_out). batch a multiple of 64. Synchronises the stream to read the
+ * fault flag (TMOP_ERR_CUDA if a GEMM gave up). */
 int tmop_mlp_forward(tmop_mlp* net, const uint16_t* X, int batch, float* Y, int ldy, void* stream);
+
+/* Reads (stream-ordered; synchronises the stream) and clears the fault flag:
+ * TMOP_ERR_CUDA if some GEMM since the last check gave up its bounded wait,
+ * else TMOP_OK. Training loops call it once per epoch: the asynchronous
+ * tmop_mlp_gradients / tmop_mlp_adam do not synchronise. */
+int tmop_mlp_check(tmop_mlp* net, void* stream);
 
 /* Loss L = (1/batch) sum |Y - T|^2 and all parameter gradients (kept inside
  * the network; tmop_mlp_get(..., 1, ...) reads them). T DEVICE float

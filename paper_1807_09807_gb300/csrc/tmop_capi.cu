@@ -6,6 +6,7 @@
 // device reductions. All arithmetic on mesh-sized data runs in the CUDA
 // kernels of this library; there is no host fallback.
 #include <cuda_runtime.h>
+#include <utility>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -525,36 +526,36 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
 
 struct NewtonState {
   double F, mdet, gnorm;
+  // the current iterate and its gradient, and the buffers the line search
+  // writes its trial into: an accepted trial swaps roles with the current
+  // pair instead of being copied over it (x starts as the caller's array)
+  double *x, *xt, *g, *gt;
 };
 
-// One Section 3.4 step from x with cached F, det, g (in V_G) and |g|.
-int newton_iter(tmop_ctx* c, double* x, const tmop_newton_opts& o, NewtonState* ns, tmop_newton_report* rep,
-                cudaStream_t s) {
-  double* g = vec(c, V_G);
+// One Section 3.4 step from ns->x with cached F, det, g (ns->g) and |g|.
+int newton_iter(tmop_ctx* c, const tmop_newton_opts& o, NewtonState* ns, tmop_newton_report* rep, cudaStream_t s) {
   double* p = vec(c, V_P);
-  double* xt = vec(c, V_XT);
-  double* gt = vec(c, V_GT);
   int kit = 0;
-  int rc = krylov(c, x, g, p, o, &kit, s);
+  int rc = krylov(c, ns->x, ns->g, p, o, &kit, s);
   if (rc) return rc;
   rep->krylov_iterations += kit < 0 ? -kit : kit;
   double alpha = 1.0;
   for (int h = 0; h <= o.max_halvings; ++h, alpha *= o.alpha_shrink) {
-    if (step(x, p, alpha, xt, c->ndof, s)) return TMOP_ERR_CUDA;
+    if (step(ns->x, p, alpha, ns->xt, c->ndof, s)) return TMOP_ERR_CUDA;
     double Ft, mdt;
-    rc = energy_host(c, xt, &Ft, &mdt, s);
+    rc = energy_host(c, ns->xt, &Ft, &mdt, s);
     if (rc) return rc;
     // the new configuration must be valid (det A > 0 everywhere) and F may
     // grow by at most the f_factor
     if (!(mdt > 0.0) || !(Ft < o.f_factor * ns->F)) continue;
-    rc = launch_op(c, OP_GRADIENT, xt, nullptr, gt, nullptr, s);
+    rc = launch_op(c, OP_GRADIENT, ns->xt, nullptr, ns->gt, nullptr, s);
     if (rc) return rc;
     double gn;
-    rc = norm_host(c, gt, &gn, s);
+    rc = norm_host(c, ns->gt, &gn, s);
     if (rc) return rc;
     if (!(gn < o.g_factor * ns->gnorm)) continue;
-    CUDA_TRY(cudaMemcpyAsync(x, xt, sizeof(double) * c->ndof, cudaMemcpyDeviceToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(g, gt, sizeof(double) * c->ndof, cudaMemcpyDeviceToDevice, s));
+    std::swap(ns->x, ns->xt);
+    std::swap(ns->g, ns->gt);
     ns->F = Ft;
     ns->mdet = mdt;
     ns->gnorm = gn;
@@ -565,15 +566,26 @@ int newton_iter(tmop_ctx* c, double* x, const tmop_newton_opts& o, NewtonState* 
   return TMOP_ERR_LINESEARCH;
 }
 
-int newton_start(tmop_ctx* c, const double* x, NewtonState* ns, cudaStream_t s) {
+int newton_start(tmop_ctx* c, double* x, NewtonState* ns, cudaStream_t s) {
   int rc = ensure_vectors(c);
   if (rc) return rc;
+  ns->x = x;
+  ns->xt = vec(c, V_XT);
+  ns->g = vec(c, V_G);
+  ns->gt = vec(c, V_GT);
   rc = energy_host(c, x, &ns->F, &ns->mdet, s);
   if (rc) return rc;
   if (!(ns->mdet > 0.0)) return TMOP_ERR_INVERTED;
-  rc = launch_op(c, OP_GRADIENT, x, nullptr, vec(c, V_G), nullptr, s);
+  rc = launch_op(c, OP_GRADIENT, x, nullptr, ns->g, nullptr, s);
   if (rc) return rc;
-  return norm_host(c, vec(c, V_G), &ns->gnorm, s);
+  return norm_host(c, ns->g, &ns->gnorm, s);
+}
+
+// The last accepted iterate into the caller's array (one copy, only when it
+// sits in the context's buffer).
+int newton_finish(tmop_ctx* c, double* x, const NewtonState& ns, cudaStream_t s) {
+  if (ns.x && ns.x != x) CUDA_TRY(cudaMemcpyAsync(x, ns.x, sizeof(double) * c->ndof, cudaMemcpyDeviceToDevice, s));
+  return TMOP_OK;
 }
 
 }  // namespace
@@ -972,13 +984,15 @@ int tmop_newton_step(tmop_ctx* c, double* x, const tmop_newton_opts* opts, tmop_
   tmop_newton_opts o = defaults(c, opts);
   tmop_newton_report rep;
   memset(&rep, 0, sizeof(rep));
-  NewtonState ns = {0.0, 0.0, 0.0};
+  NewtonState ns = {0.0, 0.0, 0.0, nullptr, nullptr, nullptr, nullptr};
   int rc = newton_start(c, x, &ns, s);
   rep.grad_norm0 = (rc == TMOP_OK) ? ns.gnorm : 0.0;
   if (rc == TMOP_OK) {
-    rc = newton_iter(c, x, o, &ns, &rep, s);
+    rc = newton_iter(c, o, &ns, &rep, s);
     rep.iterations = 1;
   }
+  const int rf = newton_finish(c, x, ns, s);
+  if (rc == TMOP_OK) rc = rf;
   rep.status = rc;
   rep.F = ns.F;
   rep.grad_norm = ns.gnorm;
@@ -994,19 +1008,21 @@ int tmop_newton_solve(tmop_ctx* c, double* x, const tmop_newton_opts* opts, tmop
   tmop_newton_opts o = defaults(c, opts);
   tmop_newton_report rep;
   memset(&rep, 0, sizeof(rep));
-  NewtonState ns = {0.0, 0.0, 0.0};
+  NewtonState ns = {0.0, 0.0, 0.0, nullptr, nullptr, nullptr, nullptr};
   int rc = newton_start(c, x, &ns, s);
   if (rc == TMOP_OK) {
     rep.grad_norm0 = ns.gnorm;
     rc = TMOP_ERR_NOT_CONVERGED;
     for (int it = 0; it < o.max_newton; ++it) {
       if (ns.gnorm <= o.rtol * rep.grad_norm0 || ns.gnorm <= o.atol) { rc = TMOP_OK; break; }
-      int r = newton_iter(c, x, o, &ns, &rep, s);
+      int r = newton_iter(c, o, &ns, &rep, s);
       rep.iterations = it + 1;
       if (r != TMOP_OK) { rc = r; break; }
     }
     if (rc == TMOP_ERR_NOT_CONVERGED && (ns.gnorm <= o.rtol * rep.grad_norm0 || ns.gnorm <= o.atol)) rc = TMOP_OK;
   }
+  const int rf = newton_finish(c, x, ns, s);
+  if (rc == TMOP_OK) rc = rf;
   rep.status = rc;
   rep.F = ns.F;
   rep.grad_norm = ns.gnorm;

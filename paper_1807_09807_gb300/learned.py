@@ -39,6 +39,7 @@ _MLP_SIGS = {
     "tmop_mlp_forward": ([C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "tmop_mlp_gradients": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_mlp_adam": ([C.c_void_p, C.c_float, C.c_void_p], C.c_int),
+    "tmop_mlp_check": ([C.c_void_p, C.c_void_p], C.c_int),
     "tmop_mlp_num_params": ([C.c_void_p], C.c_size_t),
     "tmop_mlp_get": ([C.c_void_p, C.c_int, C.c_void_p, C.c_size_t], C.c_int),
     "tmop_mlp_set": ([C.c_void_p, C.c_void_p, C.c_size_t], C.c_int),
@@ -135,6 +136,10 @@ class MLP:
 
     def adam(self, lr: float):
         _check(lib().tmop_mlp_adam(self._h, lr, _s()), "tmop_mlp_adam")
+
+    def check(self):
+        """Raise if some GEMM since the last check gave up its bounded wait."""
+        _check(lib().tmop_mlp_check(self._h, _s()), "tmop_mlp_check")
 
 
 def features(m: mg.Mesh, x, ldf: int, first: int = 0, count: int | None = None, ldx: int | None = None, out=None):
@@ -236,6 +241,7 @@ def train(net: MLP, ds: Dataset, epochs=20, batch=4096, lr=1e-3, seed=0, log_eve
             net.adam(lr_ep)
             if b % 50 == 0 or b == nb - 1:
                 acc = loss.item()
+        net.check()
         hist.append(acc)
         if log_every and ep % log_every == 0:
             print(f"epoch {ep} loss {acc:.4e}")

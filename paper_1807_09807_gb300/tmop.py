@@ -91,6 +91,8 @@ _SIGNATURES = {
     "tmop_set_targets_from_positions": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_selftest_convert": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p], C.c_int),
     "tmop_selftest_rcbrt": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p], C.c_int),
+    "tmop_fma_peak": ([C.c_int, C.c_void_p, C.c_size_t, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p],
+                      C.c_int),
     "tmop_destroy": ([C.c_void_p], None),
     "tmop_status_string": ([C.c_int], C.c_char_p),
 }
@@ -155,6 +157,23 @@ def selftest_rcbrt(x):
     if rc != OK:
         raise TmopError(rc, "tmop_selftest_rcbrt")
     return out
+
+
+PEAK_FP64, PEAK_FP32, PEAK_FP32X2 = 0, 1, 2
+
+
+def fma_peak(kind=PEAK_FP64):
+    """(GFLOP/s, ms): the measured FMA throughput of the current GPU
+    (tmop_fma_peak), the denominator of the FP64 / FP32 ALU rooflines."""
+    import torch
+    dev = torch.cuda.current_device()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    scratch = torch.empty(sms * 1024 * 8, dtype=torch.uint8, device=f"cuda:{dev}")
+    g, ms = C.c_double(0.0), C.c_double(0.0)
+    rc = load().tmop_fma_peak(kind, _ptr(scratch), scratch.numel(), C.byref(g), C.byref(ms), _stream())
+    if rc != OK:
+        raise TmopError(rc, "tmop_fma_peak")
+    return g.value, ms.value
 
 
 def energy_noalloc(dim, order, structured, nq, metric, x, F, min_detA, quad_kind=GL, target_kind=W_IDENTITY,

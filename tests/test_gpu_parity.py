@@ -795,3 +795,26 @@ def test_fp32_mixed_newton_reaches_fp64_solution(tm):
     assert abs(F32 - F64) <= 1e-10 * F0
     assert np.abs(host(x32) - host(x64)).max() <= 1e-8 / 16
     assert r32.report["min_detA"] > 0
+
+
+@pytest.mark.gpu
+def test_fma_peak_is_measured_and_plausible(tm):
+    """The roofline denominators of the ALU-bound kernels: tmop_fma_peak
+    measures FP64 and FP32 multiply-add throughput on this GPU. Each is
+    positive and no higher than the unit-count bound at the 2.07 GHz maximum
+    clock of a GB300-class part (152 SMs; 2 FP64 and 128 FP32 FMA per SM and
+    clock), and FP32 runs far faster than FP64 on this part."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    g64, ms64 = tm.fma_peak(tm.PEAK_FP64)
+    g32, _ = tm.fma_peak(tm.PEAK_FP32)
+    g32x2, _ = tm.fma_peak(tm.PEAK_FP32X2)
+    assert ms64 > 0.1
+    assert 0 < g64 <= sms * 2.2 * 2 * 2 * 1.02
+    assert 0 < max(g32, g32x2) <= sms * 2.2 * 128 * 2 * 1.02
+    assert max(g32, g32x2) > 8 * g64
+    small = torch.empty(16, dtype=torch.uint8, device="cuda")
+    import ctypes as C
+    g = C.c_double(0.0)
+    assert tm.load().tmop_fma_peak(tm.PEAK_FP64, C.c_void_p(small.data_ptr()), 16, C.byref(g), None, None) == tm.ERR_CAPACITY
+    assert tm.load().tmop_fma_peak(7, C.c_void_p(small.data_ptr()), 16, C.byref(g), None, None) == tm.ERR_ARG

@@ -82,3 +82,18 @@ def test_noalloc_rejects_grids_beyond_its_scratch(tm):
     assert rc == tm.ERR_CAPACITY
     assert "scratch" in tm.status_string(rc)
     assert tm.energy_noalloc(2, 1, [4, 4], 2, 2, x[:, :25].contiguous(), F, md, target_kind=tm.W_PER_QP) == tm.ERR_ARG
+
+
+@pytest.mark.parametrize("name,kw", [("c1", {}), ("c3", dict(nx=4))])
+def test_noalloc_matches_the_oracle(tm, name, kw):
+    """The same entry point against the FP64 CPU oracle of eq. (2.4) (not
+    only against the library's own context), on a 2D and a 3D grid."""
+    import oracle
+    m = mg.make_mesh(name, 1, **kw)
+    F = torch.empty((), dtype=torch.float64, device="cuda")
+    md = torch.empty((), dtype=torch.float64, device="cuda")
+    rc, _ = _call_capi(tm, m, F, md)
+    assert rc == tm.OK
+    _, Fo, mdo = oracle.Problem(m.dim, m.order, m.elem_nodes, m.nnode, m.fixed, m.nq, m.metric).energy(m.x)
+    assert abs(F.item() - Fo) <= RTOL * abs(Fo), (F.item(), Fo)
+    assert abs(md.item() - mdo) <= RTOL * abs(mdo), (md.item(), mdo)
