@@ -185,7 +185,10 @@ typedef struct {
   int matrix_free;       /* [0] 0: the Krylov operator is partially assembled once per Newton
                             step (tmop_linearize), 1: recomputed from x at every product */
   int precond;           /* [0] 0: none (the paper's standard MINRES), 1: Jacobi, the diagonal of the
-                            partially assembled Hessian (MINRES only; needs matrix_free = 0) */
+                            partially assembled Hessian (MINRES only; needs matrix_free = 0),
+                            2: two-level, Jacobi plus an exact coarse correction on the element
+                            vertices (structured grids whose fixed dofs are exactly the
+                            boundary; else TMOP_ERR_ARG): see tmop_precond_apply */
 } tmop_newton_opts;
 
 typedef struct {
@@ -215,6 +218,24 @@ int tmop_newton_step(tmop_ctx* ctx, double* x, const tmop_newton_opts* opts, tmo
  * max_newton steps (TMOP_ERR_NOT_CONVERGED). x: DEVICE, in/out. */
 int tmop_newton_solve(tmop_ctx* ctx, double* x, const tmop_newton_opts* opts, tmop_newton_report* report,
                       void* stream);
+
+/* The preconditioner of the Krylov solves (Section 5 runs MINRES; the paper
+ * does not state its preconditioner): z = M^-1 r for the linearisation at x
+ * (stored as by tmop_linearize). precond 1: M^-1 = D^-1, the floored
+ * inverse diagonal of the stored Hessian (fixed dofs 1). precond 2:
+ *   M^-1 r = D^-1 r + P (alpha K_c)^-1 P^t r,
+ * with P the interpolation of a bilinear (2D) / trilinear (3D) field on the
+ * element vertices at the Gauss-Lobatto nodes of each element, K_c the
+ * reference-space Laplacian of the vertex field (per component, interior
+ * vertices; the Kronecker sum of the 1D element stiffness and mass
+ * matrices, applied inversely by sine transforms, in FP64 for TMOP_FP64
+ * and FP32 otherwise) and alpha = (P w)^t H (P w) / (w^t K_c w) for the
+ * smoothest coarse mode w in every component (*alpha, 0 if H is not
+ * positive on it: then the coarse part is left out). Needs a structured
+ * grid whose fixed dofs are exactly the boundary (TMOP_ERR_ARG otherwise).
+ * r, z DEVICE [d][nnode]; alpha HOST or NULL. Synchronises the stream. */
+int tmop_precond_apply(tmop_ctx* ctx, const double* x, int precond, const double* r, double* z, double* alpha,
+                       void* stream);
 
 /* Inner Krylov solve H(x) p = b alone (MINRES or CG, zero initial guess),
  * for tests: b, p DEVICE [d][nnode]. Returns iterations through *iters

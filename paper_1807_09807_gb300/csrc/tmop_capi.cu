@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/tmop.h"
+#include "tmop_coarse.h"
 #include "tmop_diag.h"
 #include "tmop_targets.h"
 #include "tmop_kparams.h"
@@ -194,6 +195,12 @@ struct tmop_ctx {
   int mass_grid = 1;
   double* d_diag = nullptr;   // Hessian diagonal [d][nnode] and its floored inverse [d][nnode]
   double* d_vdot = nullptr;   // per-warp partials of v . (H v) from the compact-record product
+  // two-level preconditioner (structured grids whose fixed dofs are exactly the boundary)
+  bool boundary_fixed = false;
+  int grid_n[3] = {0, 0, 0};
+  CoarseSpace* coarse = nullptr;
+  double* d_coarse_w = nullptr;  // [dim][coarse vertices], the smoothest coarse mode
+  double coarse_alpha = 0.0;     // Rayleigh quotient of the last linearisation (0: coarse part off)
   cudaStream_t cap = nullptr; // internal stream for capturing Krylov iterations into a graph
   cudaEvent_t ev = nullptr;   // orders the internal stream after / before the caller's stream
 };
@@ -401,6 +408,35 @@ int hessian_diagonal(tmop_ctx* c, bool inverse, cudaStream_t s) {
   return TMOP_OK;
 }
 
+// The coarse part of the two-level preconditioner for the linearisation at
+// x: the transfer and transform tables (once per context) and alpha, the
+// Rayleigh quotient (P w)^t H (P w) / (w^t K_c w) of the smoothest coarse
+// mode w in every component (one product with the Krylov operator). A
+// Hessian that is not positive on that mode leaves the coarse part off
+// (alpha = 0) for this solve.
+int coarse_setup(tmop_ctx* c, const double* x, int hop, cudaStream_t s) {
+  if (!c->coarse) {
+    double z[kMaxN], zw[kMaxN];
+    rule_gll(c->n, z, zw);
+    c->coarse = coarse_create(c->dim, c->order, c->grid_n, z, c->precision != TMOP_FP64);
+    if (!c->coarse) return TMOP_ERR_CUDA;
+    CUDA_TRY(cudaMalloc(&c->d_coarse_w, sizeof(double) * c->dim * coarse_size(c->coarse)));
+  }
+  double lam0 = 0.0;
+  double *w = vec(c, V_K0), *hw = vec(c, V_K1);
+  if (coarse_mode0(c->coarse, c->d_coarse_w, &lam0, s) != 0) return TMOP_ERR_CUDA;
+  if (coarse_prolong(c->coarse, c->d_coarse_w, w, s) != 0) return TMOP_ERR_CUDA;
+  int rc = launch_op(c, hop, x, w, hw, nullptr, s);
+  if (rc) return rc;
+  if (dot(w, hw, c->ndof, c->d_part, c->d_res + 2, s)) return TMOP_ERR_CUDA;
+  rc = read_res(c, 2, 1, s);
+  if (rc) return rc;
+  const double q = c->h_res[2] / (c->dim * lam0);
+  c->coarse_alpha = (q > 0.0 && isfinite(q)) ? q : 0.0;
+  coarse_set_alpha(c->coarse, c->coarse_alpha);
+  return TMOP_OK;
+}
+
 // Krylov solve H(x) p = b; returns iterations (negative if the cap was hit).
 int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_newton_opts& o, int* iters,
            cudaStream_t s) {
@@ -408,7 +444,9 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
   if (rc) return rc;
   // the Krylov operator: partially assembled at x (default) or recomputed from x
   const int hop = o.matrix_free ? OP_HESS : OP_HESS_PA;
+  if (o.precond < 0 || o.precond > 2) return TMOP_ERR_ARG;
   if (o.precond && (hop != OP_HESS_PA || o.krylov == TMOP_KRYLOV_CG)) return TMOP_ERR_ARG;
+  if (o.precond == 2 && !c->boundary_fixed) return TMOP_ERR_ARG;
   if (hop == OP_HESS_PA) {
     rc = linearize(c, x, s);
     if (rc) return rc;
@@ -418,6 +456,16 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
     rc = hessian_diagonal(c, true, s);
     if (rc) return rc;
     minv = c->d_diag + c->ndof;
+  }
+  PrecondAdd pc_add{coarse_apply_add, nullptr};
+  const PrecondAdd* pc = nullptr;
+  if (o.precond == 2) {  // two-level: plus the coarse correction on the element vertices
+    rc = coarse_setup(c, x, hop, s);
+    if (rc) return rc;
+    if (c->coarse_alpha > 0.0) {
+      pc_add.obj = c->coarse;
+      pc = &pc_add;
+    }
   }
   double* st = c->d_res + kResKrylov;
   double* part = c->d_part;
@@ -437,7 +485,7 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
   if (cg) {
     if (cg_init(b, k0, k1, p, st, part, n, o.krylov_rtol, o.krylov_maxit, s)) return TMOP_ERR_CUDA;
   } else if (minv) {  // r1 = k0, r2 = k1, y = k2, v = k3, w = k4, wprev = k5
-    if (pminres_init(b, minv, k0, k1, k2, k4, k5, p, st, part, n, o.krylov_rtol, o.krylov_maxit, s))
+    if (pminres_init(b, minv, k0, k1, k2, k4, k5, p, st, part, n, o.krylov_rtol, o.krylov_maxit, s, pc))
       return TMOP_ERR_CUDA;
   } else {
     if (minres_init(b, k0, k1, k3, k4, p, st, part, n, o.krylov_rtol, o.krylov_maxit, s)) return TMOP_ERR_CUDA;
@@ -458,7 +506,7 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
         if (pminres_v(k3, k2, st, n, q)) return TMOP_ERR_CUDA;
         r = launch_op(c, hop, x, k3, k2, nullptr, q);
         if (r) return r;
-        if (pminres_after_hv(minv, k0, k1, k2, k3, k4, k5, p, st, part, n, q)) return TMOP_ERR_CUDA;
+        if (pminres_after_hv(minv, k0, k1, k2, k3, k4, k5, p, st, part, n, q, pc)) return TMOP_ERR_CUDA;
         continue;
       }
       if (cg) {  // r = k0, d = k1, Hd = k2
@@ -619,6 +667,8 @@ void tmop_destroy(tmop_ctx* c) {
   cudaFree(c->d_x_init);
   cudaFree(c->d_diag);
   cudaFree(c->d_vdot);
+  coarse_destroy(c->coarse);
+  cudaFree(c->d_coarse_w);
   cudaFreeHost(c->h_res);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->ev) cudaEventDestroy(c->ev);
@@ -760,6 +810,20 @@ int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metr
         cudaMemcpy(c->d_fixed, mesh->fixed, c->ndof, cudaMemcpyHostToDevice) != cudaSuccess)
       rc = TMOP_ERR_CUDA;
     p.fixed = c->d_fixed;
+  }
+  // the two-level preconditioner's coarse space has the boundary fixed: record
+  // whether the fixed dofs are exactly the boundary of a structured grid
+  if (rc == TMOP_OK && structured && mesh->fixed) {
+    const int Nx = order * sd[0] + 1, Ny = order * sd[1] + 1, Nz = d == 3 ? order * sd[2] + 1 : 1;
+    bool ok = true;
+    for (int comp = 0; comp < d && ok; ++comp)
+      for (int node = 0; node < mesh->nnode && ok; ++node) {
+        const int gx = node % Nx, gy = (node / Nx) % Ny, gz = node / (Nx * Ny);
+        const bool bnd = gx == 0 || gx == Nx - 1 || gy == 0 || gy == Ny - 1 || (d == 3 && (gz == 0 || gz == Nz - 1));
+        if ((mesh->fixed[(size_t)comp * mesh->nnode + node] != 0) != bnd) ok = false;
+      }
+    c->boundary_fixed = ok;
+    for (int a = 0; a < d; ++a) c->grid_n[a] = sd[a];
   }
   // launch shapes and workspace
   for (int op = 0; op < OP_COUNT && rc == TMOP_OK; ++op) {
@@ -968,6 +1032,28 @@ int tmop_hessian_diagonal(tmop_ctx* c, double* out, void* stream) {
 int tmop_element_min_detA(tmop_ctx* c, const double* x, double* out, void* stream) {
   if (!c || !x || !out) return TMOP_ERR_ARG;
   return launch_op(c, OP_ENERGY, x, nullptr, nullptr, out, (cudaStream_t)stream);
+}
+
+int tmop_precond_apply(tmop_ctx* c, const double* x, int precond, const double* r, double* z, double* alpha,
+                       void* stream) {
+  if (!c || !x || !r || !z || precond < 1 || precond > 2) return TMOP_ERR_ARG;
+  if (precond == 2 && !c->boundary_fixed) return TMOP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = ensure_vectors(c);
+  if (!rc) rc = linearize(c, x, s);
+  if (!rc) rc = hessian_diagonal(c, true, s);
+  if (rc) return rc;
+  double a = 0.0;
+  if (precond == 2) {
+    rc = coarse_setup(c, x, OP_HESS_PA, s);
+    if (rc) return rc;
+    a = c->coarse_alpha;
+  }
+  if (vec_mul(c->d_diag + c->ndof, r, z, c->ndof, s)) return TMOP_ERR_CUDA;
+  if (a > 0.0 && coarse_apply_add(c->coarse, r, z, nullptr, s) < 0) return TMOP_ERR_CUDA;
+  if (alpha) *alpha = a;
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return TMOP_OK;
 }
 
 int tmop_krylov_solve(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_newton_opts* opts,

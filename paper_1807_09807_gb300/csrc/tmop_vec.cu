@@ -92,6 +92,16 @@ __global__ void k_energy_final(const double* __restrict__ pf, const double* __re
   }
 }
 
+__global__ void k_mul(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = a[i] * b[i];
+}
+
+int vec_mul(const double* a, const double* b, double* out, size_t n, cudaStream_t s) {
+  k_mul<<<red_grid(n), kThreads, 0, s>>>(a, b, out, n);
+  return (int)cudaGetLastError();
+}
+
 int dot(const double* a, const double* b, size_t n, double* part, double* out, cudaStream_t s) {
   const int g = red_grid(n);
   k_dot_part<<<g, kThreads, 0, s>>>(a, b, n, part);
@@ -272,6 +282,9 @@ int minres_after_hv_rot(const double* v, const double* vprev, double* Av, const 
 // Givens rotations (Paige and Saunders), M = diag(1 / minv). The residual
 // estimate phibar is the M^-1-norm of the residual; the solve stops when it
 // falls to rtol times its initial value.
+// (DOT = false: an additive preconditioner part still updates y, and it
+// writes the partials of b . y)
+template <bool DOT>
 __global__ void k_pm_init(const double* __restrict__ b, const double* __restrict__ minv, double* r1, double* r2,
                           double* y, double* w, double* wprev, double* sol, size_t n, double* __restrict__ part) {
   double s = 0.0;
@@ -283,10 +296,12 @@ __global__ void k_pm_init(const double* __restrict__ b, const double* __restrict
     w[i] = 0.0;
     wprev[i] = 0.0;
     sol[i] = 0.0;
-    s = fma(bi, yi, s);
+    if (DOT) s = fma(bi, yi, s);
   }
-  s = block_sum(s);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (DOT) {
+    s = block_sum(s);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+  }
 }
 
 __global__ void k_pm_init_scalar(double* st, double rtol, int maxit) {
@@ -336,6 +351,8 @@ __global__ void k_pm_a(double* __restrict__ y, const double* __restrict__ r1, co
 }
 
 // y <- y - (alpha / beta) r2; r1 <- r2; r2 <- y; y <- M^-1 r2; partials of r2 . y
+// (DOT = false: an additive preconditioner part still adds to y)
+template <bool DOT>
 __global__ void k_pm_b(const double* __restrict__ minv, double* __restrict__ r1, double* __restrict__ r2,
                        double* __restrict__ y, const double* __restrict__ st, size_t n, double* __restrict__ part) {
   const double beta = st[KS_BETA];
@@ -347,10 +364,12 @@ __global__ void k_pm_b(const double* __restrict__ minv, double* __restrict__ r1,
     r2[i] = t;
     const double yi = minv[i] * t;
     y[i] = yi;
-    s = fma(t, yi, s);
+    if (DOT) s = fma(t, yi, s);
   }
-  s = block_sum(s);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (DOT) {
+    s = block_sum(s);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+  }
 }
 
 __global__ void k_pm_scalar(double* st) {
@@ -409,9 +428,16 @@ __global__ void k_pm_w(const double* __restrict__ v, double* __restrict__ w, dou
 }
 
 int pminres_init(const double* b, const double* minv, double* r1, double* r2, double* y, double* w, double* wprev,
-                 double* sol, double* st, double* part, size_t n, double rtol, int maxit, cudaStream_t s) {
-  const int g = red_grid(n);
-  k_pm_init<<<g, kThreads, 0, s>>>(b, minv, r1, r2, y, w, wprev, sol, n, part);
+                 double* sol, double* st, double* part, size_t n, double rtol, int maxit, cudaStream_t s,
+                 const PrecondAdd* pc) {
+  int g = red_grid(n);
+  if (pc) {
+    k_pm_init<false><<<g, kThreads, 0, s>>>(b, minv, r1, r2, y, w, wprev, sol, n, part);
+    g = pc->apply(pc->obj, b, y, part, s);
+    if (g < 0) return (int)cudaErrorLaunchFailure;
+  } else {
+    k_pm_init<true><<<g, kThreads, 0, s>>>(b, minv, r1, r2, y, w, wprev, sol, n, part);
+  }
   k_sum_final<<<1, kThreads, 0, s>>>(part, g, st + KS_BETA_NEXT2);
   k_pm_init_scalar<<<1, 1, 0, s>>>(st, rtol, maxit);
   return (int)cudaGetLastError();
@@ -423,12 +449,20 @@ int pminres_v(double* v, const double* y, const double* st, size_t n, cudaStream
 }
 
 int pminres_after_hv(const double* minv, double* r1, double* r2, double* y, const double* v, double* w,
-                     double* wprev, double* sol, double* st, double* part, size_t n, cudaStream_t s) {
+                     double* wprev, double* sol, double* st, double* part, size_t n, cudaStream_t s,
+                     const PrecondAdd* pc) {
   const int g = red_grid(n);
   k_pm_a<<<g, kThreads, 0, s>>>(y, r1, v, st, n, part);
   k_sum_final<<<1, kThreads, 0, s>>>(part, g, st + KS_ALPHA);
-  k_pm_b<<<g, kThreads, 0, s>>>(minv, r1, r2, y, st, n, part);
-  k_sum_final<<<1, kThreads, 0, s>>>(part, g, st + KS_BETA_NEXT2);
+  int g2 = g;
+  if (pc) {
+    k_pm_b<false><<<g, kThreads, 0, s>>>(minv, r1, r2, y, st, n, part);
+    g2 = pc->apply(pc->obj, r2, y, part, s);
+    if (g2 < 0) return (int)cudaErrorLaunchFailure;
+  } else {
+    k_pm_b<true><<<g, kThreads, 0, s>>>(minv, r1, r2, y, st, n, part);
+  }
+  k_sum_final<<<1, kThreads, 0, s>>>(part, g2, st + KS_BETA_NEXT2);
   k_pm_scalar<<<1, 1, 0, s>>>(st);
   k_pm_w<<<g, kThreads, 0, s>>>(v, w, wprev, sol, st, n);
   return (int)cudaGetLastError();

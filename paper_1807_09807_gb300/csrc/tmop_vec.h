@@ -32,6 +32,8 @@ int dot(const double* a, const double* b, size_t n, double* part, double* out, c
 int energy_final(const double* pf, const double* pm, int np, const double* pf2, int np2, double* outF,
                  double* outMin, cudaStream_t s);
 int step(const double* x, const double* p, double alpha, double* y, size_t n, cudaStream_t s);
+// out = a * b elementwise
+int vec_mul(const double* a, const double* b, double* out, size_t n, cudaStream_t s);
 int minres_init(const double* b, double* v, double* vprev, double* w, double* wprev, double* sol, double* st,
                 double* part, size_t n, double rtol, int maxit, cudaStream_t s);
 // one MINRES step after Av = H v, on rotating buffers: afterwards (v, vprev, Av) -> (Av, v, vprev),
@@ -43,13 +45,22 @@ int minres_after_hv_rot(const double* v, const double* vprev, double* Av, const 
                         double* st, double* part, size_t n, cudaStream_t s, const double* vdot = nullptr,
                         int vdot_np = 0);
 // Preconditioned MINRES (M^-1 = minv, a diagonal): r1, r2, y, v, w, wprev, sol
+// An additive part of the preconditioner beside the diagonal minv: y += C r,
+// with the per-block partials of r . y (after the update) written to part;
+// apply returns the number of partials, or -1 on a launch error.
+struct PrecondAdd {
+  int (*apply)(void* obj, const double* r, double* y, double* part, cudaStream_t s);
+  void* obj;
+};
 int pminres_init(const double* b, const double* minv, double* r1, double* r2, double* y, double* w, double* wprev,
-                 double* sol, double* st, double* part, size_t n, double rtol, int maxit, cudaStream_t s);
+                 double* sol, double* st, double* part, size_t n, double rtol, int maxit, cudaStream_t s,
+                 const PrecondAdd* pc = nullptr);
 // before the product: v = y / beta
 int pminres_v(double* v, const double* y, const double* st, size_t n, cudaStream_t s);
 // after the product y = H v
 int pminres_after_hv(const double* minv, double* r1, double* r2, double* y, const double* v, double* w,
-                     double* wprev, double* sol, double* st, double* part, size_t n, cudaStream_t s);
+                     double* wprev, double* sol, double* st, double* part, size_t n, cudaStream_t s,
+                     const PrecondAdd* pc = nullptr);
 int cg_init(const double* b, double* r, double* d, double* sol, double* st, double* part, size_t n, double rtol,
             int maxit, cudaStream_t s);
 int cg_after_hv(double* sol, double* r, double* d, const double* Hd, double* st, double* part, size_t n,

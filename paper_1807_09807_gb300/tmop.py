@@ -93,6 +93,8 @@ _SIGNATURES = {
     "tmop_selftest_rcbrt": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p], C.c_int),
     "tmop_fma_peak": ([C.c_int, C.c_void_p, C.c_size_t, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p],
                       C.c_int),
+    "tmop_precond_apply": ([C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
+                            C.c_void_p], C.c_int),
     "tmop_destroy": ([C.c_void_p], None),
     "tmop_status_string": ([C.c_int], C.c_char_p),
 }
@@ -388,6 +390,18 @@ class Context:
                 v = CG if v == "cg" else MINRES
             setattr(o, k, v)
         return o
+
+    def precond_apply(self, x, r, precond=2):
+        """(z, alpha): z = M^-1 r for the linearisation at x (tmop_precond_apply)."""
+        import torch
+        _check_vec(x, self.shape, "x")
+        _check_vec(r, self.shape, "r")
+        z = torch.empty_like(r)
+        a = C.c_double(0.0)
+        rc = load().tmop_precond_apply(self._h, _ptr(x), int(precond), _ptr(r), _ptr(z), C.byref(a), _stream())
+        if rc != OK:
+            raise TmopError(rc, "tmop_precond_apply")
+        return z, a.value
 
     def krylov_solve(self, x, b, out=None, **kw):
         import torch

@@ -4,6 +4,8 @@ interpolation identities, the literal metric definitions (numpy.linalg),
 invariances, finite differences, closed forms on affine meshes, the exact
 area identity, the textbook Q_k stiffness matrix and brute-force Newton
 convergence."""
+import itertools
+
 import numpy as np
 import pytest
 
@@ -636,3 +638,75 @@ def test_restricted_movement_scaled_target_and_masking():
     pf = oracle.Problem(dim, order, en, x0.shape[1], fixed, nq, 2, delta=delta, x_init=xi)
     v = rng.standard_normal(x0.shape)
     np.testing.assert_array_equal(pf.hess_apply(xi, v), pf.hess_apply(xi, v * (1 - fixed)))
+
+
+# ---------------------------------------------------------------- two-level preconditioner (reference)
+from oracle import twolevel as otl  # noqa: E402
+
+
+@pytest.mark.parametrize("ns,k", [((3, 4), 3), ((3, 3, 2), 2), ((2, 3), 1)])
+def test_twolevel_interpolation_is_the_product_of_hat_functions(ns, k):
+    """Column v of P is the vertex hat function prod_a max(0, 1 - |n_a X_a - v_a|)
+    evaluated at the lattice points X = (e + z_i) / n (z: GLL nodes): the
+    textbook formula, not the (1 - z, z) construction of the reference."""
+    z, _ = oracle.gauss_lobatto(k + 1)
+    P = otl.interpolation(ns, k)
+    dim = len(ns)
+    coords = []
+    for n in ns:
+        c = np.array([(e + z[i]) / n for e in range(n) for i in range(k)] + [1.0])
+        coords.append(c)
+    grids = np.meshgrid(*coords, indexing="ij")          # [x][y][z] axes
+    pts = np.stack([g.transpose(tuple(reversed(range(dim)))).reshape(-1) for g in grids])  # x fastest
+    vs = list(itertools.product(*[range(1, n) for n in reversed(ns)]))
+    for col, v in enumerate(vs):
+        v = v[::-1]
+        hat = np.ones(pts.shape[1])
+        for a in range(dim):
+            hat *= np.maximum(0.0, 1.0 - np.abs(ns[a] * pts[a] - v[a]))
+        assert np.abs(P[:, col] - hat).max() < 1e-13
+
+
+@pytest.mark.parametrize("ns", [(3, 4), (3, 2, 3)])
+def test_twolevel_coarse_laplacian_is_half_the_order1_mu14_hessian(ns):
+    """K_c equals half the oracle's mu14 Hessian of the order-1 vertex grid
+    (mu14 = |T - I|^2 with W = I is quadratic: its Hessian is twice the
+    reference-space Q1 stiffness), on the interior vertices."""
+    dim = len(ns)
+    x0, en, fixed = mg.structured(dim, 1, ns)
+    N = x0.shape[1]
+    p = oracle.Problem(dim, 1, en, N, fixed, 2, 14)
+    interior = np.where(fixed[0] == 0)[0]
+    H = np.zeros((len(interior), len(interior)))
+    for j, node in enumerate(interior):
+        e = np.zeros_like(x0)
+        e[0, node] = 1.0
+        H[:, j] = p.hess_apply(x0, e)[0, interior]
+    assert np.abs(otl.coarse_laplacian(ns) - 0.5 * H).max() < 1e-13
+
+
+@pytest.mark.parametrize("dim,k", [(2, 1), (2, 3), (3, 2)])
+def test_twolevel_alpha_is_two_for_mu14(dim, k):
+    """For mu14 the Hessian is twice the order-k stiffness, whose energy of a
+    Q1 vertex field (which Q_k contains) is its Q1 energy: alpha = 2 exactly."""
+    ns = (3, 4) if dim == 2 else (2, 3, 3)
+    x0, en, fixed = mg.structured(dim, k, ns)
+    p = oracle.Problem(dim, k, en, x0.shape[1], fixed, k + 2, 14)
+    a = otl.alpha(lambda v: p.hess_apply(x0, v), ns, k, dim)
+    assert abs(a - 2.0) < 1e-12
+
+
+def test_twolevel_apply_is_symmetric_positive_definite():
+    """M^-1 as a matrix (2D, order 2, 3 x 4 elements, a positive diagonal):
+    symmetric and positive definite, as MINRES needs."""
+    ns, k = (3, 4), 2
+    Lf = [k * n + 1 for n in ns]
+    N = Lf[0] * Lf[1]
+    dinv = np.random.default_rng(7).uniform(0.5, 2.0, (2, N))
+    M = np.zeros((2 * N, 2 * N))
+    for j in range(2 * N):
+        e = np.zeros((2, N))
+        e.reshape(-1)[j] = 1.0
+        M[:, j] = otl.apply(e, dinv, ns, k, 1.7).reshape(-1)
+    assert np.abs(M - M.T).max() < 1e-13
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
