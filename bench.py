@@ -677,7 +677,10 @@ def time_to_converged(tm, m, dev, args):
     # plain FP64 (the paper's method as read), the FP32 Hessian-action form, and
     # that form with Jacobi-preconditioned MINRES (the diagonal of the stored
     # Hessians)
-    for name, pf, pc in (("fp64", tm.FP64, 0), ("mixed", tm.FP32_MIXED, 0), ("mixed_jacobi", tm.FP32_MIXED, 1)):
+    # and both forms with the two-level preconditioner (Jacobi plus the exact
+    # coarse correction on the element vertices)
+    for name, pf, pc in (("fp64", tm.FP64, 0), ("mixed", tm.FP32_MIXED, 0), ("mixed_jacobi", tm.FP32_MIXED, 1),
+                         ("fp64_twolevel", tm.FP64, 2), ("mixed_twolevel", tm.FP32_MIXED, 2)):
         c = tm.Context.from_mesh(m, precision=pf)
         xc = torch.tensor(m.x, device=dev)
         F0 = c.energy(xc)[1]
@@ -692,7 +695,7 @@ def time_to_converged(tm, m, dev, args):
                          "grad_rel": rep["grad_norm"] / max(rep["grad_norm0"], 1e-300), "min_detA": rep["min_detA"]}
         c.close()
     F64 = res_all["fp64"]["F"]
-    for k in ("mixed", "mixed_jacobi"):
+    for k in ("mixed", "mixed_jacobi", "fp64_twolevel", "mixed_twolevel"):
         res_all[f"{k}_vs_fp64_F_rel"] = abs(res_all[k]["F"] - F64) / abs(F64)
         res_all[f"speedup_{k}_over_fp64"] = res_all["fp64"]["seconds"] / res_all[k]["seconds"]
     return res_all
