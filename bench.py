@@ -553,6 +553,7 @@ def run_ours(args):
     pa = None
     if rank == 0 and args.pa:
         pa = measure_pa(tm, m, x, v, y, flush, stream, args)
+        pa["deterministic_sums"] = measure_deterministic(tm, m, x, v, y, flush, stream, args)
 
     # ---- time to converged mesh, both precision forms (outside the timed region)
     converge = None
@@ -665,6 +666,36 @@ def measure_pa(tm, m, x, v, y, flush, stream, args):
                     ent["roofline"]["traffic"] = tr["dram_bytes_per_launch"]
         out[name] = ent
         c.close()
+    return out
+
+
+def measure_deterministic(tm, m, x, v, y, flush, stream, args):
+    """Cost of the colour-ordered (bitwise reproducible) nodal sums against
+    the atomic ones: the timed step (FP64 gradient + recomputed Hessian
+    action) and the FP32 stored-Hessian product, same inputs, L2 flushed."""
+    import torch
+    out = {}
+    reps = max(3, min(args.steps, 10))
+    for det in (False, True):
+        c = tm.Context.from_mesh(m)
+        c32 = tm.Context.from_mesh(m, precision=tm.FP32_MIXED)
+        if det:
+            c.set_deterministic(True)
+            c32.set_deterministic(True)
+        g = torch.empty_like(x)
+        c.gradient(x, out=g)
+        c.hess_apply(x, v, out=y)
+        c32.linearize(x)
+        c32.hess_apply_pa(v, out=y)
+        torch.cuda.synchronize()
+        step_ms = _event_ms(lambda: (c.gradient(x, out=g), c.hess_apply(x, v, out=y)), reps, stream, flush)
+        pa_ms = _event_ms(lambda: c32.hess_apply_pa(v, out=y), reps, stream, flush)
+        out["colours" if det else "atomics"] = {"step_ms": step_ms, "fp32_pa_product_ms": pa_ms}
+        c.close()
+        c32.close()
+    out["step_cost"] = out["colours"]["step_ms"] / out["atomics"]["step_ms"]
+    out["pa_cost"] = out["colours"]["fp32_pa_product_ms"] / out["atomics"]["fp32_pa_product_ms"]
+    out["colours_used"] = 2 ** m.dim
     return out
 
 

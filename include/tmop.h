@@ -289,6 +289,22 @@ int tmop_energy_noalloc(int dim, int order, const int structured[3], const tmop_
  * Invalidates a stored linearisation. Errors: TMOP_ERR_ARG, TMOP_ERR_CUDA. */
 int tmop_set_composite(tmop_ctx* ctx, int metric2, const double* W2, const double* eta2);
 
+/* Deterministic sums (on = 1) or atomics (on = 0, the default). The nodal
+ * outputs -- gradient (Section 3.4, summed over the elements that contain
+ * node i), Hessian actions, the stored-Hessian product, the Jacobi
+ * diagonal, the restricted-movement terms -- are sums of element
+ * contributions. By default every element adds with FP64 atomics, whose
+ * order (and so the last bits) varies from run to run. With on = 1 the
+ * elements are split into colours whose elements share no node (the 2^dim
+ * parity classes of a structured grid; a greedy colouring otherwise, at most
+ * 64 colours) and launched one colour after another in a fixed order: each
+ * node then receives at most one add per launch, so the order of every
+ * node's sum is fixed, and every output -- and every Newton and Krylov
+ * iterate -- is the same bit for bit on every run with the same launch
+ * shapes. Costs one launch per colour per operator application. Errors:
+ * TMOP_ERR_ARG (more than 64 colours), TMOP_ERR_CUDA. */
+int tmop_set_deterministic(tmop_ctx* ctx, int on);
+
 /* Restricted node movement (Section 4.3.1, eq. (4.2)): every call then
  * evaluates F + sum_E int_{E_t} delta |x - x_init|^2 dx_t (weights w_q det W),
  * with the matching gradient and Hessian-action terms (FP64, whatever the

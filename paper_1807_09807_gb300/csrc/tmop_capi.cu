@@ -201,6 +201,12 @@ struct tmop_ctx {
   CoarseSpace* coarse = nullptr;
   double* d_coarse_w = nullptr;  // [dim][coarse vertices], the smoothest coarse mode
   double coarse_alpha = 0.0;     // Rayleigh quotient of the last linearisation (0: coarse part off)
+  // deterministic scatter: element colours (no two elements of a colour share
+  // a node), launched one after another in colour order
+  bool det = false;
+  int ncolour = 0;
+  int32_t* d_colour = nullptr;   // the elements of every colour, concatenated
+  std::vector<int> colour_off, colour_cnt;
   cudaStream_t cap = nullptr; // internal stream for capturing Krylov iterations into a graph
   cudaEvent_t ev = nullptr;   // orders the internal stream after / before the caller's stream
 };
@@ -265,14 +271,29 @@ int launch_op(tmop_ctx* c, int op, const double* x, const double* v, double* y, 
   if (c->pa_compact && op == OP_LINEARIZE) kop = OP_LINEARIZE_C;
   if (c->pa_compact && op == OP_HESS_PA) kop = OP_HESS_PA_C;
   p.vdot = kop == OP_HESS_PA_C ? vdot : nullptr;
-  if (c->ent[kop]->launch(p, c->grid[kop], s) != 0) return TMOP_ERR_CUDA;
+  const bool scatter = op == OP_GRADIENT || op == OP_HESS || op == OP_HESS_PA;
+  // deterministic scatter: one launch per colour, in colour order
+  const int passes = (c->det && scatter) ? c->ncolour : 1;
+  for (int k = 0; k < passes; ++k) {
+    if (c->det && scatter) {
+      p.elist = c->d_colour + c->colour_off[k];
+      p.ecount = c->colour_cnt[k];
+    }
+    if (c->ent[kop]->launch(p, c->grid[kop], s) != 0) return TMOP_ERR_CUDA;
+  }
   if (c->delta != 0.0 && op != OP_ENERGY && op != OP_LINEARIZE) {
     // restricted movement (eq. (4.2)): its gradient (from x) or Hessian action (from v)
     MassParams mp = mass_params(c);
     mp.x = x;
     mp.v = v;
     mp.y = y;
-    if (c->mass[op == OP_GRADIENT ? 1 : 2](mp, c->mass_grid, s) != 0) return TMOP_ERR_CUDA;
+    for (int k = 0; k < passes; ++k) {
+      if (c->det) {
+        mp.elist = c->d_colour + c->colour_off[k];
+        mp.ecount = c->colour_cnt[k];
+      }
+      if (c->mass[op == OP_GRADIENT ? 1 : 2](mp, c->mass_grid, s) != 0) return TMOP_ERR_CUDA;
+    }
   }
   return TMOP_OK;
 }
@@ -394,7 +415,13 @@ int hessian_diagonal(tmop_ctx* c, bool inverse, cudaStream_t s) {
   dp.compact = c->pa_compact ? 1 : 0;
   dp.identity = b.wkind == WK_IDENTITY ? 1 : 0;
   memcpy(dp.Winv, b.Winv, sizeof(dp.Winv));
-  if (f(dp, diag_grid(c->nelem), s) != 0) return TMOP_ERR_CUDA;
+  for (int k = 0; k < (c->det ? c->ncolour : 1); ++k) {
+    if (c->det) {
+      dp.elist = c->d_colour + c->colour_off[k];
+      dp.ecount = c->colour_cnt[k];
+    }
+    if (f(dp, diag_grid(c->nelem), s) != 0) return TMOP_ERR_CUDA;
+  }
   if (diag_finish(c->d_diag, b.fixed, c->ndof, s) != 0) return TMOP_ERR_CUDA;
   if (inverse) {
     double rms2;
@@ -494,7 +521,7 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
   // contribution it does not see)
   double* vdot = nullptr;
   int vdot_np = 0;
-  if (!cg && !minv && hop == OP_HESS_PA && c->pa_compact && c->delta == 0.0) {
+  if (!cg && !minv && hop == OP_HESS_PA && c->pa_compact && c->delta == 0.0 && !c->det) {
     vdot_np = c->grid[OP_HESS_PA_C] * c->ent[OP_HESS_PA_C]->warps;
     if (!c->d_vdot) CUDA_TRY(cudaMalloc(&c->d_vdot, sizeof(double) * vdot_np));
     vdot = c->d_vdot;
@@ -667,6 +694,7 @@ void tmop_destroy(tmop_ctx* c) {
   cudaFree(c->d_x_init);
   cudaFree(c->d_diag);
   cudaFree(c->d_vdot);
+  cudaFree(c->d_colour);
   coarse_destroy(c->coarse);
   cudaFree(c->d_coarse_w);
   cudaFreeHost(c->h_res);
@@ -872,6 +900,72 @@ int tmop_set_composite(tmop_ctx* c, int metric2, const double* W2, const double*
   c->base.detW2 = det;
   c->base.eta2 = eta2 ? c->d_eta2 : nullptr;
   c->pa_valid = false;
+  return TMOP_OK;
+}
+
+int tmop_set_deterministic(tmop_ctx* c, int on) {
+  if (!c) return TMOP_ERR_ARG;
+  if (!on) {
+    c->det = false;
+    return TMOP_OK;
+  }
+  if (c->d_colour) {
+    c->det = true;
+    return TMOP_OK;
+  }
+  const int ne = c->nelem, d = c->dim;
+  std::vector<int> colour(ne, 0);
+  int ncol = 0;
+  if (c->base.sx > 0) {
+    // structured grid: the parity of the element index along every axis;
+    // elements of equal parities are at least one element apart
+    const int sx = c->base.sx, sy = c->base.sy;
+    for (int e = 0; e < ne; ++e) {
+      const int ex = e % sx, ey = (e / sx) % sy, ez = e / (sx * sy);
+      colour[e] = (ex & 1) | ((ey & 1) << 1) | (d == 3 ? ((ez & 1) << 2) : 0);
+    }
+    ncol = 1 << d;
+  } else {
+    // greedy: each element, in order, takes the smallest colour no element
+    // sharing one of its nodes has taken
+    const int nd = d == 2 ? c->n * c->n : c->n * c->n * c->n;
+    std::vector<int32_t> en((size_t)ne * nd);
+    if (cudaMemcpy(en.data(), c->d_elem_nodes, sizeof(int32_t) * en.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return TMOP_ERR_CUDA;
+    std::vector<int> start(c->nnode + 1, 0), list((size_t)ne * nd);
+    for (size_t i = 0; i < en.size(); ++i) start[en[i] + 1]++;
+    for (int i = 0; i < c->nnode; ++i) start[i + 1] += start[i];
+    std::vector<int> fill(start.begin(), start.end() - 1);
+    for (int e = 0; e < ne; ++e)
+      for (int t = 0; t < nd; ++t) list[fill[en[(size_t)e * nd + t]]++] = e;
+    std::vector<int> seen(64, -1);
+    for (int e = 0; e < ne; ++e) {
+      for (int t = 0; t < nd; ++t) {
+        const int g = en[(size_t)e * nd + t];
+        for (int j = start[g]; j < start[g + 1]; ++j)
+          if (list[j] < e) seen[colour[list[j]]] = e;
+      }
+      int k = 0;
+      while (k < 64 && seen[k] == e) ++k;
+      if (k == 64) return TMOP_ERR_ARG;  // more than 64 colours: not a mesh this library targets
+      colour[e] = k;
+      if (k + 1 > ncol) ncol = k + 1;
+    }
+  }
+  std::vector<int32_t> order;
+  order.reserve(ne);
+  c->colour_off.assign(ncol, 0);
+  c->colour_cnt.assign(ncol, 0);
+  for (int k = 0; k < ncol; ++k) {
+    c->colour_off[k] = (int)order.size();
+    for (int e = 0; e < ne; ++e)
+      if (colour[e] == k) order.push_back(e);
+    c->colour_cnt[k] = (int)order.size() - c->colour_off[k];
+  }
+  CUDA_TRY(cudaMalloc(&c->d_colour, sizeof(int32_t) * order.size()));
+  CUDA_TRY(cudaMemcpy(c->d_colour, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice));
+  c->ncolour = ncol;
+  c->det = true;
   return TMOP_OK;
 }
 

@@ -134,7 +134,9 @@ __global__ void __launch_bounds__(kDiagWarps * 32) diag_kernel(const DiagParams 
   double *r = wr[warp], *U = wu[warp], *V = wv[warp], *Y = wy[warp];
   const R* H = static_cast<const R*>(p.pa);
   NodeMap<N> nodes(p.elem_nodes, p.sx, p.sy);
-  for (int e = blockIdx.x * kDiagWarps + warp; e < p.nelem; e += gridDim.x * kDiagWarps) {
+  const int ecount = p.elist ? p.ecount : p.nelem;
+  for (int ei = blockIdx.x * kDiagWarps + warp; ei < ecount; ei += gridDim.x * kDiagWarps) {
+    const int e = p.elist ? __ldg(p.elist + ei) : ei;
     nodes.element(e, NDOF);
     const R* He = H + (size_t)e * p.pa_stride;
     for (int a = 0; a < DIM; ++a) {

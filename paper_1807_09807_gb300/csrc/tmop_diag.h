@@ -20,6 +20,8 @@ struct DiagParams {
   int compact;                // pa holds 3D compact records (T, scaled partials of mu)
   int identity;               // W = I (else the constant Winv)
   double Winv[9];
+  const int32_t* elist;       // one colour's elements (one add per node and launch), or null: all
+  int ecount;
 };
 
 typedef int (*diag_launch_fn)(const DiagParams& p, int grid, void* stream);

@@ -138,7 +138,9 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
   static_assert(OP != OP_HESS_PA_C, "OP_HESS_PA_C runs in pac_kernel");
   static_assert(OP != OP_LINEARIZE_C || D == 3, "compact records are 3D");
   NodeMap<N> nodes(p.elem_nodes, p.sx, p.sy);
-  for (int e = blockIdx.x * WARPS + warp; e < p.nelem; e += nwarps_total) {
+  const int ecount = p.elist ? p.ecount : p.nelem;
+  for (int ei = blockIdx.x * WARPS + warp; ei < ecount; ei += nwarps_total) {
+    const int e = p.elist ? __ldg(p.elist + ei) : ei;
     nodes.element(e, NDOF);
     // Partially assembled product: the stored values of this lane's first
     // point are loaded now, so their latency overlaps the gather and the
@@ -480,6 +482,9 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
         for (int c = 0; c < D; ++c) {
           const size_t dof = (size_t)c * p.nnode + g;
           if (p.fixed && __ldg(p.fixed + dof)) continue;
+          // (one colour per launch in the deterministic mode: no other
+          // element of the launch adds to this node, so each node gets one
+          // add per launch, in colour order)
           atomicAdd(p.y + dof, to_f64(P0[c * NDOF + t]));
         }
       }

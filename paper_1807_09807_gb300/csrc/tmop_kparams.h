@@ -38,6 +38,13 @@ struct KParams {
   double* elem_min;               // [nelem] per-element min det A, or null
   void* pa;                       // [nelem][pa_stride] packed Hessians [DD(DD+1)/2][Q] (float or double)
   double* vdot;                   // product from compact records: per-warp partials of v . (H v), or null
+  // Deterministic sums: when elist is set, the launch runs only the ecount
+  // elements listed there, which share no node (one colour of the mesh), so
+  // every node receives at most one (atomic) add per launch; the host
+  // launches the colours one after another in a fixed order, which fixes the
+  // order of every node's sum.
+  const int32_t* elist;
+  int ecount;
   int pa_stride;                  // elements per element block, padded to 16 bytes
   double B[kMaxQ * kMaxN];              // B[q][i] = phi_i(xi_q)
   double G[kMaxQ * kMaxN];              // G[q][i] = phi_i'(xi_q)

@@ -145,7 +145,9 @@ __global__ void __launch_bounds__(kMassWarps * 32) mass_kernel(const MassParams 
   double* P1 = buf[warp][1];
   double acc = 0.0;
   NodeMap<N> nodes(p.elem_nodes, p.sx, p.sy);
-  for (int e = blockIdx.x * kMassWarps + warp; e < p.nelem; e += gridDim.x * kMassWarps) {
+  const int ecount = p.elist ? p.ecount : p.nelem;
+  for (int ei = blockIdx.x * kMassWarps + warp; ei < ecount; ei += gridDim.x * kMassWarps) {
+    const int e = p.elist ? __ldg(p.elist + ei) : ei;
     nodes.element(e, NDOF);
     for (int t = lane; t < NDOF; t += 32) {
       const int g = nodes(t);

@@ -20,6 +20,8 @@ struct MassParams {
   double delta;
   double detW;                // constant det W
   const double* detW_qp;      // [nelem][Q] per-point det W, or null
+  const int32_t* elist;       // one colour's elements (one add per node and launch), or null: all
+  int ecount;
 };
 
 typedef int (*mass_launch_fn)(const MassParams& p, int grid, void* stream);

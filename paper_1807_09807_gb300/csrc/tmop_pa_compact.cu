@@ -368,12 +368,17 @@ __global__ void __launch_bounds__(kPacWarps * 32, N == 4 ? 2 : 0) pac_kernel(con
   for (int i = 0; i < 9; ++i) Wi[i] = IDENT ? 0.f : f64_to_f32(p.Winv[i]);
   const float* rec = static_cast<const float*>(p.pa);
   const int stride = gridDim.x * kPacWarps;
-  int e = blockIdx.x * kPacWarps + warp;
+  // elements ei = warp slot + k stride: all elements, or one colour's list
+  // (deterministic sums: one add per node and launch, see KParams)
+  const int ecount = p.elist ? p.ecount : p.nelem;
+  auto elem = [&](int i) { return p.elist ? __ldg(p.elist + i) : i; };
+  int ei = blockIdx.x * kPacWarps + warp;
   const int gw = blockIdx.x * kPacWarps + warp;  // this warp's slot of the v . (H v) partials
-  if (e >= p.nelem) {  // whole warps only; nothing below waits on other warps
+  if (ei >= ecount) {  // whole warps only; nothing below waits on other warps
     if (p.vdot && lane == 0) p.vdot[gw] = 0.0;
     return;
   }
+  int e = elem(ei);
 
   NodeMap<N> cur(p.elem_nodes, p.sx, p.sy), nxt(p.elem_nodes, p.sx, p.sy);
   cur.element(e, NDOF);
@@ -387,8 +392,8 @@ __global__ void __launch_bounds__(kPacWarps * 32, N == 4 ? 2 : 0) pac_kernel(con
     // ---- the record block of the next element goes to L2 ahead of its loads
     // (one bulk prefetch: the block is contiguous, 16-byte aligned and padded
     // to a multiple of 16 bytes)
-    if (lane == 0 && e + stride < p.nelem)
-      l2_prefetch(rec + (size_t)(e + stride) * p.pa_stride, (unsigned)(p.pa_stride * sizeof(float)));
+    if (lane == 0 && ei + stride < ecount)
+      l2_prefetch(rec + (size_t)elem(ei + stride) * p.pa_stride, (unsigned)(p.pa_stride * sizeof(float)));
     // ---- v of this element into the stage buffer (fixed dofs read as 0)
     const unsigned fcur = fnext;
 #pragma unroll
@@ -421,8 +426,9 @@ __global__ void __launch_bounds__(kPacWarps * 32, N == 4 ? 2 : 0) pac_kernel(con
       }
     }
     // ---- the next element's loads go out before this element's adjoint and scatter
-    const int en = e + stride;
-    const bool more = en < p.nelem;
+    const int eni = ei + stride;
+    const bool more = eni < ecount;
+    const int en = more ? elem(eni) : 0;
     if (more) {
       nxt.element(en, NDOF);
       fetch_v<N, NT>(p, nxt, lane, v, fnext);
@@ -446,6 +452,7 @@ __global__ void __launch_bounds__(kPacWarps * 32, N == 4 ? 2 : 0) pac_kernel(con
     }
     __syncwarp();
     if (!more) break;
+    ei = eni;
     e = en;
     cur = nxt;
   }

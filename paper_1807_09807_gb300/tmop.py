@@ -95,6 +95,7 @@ _SIGNATURES = {
                       C.c_int),
     "tmop_precond_apply": ([C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                             C.c_void_p], C.c_int),
+    "tmop_set_deterministic": ([C.c_void_p, C.c_int], C.c_int),
     "tmop_destroy": ([C.c_void_p], None),
     "tmop_status_string": ([C.c_int], C.c_char_p),
 }
@@ -390,6 +391,12 @@ class Context:
                 v = CG if v == "cg" else MINRES
             setattr(o, k, v)
         return o
+
+    def set_deterministic(self, on=True):
+        """Colour-ordered nodal sums (bitwise reproducible) instead of atomics."""
+        rc = load().tmop_set_deterministic(self._h, 1 if on else 0)
+        if rc != OK:
+            raise TmopError(rc, "tmop_set_deterministic")
 
     def precond_apply(self, x, r, precond=2):
         """(z, alpha): z = M^-1 r for the linearisation at x (tmop_precond_apply)."""
