@@ -570,7 +570,7 @@ def run_ours(args):
     if args.learned and rank == 0:
         learned = learned_proposal(tm, dev, args)
         learned["curved_boundary"] = learned_proposal(tm, dev, args, "c5curved", "c5curved", measure_step=False,
-                                                      train_meshes=args.train_meshes_curved)
+                                                      train_meshes=args.train_meshes_curved, coarse=True)
 
     if rank == 0:
         line = {
@@ -840,19 +840,22 @@ def mlp_step_roofline(L, net, X, T, reps=20):
                          "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured)"}}
 
 
-def learned_proposal(tm, dev, args, train_preset="c5", apply_preset="c5apply", measure_step=True, train_meshes=None):
+def learned_proposal(tm, dev, args, train_preset="c5", apply_preset="c5apply", measure_step=True, train_meshes=None,
+                     coarse=False):
     """Train the proposal MLP on Newton-converged displacements of seeded
     32x32 order-3 meshes (mu2, jitter 0.15h), then on unseen meshes compare
     plain FP64 Newton from the jittered mesh with the FP32 form started from
     the proposal (with its fallback). Same absolute target |g| <= 1e-12
     |g(x0)| for both. Presets: the unit square (c5 / 128x128 c5apply, the
     optimum is the uniform grid) or the curved top boundary (c5curved, train
-    and apply at 32x32: the optimum moves ~6 h from the mapped lattice)."""
+    and apply at 32x32: the optimum moves ~6 h from the mapped lattice; with
+    coarse, the network works from the coarse stage's mesh: the element-vertex
+    problem solved and interpolated, see learned.coarse_stage)."""
     import torch
     from paper_1807_09807_gb300 import learned as L
     t0 = time.perf_counter()
     train_meshes = args.train_meshes if train_meshes is None else train_meshes
-    ds = L.make_dataset(n_meshes=train_meshes, seed0=1000, chunk=250, preset=train_preset)
+    ds = L.make_dataset(n_meshes=train_meshes, seed0=1000, chunk=250, preset=train_preset, coarse=coarse)
     t_data = time.perf_counter() - t0
     net = L.MLP(L.n_features(3), L.n_targets(3), 256, seed=0)
     t0 = time.perf_counter()
@@ -886,8 +889,18 @@ def learned_proposal(tm, dev, args, train_preset="c5", apply_preset="c5apply", m
         rc_ = c32.newton_solve(xc, max_newton=40, rtol=1e-30, atol=atol)
         torch.cuda.synchronize()
         tc = time.perf_counter() - t0
+        coarse_only = None
+        if coarse:   # the coarse stage alone, no network
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            xk, _ = L.coarse_stage(m, x0, fx)
+            rk = c32.newton_solve(xk, max_newton=40, rtol=1e-30, atol=atol)
+            torch.cuda.synchronize()
+            coarse_only = {"seconds": time.perf_counter() - t0, "status": tm.status_string(rk.status),
+                           "newton": rk.report["iterations"], "krylov": rk.report["krylov_iterations"],
+                           "F": rk.report["F"]}
         t0 = time.perf_counter()
-        prop = L.propose(net, m, c32, x0, fx)
+        prop = L.propose(net, m, c32, x0, fx, coarse=coarse)
         xb = prop.x.clone()
         rb = c32.newton_solve(xb, max_newton=40, rtol=1e-30, atol=atol)
         torch.cuda.synchronize()
@@ -898,7 +911,9 @@ def learned_proposal(tm, dev, args, train_preset="c5", apply_preset="c5apply", m
                            "krylov": ra.report["krylov_iterations"], "F": ra.report["F"]},
             "fp32_plain": {"seconds": tc, "status": tm.status_string(rc_.status), "newton": rc_.report["iterations"],
                            "krylov": rc_.report["krylov_iterations"], "F": rc_.report["F"]},
+            "fp32_coarse_only": coarse_only,
             "fp32_learned": {"seconds": tb, "status": tm.status_string(rb.status), "proposal_used": prop.used,
+                             "proposal_coarse_stage": prop.coarse,
                              "proposal_scale": prop.scale, "F_proposal": prop.F, "newton": rb.report["iterations"],
                              "krylov": rb.report["krylov_iterations"], "F": rb.report["F"],
                              "min_detA": rb.report["min_detA"]},

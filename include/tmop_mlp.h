@@ -56,6 +56,25 @@ int tmop_patch_targets(int order, int nx, int ny, const double* x0, const double
 int tmop_patch_apply(int order, int nx, int ny, const double* x0, const uint8_t* fixed, int ldx, const float* Y,
                      int ldy, double scale, double* x_out, void* stream);
 
+/* Coarse stage of the proposal (not in the paper). The curved-boundary
+ * optimum differs from the mapped lattice by a displacement of the whole
+ * domain's scale that a 3x3-element patch cannot see; the proposal
+ * therefore first solves the TMOP problem of the element-vertex grid (an
+ * order-1 context, Newton of Section 3.4) and interpolates its vertex
+ * displacement to the fine nodes, and the network predicts only the local
+ * residual from there.
+ * tmop_lattice_vertices: xv DEVICE [2][ldv] (vertex (i, j) at j (nx+1) + i)
+ * = the positions x DEVICE [2][ldx] (component stride ldx) of the lattice
+ * nodes (k i, k j) of a 2D order-k grid. */
+int tmop_lattice_vertices(int order, int nx, int ny, const double* x, int ldx, double* xv, int ldv, void* stream);
+
+/* x_out = x_in + P (xv1 - xv0) at the dofs that are not fixed, x_in at the
+ * fixed ones; P interpolates a vertex field bilinearly on each element at
+ * its Gauss-Lobatto lattice nodes. xv0, xv1 DEVICE [2][ldv]; x_in, x_out
+ * DEVICE [2][ldx] (may alias); fixed DEVICE uint8 [2][ldx] or NULL. */
+int tmop_lattice_prolong_add(int order, int nx, int ny, const double* xv0, const double* xv1, int ldv,
+                             const double* x_in, const uint8_t* fixed, int ldx, double* x_out, void* stream);
+
 /* The network: n_in -> n_hidden -> n_hidden -> n_out, ReLU between layers,
  * bfloat16 weights and activations with FP32 accumulation on the
  * fifth-generation tensor cores (tcgen05.mma, accumulators in tensor

@@ -515,6 +515,50 @@ int forward_impl(tmop_mlp* n, const bf16* X, int batch, float* Y, int ldy, cudaS
   return rc;
 }
 
+constexpr int kMaxNLat = 8;
+
+// ---------------------------------------------------------------- coarse stage of the proposal
+// Element vertices of a 2D order-k grid, and the bilinear interpolation of a
+// vertex displacement at the Gauss-Lobatto lattice nodes of every element.
+struct Lattice2 {
+  int k, nx, ny, Nx, Ny, ldx;
+  double z[kMaxNLat];  // GLL nodes on [0,1]
+};
+
+__global__ void k_lattice_vertices(Lattice2 L, const double* __restrict__ x, double* __restrict__ xv, int ldv) {
+  const int nv = (L.nx + 1) * (L.ny + 1);
+  const long long tot = 2LL * nv;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(t / nv), v = (int)(t % nv), i = v % (L.nx + 1), j = v / (L.nx + 1);
+    xv[(size_t)c * ldv + v] = x[(size_t)c * L.ldx + (size_t)(L.k * j) * L.Nx + L.k * i];
+  }
+}
+
+// x_out = x_in + P (xv1 - xv0) at the free dofs, x_in at the fixed ones
+__global__ void k_lattice_prolong(Lattice2 L, const double* __restrict__ xv0, const double* __restrict__ xv1,
+                                  int ldv, const double* x_in, const uint8_t* __restrict__ fixed, double* x_out) {
+  const long long nn = (long long)L.Nx * L.Ny, tot = 2 * nn;
+  const int nvx = L.nx + 1;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(t / nn);
+    const long long node = t % nn;
+    const int gx = (int)(node % L.Nx), gy = (int)(node / L.Nx);
+    const size_t dof = (size_t)c * L.ldx + node;
+    double val = x_in[dof];
+    if (!(fixed && fixed[dof])) {
+      const int ex = min(gx / L.k, L.nx - 1), ey = min(gy / L.k, L.ny - 1);
+      const double zx = L.z[gx - L.k * ex], zy = L.z[gy - L.k * ey];
+      const double* a = xv1 + (size_t)c * ldv;
+      const double* b = xv0 + (size_t)c * ldv;
+      const int v00 = ey * nvx + ex;
+      const double d00 = a[v00] - b[v00], d10 = a[v00 + 1] - b[v00 + 1];
+      const double d01 = a[v00 + nvx] - b[v00 + nvx], d11 = a[v00 + nvx + 1] - b[v00 + nvx + 1];
+      val += (1.0 - zy) * ((1.0 - zx) * d00 + zx * d10) + zy * ((1.0 - zx) * d01 + zx * d11);
+    }
+    x_out[dof] = val;
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -558,6 +602,27 @@ int tmop_patch_apply(int order, int nx, int ny, const double* x0, const uint8_t*
   if (ldx < G.Nx * G.Ny) return TMOP_ERR_ARG;
   const long long tot = 2LL * G.Nx * G.Ny;
   k_apply<<<(int)((tot + 255) / 256), 256, 0, (cudaStream_t)stream>>>(G, fixed, Y, ldy, scale, x_out);
+  return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
+}
+
+int tmop_lattice_vertices(int order, int nx, int ny, const double* x, int ldx, double* xv, int ldv, void* stream) {
+  if (order < 1 || order >= kMaxNLat || nx < 1 || ny < 1 || !x || !xv) return TMOP_ERR_ARG;
+  Lattice2 L{order, nx, ny, order * nx + 1, order * ny + 1, ldx, {0}};
+  if (ldx < L.Nx * L.Ny || ldv < (nx + 1) * (ny + 1)) return TMOP_ERR_ARG;
+  const long long tot = 2LL * (nx + 1) * (ny + 1);
+  k_lattice_vertices<<<(int)((tot + 255) / 256), 256, 0, (cudaStream_t)stream>>>(L, x, xv, ldv);
+  return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
+}
+
+int tmop_lattice_prolong_add(int order, int nx, int ny, const double* xv0, const double* xv1, int ldv,
+                             const double* x_in, const uint8_t* fixed, int ldx, double* x_out, void* stream) {
+  if (order < 1 || order >= kMaxNLat || nx < 1 || ny < 1 || !xv0 || !xv1 || !x_in || !x_out) return TMOP_ERR_ARG;
+  Lattice2 L{order, nx, ny, order * nx + 1, order * ny + 1, ldx, {0}};
+  if (ldx < L.Nx * L.Ny || ldv < (nx + 1) * (ny + 1)) return TMOP_ERR_ARG;
+  double zw[kMaxNLat];
+  tmop::rule_gll(order + 1, L.z, zw);
+  const long long tot = 2LL * L.Nx * L.Ny;
+  k_lattice_prolong<<<(int)((tot + 255) / 256), 256, 0, (cudaStream_t)stream>>>(L, xv0, xv1, ldv, x_in, fixed, x_out);
   return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
 }
 

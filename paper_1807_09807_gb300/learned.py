@@ -14,6 +14,13 @@ calls and marshals arguments):
 3. propose: features of a new mesh -> MLP -> x0 + h * displacement at every
    free owned node (tmop_patch_apply). The proposal is kept only if it is
    valid (min det A > 0) and lowers F; otherwise Newton starts from x0.
+
+With coarse=True (for domains whose optimum is not locally determined, such
+as the curved-boundary workload) every step starts instead from the coarse
+stage: the TMOP problem of the element-vertex grid (order 1) is solved by
+Newton, its vertex displacement interpolated to the fine nodes
+(tmop_lattice_vertices / tmop_lattice_prolong_add), and the network learns
+and predicts only the residual from there.
 """
 from __future__ import annotations
 
@@ -33,6 +40,10 @@ _MLP_SIGS = {
                             C.c_int, C.c_void_p], C.c_int),
     "tmop_patch_apply": ([C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
                           C.c_double, C.c_void_p, C.c_void_p], C.c_int),
+    "tmop_lattice_vertices": ([C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p],
+                              C.c_int),
+    "tmop_lattice_prolong_add": ([C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                  C.c_int, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_mlp_create": ([C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(C.c_void_p)], C.c_int),
     "tmop_mlp_destroy": ([C.c_void_p], None),
     "tmop_mlp_input_ld": ([C.c_void_p], C.c_int),
@@ -170,6 +181,64 @@ def apply(m: mg.Mesh, x0, fixed_dev, Y, out=None, scale: float = 1.0):
     return out
 
 
+def lattice_vertices(m: mg.Mesh, x, ldx: int, xv, ldv: int):
+    _check(lib().tmop_lattice_vertices(m.order, m.nx[0], m.nx[1], _p(x), ldx, _p(xv), ldv, _s()),
+           "tmop_lattice_vertices")
+
+
+def lattice_prolong_add(m: mg.Mesh, xv0, xv1, ldv: int, x_in, fixed_dev, ldx: int, x_out):
+    _check(lib().tmop_lattice_prolong_add(m.order, m.nx[0], m.nx[1], _p(xv0), _p(xv1), ldv, _p(x_in),
+                                          None if fixed_dev is None else _p(fixed_dev), ldx, _p(x_out), _s()),
+           "tmop_lattice_prolong_add")
+
+
+_coarse_ctx = {}
+
+
+def coarse_context(m: mg.Mesh, count: int):
+    """The order-1 TMOP problem of the element vertices of `count` meshes
+    shaped like m (same metric, boundary vertices fixed), one block each."""
+    key = (tuple(m.nx), m.metric, count)
+    if key not in _coarse_ctx:
+        xv, en, fx = mg.structured(m.dim, 1, m.nx)
+        Nv = xv.shape[1]
+        if count == 1:
+            ctx = tm.Context(m.dim, 1, Nv, None, fx, 3, m.metric, structured=list(m.nx), precision=tm.FP64,
+                             nelem=en.shape[0])
+        else:
+            enu = np.concatenate([en + i * Nv for i in range(count)]).astype(np.int32)
+            fxu = np.concatenate([fx] * count, axis=1)
+            ctx = tm.Context(m.dim, 1, Nv * count, enu, fxu, 3, m.metric, precision=tm.FP64)
+        _coarse_ctx[key] = ctx
+    return _coarse_ctx[key]
+
+
+def coarse_stage(m: mg.Mesh, x0, fixed_dev=None, count: int = 1, out=None, max_newton=30, rtol=1e-8):
+    """x0 + P (xv* - xv0) for `count` meshes shaped like m stored back to
+    back in x0 ([2][count * nnode]): the element-vertex grids of all of them
+    solved by Newton as one order-1 problem, each vertex displacement
+    interpolated to its mesh's free nodes. Returns (x, newton result); x is
+    x0 (a copy) when the coarse Newton does not converge."""
+    import torch
+    N, ldx = m.nnode, x0.shape[1]
+    Nv = (m.nx[0] + 1) * (m.nx[1] + 1)
+    ldv = Nv * count
+    xv0 = torch.empty((2, ldv), dtype=torch.float64, device=x0.device)
+    for i in range(count):
+        lattice_vertices(m, x0[:, i * N:], ldx, xv0[:, i * Nv:], ldv)
+    ctx = coarse_context(m, count)
+    xv1 = xv0.clone()
+    r = ctx.newton_solve(xv1, max_newton=max_newton, rtol=rtol)
+    out = torch.empty_like(x0) if out is None else out
+    if r.status != tm.OK:
+        out.copy_(x0)
+        return out, r
+    for i in range(count):
+        fx = None if fixed_dev is None else fixed_dev[:, i * N:]
+        lattice_prolong_add(m, xv0[:, i * Nv:], xv1[:, i * Nv:], ldv, x0[:, i * N:], fx, ldx, out[:, i * N:])
+    return out, r
+
+
 def union_context(meshes, precision=tm.FP32_MIXED):
     """One TMOP problem made of disjoint meshes (unstructured connectivity)."""
     m0 = meshes[0]
@@ -192,11 +261,12 @@ class Dataset:
 
 
 def make_dataset(n_meshes=2000, seed0=1000, nx=32, ldf=256, chunk=250, precision=tm.FP32_MIXED,
-                 preset="c5", max_newton=60, rtol=1e-10) -> Dataset:
+                 preset="c5", max_newton=60, rtol=1e-10, coarse=False) -> Dataset:
     """Newton-converged displacement targets from n_meshes seeded meshes
     (seeds seed0, seed0+1, ...), solved chunk meshes at a time as one
     block-diagonal problem, to |g| <= rtol |g0| of the chunk (far below what
-    a bf16 network resolves)."""
+    a bf16 network resolves). coarse: features and targets are taken from
+    the coarse stage's mesh (coarse_stage) instead of the jittered one."""
     import torch
     t0 = time.perf_counter()
     Xs, Ts, log = [], [], []
@@ -204,6 +274,11 @@ def make_dataset(n_meshes=2000, seed0=1000, nx=32, ldf=256, chunk=250, precision
         ms = [mg.make_mesh(preset, seed0 + i, nx=nx) for i in range(c0, min(c0 + chunk, n_meshes))]
         ctx, xh = union_context(ms, precision)
         x0 = torch.tensor(xh, device="cuda")
+        if coarse:
+            fx = torch.tensor(np.concatenate([m.fixed for m in ms], axis=1), device="cuda")
+            xc, _ = coarse_stage(ms[0], x0, fx, count=len(ms))
+            if ctx.energy(xc)[2] > 0:    # valid everywhere: the base of this chunk
+                x0 = xc
         x1 = x0.clone()
         r = ctx.newton_solve(x1, max_newton=max_newton, rtol=rtol)
         log.append((r.status, r.report["iterations"], r.report["krylov_iterations"]))
@@ -255,23 +330,36 @@ class Proposal:
     F0: float
     F: float
     min_detA: float
-    scale: float = 1.0   # the damping that was kept (0: not used)
+    scale: float = 1.0   # the damping that was kept (0: no network step)
+    coarse: bool = False  # started from the coarse stage
 
 
-def propose(net: MLP, m: mg.Mesh, ctx: tm.Context, x0, fixed_dev, scales=(1.0, 0.5, 0.25)) -> Proposal:
-    """Proposal with fallback: the first of x0 + s h Y (s in scales) with
-    min det A > 0 and F below F(x0) is kept; otherwise Newton starts from x0."""
+def propose(net: MLP, m: mg.Mesh, ctx: tm.Context, x0, fixed_dev, scales=(1.0, 0.5, 0.25),
+            coarse=False) -> Proposal:
+    """Proposal with fallback: the first of b + s h Y (s in scales) with
+    min det A > 0 and F below F(x0) is kept, where b is x0 or, with coarse,
+    the coarse stage's mesh (then b alone is the last candidate); otherwise
+    Newton starts from x0."""
     import torch
     S = m.nelem
     Sp = (S + 63) // 64 * 64
-    X = torch.zeros((Sp, net.ld), dtype=torch.int16, device=x0.device)
-    features(m, x0, net.ld, out=X[:S])
-    Y = net.forward(X)[:S].contiguous()
     _, F0, _ = ctx.energy(x0)
+    base = x0
+    if coarse:
+        xc, rc_ = coarse_stage(m, x0, fixed_dev)
+        if rc_.status == tm.OK:
+            base = xc
+    X = torch.zeros((Sp, net.ld), dtype=torch.int16, device=x0.device)
+    features(m, base, net.ld, out=X[:S])
+    Y = net.forward(X)[:S].contiguous()
     F, md = float("inf"), 0.0
     for sc in scales:
-        xp = apply(m, x0, fixed_dev, Y, scale=sc)
+        xp = apply(m, base, fixed_dev, Y, scale=sc)
         rc, F, md = ctx.energy(xp)
         if rc == tm.OK and md > 0 and F < F0:
-            return Proposal(xp, True, F0, F, md, sc)
+            return Proposal(xp, True, F0, F, md, sc, coarse=base is not x0)
+    if base is not x0:
+        rc, F, md = ctx.energy(base)
+        if rc == tm.OK and md > 0 and F < F0:
+            return Proposal(base.clone(), True, F0, F, md, 0.0, coarse=True)
     return Proposal(x0, False, F0, F, md, 0.0)
