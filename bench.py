@@ -365,6 +365,98 @@ def workload_config(m, args):
             "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU"}
 
 
+def run_sharded(args):
+    """The timed step (gradient + Hessian action) of the workload split into
+    z-slabs over the ranks (paper_1807_09807_gb300/shard.py): each rank runs
+    the element kernels on its slab, then one halo sum (NCCL send/recv of the
+    shared node planes) per operator application. Total work is fixed
+    (strong scaling); value = points of the whole mesh per second of the
+    slowest rank. End to end: each rank uploads its slab's x and v from
+    pinned host memory and downloads its g and y every step."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1807_09807_gb300 import build as cuda_build
+    from paper_1807_09807_gb300 import tmop as tm
+    from paper_1807_09807_gb300.shard import ShardedOperator
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        cuda_build.build()
+    dist.barrier()
+    tm.load()
+    m = make_workload(args.workload)
+    prec = tm.FP64 if args.precision == "fp64" else tm.FP32_MIXED
+    op = ShardedOperator(m, dist, precision=prec)
+    vh_glob = np.random.default_rng(5).standard_normal(m.x.shape) * (1 - m.fixed)
+    x = torch.tensor(op.mesh.x, device=dev)
+    v = torch.tensor(op.part.to_local(vh_glob), device=dev)
+    g, y = torch.empty_like(x), torch.empty_like(x)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        op.gradient(x, out=g)
+        op.hess_apply(x, v, out=y)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            flush.fill_(1.0)
+            evs[k][0].record(stream)
+            step()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    dist.barrier()
+    t_local = sum(a.elapsed_time(b) for a, b in evs) * 1e-3
+    tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    t_dev = float(tt.item())
+    value = m.n_qp * args.steps / t_dev
+    # end to end: the slab's inputs up from pinned host memory, its outputs down
+    xh, vh = x.cpu().pin_memory(), v.cpu().pin_memory()
+    gh, yh = torch.empty_like(xh).pin_memory(), torch.empty_like(xh).pin_memory()
+    e_steps = max(3, min(args.steps, 10))
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e_steps):
+        x.copy_(xh, non_blocking=True)
+        v.copy_(vh, non_blocking=True)
+        step()
+        gh.copy_(g, non_blocking=True)
+        yh.copy_(y, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    te = torch.tensor([e0.elapsed_time(e1) * 1e-3], dtype=torch.float64, device=dev)
+    dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    nbytes = x.numel() * 8
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f64" if prec == tm.FP64 else "f32 (f64 reductions)", "data": "synthetic",
+            "config": dict(workload_config(m, args), parallelism=f"z-slabs x{ws}, halo sum per application"),
+            "clocks": clocks.summary(), "gpu_launches": 2 * args.steps,
+            "e2e": {"value": m.n_qp * e_steps / float(te.item()), "unit": UNIT,
+                    "h2d_bytes_per_step (rank 0)": 2 * nbytes, "d2h_bytes_per_step (rank 0)": 2 * nbytes,
+                    "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": 2 * nbytes},
+            "slabs": {"elements_rank0": op.mesh.nelem, "planes_shared": ws - 1}}), flush=True)
+    op.close()
+    dist.destroy_process_group()
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -954,6 +1046,10 @@ def main():
     ap.add_argument("--train-meshes-curved", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels-only", action="store_true")
+    ap.add_argument("--shard", action="store_true",
+                    help="with N > 1: split the workload's elements into z-slabs, one per rank, with a halo "
+                         "sum of the shared node planes per operator application (strong scaling) instead "
+                         "of N independent replicas")
     ap.add_argument("--profile", choices=["step", "pa", "mlp", "newton"], default="step",
                     help="with --kernels-only: the timed step (gradient + Hessian action), the partially "
                          "assembled Hessian action alone, training steps of the proposal MLP, or one "
@@ -962,6 +1058,8 @@ def main():
     args.warmup = max(args.warmup, 3) if not args.kernels_only else args.warmup
     if args.impl == "reference":
         return run_reference(args)
+    if args.shard:
+        return run_sharded(args)
     return run_ours(args)
 
 

@@ -367,6 +367,19 @@ int tmop_selftest_rcbrt(const double* in, double* out, size_t n, void* stream);
 enum { TMOP_PEAK_FP64 = 0, TMOP_PEAK_FP32 = 1, TMOP_PEAK_FP32X2 = 2 };
 int tmop_fma_peak(int kind, void* scratch, size_t scratch_bytes, double* gflops, double* ms, void* stream);
 
+/* Vector helpers for callers that split a mesh over GPUs (slab sharding:
+ * a halo sum of the node planes two slabs share, and dot products that count
+ * each shared plane once). Not part of the paper's method.
+ * tmop_vec_add: y += b, DEVICE [n] FP64. Asynchronous.
+ * tmop_vec_dot_segments: *out (DEVICE scalar) = sum over c < ncomp, i < count
+ * of a[c stride + first + i] b[c stride + first + i] (FP64, a fixed-order
+ * two-pass reduction); scratch DEVICE, at least 2048 doubles (the block
+ * partials; TMOP_ERR_CAPACITY if scratch_len is smaller than the grid).
+ * Asynchronous. Errors: TMOP_ERR_ARG, TMOP_ERR_CAPACITY, TMOP_ERR_CUDA. */
+int tmop_vec_add(double* y, const double* b, size_t n, void* stream);
+int tmop_vec_dot_segments(const double* a, const double* b, int ncomp, size_t stride, size_t first, size_t count,
+                          double* scratch, size_t scratch_len, double* out, void* stream);
+
 /* Sizes of a context: Q (points per element), ndof = dim * nnode. */
 int tmop_sizes(const tmop_ctx* ctx, int* dim, int* nelem, int* nnode, int* Q);
 

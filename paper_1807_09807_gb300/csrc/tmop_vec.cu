@@ -591,6 +591,48 @@ __global__ void k_selftest_rcbrt(const double* __restrict__ in, double* __restri
 }
 }  // namespace
 
+namespace tmop {
+__global__ void k_add(double* __restrict__ y, const double* __restrict__ b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] += b[i];
+}
+
+// partials of sum_c sum_{i < count} a[c stride + first + i] b[...]
+__global__ void k_dot_seg(const double* __restrict__ a, const double* __restrict__ b, int ncomp, size_t stride,
+                          size_t first, size_t count, double* __restrict__ part) {
+  double s = 0.0;
+  const size_t n = (size_t)ncomp * count;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = (t / count) * stride + first + t % count;
+    s = fma(a[i], b[i], s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+}  // namespace tmop
+
+extern "C" int tmop_vec_add(double* y, const double* b, size_t n, void* stream) {
+  using namespace tmop;
+  if (n == 0) return TMOP_OK;
+  if (!y || !b) return TMOP_ERR_ARG;
+  k_add<<<red_grid(n), kThreads, 0, (cudaStream_t)stream>>>(y, b, n);
+  return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
+}
+
+extern "C" int tmop_vec_dot_segments(const double* a, const double* b, int ncomp, size_t stride, size_t first,
+                                     size_t count, double* scratch, size_t scratch_len, double* out, void* stream) {
+  using namespace tmop;
+  if (!a || !b || !scratch || !out || ncomp < 1 || first + count > stride) return TMOP_ERR_ARG;
+  const size_t n = (size_t)ncomp * count;
+  const int g = red_grid(n > 0 ? n : 1);
+  if (scratch_len < (size_t)g) return TMOP_ERR_CAPACITY;
+  cudaStream_t s = (cudaStream_t)stream;
+  k_dot_seg<<<g, kThreads, 0, s>>>(a, b, ncomp, stride, first, count, scratch);
+  k_sum_final<<<1, kThreads, 0, s>>>(scratch, g, out);
+  return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
+}
+
 extern "C" int tmop_selftest_rcbrt(const double* in, double* out, size_t n, void* stream) {
   if (n == 0) return TMOP_OK;
   if (!in || !out) return TMOP_ERR_ARG;

@@ -96,6 +96,9 @@ _SIGNATURES = {
     "tmop_precond_apply": ([C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                             C.c_void_p], C.c_int),
     "tmop_set_deterministic": ([C.c_void_p, C.c_int], C.c_int),
+    "tmop_vec_add": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p], C.c_int),
+    "tmop_vec_dot_segments": ([C.c_void_p, C.c_void_p, C.c_int, C.c_size_t, C.c_size_t, C.c_size_t, C.c_void_p,
+                               C.c_size_t, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_destroy": ([C.c_void_p], None),
     "tmop_status_string": ([C.c_int], C.c_char_p),
 }
@@ -159,6 +162,25 @@ def selftest_rcbrt(x):
     rc = load().tmop_selftest_rcbrt(_ptr(x), _ptr(out), x.numel(), _stream())
     if rc != OK:
         raise TmopError(rc, "tmop_selftest_rcbrt")
+    return out
+
+
+def vec_add(y, b):
+    """y += b (contiguous float64 CUDA tensors of equal size), tmop_vec_add."""
+    if y.numel() != b.numel() or not (y.is_contiguous() and b.is_contiguous()):
+        raise TypeError("y and b must be contiguous and of equal size")
+    rc = load().tmop_vec_add(_ptr(y), _ptr(b), y.numel(), _stream())
+    if rc != OK:
+        raise TmopError(rc, "tmop_vec_add")
+
+
+def vec_dot_segments(a, b, first, count, scratch, out):
+    """out (0-d float64 CUDA tensor) = sum over rows c of a[c, first:first+count] . b[...]
+    for [ncomp][stride] tensors, tmop_vec_dot_segments."""
+    rc = load().tmop_vec_dot_segments(_ptr(a), _ptr(b), a.shape[0], a.shape[1], first, count, _ptr(scratch),
+                                      scratch.numel(), _ptr(out), _stream())
+    if rc != OK:
+        raise TmopError(rc, "tmop_vec_dot_segments")
     return out
 
 

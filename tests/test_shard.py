@@ -1,0 +1,127 @@
+"""Slab sharding (paper_1807_09807_gb300/shard.py) on CPU ranks over gloo:
+every rank evaluates its own slab of elements (here with the FP64 oracle,
+standing in for the rank's GPU kernels) and the partition's collectives --
+the halo sum of the shared node planes, the all-reduced energy and minimum,
+the owned-node dot product -- must reproduce the single-rank results."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist          # noqa: E402
+import torch.multiprocessing as mp        # noqa: E402
+
+from paper_1807_09807_gb300 import meshgen as mg   # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+CASES = {"3d": ("c4", dict(nx=(3, 2, 5))), "2d": ("c2", dict(nx=(4, 7)))}
+
+
+def _rank(rank, ws, port, case, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    import oracle
+    from paper_1807_09807_gb300.shard import SlabPartition
+    name, kw = CASES[case]
+    m = mg.make_mesh(name, 3, **kw)
+    part = SlabPartition(m.dim, m.order, m.nx, ws, rank)
+    lm = part.local_mesh(m)
+    orc = oracle.Problem(lm.dim, lm.order, lm.elem_nodes, lm.nnode, lm.fixed, lm.nq, lm.metric)
+    v = np.random.default_rng(11).standard_normal(m.x.shape) * (1 - m.fixed)
+    _, F, md = orc.energy(lm.x)
+    F, md = part.energy(F, md, dist)
+    add = lambda dst, src: dst.add_(src)          # noqa: E731  (CPU stand-ins for the library's kernels)
+    seg = lambda a, b, i, n: (a[:, i:i + n] * b[:, i:i + n]).sum()  # noqa: E731
+    g = part.halo_sum(torch.tensor(orc.gradient(lm.x)), dist, add)
+    hv = part.halo_sum(torch.tensor(orc.hess_apply(lm.x, part.to_local(v))), dist, add)
+    gg = part.dot(g, g, dist, seg)
+    vhv = part.dot(torch.tensor(part.to_local(v)), hv, dist, seg)
+    out.put((rank, F, md, g.numpy(), hv.numpy(), gg, vhv))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("case,ws", [("3d", 2), ("3d", 3), ("2d", 2)])
+def test_slab_sharding_reproduces_the_single_rank_operator(case, ws):
+    import oracle
+    from paper_1807_09807_gb300.shard import SlabPartition
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank, args=(r, ws, port, case, q)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=300) for _ in range(ws)), key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    name, kw = CASES[case]
+    m = mg.make_mesh(name, 3, **kw)
+    orc = oracle.Problem(m.dim, m.order, m.elem_nodes, m.nnode, m.fixed, m.nq, m.metric)
+    v = np.random.default_rng(11).standard_normal(m.x.shape) * (1 - m.fixed)
+    _, F, md = orc.energy(m.x)
+    g, hv = orc.gradient(m.x), orc.hess_apply(m.x, v)
+    covered = np.zeros(m.nnode, dtype=int)
+    for rank, Fr, mdr, gr, hvr, ggr, vhvr in res:
+        part = SlabPartition(m.dim, m.order, m.nx, ws, rank)
+        assert abs(Fr - F) <= 1e-13 * F and mdr == md
+        np.testing.assert_allclose(gr, part.to_local(g), rtol=0, atol=1e-13 * np.abs(g).max())
+        np.testing.assert_allclose(hvr, part.to_local(hv), rtol=0, atol=1e-13 * np.abs(hv).max())
+        assert abs(ggr - float((g * g).sum())) <= 1e-12 * float((g * g).sum())
+        assert abs(vhvr - float((v * hv).sum())) <= 1e-12 * abs(float((v * hv).sum()))
+        covered[part.global_nodes()] += part.owned().astype(int)
+    assert np.all(covered == 1)          # every node counted once in the dot products
+
+
+def test_slab_partition_shapes():
+    from paper_1807_09807_gb300.shard import SlabPartition
+    parts = [SlabPartition(3, 3, (4, 4, 10), 4, r) for r in range(4)]
+    assert [p.e1 - p.e0 for p in parts] == [3, 3, 2, 2]
+    assert parts[0].g0 == 0 and parts[-1].g1 == 30 and all(a.g1 == b.g0 for a, b in zip(parts, parts[1:]))
+    assert [p.lo for p in parts] == [False, True, True, True] and [p.hi for p in parts] == [True, True, True, False]
+    with pytest.raises(ValueError):
+        SlabPartition(3, 3, (4, 4, 2), 3, 0)
+
+
+@pytest.mark.gpu
+def test_sharded_operator_single_rank_gpu_and_vector_helpers():
+    """On one GPU (a one-rank NCCL group) the sharded operator is the
+    context's own operator, and the library's plane add and segment dot
+    (tmop_vec_add, tmop_vec_dot_segments) match their definitions."""
+    from paper_1807_09807_gb300 import build as cuda_build
+    cuda_build.build()
+    from paper_1807_09807_gb300 import tmop as tm
+    from paper_1807_09807_gb300.shard import ShardedOperator
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(_free_port()), RANK="0", WORLD_SIZE="1")
+    dist.init_process_group("nccl", rank=0, world_size=1)
+    try:
+        m = mg.make_mesh("c4", 2, nx=(3, 3, 4))
+        op = ShardedOperator(m, dist)
+        ctx = tm.Context.from_mesh(m)
+        x = torch.tensor(m.x, device="cuda")
+        v = torch.tensor(np.random.default_rng(2).standard_normal(m.x.shape), device="cuda")
+        assert op.energy(x) == ctx.energy(x)[1:]
+        g1, g2 = op.gradient(x).cpu().numpy(), ctx.gradient(x).cpu().numpy()
+        assert np.abs(g1 - g2).max() <= 1e-13 * np.abs(g2).max()
+        y1, y2 = op.hess_apply(x, v).cpu().numpy(), ctx.hess_apply(x, v).cpu().numpy()
+        assert np.abs(y1 - y2).max() <= 1e-13 * np.abs(y2).max()
+        a = torch.tensor(np.random.default_rng(3).standard_normal((3, 1000)), device="cuda")
+        b = torch.tensor(np.random.default_rng(4).standard_normal((3, 1000)), device="cuda")
+        out = torch.empty((), dtype=torch.float64, device="cuda")
+        tm.vec_dot_segments(a, b, 17, 900, torch.empty(2048, dtype=torch.float64, device="cuda"), out)
+        ref = float((a[:, 17:917] * b[:, 17:917]).sum().item())
+        assert abs(out.item() - ref) <= 1e-13 * abs(ref) + 1e-12
+        y = a.clone()
+        tm.vec_add(y[1], b[1].contiguous())
+        assert torch.equal(y[1], a[1] + b[1]) and torch.equal(y[0], a[0])
+        op.close()
+    finally:
+        dist.destroy_process_group()
