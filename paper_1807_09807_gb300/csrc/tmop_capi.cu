@@ -733,9 +733,11 @@ int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metr
   // structured grid: sizes must match, and elem_nodes (if given) must agree
   const int* sd = mesh->structured;
   const bool structured = sd[0] > 0;
+  // 2D: structured[2] > 1 stacks that many equal grids (nodes grid after grid)
+  const int stack = (d == 2 && structured && sd[2] > 1) ? sd[2] : 1;
   if (structured) {
-    long long ne = (long long)sd[0] * sd[1] * (d == 3 ? sd[2] : 1);
-    long long nn = (long long)(order * sd[0] + 1) * (order * sd[1] + 1) * (d == 3 ? (order * sd[2] + 1) : 1);
+    long long ne = (long long)sd[0] * sd[1] * (d == 3 ? sd[2] : stack);
+    long long nn = (long long)(order * sd[0] + 1) * (order * sd[1] + 1) * (d == 3 ? (order * sd[2] + 1) : stack);
     if (sd[1] < 1 || (d == 3 && sd[2] < 1) || ne != mesh->nelem || nn != mesh->nnode) return TMOP_ERR_ARG;
   } else if (!mesh->elem_nodes) {
     return TMOP_ERR_ARG;
@@ -747,10 +749,11 @@ int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metr
     if (structured) {
       const int Nx = order * sd[0] + 1, Ny = order * sd[1] + 1;
       for (int e = 0; e < mesh->nelem; ++e) {
-        const int ex = e % sd[0], ey = (e / sd[0]) % sd[1], ez = d == 3 ? e / (sd[0] * sd[1]) : 0;
+        const int ex = e % sd[0], ey = (e / sd[0]) % sd[1], ez = e / (sd[0] * sd[1]);
         for (int t = 0; t < ndof_e; ++t) {
           const int i = t % n, j = (t / n) % n, l = d == 3 ? t / (n * n) : 0;
-          const int g = ((ez * order + l) * Ny + ey * order + j) * Nx + ex * order + i;
+          const int g = (d == 3 ? ((ez * order + l) * Ny + ey * order + j) : (ez * Ny + ey * order + j)) * Nx +
+                        ex * order + i;
           if (mesh->elem_nodes[(size_t)e * ndof_e + t] != g) return TMOP_ERR_ARG;
         }
       }
@@ -765,7 +768,8 @@ int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metr
   KParams& p = c->base;
   memset(&p, 0, sizeof(p));
   p.dim = d; p.nelem = mesh->nelem; p.nnode = mesh->nnode; p.metric = metric_id;
-  p.sx = structured ? sd[0] : 0; p.sy = structured ? sd[1] : 0; p.sz = structured && d == 3 ? sd[2] : 0;
+  p.sx = structured ? sd[0] : 0; p.sy = structured ? sd[1] : 0;
+  p.sz = structured ? (d == 3 ? sd[2] : (stack > 1 ? stack : 0)) : 0;
 
   // tables
   double qx[kMaxQ], qw[kMaxQ], z[kMaxN], zw[kMaxN];
@@ -852,6 +856,7 @@ int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metr
       }
     c->boundary_fixed = ok;
     for (int a = 0; a < d; ++a) c->grid_n[a] = sd[a];
+    if (d == 2) c->grid_n[2] = stack;   // the coarse space of a 2D stack: one vertex grid per grid
   }
   // launch shapes and workspace
   for (int op = 0; op < OP_COUNT && rc == TMOP_OK; ++op) {

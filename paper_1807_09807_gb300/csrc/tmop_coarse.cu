@@ -200,7 +200,7 @@ Wts weights(const CoarseSpace* cs) {
 void view(const CoarseSpace* cs, const int len[3], int a, size_t* outer, size_t* inner) {
   size_t in = 1, out = (size_t)cs->dim;
   for (int b = 0; b < a; ++b) in *= (size_t)len[b];
-  for (int b = a + 1; b < cs->dim; ++b) out *= (size_t)len[b];
+  for (int b = a + 1; b < 3; ++b) out *= (size_t)len[b];   // (a 2D stack's grids count as outer)
   *outer = out;
   *inner = in;
 }
@@ -256,7 +256,7 @@ R* solve_coarse(CoarseSpace* cs, R* v, cudaStream_t s) {
       const int a2 = cs->dim == 3 ? 2 : 1;
       k_eig_scale<R><<<grid_for(cs->ncoarse * cs->dim), kThr, 0, s>>>(
           cur, tab_lam<R>(cs, 0), tab_mu<R>(cs, 0), tab_lam<R>(cs, 1), tab_mu<R>(cs, 1), tab_lam<R>(cs, a2),
-          tab_mu<R>(cs, a2), cs->dim, cs->Lc[0], cs->Lc[1], cs->dim == 3 ? cs->Lc[2] : 1, 1.0 / cs->alpha);
+          tab_mu<R>(cs, a2), cs->dim, cs->Lc[0], cs->Lc[1], cs->Lc[2], 1.0 / cs->alpha);
     }
   }
   return cur;
@@ -270,7 +270,6 @@ R* prolong_upper(CoarseSpace* cs, R* cur, int len[3], cudaStream_t s) {
   R* b[2] = {static_cast<R*>(cs->buf[0]), static_cast<R*>(cs->buf[1])};
   auto other = [&](R* p) { return p == b[0] ? b[1] : b[0]; };
   for (int a = 0; a < 3; ++a) len[a] = cs->Lc[a];
-  if (cs->dim == 2) len[2] = 1;
   for (int a = cs->dim - 1; a >= 1; --a) {
     size_t outer, inner;
     view(cs, len, a, &outer, &inner);
@@ -308,10 +307,12 @@ CoarseSpace* coarse_create(int dim, int k, const int n[3], const double* z, bool
   cs->nfine = 1;
   cs->ncoarse = 1;
   for (int a = 0; a < 3; ++a) {
-    cs->n[a] = a < dim ? n[a] : 1;
+    // 2D: n[2] > 1 is a stack of that many grids, with no transfer between them
+    const int stack = (dim == 2 && a == 2 && n[2] > 1) ? n[2] : 1;
+    cs->n[a] = a < dim ? n[a] : stack;
     if (a < dim && cs->n[a] < 2) { delete cs; return nullptr; }
-    cs->Lf[a] = a < dim ? k * cs->n[a] + 1 : 1;
-    cs->Lc[a] = a < dim ? cs->n[a] - 1 : 1;
+    cs->Lf[a] = a < dim ? k * cs->n[a] + 1 : stack;
+    cs->Lc[a] = a < dim ? cs->n[a] - 1 : stack;
     cs->nfine *= (size_t)cs->Lf[a];
     cs->ncoarse *= (size_t)cs->Lc[a];
   }
@@ -384,7 +385,7 @@ void coarse_set_alpha(CoarseSpace* cs, double alpha) {
 
 int coarse_mode0(CoarseSpace* cs, double* w, double* lambda0, cudaStream_t s) {
   if (!cs || !w) return (int)cudaErrorInvalidValue;
-  const int L0 = cs->Lc[0], L1 = cs->Lc[1], L2 = cs->dim == 3 ? cs->Lc[2] : 1;
+  const int L0 = cs->Lc[0], L1 = cs->Lc[1], L2 = cs->Lc[2];
   const size_t work = cs->ncoarse * cs->dim;
   if (cs->fp32)
     k_mode0<float><<<grid_for(work), kThr, 0, s>>>(w, tab_S<float>(cs, 0), tab_S<float>(cs, 1),
@@ -402,7 +403,8 @@ int coarse_mode0(CoarseSpace* cs, double* w, double* lambda0, cudaStream_t s) {
       }
       lam += t;
     }
-    *lambda0 = lam;
+    // w^t K_c w per component: every grid of a 2D stack holds a unit mode
+    *lambda0 = lam * (cs->dim == 2 ? cs->Lc[2] : 1);
   }
   return (int)cudaGetLastError();
 }

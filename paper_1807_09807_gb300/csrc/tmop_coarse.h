@@ -20,9 +20,11 @@ namespace tmop {
 struct CoarseSpace;
 
 // Build the transfer and transform tables for a dim-dimensional structured
-// grid of n[0] x n[1] (x n[2]) order-k elements (n >= 2 per axis), Gauss-
-// Lobatto nodes z[0..k] on [0,1]. fp32: the transforms run in FP32 (the
-// FP32 forms); else FP64. Returns nullptr on a CUDA error or bad sizes.
+// grid of n[0] x n[1] (x n[2]) order-k elements (n >= 2 per axis; in 2D,
+// n[2] > 1 is a stack of that many equal grids, each with its own coarse
+// grid), Gauss-Lobatto nodes z[0..k] on [0,1]. fp32: the transforms run in
+// FP32 (the FP32 forms); else FP64. Returns nullptr on a CUDA error or bad
+// sizes.
 CoarseSpace* coarse_create(int dim, int k, const int n[3], const double* z, bool fp32);
 void coarse_destroy(CoarseSpace* cs);
 
@@ -32,8 +34,9 @@ size_t coarse_size(const CoarseSpace* cs);
 // y_fine = P w_coarse (FP64, [dim][nfine], overwritten)
 int coarse_prolong(CoarseSpace* cs, const double* w, double* y, cudaStream_t s);
 // The smoothest coarse mode (the first sine of every axis, unit norm per
-// component) in every component: w [dim][ncoarse]; *lambda0 = its K_c
-// eigenvalue.
+// component and grid) in every component: w [dim][ncoarse]; *lambda0 =
+// w_c^t K_c w_c for one component w_c (its K_c eigenvalue times the number
+// of grids of a 2D stack).
 int coarse_mode0(CoarseSpace* cs, double* w, double* lambda0, cudaStream_t s);
 void coarse_set_alpha(CoarseSpace* cs, double alpha);
 

@@ -80,18 +80,22 @@ template <class S> __device__ __forceinline__ typename base_of<S>::type sc(doubl
 // sizes are the costly part; GB300 runs their conversions on its narrow FP64
 // pipe), and local node t = i + N j + N^2 l adds compile-time digits times
 // the lattice strides. Unstructured meshes read the connectivity table.
+// zplanes: lattice planes per element layer along the last index, N - 1 in
+// 3D; in 2D, 1: a 2D "stack" of sz grids (elements e = ex + sx (ey + sy b),
+// grid b's nodes after those of grids 0..b-1), so that many equal meshes
+// form one structured problem.
 template <int N>
 struct NodeMap {
   const int32_t* conn;
-  int sx, sy, Nx, NxNy, base;
+  int sx, sy, Nx, NxNy, zplanes, base;
   const int32_t* row;
-  __device__ __forceinline__ NodeMap(const int32_t* elem_nodes, int sx_, int sy_)
+  __device__ __forceinline__ NodeMap(const int32_t* elem_nodes, int sx_, int sy_, int zplanes_ = N - 1)
       : conn(elem_nodes), sx(sx_), sy(sy_), Nx((N - 1) * sx_ + 1), NxNy(((N - 1) * sx_ + 1) * ((N - 1) * sy_ + 1)),
-        base(0), row(nullptr) {}
+        zplanes(zplanes_), base(0), row(nullptr) {}
   __device__ __forceinline__ void element(int e, int ndof) {
     if (sx > 0) {
       const int exy = sx * sy, ez = e / exy, r = e - ez * exy, ey = r / sx, ex = r - ey * sx;
-      base = (N - 1) * (ez * NxNy + ey * Nx + ex);
+      base = ez * zplanes * NxNy + (N - 1) * (ey * Nx + ex);
     } else {
       row = conn + (size_t)e * ndof;
     }

@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kDiagWarps * 32) diag_kernel(const DiagParams 
   __syncthreads();
   double *r = wr[warp], *U = wu[warp], *V = wv[warp], *Y = wy[warp];
   const R* H = static_cast<const R*>(p.pa);
-  NodeMap<N> nodes(p.elem_nodes, p.sx, p.sy);
+  NodeMap<N> nodes(p.elem_nodes, p.sx, p.sy, DIM == 3 ? N - 1 : 1);
   const int ecount = p.elist ? p.ecount : p.nelem;
   for (int ei = blockIdx.x * kDiagWarps + warp; ei < ecount; ei += gridDim.x * kDiagWarps) {
     const int e = p.elist ? __ldg(p.elist + ei) : ei;

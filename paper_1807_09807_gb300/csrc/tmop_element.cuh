@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
   constexpr int NSH = PA_APPLY ? D * D * (D * D + 1) / 2 : 1;
   static_assert(OP != OP_HESS_PA_C, "OP_HESS_PA_C runs in pac_kernel");
   static_assert(OP != OP_LINEARIZE_C || D == 3, "compact records are 3D");
-  NodeMap<N> nodes(p.elem_nodes, p.sx, p.sy);
+  NodeMap<N> nodes(p.elem_nodes, p.sx, p.sy, D == 3 ? N - 1 : 1);
   const int ecount = p.elist ? p.ecount : p.nelem;
   for (int ei = blockIdx.x * WARPS + warp; ei < ecount; ei += nwarps_total) {
     const int e = p.elist ? __ldg(p.elist + ei) : ei;

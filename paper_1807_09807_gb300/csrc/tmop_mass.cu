@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kMassWarps * 32) mass_kernel(const MassParams 
   double* P0 = buf[warp][0];
   double* P1 = buf[warp][1];
   double acc = 0.0;
-  NodeMap<N> nodes(p.elem_nodes, p.sx, p.sy);
+  NodeMap<N> nodes(p.elem_nodes, p.sx, p.sy, DIM == 3 ? N - 1 : 1);
   const int ecount = p.elist ? p.ecount : p.nelem;
   for (int ei = blockIdx.x * kMassWarps + warp; ei < ecount; ei += gridDim.x * kMassWarps) {
     const int e = p.elist ? __ldg(p.elist + ei) : ei;

@@ -29,7 +29,8 @@ __global__ void k_jacobians(const JacParams p) {
       if (p.sx > 0) {
         const int k = N - 1, Nx = k * p.sx + 1, Ny = k * p.sy + 1;
         const int ex = e % p.sx, ey = (e / p.sx) % p.sy, ez = e / (p.sx * p.sy);
-        g = ((ez * k + l) * Ny + ey * k + j) * Nx + ex * k + i;
+        // 3D: element layers of k lattice planes; 2D: ez is the grid of a stack
+        g = (D == 3 ? ((ez * k + l) * Ny + ey * k + j) : (ez * Ny + ey * k + j)) * Nx + ex * k + i;
       } else {
         g = p.elem_nodes[(size_t)e * NDOF + t];
       }

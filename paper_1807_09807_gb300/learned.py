@@ -202,13 +202,10 @@ def coarse_context(m: mg.Mesh, count: int):
     if key not in _coarse_ctx:
         xv, en, fx = mg.structured(m.dim, 1, m.nx)
         Nv = xv.shape[1]
-        if count == 1:
-            ctx = tm.Context(m.dim, 1, Nv, None, fx, 3, m.metric, structured=list(m.nx), precision=tm.FP64,
-                             nelem=en.shape[0])
-        else:
-            enu = np.concatenate([en + i * Nv for i in range(count)]).astype(np.int32)
-            fxu = np.concatenate([fx] * count, axis=1)
-            ctx = tm.Context(m.dim, 1, Nv * count, enu, fxu, 3, m.metric, precision=tm.FP64)
+        # one order-1 grid, or a stack of `count` of them (nodes grid after grid)
+        st = list(m.nx) + ([count] if count > 1 else [])
+        ctx = tm.Context(m.dim, 1, Nv * count, None, np.concatenate([fx] * count, axis=1), 3, m.metric,
+                         structured=st, precision=tm.FP64, nelem=en.shape[0] * count)
         _coarse_ctx[key] = ctx
     return _coarse_ctx[key]
 
@@ -240,14 +237,22 @@ def coarse_stage(m: mg.Mesh, x0, fixed_dev=None, count: int = 1, out=None, max_n
 
 
 def union_context(meshes, precision=tm.FP32_MIXED):
-    """One TMOP problem made of disjoint meshes (unstructured connectivity)."""
+    """One TMOP problem made of disjoint meshes: a structured stack when
+    they are 2D grids of one size (the nodes of one grid after another; the
+    two-level preconditioner applies), unstructured connectivity otherwise."""
     m0 = meshes[0]
-    N = m0.nnode
-    en = np.concatenate([m.elem_nodes + i * N for i, m in enumerate(meshes)]).astype(np.int32)
+    N, B = m0.nnode, len(meshes)
     fixed = np.concatenate([m.fixed for m in meshes], axis=1)
     x = np.concatenate([m.x for m in meshes], axis=1)
-    ctx = tm.Context(m0.dim, m0.order, N * len(meshes), en, fixed, m0.nq, m0.metric, quad_kind=m0.quad_kind,
-                     precision=precision)
+    if m0.dim == 2 and all(tuple(m.nx) == tuple(m0.nx) for m in meshes):
+        ctx = tm.Context(2, m0.order, N * B, None, fixed, m0.nq, m0.metric, quad_kind=m0.quad_kind,
+                         structured=[m0.nx[0], m0.nx[1], B], precision=precision, nelem=B * m0.nelem)
+        ctx.stacked = True
+    else:
+        en = np.concatenate([m.elem_nodes + i * N for i, m in enumerate(meshes)]).astype(np.int32)
+        ctx = tm.Context(m0.dim, m0.order, N * B, en, fixed, m0.nq, m0.metric, quad_kind=m0.quad_kind,
+                         precision=precision)
+        ctx.stacked = False
     return ctx, x
 
 
@@ -280,7 +285,9 @@ def make_dataset(n_meshes=2000, seed0=1000, nx=32, ldf=256, chunk=250, precision
             if ctx.energy(xc)[2] > 0:    # valid everywhere: the base of this chunk
                 x0 = xc
         x1 = x0.clone()
-        r = ctx.newton_solve(x1, max_newton=max_newton, rtol=rtol)
+        # a stack of boundary-fixed grids takes the two-level preconditioner
+        pc = 2 if ctx.stacked and all(np.array_equal(m.fixed, ms[0].fixed) for m in ms) else 0
+        r = ctx.newton_solve(x1, max_newton=max_newton, rtol=rtol, precond=pc)
         log.append((r.status, r.report["iterations"], r.report["krylov_iterations"]))
         if r.status != tm.OK:
             raise RuntimeError(f"data generation: Newton failed on chunk {c0}: {tm.status_string(r.status)}")

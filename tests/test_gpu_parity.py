@@ -960,3 +960,42 @@ def test_deterministic_newton_is_bitwise_reproducible(tm, prec, precond):
     F0 = ca.energy(dev(m.x))[1]
     assert abs(ra.report["F"] - reps[0]["F"]) <= 1e-12 * F0
     assert np.abs(host(xa) - xs[0]).max() < 1e-9 / 15
+
+
+# ---------------------------------------------------------------- stacks of equal 2D grids
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_grid_stack_matches_the_union_and_the_oracle(tm, prec):
+    """Three 2D grids stacked as one structured problem (structured[2] = 3,
+    the nodes of one grid after another) give the energy, gradient and
+    Hessian actions of the same meshes as one unstructured union, and of the
+    oracle on each grid; Newton with the two-level preconditioner (one coarse
+    vertex grid per grid) reaches the union's plain-MINRES F."""
+    from paper_1807_09807_gb300 import learned as L
+    ms = [make("c5", 20 + i, nx=(5, 4)) for i in range(3)]
+    pf = tm.FP64 if prec == "fp64" else tm.FP32_MIXED
+    cs, xh = L.union_context(ms, pf)
+    assert cs.stacked
+    en = np.concatenate([m.elem_nodes + i * ms[0].nnode for i, m in enumerate(ms)]).astype(np.int32)
+    fx = np.concatenate([m.fixed for m in ms], axis=1)
+    cu = tm.Context(2, 3, xh.shape[1], en, fx, ms[0].nq, ms[0].metric, precision=pf)
+    x = dev(xh)
+    v = np.random.default_rng(6).standard_normal(xh.shape)
+    tol = RTOL if prec == "fp64" else 1e-5
+    _, Fs, mds = cs.energy(x)
+    _, Fu, mdu = cu.energy(x)
+    assert abs(Fs - Fu) <= 1e-13 * Fu and mds == mdu
+    gs, gu = host(cs.gradient(x)), host(cu.gradient(x))
+    assert rel(gs, gu) <= 1e-13
+    hs, hu = host(cs.hess_apply(x, dev(v))), host(cu.hess_apply(x, dev(v)))
+    assert rel(hs, hu) <= (1e-13 if prec == "fp64" else 1e-6)
+    N = ms[0].nnode
+    for i, m in enumerate(ms):
+        orc = orc_for(m)
+        assert rel(gs[:, i * N:(i + 1) * N], orc.gradient(m.x)) <= RTOL
+        assert rel(hs[:, i * N:(i + 1) * N], orc.hess_apply(m.x, v[:, i * N:(i + 1) * N])) <= tol
+    xa, xb = dev(xh), dev(xh)
+    ra = cu.newton_solve(xa, max_newton=20)
+    rb = cs.newton_solve(xb, max_newton=20, precond=2)
+    assert ra.status == tm.OK and rb.status == tm.OK
+    assert abs(ra.report["F"] - rb.report["F"]) <= 1e-12 * Fu
+    assert rb.report["krylov_iterations"] < ra.report["krylov_iterations"]
