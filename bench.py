@@ -932,6 +932,16 @@ def mlp_step_roofline(L, net, X, T, reps=20):
                          "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured)"}}
 
 
+def prop_seconds(L, net, m, ctx, x0, fx, coarse):
+    """Wall time of one proposal (features, network, candidate checks)."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L.propose(net, m, ctx, x0, fx, coarse=coarse)
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0
+
+
 def learned_proposal(tm, dev, args, train_preset="c5", apply_preset="c5apply", measure_step=True, train_meshes=None,
                      coarse=False):
     """Train the proposal MLP on Newton-converged displacements of seeded
@@ -997,6 +1007,17 @@ def learned_proposal(tm, dev, args, train_preset="c5", apply_preset="c5apply", m
         rb = c32.newton_solve(xb, max_newton=40, rtol=1e-30, atol=atol)
         torch.cuda.synchronize()
         tb = time.perf_counter() - t0
+        # both FP32 starts again with the two-level preconditioner
+        tl = {}
+        for arm, xs in (("fp32_twolevel", x0), ("fp32_learned_twolevel", prop.x)):
+            xx = xs.clone()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            rr = c32.newton_solve(xx, max_newton=40, rtol=1e-30, atol=atol, precond=2)
+            torch.cuda.synchronize()
+            tl[arm] = {"seconds": time.perf_counter() - t1 + (0.0 if arm == "fp32_twolevel" else prop_seconds(L, net, m, c32, x0, fx, coarse)),
+                       "status": tm.status_string(rr.status), "newton": rr.report["iterations"],
+                       "krylov": rr.report["krylov_iterations"], "F": rr.report["F"]}
         out["apply"].append({
             "mesh": f"{m.nx[0]}x{m.nx[1]} order-3 quads ({apply_preset}), seed {seed}", "F0": F0,
             "fp64_plain": {"seconds": ta, "status": tm.status_string(ra.status), "newton": ra.report["iterations"],
@@ -1009,6 +1030,7 @@ def learned_proposal(tm, dev, args, train_preset="c5", apply_preset="c5apply", m
                              "proposal_scale": prop.scale, "F_proposal": prop.F, "newton": rb.report["iterations"],
                              "krylov": rb.report["krylov_iterations"], "F": rb.report["F"],
                              "min_detA": rb.report["min_detA"]},
+            **tl,
             "F_diff_over_F0": abs(ra.report["F"] - rb.report["F"]) / F0,
             "speedup": ta / tb,                       # FP32 + proposal over plain FP64
             "speedup_proposal_alone": tc / tb,        # FP32 + proposal over FP32 from x0
