@@ -109,7 +109,10 @@ int tmop_mlp_check(tmop_mlp* net, void* stream);
 int tmop_mlp_gradients(tmop_mlp* net, const uint16_t* X, const float* T, int ldt, int batch, double* loss,
                        void* stream);
 
-/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) after tmop_mlp_gradients. */
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) after tmop_mlp_gradients.
+ * The step count and its bias corrections live on the device, so a training
+ * step (tmop_mlp_gradients + tmop_mlp_adam, no host synchronisation) can be
+ * captured in a CUDA graph and replayed; lr is fixed at capture. */
 int tmop_mlp_adam(tmop_mlp* net, float lr, void* stream);
 
 /* Parameters (which = 0) or gradients (which = 1) as HOST float32 in the

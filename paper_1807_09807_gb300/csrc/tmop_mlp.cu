@@ -1,6 +1,7 @@
 // Learned initial-iterate proposal: patch features, targets, proposal
 // scatter, and a 3-layer MLP trained with hand-written bfloat16 tensor-core
 // GEMMs (tcgen05.mma, FP32 accumulation in tensor memory) and Adam.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -327,13 +328,269 @@ __global__ void k_splitk_sum(const float* __restrict__ W, int splits, size_t str
   }
 }
 
+// ---------------------------------------------------------------- GEMM, TMA-fed pipeline
+// The same C tile (128 x 64, FP32 accumulator in tensor memory) for operands
+// that are both stored K-major, fed by the Tensor Memory Accelerator: a ring
+// of kStages shared-memory stages, each holding one 64-wide K chunk of A
+// (128 rows) and B (64 rows) in the 128-byte-swizzled K-major layout that
+// both cp.async.bulk.tensor (SWIZZLE_128B) and tcgen05 (layout type
+// SWIZZLE_128B) use: row r of a chunk is 128 bytes, its 16-byte pieces
+// XOR-permuted by r mod 8, and 8-row groups 1024 bytes apart. Thread 0
+// loads: it arms a stage's "full" mbarrier with the chunk's byte count and
+// issues the two tensor copies, after waiting on the stage's "empty" mbarrier
+// for the MMAs of the chunk that last used it. Thread 32 multiplies: it
+// waits on "full", issues the chunk's four MMAs (K = 16 each: the
+// descriptors' start address advances 32 bytes within the swizzled rows),
+// and commits them to "empty"; after the last chunk it commits to "done",
+// on which every thread waits before the epilogue. So up to kStages chunks
+// are in flight while the tensor cores work. Every wait is bounded; a wait
+// that gives up raises *err, the copies and MMAs in flight are waited for
+// (bounded again) and the tile is filled with NaN.
+constexpr int kStages = 4;
+constexpr int kStageA = TM * TK * 2, kStageB = TN * TK * 2;   // bytes per stage
+constexpr size_t kTmaSmem = (size_t)kStages * (kStageA + kStageB) + 1024;   // + alignment slack
+
+// K-major, 128-byte swizzle: leading byte offset unused (1), stride byte
+// offset 1024 (8 rows of 128 bytes), version 1, layout type 2 (SWIZZLE_128B)
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) |
+         ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          saddr(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(saddr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  bool done = false;
+  for (long i = 0; i < kMmaSpin && !done; ++i) done = mbar_try(bar, parity);
+  return done;
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(128) k_gemm_tma(const __grid_constant__ CUtensorMap mapA,
+                                                  const __grid_constant__ CUtensorMap mapB, int M, int kper,
+                                                  void* __restrict__ C, int ldc, size_t split_stride,
+                                                  const float* __restrict__ bias, const bf16* __restrict__ ref,
+                                                  int ldr, bf16* __restrict__ CT, int ldct, int* err) {
+  extern __shared__ unsigned char tma_smem_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tma_smem_raw) + 1023) &
+                                                       ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  const int nch = kper / TK, c0 = blockIdx.z * nch;   // this split's K chunks
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&full[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&empty[s])) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&done)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&mapA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&mapB) : "memory");
+    fail = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  auto stageA = [&](int s) { return sm + (size_t)s * (kStageA + kStageB); };
+  auto stageB = [&](int s) { return sm + (size_t)s * (kStageA + kStageB) + kStageA; };
+
+  if (tid == 0) {              // loads
+    int c = 0;
+    for (; c < nch; ++c) {
+      const int s = c % kStages;
+      if (c >= kStages && !mbar_wait(&empty[s], (uint32_t)((c / kStages - 1) & 1))) { fail = 1; break; }
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(&full[s])),
+                   "r"((uint32_t)(kStageA + kStageB))
+                   : "memory");
+      tma_load_2d(stageA(s), &mapA, &full[s], (c0 + c) * TK, m0);
+      tma_load_2d(stageB(s), &mapB, &full[s], (c0 + c) * TK, n0);
+    }
+    // the copies issued must have landed before the CTA may end: the last
+    // phase armed on every stage (earlier ones completed before it was armed)
+    for (int s = 0; s < kStages && s < c; ++s) {
+      const int last = c - 1 - ((c - 1 - s) % kStages);
+      if (!mbar_wait(&full[s], (uint32_t)((last / kStages) & 1))) fail = 1;
+    }
+  } else if (tid == 32) {      // MMAs
+    int c = 0;
+    for (; c < nch; ++c) {
+      const int s = c % kStages;
+      if (!mbar_wait(&full[s], (uint32_t)((c / kStages) & 1))) { fail = 1; break; }
+      tc_fence_after();
+#pragma unroll
+      for (int k = 0; k < TK / 16; ++k) {
+        const uint64_t ad = umma_desc_sw128(saddr(stageA(s)) + k * 32);
+        const uint64_t bd = umma_desc_sw128(saddr(stageB(s)) + k * 32);
+        const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       saddr(&empty[s]))
+                   : "memory");
+    }
+    // "done" follows every MMA issued (also after a failed wait, so that the
+    // others stop waiting as soon as the issued work is complete)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(&done))
+                 : "memory");
+  }
+  const bool landed = mbar_wait(&done, 0u);
+  __syncthreads();
+  const bool ok = landed && !fail && nch > 0;
+  tc_fence_after();
+  const int m = m0 + warp * 32 + lane;
+  if (ok) {
+#pragma unroll
+    for (int cb = 0; cb < TN / 16; ++cb) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 16)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (m < M) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          const int n = n0 + cb * 16 + j;
+          float v0 = __uint_as_float(r[j]), v1 = __uint_as_float(r[j + 1]);
+          if (EPI == EPI_BIAS_RELU_BF16 || EPI == EPI_BIAS_F32) {
+            v0 += bias[n];
+            v1 += bias[n + 1];
+          }
+          if (EPI == EPI_BIAS_RELU_BF16) {
+            v0 = fmaxf(v0, 0.0f);
+            v1 = fmaxf(v1, 0.0f);
+          }
+          if (EPI == EPI_MASK_BF16) {
+            const __nv_bfloat162 rr = *reinterpret_cast<const __nv_bfloat162*>(&ref[(size_t)m * ldr + n]);
+            if (!(__bfloat162float(rr.x) > 0.0f)) v0 = 0.0f;
+            if (!(__bfloat162float(rr.y) > 0.0f)) v1 = 0.0f;
+          }
+          if (EPI == EPI_BIAS_RELU_BF16 || EPI == EPI_MASK_BF16) {
+            const __nv_bfloat162 o = __floats2bfloat162_rn(v0, v1);
+            *reinterpret_cast<__nv_bfloat162*>(&reinterpret_cast<bf16*>(C)[(size_t)m * ldc + n]) = o;
+            if (CT) {  // the transpose too (lanes: consecutive m, so consecutive addresses)
+              CT[(size_t)n * ldct + m] = o.x;
+              CT[(size_t)(n + 1) * ldct + m] = o.y;
+            }
+          } else {
+            float* Cf = reinterpret_cast<float*>(C) + blockIdx.z * split_stride;
+            *reinterpret_cast<float2*>(&Cf[(size_t)m * ldc + n]) = make_float2(v0, v1);
+          }
+        }
+      }
+    }
+  } else {
+    // a wait gave up (not expected): report, let the issued MMAs finish
+    // (bounded), and poison this tile
+    if (tid == 0) atomicExch(err, 1);
+    mbar_wait(&done, 0u);
+    if (m < M) {
+      const float qnan = __uint_as_float(0x7fc00000u);
+      for (int j = 0; j < TN; ++j) {
+        if (EPI == EPI_BIAS_RELU_BF16 || EPI == EPI_MASK_BF16) {
+          reinterpret_cast<bf16*>(C)[(size_t)m * ldc + n0 + j] = __float2bfloat16(qnan);
+          if (CT) CT[(size_t)(n0 + j) * ldct + m] = __float2bfloat16(qnan);
+        } else {
+          (reinterpret_cast<float*>(C) + blockIdx.z * split_stride)[(size_t)m * ldc + n0 + j] = qnan;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+typedef CUresult (*TensorMapEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                      const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                      CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+TensorMapEncodeFn tensor_map_encoder() {
+  static TensorMapEncodeFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<TensorMapEncodeFn>(p);
+  }
+  return fn;
+}
+
+// a [rows][K] bf16 matrix (leading dimension ld elements) in boxes of
+// 64 (K) x box_rows, 128-byte swizzle; rows beyond `rows` read as zero
+bool make_map(CUtensorMap* map, const bf16* ptr, int rows, int K, int ld, int box_rows) {
+  TensorMapEncodeFn enc = tensor_map_encoder();
+  if (!enc || (reinterpret_cast<uintptr_t>(ptr) & 15)) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(bf16)};
+  const cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(ptr), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Launch; FP32 outputs with a small tile grid and a long K are split along K
 // through the workspace ws (capacity ws_cap floats).
 template <bool AK, bool BK, int EPI>
 int gemm(int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb, void* C, int ldc, const float* bias,
-         const bf16* ref, int ldr, float* ws, size_t ws_cap, int* err, cudaStream_t s) {
+         const bf16* ref, int ldr, float* ws, size_t ws_cap, int* err, cudaStream_t s, bf16* CT = nullptr,
+         int ldct = 0) {
   if (M % 64 || N % TN || K % TK || lda % 8 || ldb % 8 || ldc % 2 || M <= 0 || N <= 0 || K <= 0) return TMOP_ERR_ARG;
   const int mt = (M + TM - 1) / TM, nt = N / TN;
+  if constexpr (AK && BK) {  // both operands K-major: the TMA-fed pipeline
+    // FP32 outputs of a small tile grid over a long K (the weight gradients)
+    // split K: about one CTA per SM, at least four chunks per split
+    int sp = 1;
+    if (EPI == EPI_F32 && ws) {
+      const int nchunks = K / TK;
+      while (sp < 64 && mt * nt * sp * 2 <= 152 && nchunks % (sp * 2) == 0 && nchunks / (sp * 2) >= 4 &&
+             (size_t)(sp * 2) * M * ldc <= ws_cap)
+        sp *= 2;
+    }
+    static bool attr = false;
+    if (!attr) {
+      if (cudaFuncSetAttribute(k_gemm_tma<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem) !=
+          cudaSuccess)
+        return TMOP_ERR_CUDA;
+      attr = true;
+    }
+    CUtensorMap ma, mb;
+    if (make_map(&ma, A, M, K, lda, TM) && make_map(&mb, B, N, K, ldb, TN)) {
+      const size_t stride = (size_t)M * ldc;
+      dim3 g(nt, mt, sp);
+      k_gemm_tma<EPI><<<g, 128, kTmaSmem, s>>>(ma, mb, M, K / sp, sp > 1 ? (void*)ws : C, ldc, sp > 1 ? stride : 0,
+                                               bias, ref, ldr, CT, ldct, err);
+      if (sp > 1) k_splitk_sum<<<256, 256, 0, s>>>(ws, sp, stride, stride, reinterpret_cast<float*>(C));
+      return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
+    }
+  }
+  if (CT) return TMOP_ERR_ARG;   // the transposed output exists on the TMA path only
   int splits = 1;
   if (EPI == EPI_F32 && ws) {
     while (splits < 64 && mt * nt * splits * 2 <= 512 && K % (splits * 2 * TK) == 0 &&
@@ -380,12 +637,18 @@ __global__ void k_loss_grad(const float* Y, int ldy, const float* T, int ldt, in
   if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
+// one block of 256 threads: strided partial sums, then a fixed-order tree
 __global__ void k_sum_parts(const double* part, int np, double* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < np; ++i) s += part[i];
-    *out = s;
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) *out = red[0];
 }
 
 // Column sums of a [rows][ld] matrix (float or bf16) into out[ncol] (the
@@ -431,10 +694,24 @@ int colsum(const Tv* X, int rows, int ld, int ncol, float* part, float* out, cud
 struct AdamSegs {
   size_t off[6], sz[6];
   bf16* wb[6];
+  bf16* wbT[6];   // transposed bf16 copy [cols][rows] of a [rows][cols] weight block, or null
+  int cols[6], rows[6];
 };
 
+// the step counter lives on the device (so that a captured training step
+// replays correctly): t += 1, then the bias corrections 0.9^t and 0.999^t
+__global__ void k_adam_step(float* st) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const float t = st[0] + 1.0f;
+    st[0] = t;
+    st[1] = powf(0.9f, t);
+    st[2] = powf(0.999f, t);
+  }
+}
+
 __global__ void k_adam_all(float* w, float* m, float* v, const float* g, size_t total, const AdamSegs sg, float lr,
-                           float b1t, float b2t) {
+                           const float* __restrict__ st) {
+  const float b1t = st[1], b2t = st[2];
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
     int b = 5;
     while (b > 0 && i < sg.off[b]) --b;
@@ -448,6 +725,24 @@ __global__ void k_adam_all(float* w, float* m, float* v, const float* g, size_t 
     const float wi = w[i] - lr * (mi / (1.0f - b1t)) / (sqrtf(vi / (1.0f - b2t)) + 1e-8f);
     w[i] = wi;
     if (sg.wb[b]) sg.wb[b][j] = __float2bfloat16_rn(wi);
+    if (sg.wbT[b]) sg.wbT[b][(j % sg.cols[b]) * sg.rows[b] + j / sg.cols[b]] = __float2bfloat16_rn(wi);
+  }
+}
+
+// out[c][r] = in[r][c] (bf16, [rows][ld_in] -> [cols][ld_out]), in 32 x 32
+// tiles through shared memory
+__global__ void k_transpose_bf16(const bf16* __restrict__ in, int rows, int cols, int ld_in, bf16* __restrict__ out,
+                                 int ld_out) {
+  __shared__ bf16 tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = r0 + k, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[k][threadIdx.x] = in[(size_t)r * ld_in + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int c = c0 + k, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[(size_t)c * ld_out + r] = tile[threadIdx.x][k];
   }
 }
 
@@ -467,14 +762,18 @@ struct tmop_mlp {
   size_t off[6], total;
   float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
   bf16 *W1 = nullptr, *W2 = nullptr, *W3 = nullptr;  // bf16 copies of the weight matrices
+  bf16 *W2T = nullptr, *W3T = nullptr;               // and transposed, K-major for the data gradients
   int batch_cap = 0;
   bf16 *H1 = nullptr, *H2 = nullptr, *dYb = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
+  // transposes [features][batch] of the activations and gradients: the
+  // weight-gradient GEMMs (K = batch) read both operands K-major
+  bf16 *XT = nullptr, *H1T = nullptr, *H2T = nullptr, *dYT = nullptr, *dZ2T = nullptr, *dZ1T = nullptr;
   float *Y = nullptr, *dYf = nullptr;
   double* part = nullptr;
   float* ws = nullptr;   // split-K partial tiles of the weight-gradient GEMMs
   size_t ws_cap = 0;     // in floats
   int* d_err = nullptr;  // set when a GEMM's bounded wait for its MMAs gave up
-  int t = 0;
+  float* d_adam = nullptr;  // Adam step count and its bias corrections (device)
 };
 
 namespace {
@@ -483,8 +782,12 @@ int ensure_batch(tmop_mlp* n, int batch) {
   if (batch <= n->batch_cap) return TMOP_OK;
   cudaFree(n->H1); cudaFree(n->H2); cudaFree(n->dYb); cudaFree(n->dZ2); cudaFree(n->dZ1);
   cudaFree(n->Y); cudaFree(n->dYf); cudaFree(n->part);
+  cudaFree(n->XT); cudaFree(n->H1T); cudaFree(n->H2T); cudaFree(n->dYT); cudaFree(n->dZ2T); cudaFree(n->dZ1T);
   const size_t B = batch;
-  if (cudaMalloc(&n->H1, B * n->H * sizeof(bf16)) || cudaMalloc(&n->H2, B * n->H * sizeof(bf16)) ||
+  if (cudaMalloc(&n->XT, B * n->K1 * sizeof(bf16)) || cudaMalloc(&n->H1T, B * n->H * sizeof(bf16)) ||
+      cudaMalloc(&n->H2T, B * n->H * sizeof(bf16)) || cudaMalloc(&n->dYT, B * n->N3 * sizeof(bf16)) ||
+      cudaMalloc(&n->dZ2T, B * n->H * sizeof(bf16)) || cudaMalloc(&n->dZ1T, B * n->H * sizeof(bf16)) ||
+      cudaMalloc(&n->H1, B * n->H * sizeof(bf16)) || cudaMalloc(&n->H2, B * n->H * sizeof(bf16)) ||
       cudaMalloc(&n->dZ2, B * n->H * sizeof(bf16)) || cudaMalloc(&n->dZ1, B * n->H * sizeof(bf16)) ||
       cudaMalloc(&n->dYb, B * n->N3 * sizeof(bf16)) || cudaMalloc(&n->Y, B * n->N3 * sizeof(float)) ||
       cudaMalloc(&n->dYf, B * n->N3 * sizeof(float)) || cudaMalloc(&n->part, 1024 * sizeof(double))) {
@@ -502,14 +805,22 @@ int refresh_bf16(tmop_mlp* n, cudaStream_t s) {
   k_to_bf16<<<256, 256, 0, s>>>(P(n, n->w, 0), n->W1, n1);
   k_to_bf16<<<256, 256, 0, s>>>(P(n, n->w, 2), n->W2, n2);
   k_to_bf16<<<64, 256, 0, s>>>(P(n, n->w, 4), n->W3, n3);
+  // W2 [H][H] -> W2^T, W3 [N3][H] -> W3^T [H][N3]
+  k_transpose_bf16<<<dim3((n->H + 31) / 32, (n->H + 31) / 32), dim3(32, 8), 0, s>>>(n->W2, n->H, n->H, n->H, n->W2T,
+                                                                                     n->H);
+  k_transpose_bf16<<<dim3((n->H + 31) / 32, (n->N3 + 31) / 32), dim3(32, 8), 0, s>>>(n->W3, n->N3, n->H, n->H,
+                                                                                      n->W3T, n->N3);
   return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
 }
 
-int forward_impl(tmop_mlp* n, const bf16* X, int batch, float* Y, int ldy, cudaStream_t s) {
+// train: also the transposed activations [H][batch] for the weight gradients
+int forward_impl(tmop_mlp* n, const bf16* X, int batch, float* Y, int ldy, cudaStream_t s, bool train = false) {
   int rc = gemm<true, true, EPI_BIAS_RELU_BF16>(batch, n->H, n->K1, X, n->K1, n->W1, n->K1, n->H1, n->H,
-                                                P(n, n->w, 1), nullptr, 0, n->ws, n->ws_cap, n->d_err, s);
+                                                P(n, n->w, 1), nullptr, 0, n->ws, n->ws_cap, n->d_err, s,
+                                                train ? n->H1T : nullptr, batch);
   if (!rc) rc = gemm<true, true, EPI_BIAS_RELU_BF16>(batch, n->H, n->H, n->H1, n->H, n->W2, n->H, n->H2, n->H,
-                                                     P(n, n->w, 3), nullptr, 0, n->ws, n->ws_cap, n->d_err, s);
+                                                     P(n, n->w, 3), nullptr, 0, n->ws, n->ws_cap, n->d_err, s,
+                                                     train ? n->H2T : nullptr, batch);
   if (!rc) rc = gemm<true, true, EPI_BIAS_F32>(batch, n->N3, n->H, n->H2, n->H, n->W3, n->H, Y, ldy,
                                                P(n, n->w, 5), nullptr, 0, n->ws, n->ws_cap, n->d_err, s);
   return rc;
@@ -632,7 +943,9 @@ void tmop_mlp_destroy(tmop_mlp* n) {
   cudaFree(n->W1); cudaFree(n->W2); cudaFree(n->W3);
   cudaFree(n->H1); cudaFree(n->H2); cudaFree(n->dYb); cudaFree(n->dZ2); cudaFree(n->dZ1);
   cudaFree(n->Y); cudaFree(n->dYf); cudaFree(n->part);
-  cudaFree(n->ws); cudaFree(n->d_err);
+  cudaFree(n->XT); cudaFree(n->H1T); cudaFree(n->H2T); cudaFree(n->dYT); cudaFree(n->dZ2T); cudaFree(n->dZ1T);
+  cudaFree(n->W2T); cudaFree(n->W3T);
+  cudaFree(n->ws); cudaFree(n->d_err); cudaFree(n->d_adam);
   delete n;
 }
 
@@ -663,11 +976,12 @@ int tmop_mlp_create(int n_in, int n_hidden, int n_out, uint64_t seed, tmop_mlp**
   int rc = TMOP_OK;
   // split-K workspace: up to 64 slices of the largest weight gradient (rows padded to 128)
   n->ws_cap = (size_t)64 * ((std::max(n->H, n->N3) + 127) / 128 * 128) * std::max(n->H, n->K1);
-  if (cudaMalloc(&n->ws, n->ws_cap * 4) || cudaMalloc(&n->d_err, sizeof(int)) || cudaMemset(n->d_err, 0, sizeof(int)))
+  if (cudaMalloc(&n->ws, n->ws_cap * 4) || cudaMalloc(&n->d_err, sizeof(int)) || cudaMemset(n->d_err, 0, sizeof(int)) ||
+      cudaMalloc(&n->d_adam, 4 * sizeof(float)) || cudaMemset(n->d_adam, 0, 4 * sizeof(float)))
     rc = TMOP_ERR_CUDA;
   if (rc == TMOP_OK && (cudaMalloc(&n->w, acc * 4) || cudaMalloc(&n->g, acc * 4) || cudaMalloc(&n->m, acc * 4) ||
       cudaMalloc(&n->v, acc * 4) || cudaMalloc(&n->W1, sz[0] * 2) || cudaMalloc(&n->W2, sz[2] * 2) ||
-      cudaMalloc(&n->W3, sz[4] * 2) || cudaMemcpy(n->w, host.data(), acc * 4, cudaMemcpyHostToDevice) ||
+      cudaMalloc(&n->W3, sz[4] * 2) || cudaMalloc(&n->W2T, sz[2] * 2) || cudaMalloc(&n->W3T, sz[4] * 2) || cudaMemcpy(n->w, host.data(), acc * 4, cudaMemcpyHostToDevice) ||
       cudaMemset(n->g, 0, acc * 4) || cudaMemset(n->m, 0, acc * 4) || cudaMemset(n->v, 0, acc * 4)))
     rc = TMOP_ERR_CUDA;
   if (rc == TMOP_OK) rc = refresh_bf16(n, 0);
@@ -769,26 +1083,34 @@ int tmop_mlp_gradients(tmop_mlp* n, const uint16_t* Xu, const float* T, int ldt,
   int rc = ensure_batch(n, batch);
   if (rc) return rc;
   const bf16* X = reinterpret_cast<const bf16*>(Xu);
-  rc = forward_impl(n, X, batch, n->Y, n->N3, s);
+  // X^T [K1][batch] for the first weight gradient
+  k_transpose_bf16<<<dim3((n->K1 + 31) / 32, (batch + 31) / 32), dim3(32, 8), 0, s>>>(X, batch, n->K1, n->K1, n->XT,
+                                                                                       batch);
+  rc = forward_impl(n, X, batch, n->Y, n->N3, s, true);
   if (rc) return rc;
   const int lblocks = 256;
   k_loss_grad<<<lblocks, 256, 0, s>>>(n->Y, n->N3, T, ldt, batch, n->n_out, n->N3, n->dYf, n->dYb, n->part);
-  if (loss) k_sum_parts<<<1, 32, 0, s>>>(n->part, lblocks, loss);
+  if (loss) k_sum_parts<<<1, 256, 0, s>>>(n->part, lblocks, loss);
+  k_transpose_bf16<<<dim3((n->N3 + 31) / 32, (batch + 31) / 32), dim3(32, 8), 0, s>>>(n->dYb, batch, n->N3, n->N3,
+                                                                                       n->dYT, batch);
+  // Every GEMM below reads both operands K-major (the TMA-fed kernel): the
+  // weight gradients (K = batch) take the transposes [features][batch], the
+  // data gradients the transposed weights.
   // layer 3: dW3 = dY^T H2, db3 = colsum dY, dH2 = dY W3 masked by H2 > 0
-  rc = gemm<false, false, EPI_F32>(n->N3, n->H, batch, n->dYb, n->N3, n->H2, n->H, P(n, n->g, 4), n->H, nullptr,
-                                   nullptr, 0, n->ws, n->ws_cap, n->d_err, s);
+  rc = gemm<true, true, EPI_F32>(n->N3, n->H, batch, n->dYT, batch, n->H2T, batch, P(n, n->g, 4), n->H, nullptr,
+                                 nullptr, 0, n->ws, n->ws_cap, n->d_err, s);
   if (!rc) rc = colsum<float>(n->dYf, batch, n->N3, n->N3, n->ws, P(n, n->g, 5), s);
-  if (!rc) rc = gemm<true, false, EPI_MASK_BF16>(batch, n->H, n->N3, n->dYb, n->N3, n->W3, n->H, n->dZ2, n->H,
-                                                 nullptr, n->H2, n->H, n->ws, n->ws_cap, n->d_err, s);
+  if (!rc) rc = gemm<true, true, EPI_MASK_BF16>(batch, n->H, n->N3, n->dYb, n->N3, n->W3T, n->N3, n->dZ2, n->H,
+                                                nullptr, n->H2, n->H, n->ws, n->ws_cap, n->d_err, s, n->dZ2T, batch);
   // layer 2
-  if (!rc) rc = gemm<false, false, EPI_F32>(n->H, n->H, batch, n->dZ2, n->H, n->H1, n->H, P(n, n->g, 2), n->H,
-                                            nullptr, nullptr, 0, n->ws, n->ws_cap, n->d_err, s);
+  if (!rc) rc = gemm<true, true, EPI_F32>(n->H, n->H, batch, n->dZ2T, batch, n->H1T, batch, P(n, n->g, 2), n->H,
+                                          nullptr, nullptr, 0, n->ws, n->ws_cap, n->d_err, s);
   if (!rc) rc = colsum<bf16>(n->dZ2, batch, n->H, n->H, n->ws, P(n, n->g, 3), s);
-  if (!rc) rc = gemm<true, false, EPI_MASK_BF16>(batch, n->H, n->H, n->dZ2, n->H, n->W2, n->H, n->dZ1, n->H,
-                                                 nullptr, n->H1, n->H, n->ws, n->ws_cap, n->d_err, s);
+  if (!rc) rc = gemm<true, true, EPI_MASK_BF16>(batch, n->H, n->H, n->dZ2, n->H, n->W2T, n->H, n->dZ1, n->H,
+                                                nullptr, n->H1, n->H, n->ws, n->ws_cap, n->d_err, s, n->dZ1T, batch);
   // layer 1
-  if (!rc) rc = gemm<false, false, EPI_F32>(n->H, n->K1, batch, n->dZ1, n->H, X, n->K1, P(n, n->g, 0), n->K1,
-                                            nullptr, nullptr, 0, n->ws, n->ws_cap, n->d_err, s);
+  if (!rc) rc = gemm<true, true, EPI_F32>(n->H, n->K1, batch, n->dZ1T, batch, n->XT, batch, P(n, n->g, 0), n->K1,
+                                          nullptr, nullptr, 0, n->ws, n->ws_cap, n->d_err, s);
   if (!rc) rc = colsum<bf16>(n->dZ1, batch, n->H, n->H, n->ws, P(n, n->g, 1), s);
   if (rc) return rc;
   return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
@@ -797,18 +1119,22 @@ int tmop_mlp_gradients(tmop_mlp* n, const uint16_t* Xu, const float* T, int ldt,
 int tmop_mlp_adam(tmop_mlp* n, float lr, void* stream) {
   if (!n || !(lr > 0.0f)) return TMOP_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  n->t += 1;
-  const float b1t = powf(0.9f, (float)n->t), b2t = powf(0.999f, (float)n->t);
   bf16* wb[6] = {n->W1, nullptr, n->W2, nullptr, n->W3, nullptr};
+  bf16* wbT[6] = {nullptr, nullptr, n->W2T, nullptr, n->W3T, nullptr};
   const size_t sz[6] = {(size_t)n->H * n->K1, (size_t)n->H, (size_t)n->H * n->H, (size_t)n->H,
                         (size_t)n->N3 * n->H, (size_t)n->N3};
+  const int rows[6] = {n->H, 1, n->H, 1, n->N3, 1}, cols[6] = {n->K1, n->H, n->H, n->H, n->H, n->N3};
   AdamSegs sg;
   for (int i = 0; i < 6; ++i) {
     sg.off[i] = n->off[i];
     sg.sz[i] = sz[i];
     sg.wb[i] = wb[i];
+    sg.wbT[i] = wbT[i];
+    sg.rows[i] = rows[i];
+    sg.cols[i] = cols[i];
   }
-  k_adam_all<<<304, 256, 0, s>>>(n->w, n->m, n->v, n->g, n->total, sg, lr, b1t, b2t);
+  k_adam_step<<<1, 32, 0, s>>>(n->d_adam);
+  k_adam_all<<<304, 256, 0, s>>>(n->w, n->m, n->v, n->g, n->total, sg, lr, n->d_adam);
   return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
 }
 

@@ -302,25 +302,47 @@ def make_dataset(n_meshes=2000, seed0=1000, nx=32, ldf=256, chunk=250, precision
     return Dataset(torch.cat(Xs), torch.cat(Ts), n_meshes, log, time.perf_counter() - t0)
 
 
-def train(net: MLP, ds: Dataset, epochs=20, batch=4096, lr=1e-3, seed=0, log_every=0):
-    """Adam on minibatches of the dataset (reshuffled every epoch)."""
+def train(net: MLP, ds: Dataset, epochs=20, batch=4096, lr=1e-3, seed=0, log_every=0, graph=True):
+    """Adam on minibatches of the dataset (reshuffled every epoch). With
+    graph, each epoch captures one training step (tmop_mlp_gradients +
+    tmop_mlp_adam on fixed minibatch buffers, its learning rate) in a CUDA
+    graph and replays it for every minibatch."""
     import torch
     S = ds.X.shape[0]
     g = torch.Generator(device="cuda")
     g.manual_seed(seed)
     loss = torch.zeros((), dtype=torch.float64, device="cuda")
+    Xb = torch.empty((batch, ds.X.shape[1]), dtype=ds.X.dtype, device="cuda")
+    Tb = torch.empty((batch, ds.T.shape[1]), dtype=ds.T.dtype, device="cuda")
     hist = []
     nb = S // batch
+    if graph and nb > 0:   # first use outside capture: workspace allocation, kernel attributes
+        torch.index_select(ds.X, 0, torch.arange(batch, device="cuda"), out=Xb)
+        torch.index_select(ds.T, 0, torch.arange(batch, device="cuda"), out=Tb)
+        net.gradients(Xb, Tb, loss)
+        torch.cuda.synchronize()
     for ep in range(epochs):
         perm = torch.randperm(S, device="cuda", generator=g)
         acc = 0.0
-        lr_ep = lr * 0.5 * (1 + np.cos(np.pi * ep / epochs))      # cosine decay
+        lr_ep = float(lr * 0.5 * (1 + np.cos(np.pi * ep / epochs)))      # cosine decay
+        step = None
+        if graph and nb > 0:
+            step = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side), torch.cuda.graph(step, stream=side):
+                net.gradients(Xb, Tb, loss)
+                net.adam(lr_ep)
+            torch.cuda.current_stream().wait_stream(side)
         for b in range(nb):
             idx = perm[b * batch:(b + 1) * batch]
-            X = ds.X.index_select(0, idx)
-            T = ds.T.index_select(0, idx)
-            net.gradients(X, T, loss)
-            net.adam(lr_ep)
+            torch.index_select(ds.X, 0, idx, out=Xb)
+            torch.index_select(ds.T, 0, idx, out=Tb)
+            if step is not None:
+                step.replay()
+            else:
+                net.gradients(Xb, Tb, loss)
+                net.adam(lr_ep)
             if b % 50 == 0 or b == nb - 1:
                 acc = loss.item()
         net.check()
