@@ -491,11 +491,12 @@ def run_ours(args):
         if ev is not None:
             ev[1].record(stream)
 
-    if args.kernels_only and args.profile == "newton":
-        # one FP32-mixed Newton step of the workload (linearisation, MINRES with the stored-Hessian product)
+    if args.kernels_only and args.profile in ("newton", "newton_twolevel"):
+        # one FP32-mixed Newton step of the workload (linearisation, MINRES with the stored-Hessian
+        # product; newton_twolevel: preconditioned by Jacobi plus the coarse vertex correction)
         c32 = tm.Context.from_mesh(m, precision=tm.FP32_MIXED)
         xn = x.clone()
-        c32.newton_step(xn)
+        c32.newton_step(xn, precond=2 if args.profile == "newton_twolevel" else 0)
         torch.cuda.synchronize()
         c32.close()
         return 0
@@ -1090,10 +1091,10 @@ def main():
                     help="with N > 1: split the workload's elements into z-slabs, one per rank, with a halo "
                          "sum of the shared node planes per operator application (strong scaling) instead "
                          "of N independent replicas")
-    ap.add_argument("--profile", choices=["step", "pa", "mlp", "newton"], default="step",
+    ap.add_argument("--profile", choices=["step", "pa", "mlp", "newton", "newton_twolevel"], default="step",
                     help="with --kernels-only: the timed step (gradient + Hessian action), the partially "
                          "assembled Hessian action alone, training steps of the proposal MLP, or one "
-                         "FP32-mixed Newton step")
+                         "FP32-mixed Newton step (newton_twolevel: with the two-level preconditioner)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if not args.kernels_only else args.warmup
     if args.impl == "reference":

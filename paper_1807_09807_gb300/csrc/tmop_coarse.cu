@@ -60,13 +60,13 @@ struct Wts {
 template <class Rin, class Rout>
 __global__ void k_restrict(const Rin* __restrict__ in, Rout* __restrict__ out, size_t outer, int Lf, int Lc,
                            size_t inner, int k, Wts w) {
-  const size_t total = outer * (size_t)Lc * inner;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const size_t j = idx % inner, oI = idx / inner;
-    const int I = (int)(oI % Lc);
-    const size_t o = oI / Lc;
-    const Rin* base = in + (o * Lf + (size_t)k * (I + 1)) * inner + j;
+  // (32-bit index arithmetic: every array here has fewer than 2^31 values,
+  // and 64-bit divisions by run-time sizes cost ~5x more)
+  const uint32_t total = (uint32_t)(outer * (size_t)Lc * inner), in32 = (uint32_t)inner, lc = (uint32_t)Lc;
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const uint32_t j = idx % in32, oI = idx / in32;
+    const uint32_t I = oI % lc, o = oI / lc;
+    const Rin* base = in + ((size_t)o * Lf + (size_t)k * (I + 1)) * inner + j;
     Rout acc = (Rout)base[0];   // arithmetic in the transform precision
     for (int t = 1; t < k; ++t)
       acc = fmaR((Rout)w.w[t], (Rout)base[(size_t)t * inner] + (Rout)base[-(ptrdiff_t)(t * inner)], acc);
@@ -91,12 +91,10 @@ __device__ __forceinline__ R prolong_at(const R* __restrict__ in, size_t o, int 
 template <class R>
 __global__ void k_prolong(const R* __restrict__ in, R* __restrict__ out, size_t outer, int Lc, int Lf, size_t inner,
                           int k, int n, Wts w) {
-  const size_t total = outer * (size_t)Lf * inner;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const size_t j = idx % inner, og = idx / inner;
-    const int g = (int)(og % Lf);
-    out[idx] = prolong_at(in, og / Lf, g, j, Lc, inner, k, n, w);
+  const uint32_t total = (uint32_t)(outer * (size_t)Lf * inner), in32 = (uint32_t)inner, lf = (uint32_t)Lf;
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const uint32_t j = idx % in32, og = idx / in32;
+    out[idx] = prolong_at(in, og / lf, (int)(og % lf), j, Lc, inner, k, n, w);
   }
 }
 
@@ -118,12 +116,10 @@ __device__ __forceinline__ double block_sum_c(double v) {
 template <class R>
 __global__ void k_prolong_add(const R* __restrict__ in, double* __restrict__ y, const double* __restrict__ r,
                               size_t outer, int Lc, int Lf, int k, int n, Wts w, double* __restrict__ part) {
-  const size_t total = outer * (size_t)Lf;
+  const uint32_t total = (uint32_t)(outer * (size_t)Lf), lf = (uint32_t)Lf;
   double s = 0.0;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int g = (int)(idx % Lf);
-    const double yi = y[idx] + (double)prolong_at(in, idx / Lf, g, 0, Lc, 1, k, n, w);
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const double yi = y[idx] + (double)prolong_at(in, idx / lf, (int)(idx % lf), 0, Lc, 1, k, n, w);
     y[idx] = yi;
     if (part) s = fma(r[idx], yi, s);
   }
@@ -137,13 +133,11 @@ __global__ void k_prolong_add(const R* __restrict__ in, double* __restrict__ y, 
 template <class R>
 __global__ void k_dst(const R* __restrict__ in, R* __restrict__ out, const R* __restrict__ S, size_t outer, int L,
                       size_t inner) {
-  const size_t total = outer * (size_t)L * inner;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const size_t j = idx % inner, oa = idx / inner;
-    const int a = (int)(oa % L);
-    const size_t o = oa / L;
-    const R* src = in + o * (size_t)L * inner + j;
+  const uint32_t total = (uint32_t)(outer * (size_t)L * inner), in32 = (uint32_t)inner, l32 = (uint32_t)L;
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const uint32_t j = idx % in32, oa = idx / in32;
+    const uint32_t a = oa % l32, o = oa / l32;
+    const R* src = in + (size_t)o * L * inner + j;
     const R* Sa = S + (size_t)a * L;
     R acc = R(0);
     for (int m = 0; m < L; ++m) acc = fmaR(__ldg(Sa + m), src[(size_t)m * inner], acc);
@@ -156,11 +150,10 @@ template <class R>
 __global__ void k_eig_scale(R* __restrict__ v, const R* __restrict__ lx, const R* __restrict__ mx,
                             const R* __restrict__ ly, const R* __restrict__ my, const R* __restrict__ lz,
                             const R* __restrict__ mz, int dim, int L0, int L1, int L2, double inv_alpha) {
-  const size_t per = (size_t)L0 * L1 * L2, total = per * dim;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const size_t p = idx % per;
-    const int I = (int)(p % L0), J = (int)((p / L0) % L1), K = (int)(p / ((size_t)L0 * L1));
+  const uint32_t per = (uint32_t)L0 * L1 * L2, total = per * dim, l0 = L0, l1 = L1;
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const uint32_t p = idx % per;
+    const uint32_t I = p % l0, J = (p / l0) % l1, K = p / (l0 * l1);
     double lam;
     if (dim == 2) lam = (double)lx[I] * (double)my[J] + (double)mx[I] * (double)ly[J];
     else
@@ -173,11 +166,10 @@ __global__ void k_eig_scale(R* __restrict__ v, const R* __restrict__ lx, const R
 template <class R>
 __global__ void k_mode0(double* __restrict__ w, const R* __restrict__ Sx, const R* __restrict__ Sy,
                         const R* __restrict__ Sz, int dim, int L0, int L1, int L2) {
-  const size_t per = (size_t)L0 * L1 * L2, total = per * dim;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const size_t p = idx % per;
-    const int I = (int)(p % L0), J = (int)((p / L0) % L1), K = (int)(p / ((size_t)L0 * L1));
+  const uint32_t per = (uint32_t)L0 * L1 * L2, total = per * dim, l0 = L0, l1 = L1;
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const uint32_t p = idx % per;
+    const uint32_t I = p % l0, J = (p / l0) % l1, K = p / (l0 * l1);
     double v = (double)Sx[I] * (double)Sy[J];
     if (dim == 3) v *= (double)Sz[K];
     w[idx] = v;
@@ -316,6 +308,7 @@ CoarseSpace* coarse_create(int dim, int k, const int n[3], const double* z, bool
     cs->nfine *= (size_t)cs->Lf[a];
     cs->ncoarse *= (size_t)cs->Lc[a];
   }
+  if (cs->nfine * dim >= ((size_t)1 << 31)) { delete cs; return nullptr; }   // 32-bit indices in the passes
   // tables
   const size_t elt = fp32 ? sizeof(float) : sizeof(double);
   size_t tot = 0;

@@ -6,7 +6,10 @@
 // product d_b phi_i d_c phi_i is separable: in direction d it is the 1D
 // product of (G if d == b else B) and (G if d == c else B), so every (a, b, c)
 // term is one sum-factorised contraction of a per-point scalar with three
-// per-direction tables. One warp per element, FP64 accumulation into diag.
+// per-direction tables. One warp per element; the contractions run in the
+// precision of the stored values (FP32 for the FP32 forms: the diagonal only
+// preconditions, and GB300's FP64 pipe is 64x narrower), the accumulation
+// into diag in FP64.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -21,25 +24,27 @@ namespace {
 
 constexpr int kDiagWarps = 4;
 
+__device__ __forceinline__ float fmaA(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaA(double a, double b, double c) { return fma(a, b, c); }
+
 // Y[n^DIM] += sum_q R[q] prod_d T_d[q_d][i_d]; R in `r` (QP values), tables T0,
 // T1, T2 ([Q1][N]), scratch U, V.
-template <int DIM, int N, int Q1>
-__device__ void contract_add(const double* r, const double* T0, const double* T1, const double* T2, double* U,
-                             double* V, double* Y, int lane) {
+template <int DIM, int N, int Q1, class A>
+__device__ void contract_add(const A* r, const A* T0, const A* T1, const A* T2, A* U, A* V, A* Y, int lane) {
   if constexpr (DIM == 2) {
     for (int t = lane; t < N * Q1; t += 32) {  // U[j][q0] = sum_q1 R[q1][q0] T1[q1][j]
       const int q0 = t % Q1, j = t / Q1;
-      double s = 0.0;
+      A s = A(0);
 #pragma unroll
-      for (int q1 = 0; q1 < Q1; ++q1) s = fma(r[q1 * Q1 + q0], T1[q1 * N + j], s);
+      for (int q1 = 0; q1 < Q1; ++q1) s = fmaA(r[q1 * Q1 + q0], T1[q1 * N + j], s);
       U[j * Q1 + q0] = s;
     }
     __syncwarp();
     for (int t = lane; t < N * N; t += 32) {  // Y[j][i] += sum_q0 U[j][q0] T0[q0][i]
       const int i = t % N, j = t / N;
-      double s = 0.0;
+      A s = A(0);
 #pragma unroll
-      for (int q0 = 0; q0 < Q1; ++q0) s = fma(U[j * Q1 + q0], T0[q0 * N + i], s);
+      for (int q0 = 0; q0 < Q1; ++q0) s = fmaA(U[j * Q1 + q0], T0[q0 * N + i], s);
       Y[t] += s;
     }
     __syncwarp();
@@ -47,25 +52,25 @@ __device__ void contract_add(const double* r, const double* T0, const double* T1
     constexpr int QQ = Q1 * Q1;
     for (int t = lane; t < N * QQ; t += 32) {  // U[l][q1][q0] = sum_q2 R[q2][q1][q0] T2[q2][l]
       const int q01 = t % QQ, l = t / QQ;
-      double s = 0.0;
+      A s = A(0);
 #pragma unroll
-      for (int q2 = 0; q2 < Q1; ++q2) s = fma(r[q2 * QQ + q01], T2[q2 * N + l], s);
+      for (int q2 = 0; q2 < Q1; ++q2) s = fmaA(r[q2 * QQ + q01], T2[q2 * N + l], s);
       U[l * QQ + q01] = s;
     }
     __syncwarp();
     for (int t = lane; t < N * N * Q1; t += 32) {  // V[l][j][q0] = sum_q1 U[l][q1][q0] T1[q1][j]
       const int q0 = t % Q1, j = (t / Q1) % N, l = t / (Q1 * N);
-      double s = 0.0;
+      A s = A(0);
 #pragma unroll
-      for (int q1 = 0; q1 < Q1; ++q1) s = fma(U[l * QQ + q1 * Q1 + q0], T1[q1 * N + j], s);
+      for (int q1 = 0; q1 < Q1; ++q1) s = fmaA(U[l * QQ + q1 * Q1 + q0], T1[q1 * N + j], s);
       V[(l * N + j) * Q1 + q0] = s;
     }
     __syncwarp();
     for (int t = lane; t < N * N * N; t += 32) {  // Y[l][j][i] += sum_q0 V[l][j][q0] T0[q0][i]
       const int i = t % N, lj = t / N;
-      double s = 0.0;
+      A s = A(0);
 #pragma unroll
-      for (int q0 = 0; q0 < Q1; ++q0) s = fma(V[lj * Q1 + q0], T0[q0 * N + i], s);
+      for (int q0 = 0; q0 < Q1; ++q0) s = fmaA(V[lj * Q1 + q0], T0[q0 * N + i], s);
       Y[t] += s;
     }
     __syncwarp();
@@ -117,21 +122,22 @@ __global__ void __launch_bounds__(kDiagWarps * 32) diag_kernel(const DiagParams 
   constexpr int DD = DIM * DIM, NS = DD * (DD + 1) / 2;
   constexpr int UQ = DIM == 2 ? N * Q1 : N * Q1 * Q1, VQ = DIM == 2 ? 1 : N * N * Q1;
   // tables: B, G and the three products BB, BG, GG ([Q1][N] each)
-  __shared__ double tab[5][kMaxQ * kMaxN];
-  __shared__ double sw[kMaxQ];
-  __shared__ double wr[kDiagWarps][QP], wu[kDiagWarps][UQ], wv[kDiagWarps][VQ], wy[kDiagWarps][NDOF];
+  using A = R;   // arithmetic of the contractions
+  __shared__ A tab[5][kMaxQ * kMaxN];
+  __shared__ A sw[kMaxQ];
+  __shared__ A wr[kDiagWarps][QP], wu[kDiagWarps][UQ], wv[kDiagWarps][VQ], wy[kDiagWarps][NDOF];
   // compact records (3D): entries b = 0..2 of row a of the response to E_ac
   __shared__ float whh[kDiagWarps][DIM == 3 ? 3 * QP : 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < Q1 * N; t += blockDim.x) {
     const double b = p.B[t], g = p.G[t];
-    tab[0][t] = b * b;
-    tab[1][t] = b * g;
-    tab[2][t] = g * g;
+    tab[0][t] = A(b * b);
+    tab[1][t] = A(b * g);
+    tab[2][t] = A(g * g);
   }
-  for (int t = threadIdx.x; t < Q1; t += blockDim.x) sw[t] = p.w1[t];
+  for (int t = threadIdx.x; t < Q1; t += blockDim.x) sw[t] = A(p.w1[t]);
   __syncthreads();
-  double *r = wr[warp], *U = wu[warp], *V = wv[warp], *Y = wy[warp];
+  A *r = wr[warp], *U = wu[warp], *V = wv[warp], *Y = wy[warp];
   const R* H = static_cast<const R*>(p.pa);
   NodeMap<N> nodes(p.elem_nodes, p.sx, p.sy, DIM == 3 ? N - 1 : 1);
   const int ecount = p.elist ? p.ecount : p.nelem;
@@ -140,7 +146,7 @@ __global__ void __launch_bounds__(kDiagWarps * 32) diag_kernel(const DiagParams 
     nodes.element(e, NDOF);
     const R* He = H + (size_t)e * p.pa_stride;
     for (int a = 0; a < DIM; ++a) {
-      for (int t = lane; t < NDOF; t += 32) Y[t] = 0.0;
+      for (int t = lane; t < NDOF; t += 32) Y[t] = A(0);
       __syncwarp();
       // terms (b <= c): H[(a,b),(a,c)] (twice for b != c) against the 1D
       // table products; direction d uses tab[(d == b) + (d == c)]: BB, BG or GG
@@ -156,36 +162,36 @@ __global__ void __launch_bounds__(kDiagWarps * 32) diag_kernel(const DiagParams 
           __syncwarp();
         }
         for (int b = 0; b <= c; ++b) {
-          const double m = b == c ? 1.0 : 2.0;
+          const A m = b == c ? A(1) : A(2);
           if (DIM == 3 && p.compact) {
-            for (int q = lane; q < QP; q += 32) r[q] = m * (double)hh[b * QP + q];
+            for (int q = lane; q < QP; q += 32) r[q] = m * (A)hh[b * QP + q];
           } else {
             // packed index of (row a*DIM+b, column a*DIM+c), row <= column
             const int rr = a * DIM + b, cc = a * DIM + c;
             const int s = rr * DD - rr * (rr - 1) / 2 + (cc - rr);
-            for (int q = lane; q < QP; q += 32) r[q] = m * (double)He[(size_t)s * QP + q];
+            for (int q = lane; q < QP; q += 32) r[q] = m * (A)He[(size_t)s * QP + q];
           }
           __syncwarp();
-          const double* T0 = tab[(b == 0) + (c == 0)];
-          const double* T1 = tab[(b == 1) + (c == 1)];
-          const double* T2 = tab[(b == 2) + (c == 2)];
-          contract_add<DIM, N, Q1>(r, T0, T1, T2, U, V, Y, lane);
+          const A* T0 = tab[(b == 0) + (c == 0)];
+          const A* T1 = tab[(b == 1) + (c == 1)];
+          const A* T2 = tab[(b == 2) + (c == 2)];
+          contract_add<DIM, N, Q1, A>(r, T0, T1, T2, U, V, Y, lane);
         }
       }
       if (p.delta != 0.0) {  // restricted movement: 2 delta w det W phi_i^2 (B^2 in every direction)
         for (int q = lane; q < QP; q += 32) {
           const int q0 = q % Q1, q1 = (q / Q1) % Q1;
-          double wq = sw[q0] * sw[q1];
-          if (DIM == 3) wq *= sw[q / (Q1 * Q1)];
+          double wq = (double)sw[q0] * (double)sw[q1];
+          if (DIM == 3) wq *= (double)sw[q / (Q1 * Q1)];
           const double dw = p.detW_qp ? __ldg(p.detW_qp + (size_t)e * QP + q) : p.detW;
-          r[q] = 2.0 * p.delta * wq * dw;
+          r[q] = A(2.0 * p.delta * wq * dw);
         }
         __syncwarp();
-        contract_add<DIM, N, Q1>(r, tab[0], tab[0], tab[0], U, V, Y, lane);
+        contract_add<DIM, N, Q1, A>(r, tab[0], tab[0], tab[0], U, V, Y, lane);
       }
       for (int t = lane; t < NDOF; t += 32) {
         const int g = nodes(t);
-        atomicAdd(p.diag + (size_t)a * p.nnode + g, Y[t]);
+        atomicAdd(p.diag + (size_t)a * p.nnode + g, (double)Y[t]);
       }
       __syncwarp();
     }
