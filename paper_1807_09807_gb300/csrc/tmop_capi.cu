@@ -503,15 +503,16 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
   // the converged iteration. The kCheck iterations are captured once into a
   // CUDA graph on an internal stream and replayed (direct launches if capture
   // is not possible).
-  // (6: plain MINRES renames its vectors with period 3 and 2, so a batch of
-  // 6 iterations starts and ends with the same assignment)
+  // (6: plain MINRES renames its vectors with period 3 and 2, preconditioned
+  // MINRES with period 2, so a batch of 6 iterations starts and ends with the
+  // same assignment)
   constexpr int kCheck = 6;
   const bool cg = o.krylov == TMOP_KRYLOV_CG;
   double *k0 = vec(c, V_K0), *k1 = vec(c, V_K1), *k2 = vec(c, V_K2), *k3 = vec(c, V_K3), *k4 = vec(c, V_K4);
   double* k5 = vec(c, V_K5);
   if (cg) {
     if (cg_init(b, k0, k1, p, st, part, n, o.krylov_rtol, o.krylov_maxit, s)) return TMOP_ERR_CUDA;
-  } else if (minv) {  // r1 = k0, r2 = k1, y = k2, v = k3, w = k4, wprev = k5
+  } else if (minv) {  // r1 = k0, r2 = k1, u = k2 (product into q = k3), w = k4, wprev = k5
     if (pminres_init(b, minv, k0, k1, k2, k4, k5, p, st, part, n, o.krylov_rtol, o.krylov_maxit, s, pc))
       return TMOP_ERR_CUDA;
   } else {
@@ -529,11 +530,13 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
   auto enqueue_batch = [&](cudaStream_t q) -> int {
     for (int j = 0; j < kCheck; ++j) {
       int r;
-      if (minv) {
-        if (pminres_v(k3, k2, st, n, q)) return TMOP_ERR_CUDA;
-        r = launch_op(c, hop, x, k3, k2, nullptr, q);
+      if (minv) {   // the pairs (r1, r2), (u, q), (w, wprev) swap roles every iteration
+        const bool ev = j % 2 == 0;
+        double *r1 = ev ? k0 : k1, *r2 = ev ? k1 : k0, *u = ev ? k2 : k3, *hu = ev ? k3 : k2;
+        double *w = ev ? k4 : k5, *wp = ev ? k5 : k4;
+        r = launch_op(c, hop, x, u, hu, nullptr, q);
         if (r) return r;
-        if (pminres_after_hv(minv, k0, k1, k2, k3, k4, k5, p, st, part, n, q, pc)) return TMOP_ERR_CUDA;
+        if (pminres_after_hv(minv, r1, r2, u, hu, w, wp, p, st, part, n, q, pc)) return TMOP_ERR_CUDA;
         continue;
       }
       if (cg) {  // r = k0, d = k1, Hd = k2

@@ -21,6 +21,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "tmop_coarse.h"
 #include "tmop_vec.h"
 
@@ -42,6 +44,7 @@ struct CoarseSpace {
 namespace {
 
 constexpr int kThr = 256;
+constexpr int kMaxCoarseParts = 256;   // per-block partials of the coarse dot product
 
 __device__ __forceinline__ float fmaR(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fmaR(double a, double b, double c) { return fma(a, b, c); }
@@ -52,49 +55,85 @@ int grid_for(size_t work) {
   return g < 1 ? 1 : (int)g;
 }
 
+// transfer weights in the pass precision: w[t] = 1 - z_t, z[t] = z_t, t = 0..k
+template <class R>
 struct Wts {
-  double w[8];  // w[t] = 1 - z_t, t = 0..k (w[0] = 1)
+  R w[8], z[8];
 };
 
-// out[o][I][j] = sum_{|t| < k} w(|t|) in[o][k (I + 1) + t][j]
-template <class Rin, class Rout>
-__global__ void k_restrict(const Rin* __restrict__ in, Rout* __restrict__ out, size_t outer, int Lf, int Lc,
-                           size_t inner, int k, Wts w) {
-  // (32-bit index arithmetic: every array here has fewer than 2^31 values,
-  // and 64-bit divisions by run-time sizes cost ~5x more)
-  const uint32_t total = (uint32_t)(outer * (size_t)Lc * inner), in32 = (uint32_t)inner, lc = (uint32_t)Lc;
-  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-    const uint32_t j = idx % in32, oI = idx / in32;
-    const uint32_t I = oI % lc, o = oI / lc;
-    const Rin* base = in + ((size_t)o * Lf + (size_t)k * (I + 1)) * inner + j;
+// Division by a run-time divisor d < 2^31 of dividends n < 2^31 as a
+// multiply-high and a shift (Granlund and Montgomery, "Division by invariant
+// integers using multiplication", 1994): with s = ceil(log2 d) and
+// m = floor(2^32 (2^s - d) / d) + 1, n / d = (mulhi(n, m) + n) >> s.
+struct FastDiv {
+  uint32_t d = 1, m = 0, s = 0;
+  FastDiv() = default;
+  explicit FastDiv(uint32_t d_) : d(d_) {
+    if (d > 1) {
+      s = 32u - (uint32_t)__builtin_clz(d - 1);
+      m = (uint32_t)(((((uint64_t)1) << 32) * ((((uint64_t)1) << s) - d)) / d + 1);
+    }
+  }
+  __device__ __forceinline__ uint32_t div(uint32_t n) const { return (__umulhi(n, m) + n) >> s; }
+};
+
+// One pass along an axis of an array viewed as [outer][L][inner] (L = Lin in,
+// Lout out), one output value per thread iteration, the flat output index
+// split into (o, position, j) by two multiply-high divisions and the position
+// along the axis into (element, node) by the compile-time order K.
+struct Pass {
+  uint32_t outer, Lin, Lout, inner, total;
+  FastDiv by_inner, by_Lout;
+};
+
+// out[o][I][j] = sum_{|t| < K} w(|t|) in[o][K (I + 1) + t][j]
+template <class Rin, class Rout, int K>
+__global__ void k_restrict(const Rin* __restrict__ in, Rout* __restrict__ out, Pass p, Wts<Rout> w) {
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < p.total; idx += gridDim.x * blockDim.x) {
+    const uint32_t rest = p.by_inner.div(idx), j = idx - rest * p.inner;
+    const uint32_t o = p.by_Lout.div(rest), I = rest - o * p.Lout;
+    const Rin* base = in + ((size_t)o * p.Lin + (size_t)K * (I + 1)) * p.inner + j;
     Rout acc = (Rout)base[0];   // arithmetic in the transform precision
-    for (int t = 1; t < k; ++t)
-      acc = fmaR((Rout)w.w[t], (Rout)base[(size_t)t * inner] + (Rout)base[-(ptrdiff_t)(t * inner)], acc);
+#pragma unroll
+    for (int d = 1; d < K; ++d)
+      acc = fmaR(w.w[d], (Rout)base[(size_t)d * p.inner] + (Rout)base[-(ptrdiff_t)((size_t)d * p.inner)], acc);
     out[idx] = acc;
   }
 }
 
-// out[o][g][j] = (1 - z_i) in[o][e - 1][j] + z_i in[o][e][j], g = k e + i
-// (interior vertex e - 1 is vertex e; vertices 0 and n are fixed: zero)
-template <class R>
-__device__ __forceinline__ R prolong_at(const R* __restrict__ in, size_t o, int g, size_t j, int Lc, size_t inner,
-                                        int k, int n, const Wts& w) {
-  int e = g / k;
+// (1 - z_i) in[o][e - 1][j] + z_i in[o][e][j] at g = K e + i: interior vertex
+// e - 1 is vertex e; vertices 0 and n are fixed (zero)
+template <class R, int K>
+__device__ __forceinline__ R prolong_at(const R* __restrict__ in, size_t o, uint32_t g, size_t j, uint32_t Lc,
+                                        size_t inner, uint32_t n, const Wts<R>& w) {
+  uint32_t e = g / K;
   if (e > n - 1) e = n - 1;
-  const int i = g - k * e;
+  const uint32_t i = g - K * e;
+  R wi = w.w[0], zi = w.z[0];   // by selects: no dynamic indexing into the parameter block
+#pragma unroll
+  for (int t = 1; t <= K; ++t)
+    if (i == (uint32_t)t) wi = w.w[t], zi = w.z[t];
   R v = R(0);
-  if (e >= 1) v = fmaR((R)w.w[i], in[(o * Lc + (e - 1)) * inner + j], v);
-  if (e <= n - 2) v = fmaR((R)(1.0 - w.w[i]), in[(o * Lc + e) * inner + j], v);
+  if (e >= 1) v = fmaR(wi, in[(o * Lc + (e - 1)) * inner + j], v);
+  if (e + 2 <= n) v = fmaR(zi, in[(o * Lc + e) * inner + j], v);
   return v;
 }
 
-template <class R>
-__global__ void k_prolong(const R* __restrict__ in, R* __restrict__ out, size_t outer, int Lc, int Lf, size_t inner,
-                          int k, int n, Wts w) {
-  const uint32_t total = (uint32_t)(outer * (size_t)Lf * inner), in32 = (uint32_t)inner, lf = (uint32_t)Lf;
-  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-    const uint32_t j = idx % in32, og = idx / in32;
-    out[idx] = prolong_at(in, og / lf, (int)(og % lf), j, Lc, inner, k, n, w);
+template <class R, int K>
+__global__ void k_prolong(const R* __restrict__ in, R* __restrict__ out, Pass p, uint32_t n, Wts<R> w) {
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < p.total; idx += gridDim.x * blockDim.x) {
+    const uint32_t rest = p.by_inner.div(idx), j = idx - rest * p.inner;
+    const uint32_t o = p.by_Lout.div(rest), g = rest - o * p.Lout;
+    out[idx] = prolong_at<R, K>(in, o, g, j, p.Lin, p.inner, n, w);
+  }
+}
+
+// the last prolongation pass (along x, inner = 1) into the FP64 fine array: y += P w
+template <class R, int K>
+__global__ void k_prolong_add(const R* __restrict__ in, double* __restrict__ y, Pass p, uint32_t n, Wts<R> w) {
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < p.total; idx += gridDim.x * blockDim.x) {
+    const uint32_t o = p.by_Lout.div(idx), g = idx - o * p.Lout;
+    y[idx] += (double)prolong_at<R, K>(in, o, g, 0, p.Lin, 1, n, w);
   }
 }
 
@@ -107,21 +146,91 @@ __device__ __forceinline__ double block_sum_c(double v) {
   __syncthreads();
   double s = 0.0;
   if (threadIdx.x == 0)
-    for (int i = 0; i < kThr / 32; ++i) s += red[i];  // fixed order
+    for (int i = 0; i < (int)(blockDim.x / 32); ++i) s += red[i];  // fixed order
   return s;
 }
 
-// the last prolongation pass (along x, into the FP64 fine array): y += P w,
-// per-block partials of r . y
+// The sine transform along one axis as a batched product C_b = A_b B_b
+// (M x N = (M x Kd)(Kd x N)), with A(i, k) = A[b sAb + i lda + k],
+// B(k, j) = B[b sBb + k ldb + j], C(i, j) = C[b sCb + i ldc + j]: along x
+// (inner = 1) In [rows][L] times S (symmetric), along y or z S times every
+// [L][inner] slab. 64 x 64 output tiles over 16-deep chunks staged in shared
+// memory, 4 x 4 outputs per thread (rows ty + 16 r, columns tx + 16 c).
+constexpr int kTM = 64, kTN = 64, kTK = 16;
+
 template <class R>
-__global__ void k_prolong_add(const R* __restrict__ in, double* __restrict__ y, const double* __restrict__ r,
-                              size_t outer, int Lc, int Lf, int k, int n, Wts w, double* __restrict__ part) {
-  const uint32_t total = (uint32_t)(outer * (size_t)Lf), lf = (uint32_t)Lf;
+__global__ void __launch_bounds__(256, 2) k_dst(const R* __restrict__ A, const R* __restrict__ B, R* __restrict__ C,
+                                             int M, int N, int Kd, int batch, size_t sAb, int lda, size_t sBb,
+                                             int ldb, size_t sCb, int ldc) {
+  __shared__ R As[kTK][kTM + 1];
+  __shared__ R Bs[kTK][kTN];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tiles_n = (N + kTN - 1) / kTN, tiles_m = (M + kTM - 1) / kTM;
+  for (int b = blockIdx.z; b < batch; b += gridDim.z)
+    for (int tm = blockIdx.y; tm < tiles_m; tm += gridDim.y)
+      for (int tn = blockIdx.x; tn < tiles_n; tn += gridDim.x) {
+        const R* Ab = A + b * sAb;
+        const R* Bb = B + b * sBb;
+        const int i0 = tm * kTM, j0 = tn * kTN;
+        R acc[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] = R(0);
+        for (int k0 = 0; k0 < Kd; k0 += kTK) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int i = (tid >> 4) + 16 * q, k = tid & 15;   // A tile: 16 consecutive k per row
+            As[k][i] = (i0 + i < M && k0 + k < Kd) ? Ab[(size_t)(i0 + i) * lda + k0 + k] : R(0);
+            const int kb = (tid >> 6) + 4 * q, j = tid & 63;   // B tile: 64 consecutive j per row
+            Bs[kb][j] = (k0 + kb < Kd && j0 + j < N) ? Bb[(size_t)(k0 + kb) * ldb + j0 + j] : R(0);
+          }
+          __syncthreads();
+#pragma unroll
+          for (int k = 0; k < kTK; ++k) {
+            R a[4], bb[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = As[k][ty + 16 * r];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) bb[c] = Bs[k][tx + 16 * c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+              for (int c = 0; c < 4; ++c) acc[r][c] = fmaR(a[r], bb[c], acc[r][c]);
+          }
+          __syncthreads();
+        }
+        R* Cb = C + b * sCb;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int i = i0 + ty + 16 * r, j = j0 + tx + 16 * c;
+            if (i < M && j < N) Cb[(size_t)i * ldc + j] = acc[r][c];
+          }
+      }
+}
+
+// divide by alpha times the eigenvalue of K_c at every coarse point, in the
+// sine basis; per-block partials of v_old . v_new into part (if given): with
+// S orthogonal and symmetric that is c . (alpha K_c)^-1 c for the restricted
+// residual c, the coarse share of r . M^-1 r
+template <class R>
+__global__ void k_eig_scale(R* __restrict__ v, const R* __restrict__ lx, const R* __restrict__ mx,
+                            const R* __restrict__ ly, const R* __restrict__ my, const R* __restrict__ lz,
+                            const R* __restrict__ mz, int dim, uint32_t L0, uint32_t L1, uint32_t L2, uint32_t total,
+                            FastDiv by0, FastDiv by1, FastDiv by2, R inv_alpha, double* __restrict__ part) {
   double s = 0.0;
   for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-    const double yi = y[idx] + (double)prolong_at(in, idx / lf, (int)(idx % lf), 0, Lc, 1, k, n, w);
-    y[idx] = yi;
-    if (part) s = fma(r[idx], yi, s);
+    const uint32_t row = by0.div(idx), I = idx - row * L0;
+    const uint32_t rr = by1.div(row), J = row - rr * L1;
+    const uint32_t K = rr - by2.div(rr) * L2;
+    R lam;
+    if (dim == 2) lam = fmaR(lx[I], my[J], mx[I] * ly[J]);
+    else lam = fmaR(fmaR(lx[I], my[J], mx[I] * ly[J]), mz[K], mx[I] * my[J] * lz[K]);
+    const R c = v[idx], w = c * (inv_alpha / lam);
+    v[idx] = w;
+    s = fma((double)c, (double)w, s);
   }
   if (part) {
     s = block_sum_c(s);
@@ -129,47 +238,12 @@ __global__ void k_prolong_add(const R* __restrict__ in, double* __restrict__ y, 
   }
 }
 
-// out[o][a][j] = sum_m S[a][m] in[o][m][j] along an axis of length L
-template <class R>
-__global__ void k_dst(const R* __restrict__ in, R* __restrict__ out, const R* __restrict__ S, size_t outer, int L,
-                      size_t inner) {
-  const uint32_t total = (uint32_t)(outer * (size_t)L * inner), in32 = (uint32_t)inner, l32 = (uint32_t)L;
-  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-    const uint32_t j = idx % in32, oa = idx / in32;
-    const uint32_t a = oa % l32, o = oa / l32;
-    const R* src = in + (size_t)o * L * inner + j;
-    const R* Sa = S + (size_t)a * L;
-    R acc = R(0);
-    for (int m = 0; m < L; ++m) acc = fmaR(__ldg(Sa + m), src[(size_t)m * inner], acc);
-    out[idx] = acc;
-  }
-}
-
-// divide by alpha times the eigenvalue of K_c at every coarse point
-template <class R>
-__global__ void k_eig_scale(R* __restrict__ v, const R* __restrict__ lx, const R* __restrict__ mx,
-                            const R* __restrict__ ly, const R* __restrict__ my, const R* __restrict__ lz,
-                            const R* __restrict__ mz, int dim, int L0, int L1, int L2, double inv_alpha) {
-  const uint32_t per = (uint32_t)L0 * L1 * L2, total = per * dim, l0 = L0, l1 = L1;
-  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-    const uint32_t p = idx % per;
-    const uint32_t I = p % l0, J = (p / l0) % l1, K = p / (l0 * l1);
-    double lam;
-    if (dim == 2) lam = (double)lx[I] * (double)my[J] + (double)mx[I] * (double)ly[J];
-    else
-      lam = (double)lx[I] * (double)my[J] * (double)mz[K] + (double)mx[I] * (double)ly[J] * (double)mz[K] +
-            (double)mx[I] * (double)my[J] * (double)lz[K];
-    v[idx] = (R)((double)v[idx] * inv_alpha / lam);
-  }
-}
-
 template <class R>
 __global__ void k_mode0(double* __restrict__ w, const R* __restrict__ Sx, const R* __restrict__ Sy,
-                        const R* __restrict__ Sz, int dim, int L0, int L1, int L2) {
-  const uint32_t per = (uint32_t)L0 * L1 * L2, total = per * dim, l0 = L0, l1 = L1;
+                        const R* __restrict__ Sz, int dim, uint32_t L0, uint32_t L1, uint32_t L2) {
+  const uint32_t total = (uint32_t)dim * L0 * L1 * L2;
   for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-    const uint32_t p = idx % per;
-    const uint32_t I = p % l0, J = (p / l0) % l1, K = p / (l0 * l1);
+    const uint32_t I = idx % L0, J = (idx / L0) % L1, K = (idx / (L0 * L1)) % L2;
     double v = (double)Sx[I] * (double)Sy[J];
     if (dim == 3) v *= (double)Sz[K];
     w[idx] = v;
@@ -181,9 +255,13 @@ __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ ou
     out[i] = (float)in[i];
 }
 
-Wts weights(const CoarseSpace* cs) {
-  Wts w;
-  for (int t = 0; t < 8; ++t) w.w[t] = t <= cs->k ? 1.0 - cs->z[t] : 0.0;
+template <class R>
+Wts<R> weights(const CoarseSpace* cs) {
+  Wts<R> w;
+  for (int t = 0; t < 8; ++t) {
+    w.w[t] = (R)(t <= cs->k ? 1.0 - cs->z[t] : 0.0);
+    w.z[t] = (R)(t <= cs->k ? cs->z[t] : 0.0);
+  }
   return w;
 }
 
@@ -210,45 +288,101 @@ const R* tab_mu(const CoarseSpace* cs, int a) {
   return tab_lam<R>(cs, a) + cs->Lc[a];
 }
 
+// calls f(std::integral_constant<int, K>{}) for the order K = k (1..7)
+template <class F>
+int with_order(int k, F&& f) {
+  switch (k) {
+    case 1: f(std::integral_constant<int, 1>{}); break;
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    case 3: f(std::integral_constant<int, 3>{}); break;
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    case 5: f(std::integral_constant<int, 5>{}); break;
+    case 6: f(std::integral_constant<int, 6>{}); break;
+    case 7: f(std::integral_constant<int, 7>{}); break;
+    default: return -1;
+  }
+  return 0;
+}
+
+Pass make_pass(const CoarseSpace* cs, const int len[3], int a, int Lout) {
+  size_t outer, inner;
+  view(cs, len, a, &outer, &inner);
+  Pass p;
+  p.outer = (uint32_t)outer;
+  p.Lin = (uint32_t)len[a];
+  p.Lout = (uint32_t)Lout;
+  p.inner = (uint32_t)inner;
+  p.total = (uint32_t)(outer * (size_t)Lout * inner);
+  p.by_inner = FastDiv(p.inner);
+  p.by_Lout = FastDiv(p.Lout);
+  return p;
+}
+
 // w_c = P^t r (FP64 fine -> R coarse in buf[0] or buf[1]); returns the buffer
 template <class R>
 R* restrict_all(CoarseSpace* cs, const double* r, cudaStream_t s) {
-  const Wts w = weights(cs);
+  const Wts<R> w = weights<R>(cs);
   int len[3] = {cs->Lf[0], cs->Lf[1], cs->Lf[2]};
   R* b[2] = {static_cast<R*>(cs->buf[0]), static_cast<R*>(cs->buf[1])};
   for (int a = 0; a < cs->dim; ++a) {
-    size_t outer, inner;
-    view(cs, len, a, &outer, &inner);
+    const Pass p = make_pass(cs, len, a, cs->Lc[a]);
     R* dst = b[a % 2];
-    const size_t work = outer * (size_t)cs->Lc[a] * inner;
-    if (a == 0)
-      k_restrict<double, R><<<grid_for(work), kThr, 0, s>>>(r, dst, outer, len[a], cs->Lc[a], inner, cs->k, w);
-    else
-      k_restrict<R, R><<<grid_for(work), kThr, 0, s>>>(b[(a - 1) % 2], dst, outer, len[a], cs->Lc[a], inner, cs->k, w);
+    const R* src = a == 0 ? nullptr : b[(a - 1) % 2];
+    const int g = grid_for(p.total);
+    with_order(cs->k, [&](auto K) {
+      if (a == 0) k_restrict<double, R, K.value><<<g, kThr, 0, s>>>(r, dst, p, w);
+      else k_restrict<R, R, K.value><<<g, kThr, 0, s>>>(src, dst, p, w);
+    });
     len[a] = cs->Lc[a];
   }
   return b[(cs->dim - 1) % 2];
 }
 
-// v <- (alpha K_c)^-1 v on the coarse array held in buf[src]; returns the buffer with the result
+// one sine transform along axis a of the coarse array: src -> dst
 template <class R>
-R* solve_coarse(CoarseSpace* cs, R* v, cudaStream_t s) {
+void dst_pass(CoarseSpace* cs, int a, const R* src, R* dst, cudaStream_t s) {
+  size_t outer, inner;
+  view(cs, cs->Lc, a, &outer, &inner);
+  const int L = cs->Lc[a];
+  const R* S = tab_S<R>(cs, a);
+  if (inner == 1) {   // [rows][L] S
+    const int M = (int)outer;
+    const int tm = (M + kTM - 1) / kTM, tn = (L + kTN - 1) / kTN;
+    const dim3 g(tn, tm < 65535 ? tm : 65535, 1);
+    k_dst<R><<<g, 256, 0, s>>>(src, S, dst, M, L, L, 1, 0, L, 0, L, 0, L);
+  } else {            // S [L][inner] for every outer slab
+    const int N = (int)inner, batch = (int)outer;
+    const int tm = (L + kTM - 1) / kTM, tn = (N + kTN - 1) / kTN;
+    const dim3 g(tn < 65535 ? tn : 65535, tm < 65535 ? tm : 65535, batch < 65535 ? batch : 65535);
+    const size_t slab = (size_t)L * inner;
+    k_dst<R><<<g, 256, 0, s>>>(S, src, dst, L, N, L, batch, 0, L, slab, N, slab, N);
+  }
+}
+
+// v <- (alpha K_c)^-1 v on the coarse array in v (one of the pass buffers);
+// returns the buffer with the result. part (if given): per-block partials of
+// c . (alpha K_c)^-1 c; *np their number.
+template <class R>
+R* solve_coarse(CoarseSpace* cs, R* v, double* part, int* np, cudaStream_t s) {
   R* b[2] = {static_cast<R*>(cs->buf[0]), static_cast<R*>(cs->buf[1])};
   R* cur = v;
   auto other = [&](R* p) { return p == b[0] ? b[1] : b[0]; };
   for (int pass = 0; pass < 2; ++pass) {
     for (int a = 0; a < cs->dim; ++a) {
-      size_t outer, inner;
-      view(cs, cs->Lc, a, &outer, &inner);
       R* dst = other(cur);
-      k_dst<R><<<grid_for(cs->ncoarse * cs->dim), kThr, 0, s>>>(cur, dst, tab_S<R>(cs, a), outer, cs->Lc[a], inner);
+      dst_pass<R>(cs, a, cur, dst, s);
       cur = dst;
     }
     if (pass == 0) {
       const int a2 = cs->dim == 3 ? 2 : 1;
-      k_eig_scale<R><<<grid_for(cs->ncoarse * cs->dim), kThr, 0, s>>>(
-          cur, tab_lam<R>(cs, 0), tab_mu<R>(cs, 0), tab_lam<R>(cs, 1), tab_mu<R>(cs, 1), tab_lam<R>(cs, a2),
-          tab_mu<R>(cs, a2), cs->dim, cs->Lc[0], cs->Lc[1], cs->Lc[2], 1.0 / cs->alpha);
+      const uint32_t L0 = cs->Lc[0], L1 = cs->Lc[1], L2 = cs->Lc[2];
+      const uint32_t total = (uint32_t)(cs->ncoarse * cs->dim);
+      int g = grid_for(total);
+      if (g > kMaxCoarseParts) g = kMaxCoarseParts;
+      k_eig_scale<R><<<g, kThr, 0, s>>>(cur, tab_lam<R>(cs, 0), tab_mu<R>(cs, 0), tab_lam<R>(cs, 1), tab_mu<R>(cs, 1),
+                                        tab_lam<R>(cs, a2), tab_mu<R>(cs, a2), cs->dim, L0, L1, L2, total,
+                                        FastDiv(L0), FastDiv(L1), FastDiv(L2), (R)(1.0 / cs->alpha), part);
+      *np = g;
     }
   }
   return cur;
@@ -258,33 +392,41 @@ R* solve_coarse(CoarseSpace* cs, R* v, cudaStream_t s) {
 // pass buffers); returns the array whose last pass (along x) is still to do
 template <class R>
 R* prolong_upper(CoarseSpace* cs, R* cur, int len[3], cudaStream_t s) {
-  const Wts w = weights(cs);
+  const Wts<R> w = weights<R>(cs);
   R* b[2] = {static_cast<R*>(cs->buf[0]), static_cast<R*>(cs->buf[1])};
   auto other = [&](R* p) { return p == b[0] ? b[1] : b[0]; };
   for (int a = 0; a < 3; ++a) len[a] = cs->Lc[a];
   for (int a = cs->dim - 1; a >= 1; --a) {
-    size_t outer, inner;
-    view(cs, len, a, &outer, &inner);
+    const Pass p = make_pass(cs, len, a, cs->Lf[a]);
     R* dst = other(cur);
-    const size_t work = outer * (size_t)cs->Lf[a] * inner;
-    k_prolong<R><<<grid_for(work), kThr, 0, s>>>(cur, dst, outer, cs->Lc[a], cs->Lf[a], inner, cs->k, cs->n[a], w);
+    with_order(cs->k, [&](auto K) {
+      k_prolong<R, K.value><<<grid_for(p.total), kThr, 0, s>>>(cur, dst, p, (uint32_t)cs->n[a], w);
+    });
     len[a] = cs->Lf[a];
     cur = dst;
   }
   return cur;
 }
 
+// the last pass (along x) into y
+template <class R>
+void prolong_last(CoarseSpace* cs, const R* c, const int len[3], double* y, cudaStream_t s) {
+  const Pass p = make_pass(cs, len, 0, cs->Lf[0]);
+  const Wts<R> w = weights<R>(cs);
+  with_order(cs->k, [&](auto K) {
+    k_prolong_add<R, K.value><<<grid_for(p.total), kThr, 0, s>>>(c, y, p, (uint32_t)cs->n[0], w);
+  });
+}
+
 template <class R>
 int apply_add_t(CoarseSpace* cs, const double* r, double* y, double* part, cudaStream_t s) {
   R* c = restrict_all<R>(cs, r, s);
-  c = solve_coarse<R>(cs, c, s);
+  int np = 0;
+  c = solve_coarse<R>(cs, c, part, &np, s);
   int len[3];
   c = prolong_upper<R>(cs, c, len, s);
-  size_t outer, inner;
-  view(cs, len, 0, &outer, &inner);
-  const int g = red_grid(outer * (size_t)cs->Lf[0]);
-  k_prolong_add<R><<<g, kThr, 0, s>>>(c, y, r, outer, cs->Lc[0], cs->Lf[0], cs->k, cs->n[0], weights(cs), part);
-  return cudaGetLastError() == cudaSuccess ? g : -1;
+  prolong_last<R>(cs, c, len, y, s);
+  return cudaGetLastError() == cudaSuccess ? np : -1;
 }
 
 }  // namespace
@@ -378,14 +520,14 @@ void coarse_set_alpha(CoarseSpace* cs, double alpha) {
 
 int coarse_mode0(CoarseSpace* cs, double* w, double* lambda0, cudaStream_t s) {
   if (!cs || !w) return (int)cudaErrorInvalidValue;
-  const int L0 = cs->Lc[0], L1 = cs->Lc[1], L2 = cs->Lc[2];
-  const size_t work = cs->ncoarse * cs->dim;
+  const uint32_t L0 = cs->Lc[0], L1 = cs->Lc[1], L2 = cs->Lc[2];
+  const int g = grid_for(cs->ncoarse * cs->dim);
   if (cs->fp32)
-    k_mode0<float><<<grid_for(work), kThr, 0, s>>>(w, tab_S<float>(cs, 0), tab_S<float>(cs, 1),
-                                                   tab_S<float>(cs, cs->dim == 3 ? 2 : 1), cs->dim, L0, L1, L2);
+    k_mode0<float><<<g, kThr, 0, s>>>(w, tab_S<float>(cs, 0), tab_S<float>(cs, 1),
+                                      tab_S<float>(cs, cs->dim == 3 ? 2 : 1), cs->dim, L0, L1, L2);
   else
-    k_mode0<double><<<grid_for(work), kThr, 0, s>>>(w, tab_S<double>(cs, 0), tab_S<double>(cs, 1),
-                                                    tab_S<double>(cs, cs->dim == 3 ? 2 : 1), cs->dim, L0, L1, L2);
+    k_mode0<double><<<g, kThr, 0, s>>>(w, tab_S<double>(cs, 0), tab_S<double>(cs, 1),
+                                       tab_S<double>(cs, cs->dim == 3 ? 2 : 1), cs->dim, L0, L1, L2);
   if (lambda0) {
     double lam = 0.0;
     for (int a = 0; a < cs->dim; ++a) {
@@ -407,26 +549,18 @@ int coarse_prolong(CoarseSpace* cs, const double* w, double* y, cudaStream_t s) 
   if (cudaMemsetAsync(y, 0, sizeof(double) * cs->nfine * cs->dim, s) != cudaSuccess) return (int)cudaErrorUnknown;
   // the FP64 coarse field goes through the pass buffers in the transform precision
   int len[3];
-  int rc;
   if (cs->fp32) {
     float* c = static_cast<float*>(cs->buf[0]);
     k_to_float<<<grid_for(cs->ncoarse * cs->dim), kThr, 0, s>>>(w, c, cs->ncoarse * cs->dim);
     c = prolong_upper<float>(cs, c, len, s);
-    size_t outer, inner;
-    view(cs, len, 0, &outer, &inner);
-    k_prolong_add<float><<<red_grid(outer * (size_t)cs->Lf[0]), kThr, 0, s>>>(c, y, nullptr, outer, cs->Lc[0], cs->Lf[0],
-                                                                            cs->k, cs->n[0], weights(cs), nullptr);
+    prolong_last<float>(cs, c, len, y, s);
   } else {
     double* c = static_cast<double*>(cs->buf[0]);
     cudaMemcpyAsync(c, w, sizeof(double) * cs->ncoarse * cs->dim, cudaMemcpyDeviceToDevice, s);
     c = prolong_upper<double>(cs, c, len, s);
-    size_t outer, inner;
-    view(cs, len, 0, &outer, &inner);
-    k_prolong_add<double><<<red_grid(outer * (size_t)cs->Lf[0]), kThr, 0, s>>>(
-        c, y, nullptr, outer, cs->Lc[0], cs->Lf[0], cs->k, cs->n[0], weights(cs), nullptr);
+    prolong_last<double>(cs, c, len, y, s);
   }
-  rc = (int)cudaGetLastError();
-  return rc;
+  return (int)cudaGetLastError();
 }
 
 int coarse_apply_add(void* obj, const double* r, double* y, double* part, cudaStream_t s) {

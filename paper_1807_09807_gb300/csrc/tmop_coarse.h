@@ -40,8 +40,10 @@ int coarse_prolong(CoarseSpace* cs, const double* w, double* y, cudaStream_t s);
 int coarse_mode0(CoarseSpace* cs, double* w, double* lambda0, cudaStream_t s);
 void coarse_set_alpha(CoarseSpace* cs, double alpha);
 
-// y += P (alpha K_c)^-1 P^t r (r, y FP64 [dim][nfine]); per-block partials of
-// r . y (after the update) into part. Returns the number of partials, or -1.
+// y += P (alpha K_c)^-1 P^t r (r, y FP64 [dim][nfine]); if part is given,
+// per-block partials (at most 256) of r . P (alpha K_c)^-1 P^t r, summed on
+// the coarse grid in the sine basis, into part. Returns the number of
+// partials, or -1.
 int coarse_apply_add(void* cs, const double* r, double* y, double* part, cudaStream_t s);
 
 }  // namespace tmop

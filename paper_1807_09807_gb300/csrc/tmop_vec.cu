@@ -282,9 +282,6 @@ int minres_after_hv_rot(const double* v, const double* vprev, double* Av, const 
 // Givens rotations (Paige and Saunders), M = diag(1 / minv). The residual
 // estimate phibar is the M^-1-norm of the residual; the solve stops when it
 // falls to rtol times its initial value.
-// (DOT = false: an additive preconditioner part still updates y, and it
-// writes the partials of b . y)
-template <bool DOT>
 __global__ void k_pm_init(const double* __restrict__ b, const double* __restrict__ minv, double* r1, double* r2,
                           double* y, double* w, double* wprev, double* sol, size_t n, double* __restrict__ part) {
   double s = 0.0;
@@ -296,12 +293,10 @@ __global__ void k_pm_init(const double* __restrict__ b, const double* __restrict
     w[i] = 0.0;
     wprev[i] = 0.0;
     sol[i] = 0.0;
-    if (DOT) s = fma(bi, yi, s);
+    s = fma(bi, yi, s);
   }
-  if (DOT) {
-    s = block_sum(s);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
-  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
 __global__ void k_pm_init_scalar(double* st, double rtol, int maxit) {
@@ -329,47 +324,47 @@ __global__ void k_pm_init_scalar(double* st, double rtol, int maxit) {
   st[KS_BREAKDOWN] = 0.0;
 }
 
-__global__ void k_pm_v(double* __restrict__ v, const double* __restrict__ y, const double* __restrict__ st, size_t n) {
-  const double ib = st[KS_INV_BETA];
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    v[i] = y[i] * ib;
-}
-
-// y <- y - (beta / oldb) r1 (from the second iteration on), partials of v . y
-__global__ void k_pm_a(double* __restrict__ y, const double* __restrict__ r1, const double* __restrict__ v,
+// q <- q / beta - (beta / oldb) r1 (the r1 term from the second iteration
+// on), partials of u . q (alpha = their sum / beta)
+__global__ void k_pm_a(double* __restrict__ q, const double* __restrict__ r1, const double* __restrict__ u,
                        const double* __restrict__ st, size_t n, double* __restrict__ part) {
-  const double oldb = st[KS_OLDB];
+  const double oldb = st[KS_OLDB], ib = st[KS_INV_BETA];
   const double c = oldb > 0.0 ? st[KS_BETA] / oldb : 0.0;
   double s = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double yi = fma(-c, r1[i], y[i]);
-    y[i] = yi;
-    s = fma(v[i], yi, s);
+    const double qi = fma(-c, r1[i], q[i] * ib);
+    q[i] = qi;
+    s = fma(u[i], qi, s);
   }
   s = block_sum(s);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-// y <- y - (alpha / beta) r2; r1 <- r2; r2 <- y; y <- M^-1 r2; partials of r2 . y
-// (DOT = false: an additive preconditioner part still adds to y)
-template <bool DOT>
-__global__ void k_pm_b(const double* __restrict__ minv, double* __restrict__ r1, double* __restrict__ r2,
-                       double* __restrict__ y, const double* __restrict__ st, size_t n, double* __restrict__ part) {
+// out = (sum of the partials) * *scale
+__global__ void k_sum_scaled(const double* __restrict__ part, int np, const double* __restrict__ scale,
+                             double* __restrict__ out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) *out = s * *scale;
+}
+
+// t = q - (alpha / beta) r2 into r1's buffer (the old r1 is dead), then
+// q <- M^-1 t (diagonal part); partials of t . q
+__global__ void k_pm_b(const double* __restrict__ minv, double* __restrict__ r1, const double* __restrict__ r2,
+                       double* __restrict__ q, const double* __restrict__ st, size_t n, double* __restrict__ part) {
   const double beta = st[KS_BETA];
   const double c = beta > 0.0 ? st[KS_ALPHA] / beta : 0.0;
   double s = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double t = fma(-c, r2[i], y[i]);
-    r1[i] = r2[i];
-    r2[i] = t;
+    const double t = fma(-c, r2[i], q[i]);
+    r1[i] = t;
     const double yi = minv[i] * t;
-    y[i] = yi;
-    if (DOT) s = fma(t, yi, s);
+    q[i] = yi;
+    s = fma(t, yi, s);
   }
-  if (DOT) {
-    s = block_sum(s);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
-  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
 __global__ void k_pm_scalar(double* st) {
@@ -386,6 +381,7 @@ __global__ void k_pm_scalar(double* st) {
     st[KS_INV_BETA] = 0.0;
     return;
   }
+  st[KS_INV_BETA_OLD] = st[KS_INV_BETA];   // the direction update reads this iteration's v = u / beta
   st[KS_ITER] += 1.0;
   const double alpha = st[KS_ALPHA];
   const double beta = sqrt(fmax(st[KS_BETA_NEXT2], 0.0));
@@ -407,6 +403,9 @@ __global__ void k_pm_scalar(double* st) {
   st[KS_PHIBAR] = sn_new * phibar;
   st[KS_RESID] = fabs(sn_new * phibar);
   st[KS_INV_GAMMA] = 1.0 / gamma;
+  st[KS_WU] = st[KS_INV_BETA_OLD] / gamma;
+  st[KS_WP] = st[KS_OLDEPS] / gamma;
+  st[KS_WW] = st[KS_DELTA] / gamma;
   st[KS_INV_BETA] = beta > 0.0 ? 1.0 / beta : 0.0;
   if (fabs(sn_new * phibar) <= st[KS_TOL] || beta == 0.0) {
     st[KS_DONE] = 1.0;
@@ -414,57 +413,52 @@ __global__ void k_pm_scalar(double* st) {
   }
 }
 
-// w_k = (v - oldeps w_{k-2} - delta w_{k-1}) / gamma, x += phi w_k
-__global__ void k_pm_w(const double* __restrict__ v, double* __restrict__ w, double* __restrict__ wprev,
+// w_k = (v - oldeps w_{k-2} - delta w_{k-1}) / gamma with v = u / beta
+// (the three coefficients divided by gamma beforehand), written over
+// w_{k-2}; x += phi w_k
+__global__ void k_pm_w(const double* __restrict__ u, const double* __restrict__ w, double* __restrict__ wprev,
                        double* __restrict__ sol, const double* __restrict__ st, size_t n) {
-  const double oe = st[KS_OLDEPS], dl = st[KS_DELTA], ig = st[KS_INV_GAMMA], phi = st[KS_PHI];
+  const double ig = st[KS_INV_GAMMA], phi = st[KS_PHI];
+  const double cu = st[KS_WU], cp = st[KS_WP], cw = st[KS_WW];
   if (phi == 0.0 && ig == 0.0) return;  // frozen
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double wn = (v[i] - oe * wprev[i] - dl * w[i]) * ig;
-    wprev[i] = w[i];
-    w[i] = wn;
+    const double wn = fma(-cw, w[i], fma(-cp, wprev[i], u[i] * cu));
+    wprev[i] = wn;
     sol[i] = fma(phi, wn, sol[i]);
   }
 }
 
-int pminres_init(const double* b, const double* minv, double* r1, double* r2, double* y, double* w, double* wprev,
+int pminres_init(const double* b, const double* minv, double* r1, double* r2, double* u, double* w, double* wprev,
                  double* sol, double* st, double* part, size_t n, double rtol, int maxit, cudaStream_t s,
                  const PrecondAdd* pc) {
   int g = red_grid(n);
-  if (pc) {
-    k_pm_init<false><<<g, kThreads, 0, s>>>(b, minv, r1, r2, y, w, wprev, sol, n, part);
-    g = pc->apply(pc->obj, b, y, part, s);
-    if (g < 0) return (int)cudaErrorLaunchFailure;
-  } else {
-    k_pm_init<true><<<g, kThreads, 0, s>>>(b, minv, r1, r2, y, w, wprev, sol, n, part);
+  k_pm_init<<<g, kThreads, 0, s>>>(b, minv, r1, r2, u, w, wprev, sol, n, part);
+  if (pc) {   // u += C b, and the partials of b . C b after the diagonal part's
+    const int np = pc->apply(pc->obj, b, u, part + g, s);
+    if (np < 0) return (int)cudaErrorLaunchFailure;
+    g += np;
   }
   k_sum_final<<<1, kThreads, 0, s>>>(part, g, st + KS_BETA_NEXT2);
   k_pm_init_scalar<<<1, 1, 0, s>>>(st, rtol, maxit);
   return (int)cudaGetLastError();
 }
 
-int pminres_v(double* v, const double* y, const double* st, size_t n, cudaStream_t s) {
-  k_pm_v<<<red_grid(n), kThreads, 0, s>>>(v, y, st, n);
-  return (int)cudaGetLastError();
-}
-
-int pminres_after_hv(const double* minv, double* r1, double* r2, double* y, const double* v, double* w,
+int pminres_after_hv(const double* minv, double* r1, const double* r2, const double* u, double* q, const double* w,
                      double* wprev, double* sol, double* st, double* part, size_t n, cudaStream_t s,
                      const PrecondAdd* pc) {
   const int g = red_grid(n);
-  k_pm_a<<<g, kThreads, 0, s>>>(y, r1, v, st, n, part);
-  k_sum_final<<<1, kThreads, 0, s>>>(part, g, st + KS_ALPHA);
+  k_pm_a<<<g, kThreads, 0, s>>>(q, r1, u, st, n, part);
+  k_sum_scaled<<<1, kThreads, 0, s>>>(part, g, st + KS_INV_BETA, st + KS_ALPHA);
   int g2 = g;
-  if (pc) {
-    k_pm_b<false><<<g, kThreads, 0, s>>>(minv, r1, r2, y, st, n, part);
-    g2 = pc->apply(pc->obj, r2, y, part, s);
-    if (g2 < 0) return (int)cudaErrorLaunchFailure;
-  } else {
-    k_pm_b<true><<<g, kThreads, 0, s>>>(minv, r1, r2, y, st, n, part);
+  k_pm_b<<<g, kThreads, 0, s>>>(minv, r1, r2, q, st, n, part);
+  if (pc) {   // q += C t (t now in r1's buffer), and the partials of t . C t after the diagonal part's
+    const int np = pc->apply(pc->obj, r1, q, part + g, s);
+    if (np < 0) return (int)cudaErrorLaunchFailure;
+    g2 += np;
   }
   k_sum_final<<<1, kThreads, 0, s>>>(part, g2, st + KS_BETA_NEXT2);
   k_pm_scalar<<<1, 1, 0, s>>>(st);
-  k_pm_w<<<g, kThreads, 0, s>>>(v, w, wprev, sol, st, n);
+  k_pm_w<<<g, kThreads, 0, s>>>(u, w, wprev, sol, st, n);
   return (int)cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@ enum {
   KS_SV, KS_SVP, KS_SW,
   // preconditioned MINRES
   KS_OLDB, KS_DBAR, KS_EPSLN, KS_OLDEPS, KS_PHIBAR, KS_CS, KS_SN, KS_DELTA, KS_INV_GAMMA, KS_INV_BETA,
+  KS_INV_BETA_OLD, KS_WU, KS_WP, KS_WW,   // direction update coefficients of u, w_{k-2}, w_{k-1}
   KS_COUNT
 };
 
@@ -46,19 +47,25 @@ int minres_after_hv_rot(const double* v, const double* vprev, double* Av, const 
                         int vdot_np = 0);
 // Preconditioned MINRES (M^-1 = minv, a diagonal): r1, r2, y, v, w, wprev, sol
 // An additive part of the preconditioner beside the diagonal minv: y += C r,
-// with the per-block partials of r . y (after the update) written to part;
-// apply returns the number of partials, or -1 on a launch error.
+// with the per-block partials of r . (C r) written to part (at most
+// kMaxRedBlocks of them; they are summed with the diagonal part's partials
+// of r . (minv r)); apply returns the number of partials, or -1 on a launch
+// error.
 struct PrecondAdd {
   int (*apply)(void* obj, const double* r, double* y, double* part, cudaStream_t s);
   void* obj;
 };
-int pminres_init(const double* b, const double* minv, double* r1, double* r2, double* y, double* w, double* wprev,
+// Preconditioned MINRES on rotating buffers. The Lanczos vector is kept
+// unnormalised: u = beta v, and the product runs on u (q = H u). Per
+// iteration: pminres_after_hv writes the new residual-direction vector into
+// r1's buffer, the new u = M^-1 r into q's buffer and the new direction into
+// wprev's buffer, so the caller then swaps (r1, r2), (u, q) and (w, wprev).
+// Initially r1 = r2 = b, u = M^-1 b, w = wprev = sol = 0.
+int pminres_init(const double* b, const double* minv, double* r1, double* r2, double* u, double* w, double* wprev,
                  double* sol, double* st, double* part, size_t n, double rtol, int maxit, cudaStream_t s,
                  const PrecondAdd* pc = nullptr);
-// before the product: v = y / beta
-int pminres_v(double* v, const double* y, const double* st, size_t n, cudaStream_t s);
-// after the product y = H v
-int pminres_after_hv(const double* minv, double* r1, double* r2, double* y, const double* v, double* w,
+// after the product q = H u
+int pminres_after_hv(const double* minv, double* r1, const double* r2, const double* u, double* q, const double* w,
                      double* wprev, double* sol, double* st, double* part, size_t n, cudaStream_t s,
                      const PrecondAdd* pc = nullptr);
 int cg_init(const double* b, double* r, double* d, double* sol, double* st, double* part, size_t n, double rtol,
