@@ -271,9 +271,13 @@ __device__ __forceinline__ void pac_adj(const float2 (&tBG)[Q1 * N], float* P0, 
   __syncwarp();
 }
 
-// v and the fixed flags at the nodes this lane gathers
+// v (rounded to FP32 as it arrives: the product's input, and half the
+// registers of the prefetched copy) and the fixed flags at the nodes this
+// lane gathers. Hardware conversions: this kernel is bound by instruction
+// issue and leaves the FP64 pipe mostly idle, so one F2F beats the ~20
+// integer instructions of f64_to_f32.
 template <int N, int NT>
-__device__ __forceinline__ void fetch_v(const KParams& p, const NodeMap<N>& m, int lane, double (&v)[NT][3],
+__device__ __forceinline__ void fetch_v(const KParams& p, const NodeMap<N>& m, int lane, float (&v)[NT][3],
                                         unsigned& fmask) {
   constexpr int NDOF = N * N * N;
   fmask = 0u;
@@ -285,7 +289,7 @@ __device__ __forceinline__ void fetch_v(const KParams& p, const NodeMap<N>& m, i
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const size_t dof = (size_t)c * p.nnode + g;
-        v[s][c] = __ldg(p.v + dof);
+        v[s][c] = __double2float_rn(__ldg(p.v + dof));
         if (p.fixed && __ldg(p.fixed + dof)) fmask |= 1u << (s * 3 + c);
       }
     }
@@ -382,10 +386,12 @@ __global__ void __launch_bounds__(kPacWarps * 32, N == 4 ? 2 : 0) pac_kernel(con
 
   NodeMap<N> cur(p.elem_nodes, p.sx, p.sy), nxt(p.elem_nodes, p.sx, p.sy);
   cur.element(e, NDOF);
-  double v[NT][3], vc[NT][3];
+  float v[NT][3], vc[NT][3];
   unsigned fnext;
   float hq[kCompactRec];
-  double vdot = 0.0;  // sum over this warp's elements of v_E . (H_E v_E), FP64
+  // sum over this warp's elements of v_E . (H_E v_E): each lane's share of
+  // an element in FP32 (v_E as the product reads it, FP32), the elements in FP64
+  double vdot = 0.0;
   fetch_v<N, NT>(p, cur, lane, v, fnext);
   fetch_rec<QP>(rec, p.pa_stride, e, lane, hq);
   for (;;) {
@@ -402,11 +408,8 @@ __global__ void __launch_bounds__(kPacWarps * 32, N == 4 ? 2 : 0) pac_kernel(con
       if (t < NDOF) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          vc[s][c] = (fcur >> (s * 3 + c)) & 1u ? 0.0 : v[s][c];
-          // hardware conversions here: this kernel is bound by instruction
-          // issue and leaves the FP64 pipe two-thirds idle, so one F2F beats
-          // the ~20 integer instructions of f64_to_f32 (0.350 -> 0.336 ms)
-          P0[c * L::XC + (t / N) * L::XR + t % N] = __double2float_rn(vc[s][c]);
+          vc[s][c] = (fcur >> (s * 3 + c)) & 1u ? 0.f : v[s][c];
+          P0[c * L::XC + (t / N) * L::XR + t % N] = vc[s][c];
         }
       }
     }
@@ -437,6 +440,7 @@ __global__ void __launch_bounds__(kPacWarps * 32, N == 4 ? 2 : 0) pac_kernel(con
     __syncwarp();
     // ---- adjoint contraction into y (buffer 0), scatter
     pac_adj<N, Q1, L>(tBG, P0, P1, lane);
+    float vdot_e = 0.f;
 #pragma unroll
     for (int s = 0; s < NT; ++s) {
       const int t = lane + 32 * s;
@@ -444,12 +448,13 @@ __global__ void __launch_bounds__(kPacWarps * 32, N == 4 ? 2 : 0) pac_kernel(con
         const int g = cur(t);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const double yc = (double)P0[c * L::XC + (t / N) * L::XR + t % N];
-          vdot = fma(vc[s][c], yc, vdot);  // 0 at fixed dofs (vc = 0 there)
-          if (!((fcur >> (s * 3 + c)) & 1u)) atomicAdd(p.y + (size_t)c * p.nnode + g, yc);
+          const float yf = P0[c * L::XC + (t / N) * L::XR + t % N];
+          vdot_e = fmaf(vc[s][c], yf, vdot_e);  // 0 at fixed dofs (vc = 0 there)
+          if (!((fcur >> (s * 3 + c)) & 1u)) atomicAdd(p.y + (size_t)c * p.nnode + g, (double)yf);
         }
       }
     }
+    vdot += (double)vdot_e;
     __syncwarp();
     if (!more) break;
     ei = eni;
