@@ -709,10 +709,14 @@ def _event_ms(fn, reps, stream, flush=None):
 def measure_pa(tm, m, x, v, y, flush, stream, args):
     """Linearize (once per Newton step) and the partially assembled Hessian
     action (once per Krylov iteration), FP64 and FP32, with the HBM roofline
-    of the FP32 product: it reads the stored values (the 14-value compact
-    record or the dim^2 (dim^2+1)/2 packed Hessian entries, FP32, per point)
-    and v, and writes y. In 3D the packed form is also timed on the same mesh
-    with mu302, whose Hessian is not written in (|T|^2, det T)."""
+    of the FP32 product. The product is timed in the form the Krylov solves
+    run it, y += H v into a buffer their previous vector pass zeroed
+    (tmop_hess_apply_pa_add: the product kernel alone); it reads the stored
+    values (the 14-value compact record or the dim^2 (dim^2+1)/2 packed
+    Hessian entries, FP32, per point) and v, and reads and writes y. The
+    zeroing form (memset + kernel, tmop_hess_apply_pa) is timed beside it. In
+    3D the packed form is also timed on the same mesh with mu302, whose
+    Hessian is not written in (|T|^2, det T)."""
     import torch
     peaks = measured_peaks()
     out = {}
@@ -725,15 +729,18 @@ def measure_pa(tm, m, x, v, y, flush, stream, args):
         c.hess_apply_pa(v, out=y)
         torch.cuda.synchronize()
         lin_ms = _event_ms(lambda: c.linearize(x), 2, stream, flush)
-        hv_ms = _event_ms(lambda: c.hess_apply_pa(v, out=y), max(3, min(args.steps, 10)), stream, flush)
+        reps = max(3, min(args.steps, 10))
+        hv_ms = _event_ms(lambda: c.hess_apply_pa(v, out=y, accumulate=True), reps, stream, flush)
+        hv0_ms = _event_ms(lambda: c.hess_apply_pa(v, out=y), reps, stream, flush)
         dd = m.dim * m.dim
         ns, _, elt = c.pa_layout()     # packed Hessian entries or compact record values per point
         compact = ns != dd * (dd + 1) // 2
-        nbytes = m.n_qp * ns * elt + 2 * x.numel() * 8 + x.numel() * 8   # stored values + v read + y memset/write
+        nbytes = m.n_qp * ns * elt + 3 * x.numel() * 8   # stored values + v read + y read and written
         n = m.order + 1
         fwd, adj = contraction_fmas(m.dim, n, m.nq, m.dim)
         flops = m.nelem * (2 * (fwd + adj) + 2 * dd * dd * m.Q)   # contractions + the d^2 x d^2 product
-        ent = {"linearize_ms": lin_ms, "hess_pa_ms": hv_ms, "bytes_per_launch": nbytes,
+        ent = {"linearize_ms": lin_ms, "hess_pa_ms": hv_ms, "hess_pa_zeroing_ms": hv0_ms,
+               "product_form": "y += H v (tmop_hess_apply_pa_add, as in the Krylov loops)", "bytes_per_launch": nbytes,
                "achieved_GBps": nbytes / (hv_ms * 1e-3) / 1e9, "achieved_TFLOPs": flops / (hv_ms * 1e-3) / 1e12}
         if pf == tm.FP64:
             alu = getattr(args, "_alu_peaks", None)

@@ -153,6 +153,13 @@ int tmop_linearize(tmop_ctx* ctx, const double* x, void* stream);
  * TMOP_ERR_ARG if the context holds no linearisation. Asynchronous. */
 int tmop_hess_apply_pa(tmop_ctx* ctx, const double* v, double* y, void* stream);
 
+/* y += H(x) v at the free dofs (y unchanged at the fixed ones), with the
+ * Hessians stored by the last tmop_linearize(x): tmop_hess_apply_pa without
+ * zeroing y first. The Krylov solves use this form on a buffer that their
+ * previous vector pass left zero. TMOP_ERR_ARG if the context holds no
+ * linearisation. Asynchronous. */
+int tmop_hess_apply_pa_add(tmop_ctx* ctx, const double* v, double* y, void* stream);
+
 /* Layout of the stored linearisation: values per quadrature point (the
  * packed upper triangle of the d^2 x d^2 A-space Hessian, 10 in 2D and 45 in
  * 3D; or, for a 3D FP32 context with an (|T|^2, det T) metric, a constant

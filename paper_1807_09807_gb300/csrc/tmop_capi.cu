@@ -255,8 +255,9 @@ JacParams jac_params(const tmop_ctx* c, const double* x, double* J) {
   return jp;
 }
 
+// accumulate: y += the scatter op's result (y not zeroed first)
 int launch_op(tmop_ctx* c, int op, const double* x, const double* v, double* y, double* elem_min,
-              cudaStream_t s, double* vdot = nullptr) {
+              cudaStream_t s, double* vdot = nullptr, bool accumulate = false) {
   KParams p = c->base;
   p.x = x;
   p.v = v;
@@ -265,7 +266,7 @@ int launch_op(tmop_ctx* c, int op, const double* x, const double* v, double* y, 
   p.part_F = c->d_part;
   p.part_min = c->d_part + kMaxRedBlocks;
   p.pa = c->d_pa;
-  if (op == OP_GRADIENT || op == OP_HESS || op == OP_HESS_PA)
+  if ((op == OP_GRADIENT || op == OP_HESS || op == OP_HESS_PA) && !accumulate)
     CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * c->ndof, s));
   int kop = op;  // the stored linearisation decides which form of the pair runs
   if (c->pa_compact && op == OP_LINEARIZE) kop = OP_LINEARIZE_C;
@@ -513,10 +514,10 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
   if (cg) {
     if (cg_init(b, k0, k1, p, st, part, n, o.krylov_rtol, o.krylov_maxit, s)) return TMOP_ERR_CUDA;
   } else if (minv) {  // r1 = k0, r2 = k1, u = k2 (product into q = k3), w = k4, wprev = k5
-    if (pminres_init(b, minv, k0, k1, k2, k4, k5, p, st, part, n, o.krylov_rtol, o.krylov_maxit, s, pc))
+    if (pminres_init(b, minv, k0, k1, k2, k3, k4, k5, p, st, part, n, o.krylov_rtol, o.krylov_maxit, s, pc))
       return TMOP_ERR_CUDA;
   } else {
-    if (minres_init(b, k0, k1, k3, k4, p, st, part, n, o.krylov_rtol, o.krylov_maxit, s)) return TMOP_ERR_CUDA;
+    if (minres_init(b, k0, k1, k2, k3, k4, p, st, part, n, o.krylov_rtol, o.krylov_maxit, s)) return TMOP_ERR_CUDA;
   }
   // the compact-record product also returns v . (H v) (not with the restricted-movement term, whose
   // contribution it does not see)
@@ -534,7 +535,7 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
         const bool ev = j % 2 == 0;
         double *r1 = ev ? k0 : k1, *r2 = ev ? k1 : k0, *u = ev ? k2 : k3, *hu = ev ? k3 : k2;
         double *w = ev ? k4 : k5, *wp = ev ? k5 : k4;
-        r = launch_op(c, hop, x, u, hu, nullptr, q);
+        r = launch_op(c, hop, x, u, hu, nullptr, q, nullptr, true);   // hu was left zero
         if (r) return r;
         if (pminres_after_hv(minv, r1, r2, u, hu, w, wp, p, st, part, n, q, pc)) return TMOP_ERR_CUDA;
         continue;
@@ -549,7 +550,7 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
         const int iv = (3 - j % 3) % 3;
         double *v = V[iv], *vprev = V[(iv + 1) % 3], *Av = V[(iv + 2) % 3];
         double *w = W[j % 2], *wp = W[(j + 1) % 2];
-        r = launch_op(c, hop, x, v, Av, nullptr, q, vdot);
+        r = launch_op(c, hop, x, v, Av, nullptr, q, vdot, true);   // Av was left zero
         if (r) return r;
         if (minres_after_hv_rot(v, vprev, Av, w, wp, p, st, part, n, q, vdot, vdot_np)) return TMOP_ERR_CUDA;
       }
@@ -1111,6 +1112,12 @@ int tmop_hess_apply_pa(tmop_ctx* c, const double* v, double* y, void* stream) {
   if (!c || !v || !y) return TMOP_ERR_ARG;
   if (!c->pa_valid) return TMOP_ERR_ARG;
   return launch_op(c, OP_HESS_PA, nullptr, v, y, nullptr, (cudaStream_t)stream);
+}
+
+int tmop_hess_apply_pa_add(tmop_ctx* c, const double* v, double* y, void* stream) {
+  if (!c || !v || !y) return TMOP_ERR_ARG;
+  if (!c->pa_valid) return TMOP_ERR_ARG;
+  return launch_op(c, OP_HESS_PA, nullptr, v, y, nullptr, (cudaStream_t)stream, nullptr, true);
 }
 
 int tmop_pa_layout(const tmop_ctx* c, int* values_per_point, int* stride, int* elt_bytes) {

@@ -129,13 +129,14 @@ int step(const double* x, const double* p, double alpha, double* y, size_t n, cu
 
 // ---------------------------------------------------------------- MINRES
 // v = b / beta1, vprev = w = wprev = sol = 0 and the rotation state.
-__global__ void k_minres_init(const double* __restrict__ b, double* v, double* vprev, double* w, double* wprev,
-                              double* sol, double* st, size_t n, double rtol, int maxit) {
+__global__ void k_minres_init(const double* __restrict__ b, double* v, double* vprev, double* Av, double* w,
+                              double* wprev, double* sol, double* st, size_t n, double rtol, int maxit) {
   const double beta1 = sqrt(st[KS_BETA_NEXT2]);
   const double inv = beta1 > 0.0 ? 1.0 / beta1 : 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     v[i] = b[i] * inv;
     vprev[i] = 0.0;
+    Av[i] = 0.0;
     w[i] = 0.0;
     wprev[i] = 0.0;
     sol[i] = 0.0;
@@ -159,8 +160,9 @@ __global__ void k_minres_init(const double* __restrict__ b, double* v, double* v
 // The next Lanczos vector, unnormalised, over Av, with per-block partials of
 // its squared norm. The arrays hold v / sv, vprev / svp and H (v / sv), so
 // H v - alpha v - beta vprev = sv Av - (alpha sv) v - (beta svp) vprev, and
-// alpha = v . H v = sv^2 (v array . Av) from the sum in st[KS_ALPHA].
-__global__ void k_lanczos(double* __restrict__ Av, const double* __restrict__ v, const double* __restrict__ vprev,
+// alpha = v . H v = sv^2 (v array . Av) from the sum in st[KS_ALPHA]. vprev
+// is read here for the last time and zeroed: it is the next product's output.
+__global__ void k_lanczos(double* __restrict__ Av, const double* __restrict__ v, double* __restrict__ vprev,
                           const double* __restrict__ st, size_t n, double* __restrict__ part) {
   const double sv = st[KS_SV];
   const double av = st[KS_ALPHA] * sv * sv * sv, bv = st[KS_BETA] * st[KS_SVP];
@@ -168,6 +170,7 @@ __global__ void k_lanczos(double* __restrict__ Av, const double* __restrict__ v,
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const double r = fma(sv, Av[i], -av * v[i]) - bv * vprev[i];
     Av[i] = r;
+    vprev[i] = 0.0;
     s = fma(r, r, s);
   }
   s = block_sum(s);
@@ -238,12 +241,12 @@ __global__ void k_minres_scalar(const double* __restrict__ part, int np, double*
 // k_minres_vec_rot. (Once KS_DONE is set, phi = 0 keeps sol fixed and the
 // next Lanczos vector is 0, so every later product is zero.)
 
-int minres_init(const double* b, double* v, double* vprev, double* w, double* wprev, double* sol, double* st,
-                double* part, size_t n, double rtol, int maxit, cudaStream_t s) {
+int minres_init(const double* b, double* v, double* vprev, double* Av, double* w, double* wprev, double* sol,
+                double* st, double* part, size_t n, double rtol, int maxit, cudaStream_t s) {
   int g = red_grid(n);
   k_dot_part<<<g, kThreads, 0, s>>>(b, b, n, part);
   k_sum_final<<<1, kThreads, 0, s>>>(part, g, st + KS_BETA_NEXT2);
-  k_minres_init<<<g, kThreads, 0, s>>>(b, v, vprev, w, wprev, sol, st, n, rtol, maxit);
+  k_minres_init<<<g, kThreads, 0, s>>>(b, v, vprev, Av, w, wprev, sol, st, n, rtol, maxit);
   return (int)cudaGetLastError();
 }
 
@@ -262,7 +265,7 @@ __global__ void k_minres_vec_rot(const double* __restrict__ v, const double* __r
   }
 }
 
-int minres_after_hv_rot(const double* v, const double* vprev, double* Av, const double* w, double* wp, double* sol,
+int minres_after_hv_rot(const double* v, double* vprev, double* Av, const double* w, double* wp, double* sol,
                         double* st, double* part, size_t n, cudaStream_t s, const double* vdot, int vdot_np) {
   int g = red_grid(n);
   if (vdot) {  // alpha = v . (H v) from the product kernel's own partials
@@ -283,13 +286,15 @@ int minres_after_hv_rot(const double* v, const double* vprev, double* Av, const 
 // estimate phibar is the M^-1-norm of the residual; the solve stops when it
 // falls to rtol times its initial value.
 __global__ void k_pm_init(const double* __restrict__ b, const double* __restrict__ minv, double* r1, double* r2,
-                          double* y, double* w, double* wprev, double* sol, size_t n, double* __restrict__ part) {
+                          double* y, double* q, double* w, double* wprev, double* sol, size_t n,
+                          double* __restrict__ part) {
   double s = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const double bi = b[i], yi = minv[i] * bi;
     r1[i] = bi;
     r2[i] = bi;
     y[i] = yi;
+    q[i] = 0.0;
     w[i] = 0.0;
     wprev[i] = 0.0;
     sol[i] = 0.0;
@@ -415,24 +420,29 @@ __global__ void k_pm_scalar(double* st) {
 
 // w_k = (v - oldeps w_{k-2} - delta w_{k-1}) / gamma with v = u / beta
 // (the three coefficients divided by gamma beforehand), written over
-// w_{k-2}; x += phi w_k
-__global__ void k_pm_w(const double* __restrict__ u, const double* __restrict__ w, double* __restrict__ wprev,
+// w_{k-2}; x += phi w_k. u is read here for the last time and zeroed: it is
+// the next product's output (also once frozen, so that the frozen
+// iterations' products stay bounded).
+__global__ void k_pm_w(double* __restrict__ u, const double* __restrict__ w, double* __restrict__ wprev,
                        double* __restrict__ sol, const double* __restrict__ st, size_t n) {
   const double ig = st[KS_INV_GAMMA], phi = st[KS_PHI];
   const double cu = st[KS_WU], cp = st[KS_WP], cw = st[KS_WW];
-  if (phi == 0.0 && ig == 0.0) return;  // frozen
+  const bool frozen = phi == 0.0 && ig == 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double wn = fma(-cw, w[i], fma(-cp, wprev[i], u[i] * cu));
-    wprev[i] = wn;
-    sol[i] = fma(phi, wn, sol[i]);
+    if (!frozen) {
+      const double wn = fma(-cw, w[i], fma(-cp, wprev[i], u[i] * cu));
+      wprev[i] = wn;
+      sol[i] = fma(phi, wn, sol[i]);
+    }
+    u[i] = 0.0;
   }
 }
 
-int pminres_init(const double* b, const double* minv, double* r1, double* r2, double* u, double* w, double* wprev,
-                 double* sol, double* st, double* part, size_t n, double rtol, int maxit, cudaStream_t s,
-                 const PrecondAdd* pc) {
+int pminres_init(const double* b, const double* minv, double* r1, double* r2, double* u, double* q, double* w,
+                 double* wprev, double* sol, double* st, double* part, size_t n, double rtol, int maxit,
+                 cudaStream_t s, const PrecondAdd* pc) {
   int g = red_grid(n);
-  k_pm_init<<<g, kThreads, 0, s>>>(b, minv, r1, r2, u, w, wprev, sol, n, part);
+  k_pm_init<<<g, kThreads, 0, s>>>(b, minv, r1, r2, u, q, w, wprev, sol, n, part);
   if (pc) {   // u += C b, and the partials of b . C b after the diagonal part's
     const int np = pc->apply(pc->obj, b, u, part + g, s);
     if (np < 0) return (int)cudaErrorLaunchFailure;
@@ -443,7 +453,7 @@ int pminres_init(const double* b, const double* minv, double* r1, double* r2, do
   return (int)cudaGetLastError();
 }
 
-int pminres_after_hv(const double* minv, double* r1, const double* r2, const double* u, double* q, const double* w,
+int pminres_after_hv(const double* minv, double* r1, const double* r2, double* u, double* q, const double* w,
                      double* wprev, double* sol, double* st, double* part, size_t n, cudaStream_t s,
                      const PrecondAdd* pc) {
   const int g = red_grid(n);

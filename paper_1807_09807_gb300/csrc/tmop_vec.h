@@ -35,14 +35,18 @@ int energy_final(const double* pf, const double* pm, int np, const double* pf2, 
 int step(const double* x, const double* p, double alpha, double* y, size_t n, cudaStream_t s);
 // out = a * b elementwise
 int vec_mul(const double* a, const double* b, double* out, size_t n, cudaStream_t s);
-int minres_init(const double* b, double* v, double* vprev, double* w, double* wprev, double* sol, double* st,
-                double* part, size_t n, double rtol, int maxit, cudaStream_t s);
+// (Av: the first product's output buffer, zeroed here; every later product
+// accumulates into the buffer the Lanczos step of the previous iteration
+// zeroed)
+int minres_init(const double* b, double* v, double* vprev, double* Av, double* w, double* wprev, double* sol,
+                double* st, double* part, size_t n, double rtol, int maxit, cudaStream_t s);
 // one MINRES step after Av = H v, on rotating buffers: afterwards (v, vprev, Av) -> (Av, v, vprev),
 // (w, wp) -> (wp, w);
 // Av is the product of the stored v array (not of the scaled vector); vdot (vdot_np partials of
 // v array . Av from the product kernel) replaces the dot-product pass when given. The new Lanczos
-// vector is left in Av unnormalised, its scale in st[KS_SV].
-int minres_after_hv_rot(const double* v, const double* vprev, double* Av, const double* w, double* wp, double* sol,
+// vector is left in Av unnormalised, its scale in st[KS_SV]; vprev is zeroed (the next product
+// accumulates into it).
+int minres_after_hv_rot(const double* v, double* vprev, double* Av, const double* w, double* wp, double* sol,
                         double* st, double* part, size_t n, cudaStream_t s, const double* vdot = nullptr,
                         int vdot_np = 0);
 // Preconditioned MINRES (M^-1 = minv, a diagonal): r1, r2, y, v, w, wprev, sol
@@ -60,12 +64,14 @@ struct PrecondAdd {
 // iteration: pminres_after_hv writes the new residual-direction vector into
 // r1's buffer, the new u = M^-1 r into q's buffer and the new direction into
 // wprev's buffer, so the caller then swaps (r1, r2), (u, q) and (w, wprev).
-// Initially r1 = r2 = b, u = M^-1 b, w = wprev = sol = 0.
-int pminres_init(const double* b, const double* minv, double* r1, double* r2, double* u, double* w, double* wprev,
-                 double* sol, double* st, double* part, size_t n, double rtol, int maxit, cudaStream_t s,
-                 const PrecondAdd* pc = nullptr);
+// Initially r1 = r2 = b, u = M^-1 b, q = w = wprev = sol = 0. The product
+// accumulates into q: the direction pass zeroes u once it has read it, so
+// the next iteration's q starts at zero.
+int pminres_init(const double* b, const double* minv, double* r1, double* r2, double* u, double* q, double* w,
+                 double* wprev, double* sol, double* st, double* part, size_t n, double rtol, int maxit,
+                 cudaStream_t s, const PrecondAdd* pc = nullptr);
 // after the product q = H u
-int pminres_after_hv(const double* minv, double* r1, const double* r2, const double* u, double* q, const double* w,
+int pminres_after_hv(const double* minv, double* r1, const double* r2, double* u, double* q, const double* w,
                      double* wprev, double* sol, double* st, double* part, size_t n, cudaStream_t s,
                      const PrecondAdd* pc = nullptr);
 int cg_init(const double* b, double* r, double* d, double* sol, double* st, double* part, size_t n, double rtol,

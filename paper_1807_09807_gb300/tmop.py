@@ -79,6 +79,7 @@ _SIGNATURES = {
     "tmop_element_min_detA": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_linearize": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_hess_apply_pa": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "tmop_hess_apply_pa_add": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_hessian_diagonal": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_pa_layout": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "tmop_sizes": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
@@ -367,15 +368,19 @@ class Context:
         if rc != OK:
             raise TmopError(rc, "tmop_linearize")
 
-    def hess_apply_pa(self, v, out=None):
-        """y = H v with the Hessians of the last linearize()."""
+    def hess_apply_pa(self, v, out=None, accumulate=False):
+        """y = H v with the Hessians of the last linearize(); accumulate: y += H v
+        into `out` (tmop_hess_apply_pa_add: y is not zeroed first)."""
         import torch
         _check_vec(v, self.shape, "v")
+        if accumulate and out is None:
+            raise ValueError("accumulate needs out")
         y = torch.empty_like(v) if out is None else out
         _check_vec(y, self.shape, "y")
-        rc = load().tmop_hess_apply_pa(self._h, _ptr(v), _ptr(y), _stream())
+        fn = "tmop_hess_apply_pa_add" if accumulate else "tmop_hess_apply_pa"
+        rc = getattr(load(), fn)(self._h, _ptr(v), _ptr(y), _stream())
         if rc != OK:
-            raise TmopError(rc, "tmop_hess_apply_pa")
+            raise TmopError(rc, fn)
         return y
 
     def pa_layout(self):

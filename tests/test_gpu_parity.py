@@ -488,6 +488,12 @@ def test_fp32_stored_hessian_product_3d(tm, order, nq, nx, structured):
     y = host(c32.hess_apply_pa(dev(v)))
     assert rel(y, yo) <= 1e-5, rel(y, yo)
     assert np.all(y[m.fixed == 1] == 0.0)
+    # the accumulating form: y0 + H v at the free dofs, y0 kept at the fixed ones
+    y0 = rng.standard_normal(m.x.shape)
+    ya = host(c32.hess_apply_pa(dev(v), out=dev(y0), accumulate=True))
+    free = m.fixed == 0
+    assert np.all(ya[~free] == y0[~free])
+    assert np.abs(ya[free] - (y0[free] + y[free])).max() <= 1e-12 * (np.abs(y0).max() + np.abs(y).max())
 
 
 @pytest.mark.parametrize("case", ["mu14", "mu1", "W", "mu302", "mu98", "composite", "per_point_W", "bulk"])
