@@ -516,11 +516,13 @@ def run_ours(args):
         net.close()
         return 0
     if args.kernels_only and args.profile == "pa":
-        # the partially assembled product alone: one linearisation, then W + K products
+        # the partially assembled product alone, in the form the Krylov loops run
+        # it (y += H v): one linearisation, then W + K products
         ctx.linearize(x)
+        y.zero_()
         for _ in range(args.warmup + args.steps):
             flush.fill_(1.0)
-            ctx.hess_apply_pa(v, out=y)
+            ctx.hess_apply_pa(v, out=y, accumulate=True)
         torch.cuda.synchronize()
         return 0
     for _ in range(args.warmup):

@@ -130,6 +130,15 @@ int tmop_energy_device(tmop_ctx* ctx, const double* x, double* F, double* min_de
  * barrier metric; check tmop_energy first. */
 int tmop_gradient(tmop_ctx* ctx, const double* x, double* g, void* stream);
 
+/* The gradient (as tmop_gradient, g: DEVICE [d][nnode], overwritten) and F
+ * and min det A (as tmop_energy_device: DEVICE pointers, one double each) of
+ * the same x in one element pass where the context allows it (not with
+ * tmop_set_deterministic or the restricted-movement term, and FP64 element
+ * kernels: TMOP_FP64 or TMOP_FP32_MIXED), else the two passes one after the
+ * other; the results agree with the separate calls up to the order of the
+ * sums. The Newton line search uses it at every trial. Asynchronous. */
+int tmop_energy_gradient(tmop_ctx* ctx, const double* x, double* g, double* F, double* min_detA, void* stream);
+
 /* Hessian action y = (d^2 F_V / dx^2)(x) v (Section 3.4: second derivatives
  * of mu with respect to T): y_{i,a} = sum_E sum_q w_q det W
  * [ (d^2mu/dT^2 : dT) W^-t grad w_i ]_a with dT = (sum_j v_j grad w_j) W^-1,

@@ -266,13 +266,13 @@ int launch_op(tmop_ctx* c, int op, const double* x, const double* v, double* y, 
   p.part_F = c->d_part;
   p.part_min = c->d_part + kMaxRedBlocks;
   p.pa = c->d_pa;
-  if ((op == OP_GRADIENT || op == OP_HESS || op == OP_HESS_PA) && !accumulate)
+  if ((op == OP_GRADIENT || op == OP_HESS || op == OP_HESS_PA || op == OP_ENERGY_GRAD) && !accumulate)
     CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * c->ndof, s));
   int kop = op;  // the stored linearisation decides which form of the pair runs
   if (c->pa_compact && op == OP_LINEARIZE) kop = OP_LINEARIZE_C;
   if (c->pa_compact && op == OP_HESS_PA) kop = OP_HESS_PA_C;
   p.vdot = kop == OP_HESS_PA_C ? vdot : nullptr;
-  const bool scatter = op == OP_GRADIENT || op == OP_HESS || op == OP_HESS_PA;
+  const bool scatter = op == OP_GRADIENT || op == OP_HESS || op == OP_HESS_PA || op == OP_ENERGY_GRAD;
   // deterministic scatter: one launch per colour, in colour order
   const int passes = (c->det && scatter) ? c->ncolour : 1;
   for (int k = 0; k < passes; ++k) {
@@ -311,6 +311,28 @@ int energy_async(tmop_ctx* c, const double* x, cudaStream_t s, double* outF = nu
     extra = mp.part;
   }
   if (energy_final(c->d_part, c->d_part + kMaxRedBlocks, c->grid[OP_ENERGY], extra, c->mass_grid,
+                   outF ? outF : c->d_res, outMin ? outMin : c->d_res + 1, s))
+    return TMOP_ERR_CUDA;
+  return TMOP_OK;
+}
+
+// The fused energy + gradient pass (one element pass instead of two): not in
+// the deterministic mode (whose per-colour launches would each overwrite the
+// energy partials) nor with the restricted-movement term (its own kernels).
+bool fused_energy_grad(const tmop_ctx* c) { return c->ent[OP_ENERGY_GRAD] && !c->det && c->delta == 0.0; }
+
+// g = dF/dx and (F, min det A) into device memory (d_res[0..1] by default),
+// asynchronously: one fused pass, or the two separate ones.
+int energy_grad_async(tmop_ctx* c, const double* x, double* g, cudaStream_t s, double* outF = nullptr,
+                      double* outMin = nullptr) {
+  if (!fused_energy_grad(c)) {
+    int rc = energy_async(c, x, s, outF, outMin);
+    if (rc) return rc;
+    return launch_op(c, OP_GRADIENT, x, nullptr, g, nullptr, s);
+  }
+  int rc = launch_op(c, OP_ENERGY_GRAD, x, nullptr, g, nullptr, s);
+  if (rc) return rc;
+  if (energy_final(c->d_part, c->d_part + kMaxRedBlocks, c->grid[OP_ENERGY_GRAD], nullptr, 0,
                    outF ? outF : c->d_res, outMin ? outMin : c->d_res + 1, s))
     return TMOP_ERR_CUDA;
   return TMOP_OK;
@@ -622,13 +644,22 @@ int newton_iter(tmop_ctx* c, const tmop_newton_opts& o, NewtonState* ns, tmop_ne
   for (int h = 0; h <= o.max_halvings; ++h, alpha *= o.alpha_shrink) {
     if (step(ns->x, p, alpha, ns->xt, c->ndof, s)) return TMOP_ERR_CUDA;
     double Ft, mdt;
-    rc = energy_host(c, ns->xt, &Ft, &mdt, s);
+    // the trial's energy, and with the fused pass its gradient too (wasted
+    // only when the trial is rejected)
+    const bool fused = fused_energy_grad(c);
+    rc = fused ? energy_grad_async(c, ns->xt, ns->gt, s) : energy_async(c, ns->xt, s);
     if (rc) return rc;
+    rc = read_res(c, 0, 2, s);
+    if (rc) return rc;
+    Ft = c->h_res[0];
+    mdt = c->h_res[1];
     // the new configuration must be valid (det A > 0 everywhere) and F may
     // grow by at most the f_factor
     if (!(mdt > 0.0) || !(Ft < o.f_factor * ns->F)) continue;
-    rc = launch_op(c, OP_GRADIENT, ns->xt, nullptr, ns->gt, nullptr, s);
-    if (rc) return rc;
+    if (!fused) {
+      rc = launch_op(c, OP_GRADIENT, ns->xt, nullptr, ns->gt, nullptr, s);
+      if (rc) return rc;
+    }
     double gn;
     rc = norm_host(c, ns->gt, &gn, s);
     if (rc) return rc;
@@ -652,11 +683,13 @@ int newton_start(tmop_ctx* c, double* x, NewtonState* ns, cudaStream_t s) {
   ns->xt = vec(c, V_XT);
   ns->g = vec(c, V_G);
   ns->gt = vec(c, V_GT);
-  rc = energy_host(c, x, &ns->F, &ns->mdet, s);
+  rc = energy_grad_async(c, x, ns->g, s);
   if (rc) return rc;
+  rc = read_res(c, 0, 2, s);
+  if (rc) return rc;
+  ns->F = c->h_res[0];
+  ns->mdet = c->h_res[1];
   if (!(ns->mdet > 0.0)) return TMOP_ERR_INVERTED;
-  rc = launch_op(c, OP_GRADIENT, x, nullptr, ns->g, nullptr, s);
-  if (rc) return rc;
   return norm_host(c, ns->g, &ns->gnorm, s);
 }
 
@@ -1091,6 +1124,11 @@ int tmop_energy(tmop_ctx* c, const double* x, double* F, double* min_detA, void*
 int tmop_energy_device(tmop_ctx* c, const double* x, double* F, double* min_detA, void* stream) {
   if (!c || !x || !F || !min_detA) return TMOP_ERR_ARG;
   return energy_async(c, x, (cudaStream_t)stream, F, min_detA);
+}
+
+int tmop_energy_gradient(tmop_ctx* c, const double* x, double* g, double* F, double* min_detA, void* stream) {
+  if (!c || !x || !g || !F || !min_detA) return TMOP_ERR_ARG;
+  return energy_grad_async(c, x, g, (cudaStream_t)stream, F, min_detA);
 }
 
 int tmop_gradient(tmop_ctx* c, const double* x, double* g, void* stream) {

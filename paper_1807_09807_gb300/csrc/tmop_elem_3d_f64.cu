@@ -8,7 +8,7 @@ namespace tmop {
      ElemCfg<3, N, Q, double, OP>::WARPS}
 #define TMOP_ENTRIES(N, Q)                                                                      \
   TMOP_ENTRY(N, Q, OP_ENERGY), TMOP_ENTRY(N, Q, OP_GRADIENT), TMOP_ENTRY(N, Q, OP_HESS),         \
-      TMOP_ENTRY(N, Q, OP_LINEARIZE), TMOP_ENTRY(N, Q, OP_HESS_PA)
+      TMOP_ENTRY(N, Q, OP_LINEARIZE), TMOP_ENTRY(N, Q, OP_HESS_PA), TMOP_ENTRY(N, Q, OP_ENERGY_GRAD)
 
 extern const ElemEntry kElem_3d_f64[] = {
     TMOP_ENTRIES(2,2),

@@ -7,7 +7,9 @@
 //   scatter FP64 atomics into the nodal output, fixed dofs skipped
 //
 // OP_ENERGY instead accumulates w_q det W mu and min det A in FP64 and writes
-// one partial per block (reduced in a second, fixed-order pass).
+// one partial per block (reduced in a second, fixed-order pass);
+// OP_ENERGY_GRAD does both: the gradient, and the energy partials from the
+// mu it evaluates anyway.
 #pragma once
 #include "tmop_device.cuh"
 #include "tmop_kparams.h"
@@ -134,6 +136,8 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
   const int nwarps_total = gridDim.x * WARPS;
   // (the product from compact records, OP_HESS_PA_C, is pac_kernel in tmop_pa_compact.cu)
   constexpr bool PA_APPLY = OP == OP_HESS_PA;
+  constexpr bool EG = OP == OP_ENERGY_GRAD;                // gradient + energy partials
+  constexpr bool GRADLIKE = OP == OP_GRADIENT || EG;
   constexpr int NSH = PA_APPLY ? D * D * (D * D + 1) / 2 : 1;
   static_assert(OP != OP_HESS_PA_C, "OP_HESS_PA_C runs in pac_kernel");
   static_assert(OP != OP_LINEARIZE_C || D == 3, "compact records are 3D");
@@ -383,9 +387,17 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
       } else {
         R S[DD], dA[DD];
         bool ok;
-        if constexpr (OP == OP_GRADIENT) {
+        if constexpr (GRADLIKE) {
           R mu;
           ok = metric_P<D>(p.metric, T, mu, S);
+          if constexpr (EG) {   // the energy of OP_ENERGY from the same point
+            double Ad[DD];
+#pragma unroll
+            for (int i = 0; i < DD; ++i) Ad[i] = double(A[i]);
+            emin = fmin(emin, det_m<D>(Ad));
+            if (ok) accF += double(wq * detW) * double(mu);
+            else accF = INFINITY;
+          }
         } else {
           R dT[DD];
 #pragma unroll
@@ -438,9 +450,14 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
           R T2[DD], S2[DD];
           times_w2<D>(p, A, T2);
           bool ok2;
-          if constexpr (OP == OP_GRADIENT) {
+          if constexpr (GRADLIKE) {
             R mu2;
             ok2 = metric_P<D>(p.metric2, T2, mu2, S2);
+            if constexpr (EG) {
+              const double eta = p.eta2 ? __ldg(p.eta2 + (size_t)e * QP + q) : 1.0;
+              if (ok2) accF += double(wq) * p.detW2 * eta * double(mu2);
+              else accF = INFINITY;
+            }
           } else {
             R dT2[DD];
             times_w2<D>(p, dA, dT2);
@@ -471,6 +488,7 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
         if (lane == 0) p.elem_min[e] = emin;
       }
     } else {
+      if constexpr (EG) accMin = fmin(accMin, emin);
       __syncwarp();
       // ---- adjoint contraction and scatter
       if constexpr (D == 2) adj2<N, Q1, D, R>(sB, sG, P0, P1, lane);
@@ -492,7 +510,7 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
     __syncwarp();
   }
 
-  if constexpr (OP == OP_ENERGY) {
+  if constexpr (OP == OP_ENERGY || EG) {
     __shared__ double redF[WARPS], redM[WARPS];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

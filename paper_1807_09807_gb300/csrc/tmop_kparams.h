@@ -15,10 +15,12 @@ constexpr int kMaxN = 5;   // 1D nodes (order <= 4)
 // pair (3D FP32 only) stores instead what the second derivative of an
 // (|T|^2, det T) metric is made of: T and the five scaled partials
 // w det W (mu_1, mu_t, mu_11, mu_1t, mu_tt), 14 values per point instead of
-// 45, and OP_HESS_PA_C rebuilds dP from them.
+// 45, and OP_HESS_PA_C rebuilds dP from them. OP_ENERGY_GRAD is the
+// gradient with the energy partials of OP_ENERGY taken from the same points
+// (one pass where the line search of the Newton step needs both).
 enum {
   OP_ENERGY = 0, OP_GRADIENT = 1, OP_HESS = 2, OP_LINEARIZE = 3, OP_HESS_PA = 4,
-  OP_LINEARIZE_C = 5, OP_HESS_PA_C = 6, OP_COUNT = 7
+  OP_LINEARIZE_C = 5, OP_HESS_PA_C = 6, OP_ENERGY_GRAD = 7, OP_COUNT = 8
 };
 constexpr int kCompactRec = 14;  // values per point of the compact record (3D)
 enum { WK_IDENTITY = 0, WK_CONST = 1, WK_PER_QP = 2 };

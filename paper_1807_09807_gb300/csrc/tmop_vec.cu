@@ -235,6 +235,12 @@ __global__ void k_minres_scalar(const double* __restrict__ part, int np, double*
   st[KS_SW] = st[KS_SV];
   st[KS_SVP] = st[KS_SV];
   st[KS_SV] = st[KS_INV_BETA_NEXT];
+  // the direction update's coefficients of v, w_{k-2}, w_{k-1}, divided by rho
+  // here once (all 0 once done: INV_RHO = 0)
+  const double ir = st[KS_INV_RHO];
+  st[KS_WU] = st[KS_SW] * ir;
+  st[KS_WP] = st[KS_R1] * ir;
+  st[KS_WW] = st[KS_R2] * ir;
 }
 
 // The direction/solution update and the next Lanczos vector follow in
@@ -257,9 +263,9 @@ int minres_init(const double* b, double* v, double* vprev, double* Av, double* w
 // caller then renames (v, vprev, Av) -> (Av, v, vprev) and (w, wp) -> (wp, w).
 __global__ void k_minres_vec_rot(const double* __restrict__ v, const double* __restrict__ w, double* __restrict__ wp,
                                  double* __restrict__ sol, const double* __restrict__ st, size_t n) {
-  const double r1 = st[KS_R1], r2 = st[KS_R2], ir = st[KS_INV_RHO], phi = st[KS_PHI], sw = st[KS_SW];
+  const double cu = st[KS_WU], cp = st[KS_WP], cw = st[KS_WW], phi = st[KS_PHI];
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double wn = (fma(sw, v[i], -r1 * wp[i]) - r2 * w[i]) * ir;
+    const double wn = fma(-cw, w[i], fma(-cp, wp[i], v[i] * cu));   // (sw v - r1 w_{k-2} - r2 w_{k-1}) / rho
     wp[i] = wn;
     sol[i] = fma(phi, wn, sol[i]);
   }

@@ -24,7 +24,7 @@ enum {
   KS_SV, KS_SVP, KS_SW,
   // preconditioned MINRES
   KS_OLDB, KS_DBAR, KS_EPSLN, KS_OLDEPS, KS_PHIBAR, KS_CS, KS_SN, KS_DELTA, KS_INV_GAMMA, KS_INV_BETA,
-  KS_INV_BETA_OLD, KS_WU, KS_WP, KS_WW,   // direction update coefficients of u, w_{k-2}, w_{k-1}
+  KS_INV_BETA_OLD, KS_WU, KS_WP, KS_WW,   // direction update coefficients of v (u), w_{k-2}, w_{k-1}
   KS_COUNT
 };
 

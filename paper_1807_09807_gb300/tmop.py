@@ -69,6 +69,7 @@ _SIGNATURES = {
     "tmop_energy": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p], C.c_int),
     "tmop_energy_device": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_gradient": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "tmop_energy_gradient": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_hess_apply": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_newton_step": ([C.c_void_p, C.c_void_p, C.POINTER(NewtonOpts), C.POINTER(NewtonReport), C.c_void_p],
                          C.c_int),
@@ -307,6 +308,19 @@ class Context:
         if rc != OK:
             raise TmopError(rc, "tmop_gradient")
         return g
+
+    def energy_gradient(self, x, out=None):
+        """(g, F, min det A) of x: g = dF/dx into `out` and F, min det A as
+        0-d device tensors, in one element pass where the context allows it."""
+        import torch
+        _check_vec(x, self.shape, "x")
+        g = torch.empty_like(x) if out is None else out
+        _check_vec(g, self.shape, "g")
+        fm = torch.empty(2, dtype=torch.float64, device=x.device)
+        rc = load().tmop_energy_gradient(self._h, _ptr(x), _ptr(g), fm.data_ptr(), fm.data_ptr() + 8, _stream())
+        if rc != OK:
+            raise TmopError(rc, "tmop_energy_gradient")
+        return g, fm[0], fm[1]
 
     def hess_apply(self, x, v, out=None):
         import torch

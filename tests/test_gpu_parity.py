@@ -68,6 +68,11 @@ def check_all(tm, m, ctx, orc, rtol_F=RTOL, rtol_vec=RTOL, seed=0):
     go = orc.gradient(m.x)
     assert rel(g, go) <= rtol_vec, rel(g, go)
     assert np.all(g[m.fixed == 1] == 0.0)
+    # the one-pass energy + gradient of the line search: the same F, min det A
+    # and g up to the order of the sums
+    g2, F2, md2 = ctx.energy_gradient(x)
+    assert abs(F2.item() - F) <= 1e-13 * abs(F) and md2.item() == md
+    assert rel(host(g2), g) <= 1e-13
     v = np.random.default_rng(seed).standard_normal(m.x.shape)
     y = host(ctx.hess_apply(x, dev(v)))
     yo = orc.hess_apply(m.x, v)
