@@ -205,6 +205,11 @@ typedef struct {
                             2: two-level, Jacobi plus an exact coarse correction on the element
                             vertices (structured grids whose fixed dofs are exactly the
                             boundary; else TMOP_ERR_ARG): see tmop_precond_apply */
+  int krylov_fp64;       /* [0] the FP32 forms run MINRES on FP32 vectors (the Hessian action
+                            is FP32 there; scalars, reductions and the Newton step stay FP64)
+                            whenever the operator is partially assembled and no
+                            restricted-movement term is set; 1: FP64 vectors. TMOP_FP64: always
+                            FP64. */
 } tmop_newton_opts;
 
 typedef struct {

@@ -5,6 +5,7 @@
 // kernels, and take the Newton line-search decisions (Section 3.4) from FP64
 // device reductions. All arithmetic on mesh-sized data runs in the CUDA
 // kernels of this library; there is no host fallback.
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <utility>
 #include <math.h>
@@ -195,6 +196,7 @@ struct tmop_ctx {
   int mass_grid = 1;
   double* d_diag = nullptr;   // Hessian diagonal [d][nnode] and its floored inverse [d][nnode]
   double* d_vdot = nullptr;   // per-warp partials of v . (H v) from the compact-record product
+  float* d_kvec32 = nullptr;  // FP32 Krylov vectors of the FP32 forms (8 x ndof: 6 work, solution, Jacobi inverse)
   // two-level preconditioner (structured grids whose fixed dofs are exactly the boundary)
   bool boundary_fixed = false;
   int grid_n[3] = {0, 0, 0};
@@ -255,19 +257,26 @@ JacParams jac_params(const tmop_ctx* c, const double* x, double* J) {
   return jp;
 }
 
-// accumulate: y += the scatter op's result (y not zeroed first)
+// accumulate: y += the scatter op's result (y not zeroed first); v32, y32:
+// FP32 direction and output of the stored-Hessian products instead of v, y
 int launch_op(tmop_ctx* c, int op, const double* x, const double* v, double* y, double* elem_min,
-              cudaStream_t s, double* vdot = nullptr, bool accumulate = false) {
+              cudaStream_t s, double* vdot = nullptr, bool accumulate = false, const float* v32 = nullptr,
+              float* y32 = nullptr) {
+  if ((v32 || y32) && !(v32 && y32 && op == OP_HESS_PA && c->delta == 0.0)) return TMOP_ERR_ARG;
   KParams p = c->base;
   p.x = x;
   p.v = v;
   p.y = y;
+  p.v32 = v32;
+  p.y32 = y32;
   p.elem_min = elem_min;
   p.part_F = c->d_part;
   p.part_min = c->d_part + kMaxRedBlocks;
   p.pa = c->d_pa;
-  if ((op == OP_GRADIENT || op == OP_HESS || op == OP_HESS_PA || op == OP_ENERGY_GRAD) && !accumulate)
-    CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * c->ndof, s));
+  if ((op == OP_GRADIENT || op == OP_HESS || op == OP_HESS_PA || op == OP_ENERGY_GRAD) && !accumulate) {
+    if (y32) CUDA_TRY(cudaMemsetAsync(y32, 0, sizeof(float) * c->ndof, s));
+    else CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * c->ndof, s));
+  }
   int kop = op;  // the stored linearisation decides which form of the pair runs
   if (c->pa_compact && op == OP_LINEARIZE) kop = OP_LINEARIZE_C;
   if (c->pa_compact && op == OP_HESS_PA) kop = OP_HESS_PA_C;
@@ -488,35 +497,11 @@ int coarse_setup(tmop_ctx* c, const double* x, int hop, cudaStream_t s) {
 }
 
 // Krylov solve H(x) p = b; returns iterations (negative if the cap was hit).
-int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_newton_opts& o, int* iters,
-           cudaStream_t s) {
-  int rc = ensure_vectors(c);
-  if (rc) return rc;
-  // the Krylov operator: partially assembled at x (default) or recomputed from x
-  const int hop = o.matrix_free ? OP_HESS : OP_HESS_PA;
-  if (o.precond < 0 || o.precond > 2) return TMOP_ERR_ARG;
-  if (o.precond && (hop != OP_HESS_PA || o.krylov == TMOP_KRYLOV_CG)) return TMOP_ERR_ARG;
-  if (o.precond == 2 && !c->boundary_fixed) return TMOP_ERR_ARG;
-  if (hop == OP_HESS_PA) {
-    rc = linearize(c, x, s);
-    if (rc) return rc;
-  }
-  const double* minv = nullptr;
-  if (o.precond) {  // Jacobi: the diagonal of the linearisation just stored
-    rc = hessian_diagonal(c, true, s);
-    if (rc) return rc;
-    minv = c->d_diag + c->ndof;
-  }
-  PrecondAdd pc_add{coarse_apply_add, nullptr};
-  const PrecondAdd* pc = nullptr;
-  if (o.precond == 2) {  // two-level: plus the coarse correction on the element vertices
-    rc = coarse_setup(c, x, hop, s);
-    if (rc) return rc;
-    if (c->coarse_alpha > 0.0) {
-      pc_add.obj = c->coarse;
-      pc = &pc_add;
-    }
-  }
+// The Krylov solve of H p = b on T vectors (FP64, or FP32 for the FP32
+// forms), after the linearisation and the preconditioner set-up.
+template <class T>
+int krylov_run(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_newton_opts& o, int* iters,
+               cudaStream_t s, int hop, const double* minv, const PrecondAdd* pc) {
   double* st = c->d_res + kResKrylov;
   double* part = c->d_part;
   const size_t n = c->ndof;
@@ -531,15 +516,38 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
   // same assignment)
   constexpr int kCheck = 6;
   const bool cg = o.krylov == TMOP_KRYLOV_CG;
-  double *k0 = vec(c, V_K0), *k1 = vec(c, V_K1), *k2 = vec(c, V_K2), *k3 = vec(c, V_K3), *k4 = vec(c, V_K4);
-  double* k5 = vec(c, V_K5);
+  if (cg && !std::is_same<T, double>::value) return TMOP_ERR_ARG;
+  int rc = TMOP_OK;
+  T *k0, *k1, *k2, *k3, *k4, *k5, *sol;
+  const T* minvT = nullptr;
+  if constexpr (std::is_same<T, double>::value) {
+    k0 = vec(c, V_K0), k1 = vec(c, V_K1), k2 = vec(c, V_K2), k3 = vec(c, V_K3), k4 = vec(c, V_K4), k5 = vec(c, V_K5);
+    sol = p;
+    minvT = minv;
+  } else {   // FP32 Krylov vectors: six work vectors, the solution, the FP32 Jacobi inverse
+    if (!c->d_kvec32) CUDA_TRY(cudaMalloc(&c->d_kvec32, sizeof(float) * n * 8));
+    float* b32 = c->d_kvec32;
+    k0 = b32, k1 = b32 + n, k2 = b32 + 2 * n, k3 = b32 + 3 * n, k4 = b32 + 4 * n, k5 = b32 + 5 * n;
+    sol = b32 + 6 * n;
+    if (minv) {
+      if (narrow(minv, b32 + 7 * n, n, s)) return TMOP_ERR_CUDA;
+      minvT = b32 + 7 * n;
+    }
+  }
+  // the product of the stored Hessians on T vectors, accumulating into a zeroed buffer
+  auto product = [&](T* v, T* y, cudaStream_t q, double* vd) -> int {
+    if constexpr (std::is_same<T, double>::value) return launch_op(c, hop, x, v, y, nullptr, q, vd, true);
+    else return launch_op(c, hop, x, nullptr, nullptr, nullptr, q, vd, true, v, y);
+  };
   if (cg) {
-    if (cg_init(b, k0, k1, p, st, part, n, o.krylov_rtol, o.krylov_maxit, s)) return TMOP_ERR_CUDA;
+    if constexpr (std::is_same<T, double>::value)
+      if (cg_init(b, k0, k1, p, st, part, n, o.krylov_rtol, o.krylov_maxit, s)) return TMOP_ERR_CUDA;
   } else if (minv) {  // r1 = k0, r2 = k1, u = k2 (product into q = k3), w = k4, wprev = k5
-    if (pminres_init(b, minv, k0, k1, k2, k3, k4, k5, p, st, part, n, o.krylov_rtol, o.krylov_maxit, s, pc))
+    if (pminres_init<T>(b, minvT, k0, k1, k2, k3, k4, k5, sol, st, part, n, o.krylov_rtol, o.krylov_maxit, s, pc))
       return TMOP_ERR_CUDA;
   } else {
-    if (minres_init(b, k0, k1, k2, k3, k4, p, st, part, n, o.krylov_rtol, o.krylov_maxit, s)) return TMOP_ERR_CUDA;
+    if (minres_init<T>(b, k0, k1, k2, k3, k4, sol, st, part, n, o.krylov_rtol, o.krylov_maxit, s))
+      return TMOP_ERR_CUDA;
   }
   // the compact-record product also returns v . (H v) (not with the restricted-movement term, whose
   // contribution it does not see)
@@ -555,26 +563,28 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
       int r;
       if (minv) {   // the pairs (r1, r2), (u, q), (w, wprev) swap roles every iteration
         const bool ev = j % 2 == 0;
-        double *r1 = ev ? k0 : k1, *r2 = ev ? k1 : k0, *u = ev ? k2 : k3, *hu = ev ? k3 : k2;
-        double *w = ev ? k4 : k5, *wp = ev ? k5 : k4;
-        r = launch_op(c, hop, x, u, hu, nullptr, q, nullptr, true);   // hu was left zero
+        T *r1 = ev ? k0 : k1, *r2 = ev ? k1 : k0, *u = ev ? k2 : k3, *hu = ev ? k3 : k2;
+        T *w = ev ? k4 : k5, *wp = ev ? k5 : k4;
+        r = product(u, hu, q, nullptr);   // hu was left zero
         if (r) return r;
-        if (pminres_after_hv(minv, r1, r2, u, hu, w, wp, p, st, part, n, q, pc)) return TMOP_ERR_CUDA;
+        if (pminres_after_hv<T>(minvT, r1, r2, u, hu, w, wp, sol, st, part, n, q, pc)) return TMOP_ERR_CUDA;
         continue;
       }
       if (cg) {  // r = k0, d = k1, Hd = k2
-        r = launch_op(c, hop, x, k1, k2, nullptr, q);
-        if (r) return r;
-        if (cg_after_hv(p, k0, k1, k2, st, part, n, q)) return TMOP_ERR_CUDA;
+        if constexpr (std::is_same<T, double>::value) {
+          r = launch_op(c, hop, x, k1, k2, nullptr, q);
+          if (r) return r;
+          if (cg_after_hv(p, k0, k1, k2, st, part, n, q)) return TMOP_ERR_CUDA;
+        }
       } else {   // Lanczos vectors rotate over k0, k1, k2 (period 3), search directions over k3, k4
-        double* V[3] = {k0, k1, k2};
-        double* W[2] = {k3, k4};
+        T* V[3] = {k0, k1, k2};
+        T* W[2] = {k3, k4};
         const int iv = (3 - j % 3) % 3;
-        double *v = V[iv], *vprev = V[(iv + 1) % 3], *Av = V[(iv + 2) % 3];
-        double *w = W[j % 2], *wp = W[(j + 1) % 2];
-        r = launch_op(c, hop, x, v, Av, nullptr, q, vdot, true);   // Av was left zero
+        T *v = V[iv], *vprev = V[(iv + 1) % 3], *Av = V[(iv + 2) % 3];
+        T *w = W[j % 2], *wp = W[(j + 1) % 2];
+        r = product(v, Av, q, vdot);   // Av was left zero
         if (r) return r;
-        if (minres_after_hv_rot(v, vprev, Av, w, wp, p, st, part, n, q, vdot, vdot_np)) return TMOP_ERR_CUDA;
+        if (minres_after_hv_rot<T>(v, vprev, Av, w, wp, sol, st, part, n, q, vdot, vdot_np)) return TMOP_ERR_CUDA;
       }
     }
     return TMOP_OK;
@@ -619,10 +629,48 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
     if (cudaEventRecord(c->ev, q) != cudaSuccess || cudaStreamWaitEvent(s, c->ev, 0) != cudaSuccess)
       return TMOP_ERR_CUDA;
   }
+  if constexpr (!std::is_same<T, double>::value)
+    if (widen(sol, p, n, s)) return TMOP_ERR_CUDA;   // the Newton step in FP64
   const int it = h[KS_DONE] != 0.0 ? (int)h[KS_CONV_IT] : (int)h[KS_ITER];
   const bool converged = h[KS_DONE] != 0.0 && h[KS_BREAKDOWN] == 0.0 && h[KS_HITMAX] == 0.0;
   *iters = converged ? it : -it;
   return TMOP_OK;
+}
+
+int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_newton_opts& o, int* iters,
+           cudaStream_t s) {
+  int rc = ensure_vectors(c);
+  if (rc) return rc;
+  // the Krylov operator: partially assembled at x (default) or recomputed from x
+  const int hop = o.matrix_free ? OP_HESS : OP_HESS_PA;
+  if (o.precond < 0 || o.precond > 2) return TMOP_ERR_ARG;
+  if (o.precond && (hop != OP_HESS_PA || o.krylov == TMOP_KRYLOV_CG)) return TMOP_ERR_ARG;
+  if (o.precond == 2 && !c->boundary_fixed) return TMOP_ERR_ARG;
+  if (hop == OP_HESS_PA) {
+    rc = linearize(c, x, s);
+    if (rc) return rc;
+  }
+  const double* minv = nullptr;
+  if (o.precond) {  // Jacobi: the diagonal of the linearisation just stored
+    rc = hessian_diagonal(c, true, s);
+    if (rc) return rc;
+    minv = c->d_diag + c->ndof;
+  }
+  PrecondAdd pc_add{coarse_apply_add, coarse_apply_add32, nullptr};
+  const PrecondAdd* pc = nullptr;
+  if (o.precond == 2) {  // two-level: plus the coarse correction on the element vertices
+    rc = coarse_setup(c, x, hop, s);
+    if (rc) return rc;
+    if (c->coarse_alpha > 0.0) {
+      pc_add.obj = c->coarse;
+      pc = &pc_add;
+    }
+  }
+  // FP32 forms: MINRES on FP32 vectors (the operator is FP32 there), unless asked otherwise
+  const bool cg = o.krylov == TMOP_KRYLOV_CG;
+  const bool use32 = c->precision != TMOP_FP64 && !o.krylov_fp64 && hop == OP_HESS_PA && !cg && c->delta == 0.0;
+  if (use32) return krylov_run<float>(c, x, b, p, o, iters, s, hop, minv, pc);
+  return krylov_run<double>(c, x, b, p, o, iters, s, hop, minv, pc);
 }
 
 struct NewtonState {
@@ -731,6 +779,7 @@ void tmop_destroy(tmop_ctx* c) {
   cudaFree(c->d_x_init);
   cudaFree(c->d_diag);
   cudaFree(c->d_vdot);
+  cudaFree(c->d_kvec32);
   cudaFree(c->d_colour);
   coarse_destroy(c->coarse);
   cudaFree(c->d_coarse_w);

@@ -128,12 +128,13 @@ __global__ void k_prolong(const R* __restrict__ in, R* __restrict__ out, Pass p,
   }
 }
 
-// the last prolongation pass (along x, inner = 1) into the FP64 fine array: y += P w
-template <class R, int K>
-__global__ void k_prolong_add(const R* __restrict__ in, double* __restrict__ y, Pass p, uint32_t n, Wts<R> w) {
+// the last prolongation pass (along x, inner = 1) into the fine array (FP64,
+// or FP32 for FP32 Krylov vectors): y += P w
+template <class R, class Ry, int K>
+__global__ void k_prolong_add(const R* __restrict__ in, Ry* __restrict__ y, Pass p, uint32_t n, Wts<R> w) {
   for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < p.total; idx += gridDim.x * blockDim.x) {
     const uint32_t o = p.by_Lout.div(idx), g = idx - o * p.Lout;
-    y[idx] += (double)prolong_at<R, K>(in, o, g, 0, p.Lin, 1, n, w);
+    y[idx] += (Ry)prolong_at<R, K>(in, o, g, 0, p.Lin, 1, n, w);
   }
 }
 
@@ -318,9 +319,9 @@ Pass make_pass(const CoarseSpace* cs, const int len[3], int a, int Lout) {
   return p;
 }
 
-// w_c = P^t r (FP64 fine -> R coarse in buf[0] or buf[1]); returns the buffer
-template <class R>
-R* restrict_all(CoarseSpace* cs, const double* r, cudaStream_t s) {
+// w_c = P^t r (fine, FP64 or FP32 -> R coarse in buf[0] or buf[1]); returns the buffer
+template <class R, class Rf>
+R* restrict_all(CoarseSpace* cs, const Rf* r, cudaStream_t s) {
   const Wts<R> w = weights<R>(cs);
   int len[3] = {cs->Lf[0], cs->Lf[1], cs->Lf[2]};
   R* b[2] = {static_cast<R*>(cs->buf[0]), static_cast<R*>(cs->buf[1])};
@@ -330,7 +331,7 @@ R* restrict_all(CoarseSpace* cs, const double* r, cudaStream_t s) {
     const R* src = a == 0 ? nullptr : b[(a - 1) % 2];
     const int g = grid_for(p.total);
     with_order(cs->k, [&](auto K) {
-      if (a == 0) k_restrict<double, R, K.value><<<g, kThr, 0, s>>>(r, dst, p, w);
+      if (a == 0) k_restrict<Rf, R, K.value><<<g, kThr, 0, s>>>(r, dst, p, w);
       else k_restrict<R, R, K.value><<<g, kThr, 0, s>>>(src, dst, p, w);
     });
     len[a] = cs->Lc[a];
@@ -409,23 +410,23 @@ R* prolong_upper(CoarseSpace* cs, R* cur, int len[3], cudaStream_t s) {
 }
 
 // the last pass (along x) into y
-template <class R>
-void prolong_last(CoarseSpace* cs, const R* c, const int len[3], double* y, cudaStream_t s) {
+template <class R, class Ry>
+void prolong_last(CoarseSpace* cs, const R* c, const int len[3], Ry* y, cudaStream_t s) {
   const Pass p = make_pass(cs, len, 0, cs->Lf[0]);
   const Wts<R> w = weights<R>(cs);
   with_order(cs->k, [&](auto K) {
-    k_prolong_add<R, K.value><<<grid_for(p.total), kThr, 0, s>>>(c, y, p, (uint32_t)cs->n[0], w);
+    k_prolong_add<R, Ry, K.value><<<grid_for(p.total), kThr, 0, s>>>(c, y, p, (uint32_t)cs->n[0], w);
   });
 }
 
-template <class R>
-int apply_add_t(CoarseSpace* cs, const double* r, double* y, double* part, cudaStream_t s) {
-  R* c = restrict_all<R>(cs, r, s);
+template <class R, class Rf>
+int apply_add_t(CoarseSpace* cs, const Rf* r, Rf* y, double* part, cudaStream_t s) {
+  R* c = restrict_all<R, Rf>(cs, r, s);
   int np = 0;
   c = solve_coarse<R>(cs, c, part, &np, s);
   int len[3];
   c = prolong_upper<R>(cs, c, len, s);
-  prolong_last<R>(cs, c, len, y, s);
+  prolong_last<R, Rf>(cs, c, len, y, s);
   return cudaGetLastError() == cudaSuccess ? np : -1;
 }
 
@@ -553,12 +554,12 @@ int coarse_prolong(CoarseSpace* cs, const double* w, double* y, cudaStream_t s) 
     float* c = static_cast<float*>(cs->buf[0]);
     k_to_float<<<grid_for(cs->ncoarse * cs->dim), kThr, 0, s>>>(w, c, cs->ncoarse * cs->dim);
     c = prolong_upper<float>(cs, c, len, s);
-    prolong_last<float>(cs, c, len, y, s);
+    prolong_last<float, double>(cs, c, len, y, s);
   } else {
     double* c = static_cast<double*>(cs->buf[0]);
     cudaMemcpyAsync(c, w, sizeof(double) * cs->ncoarse * cs->dim, cudaMemcpyDeviceToDevice, s);
     c = prolong_upper<double>(cs, c, len, s);
-    prolong_last<double>(cs, c, len, y, s);
+    prolong_last<double, double>(cs, c, len, y, s);
   }
   return (int)cudaGetLastError();
 }
@@ -566,7 +567,13 @@ int coarse_prolong(CoarseSpace* cs, const double* w, double* y, cudaStream_t s) 
 int coarse_apply_add(void* obj, const double* r, double* y, double* part, cudaStream_t s) {
   CoarseSpace* cs = static_cast<CoarseSpace*>(obj);
   if (!cs || !r || !y) return -1;
-  return cs->fp32 ? apply_add_t<float>(cs, r, y, part, s) : apply_add_t<double>(cs, r, y, part, s);
+  return cs->fp32 ? apply_add_t<float, double>(cs, r, y, part, s) : apply_add_t<double, double>(cs, r, y, part, s);
+}
+
+int coarse_apply_add32(void* obj, const float* r, float* y, double* part, cudaStream_t s) {
+  CoarseSpace* cs = static_cast<CoarseSpace*>(obj);
+  if (!cs || !r || !y) return -1;
+  return cs->fp32 ? apply_add_t<float, float>(cs, r, y, part, s) : apply_add_t<double, float>(cs, r, y, part, s);
 }
 
 }  // namespace tmop

@@ -45,5 +45,7 @@ void coarse_set_alpha(CoarseSpace* cs, double alpha);
 // the coarse grid in the sine basis, into part. Returns the number of
 // partials, or -1.
 int coarse_apply_add(void* cs, const double* r, double* y, double* part, cudaStream_t s);
+// the same for FP32 fine vectors r, y (the FP32 forms' Krylov vectors)
+int coarse_apply_add32(void* cs, const float* r, float* y, double* part, cudaStream_t s);
 
 }  // namespace tmop

@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
         for (int c = 0; c < D; ++c) {
           const size_t dof = (size_t)c * p.nnode + g;
           const bool fx = p.fixed && __ldg(p.fixed + dof);
-          P0[c * NDOF + t] = fx ? R(0) : from_f64<R>(__ldg(p.v + dof));
+          P0[c * NDOF + t] = fx ? R(0) : (p.v32 ? R(__ldg(p.v32 + dof)) : from_f64<R>(__ldg(p.v + dof)));
         }
         continue;
       }
@@ -503,7 +503,8 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
           // (one colour per launch in the deterministic mode: no other
           // element of the launch adds to this node, so each node gets one
           // add per launch, in colour order)
-          atomicAdd(p.y + dof, to_f64(P0[c * NDOF + t]));
+          if (PA_APPLY && p.y32) atomicAdd(p.y32 + dof, float(P0[c * NDOF + t]));   // FP32 Krylov vectors
+          else atomicAdd(p.y + dof, to_f64(P0[c * NDOF + t]));
         }
       }
     }

@@ -33,6 +33,10 @@ struct KParams {
   const double* x;                // [d][nnode]
   const double* v;                // [d][nnode] (Hessian action)
   double* y;                      // [d][nnode] accumulated output
+  // FP32 direction and output of the stored-Hessian products (the FP32
+  // forms' Krylov vectors), used instead of v and y when set
+  const float* v32;
+  float* y32;
   const double* Winv_qp;          // [nelem][Q][d][d] (per-point targets)
   const double* detW_qp;          // [nelem][Q]
   double* part_F;                 // [grid] energy partials

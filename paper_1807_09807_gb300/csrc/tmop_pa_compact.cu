@@ -276,7 +276,7 @@ __device__ __forceinline__ void pac_adj(const float2 (&tBG)[Q1 * N], float* P0, 
 // lane gathers. Hardware conversions: this kernel is bound by instruction
 // issue and leaves the FP64 pipe mostly idle, so one F2F beats the ~20
 // integer instructions of f64_to_f32.
-template <int N, int NT>
+template <int N, int NT, bool IO32>
 __device__ __forceinline__ void fetch_v(const KParams& p, const NodeMap<N>& m, int lane, float (&v)[NT][3],
                                         unsigned& fmask) {
   constexpr int NDOF = N * N * N;
@@ -289,7 +289,8 @@ __device__ __forceinline__ void fetch_v(const KParams& p, const NodeMap<N>& m, i
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const size_t dof = (size_t)c * p.nnode + g;
-        v[s][c] = __double2float_rn(__ldg(p.v + dof));
+        if constexpr (IO32) v[s][c] = __ldg(p.v32 + dof);
+        else v[s][c] = __double2float_rn(__ldg(p.v + dof));
         if (p.fixed && __ldg(p.fixed + dof)) fmask |= 1u << (s * 3 + c);
       }
     }
@@ -354,8 +355,9 @@ __device__ __forceinline__ void pac_point(const float (&h)[kCompactRec], const f
 }
 
 // IDENT: the target is W = I (p.wkind == WK_IDENTITY); otherwise one constant W^-1.
+// IO32: v and y are the FP32 vectors p.v32, p.y32 (FP32 atomics into y).
 // For n = 4 the kernel is held to 128 registers, two blocks per SM (0: no bound).
-template <int N, int Q1, bool IDENT>
+template <int N, int Q1, bool IDENT, bool IO32>
 __global__ void __launch_bounds__(kPacWarps * 32, N == 4 ? 2 : 0) pac_kernel(const KParams p) {
   using Cfg = PacCfg<N, Q1>;
   using L = typename Cfg::L;
@@ -392,7 +394,7 @@ __global__ void __launch_bounds__(kPacWarps * 32, N == 4 ? 2 : 0) pac_kernel(con
   // sum over this warp's elements of v_E . (H_E v_E): each lane's share of
   // an element in FP32 (v_E as the product reads it, FP32), the elements in FP64
   double vdot = 0.0;
-  fetch_v<N, NT>(p, cur, lane, v, fnext);
+  fetch_v<N, NT, IO32>(p, cur, lane, v, fnext);
   fetch_rec<QP>(rec, p.pa_stride, e, lane, hq);
   for (;;) {
     // ---- the record block of the next element goes to L2 ahead of its loads
@@ -434,7 +436,7 @@ __global__ void __launch_bounds__(kPacWarps * 32, N == 4 ? 2 : 0) pac_kernel(con
     const int en = more ? elem(eni) : 0;
     if (more) {
       nxt.element(en, NDOF);
-      fetch_v<N, NT>(p, nxt, lane, v, fnext);
+      fetch_v<N, NT, IO32>(p, nxt, lane, v, fnext);
       fetch_rec<QP>(rec, p.pa_stride, en, lane, hq);
     }
     __syncwarp();
@@ -450,7 +452,10 @@ __global__ void __launch_bounds__(kPacWarps * 32, N == 4 ? 2 : 0) pac_kernel(con
         for (int c = 0; c < 3; ++c) {
           const float yf = P0[c * L::XC + (t / N) * L::XR + t % N];
           vdot_e = fmaf(vc[s][c], yf, vdot_e);  // 0 at fixed dofs (vc = 0 there)
-          if (!((fcur >> (s * 3 + c)) & 1u)) atomicAdd(p.y + (size_t)c * p.nnode + g, (double)yf);
+          if (!((fcur >> (s * 3 + c)) & 1u)) {
+            if constexpr (IO32) atomicAdd(p.y32 + (size_t)c * p.nnode + g, yf);
+            else atomicAdd(p.y + (size_t)c * p.nnode + g, (double)yf);
+          }
         }
       }
     }
@@ -473,8 +478,13 @@ __global__ void __launch_bounds__(kPacWarps * 32, N == 4 ? 2 : 0) pac_kernel(con
 template <int N, int Q1>
 int launch_pac(const KParams& p, int grid, void* stream) {
   const size_t smem = PacCfg<N, Q1>::smem_bytes();
-  if (p.wkind == WK_IDENTITY) pac_kernel<N, Q1, true><<<grid, kPacWarps * 32, smem, (cudaStream_t)stream>>>(p);
-  else pac_kernel<N, Q1, false><<<grid, kPacWarps * 32, smem, (cudaStream_t)stream>>>(p);
+  const bool id = p.wkind == WK_IDENTITY, io32 = p.v32 != nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (io32 != (p.y32 != nullptr)) return (int)cudaErrorInvalidValue;
+  if (id && io32) pac_kernel<N, Q1, true, true><<<grid, kPacWarps * 32, smem, s>>>(p);
+  else if (id) pac_kernel<N, Q1, true, false><<<grid, kPacWarps * 32, smem, s>>>(p);
+  else if (io32) pac_kernel<N, Q1, false, true><<<grid, kPacWarps * 32, smem, s>>>(p);
+  else pac_kernel<N, Q1, false, false><<<grid, kPacWarps * 32, smem, s>>>(p);
   return (int)cudaGetLastError();
 }
 
@@ -482,7 +492,8 @@ int launch_pac(const KParams& p, int grid, void* stream) {
 template <int N, int Q1>
 int prepare_pac(int nelem, int* grid) {
   const size_t smem = PacCfg<N, Q1>::smem_bytes();
-  const void* fn[2] = {(const void*)pac_kernel<N, Q1, true>, (const void*)pac_kernel<N, Q1, false>};
+  const void* fn[4] = {(const void*)pac_kernel<N, Q1, true, false>, (const void*)pac_kernel<N, Q1, false, false>,
+                       (const void*)pac_kernel<N, Q1, true, true>, (const void*)pac_kernel<N, Q1, false, true>};
   int per_sm = 1 << 30, dev = 0, sms = 0;
   for (const void* f : fn) {
     cudaError_t err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

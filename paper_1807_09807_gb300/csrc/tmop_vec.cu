@@ -65,6 +65,17 @@ __global__ void k_dot_part(const double* __restrict__ a, const double* __restric
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// a . b over T vectors: each thread sums its elements in T (FP32 vectors:
+// ~30 elements per thread at full occupancy), the blocks in FP64
+template <class T>
+__global__ void k_dot_part_t(const T* __restrict__ a, const T* __restrict__ b, size_t n, double* __restrict__ part) {
+  T s = T(0);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    s = fma(a[i], b[i], s);
+  const double t = block_sum((double)s);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
 __global__ void k_sum_final(const double* __restrict__ part, int np, double* __restrict__ out) {
   double s = 0.0;
   for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
@@ -128,18 +139,21 @@ int step(const double* x, const double* p, double alpha, double* y, size_t n, cu
 }
 
 // ---------------------------------------------------------------- MINRES
-// v = b / beta1, vprev = w = wprev = sol = 0 and the rotation state.
-__global__ void k_minres_init(const double* __restrict__ b, double* v, double* vprev, double* Av, double* w,
-                              double* wprev, double* sol, double* st, size_t n, double rtol, int maxit) {
+// v = b / beta1, vprev = w = wprev = sol = 0 and the rotation state. (The
+// vectors are T: FP64, or FP32 for the FP32 forms' Krylov solves; b is the
+// FP64 gradient.)
+template <class T>
+__global__ void k_minres_init(const double* __restrict__ b, T* v, T* vprev, T* Av, T* w, T* wprev, T* sol,
+                              double* st, size_t n, double rtol, int maxit) {
   const double beta1 = sqrt(st[KS_BETA_NEXT2]);
   const double inv = beta1 > 0.0 ? 1.0 / beta1 : 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    v[i] = b[i] * inv;
-    vprev[i] = 0.0;
-    Av[i] = 0.0;
-    w[i] = 0.0;
-    wprev[i] = 0.0;
-    sol[i] = 0.0;
+    v[i] = (T)(b[i] * inv);
+    vprev[i] = T(0);
+    Av[i] = T(0);
+    w[i] = T(0);
+    wprev[i] = T(0);
+    sol[i] = T(0);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st[KS_BETA1] = beta1;
@@ -162,19 +176,20 @@ __global__ void k_minres_init(const double* __restrict__ b, double* v, double* v
 // H v - alpha v - beta vprev = sv Av - (alpha sv) v - (beta svp) vprev, and
 // alpha = v . H v = sv^2 (v array . Av) from the sum in st[KS_ALPHA]. vprev
 // is read here for the last time and zeroed: it is the next product's output.
-__global__ void k_lanczos(double* __restrict__ Av, const double* __restrict__ v, double* __restrict__ vprev,
+template <class T>
+__global__ void k_lanczos(T* __restrict__ Av, const T* __restrict__ v, T* __restrict__ vprev,
                           const double* __restrict__ st, size_t n, double* __restrict__ part) {
-  const double sv = st[KS_SV];
-  const double av = st[KS_ALPHA] * sv * sv * sv, bv = st[KS_BETA] * st[KS_SVP];
-  double s = 0.0;
+  const double svd = st[KS_SV];
+  const T sv = (T)svd, av = (T)(st[KS_ALPHA] * svd * svd * svd), bv = (T)(st[KS_BETA] * st[KS_SVP]);
+  T s = T(0);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double r = fma(sv, Av[i], -av * v[i]) - bv * vprev[i];
+    const T r = fma(sv, Av[i], -av * v[i]) - bv * vprev[i];
     Av[i] = r;
-    vprev[i] = 0.0;
+    vprev[i] = T(0);
     s = fma(r, r, s);
   }
-  s = block_sum(s);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  const double t = block_sum((double)s);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 // Apply the two previous rotations to the new tridiagonal column
@@ -247,67 +262,78 @@ __global__ void k_minres_scalar(const double* __restrict__ part, int np, double*
 // k_minres_vec_rot. (Once KS_DONE is set, phi = 0 keeps sol fixed and the
 // next Lanczos vector is 0, so every later product is zero.)
 
-int minres_init(const double* b, double* v, double* vprev, double* Av, double* w, double* wprev, double* sol,
-                double* st, double* part, size_t n, double rtol, int maxit, cudaStream_t s) {
+template <class T>
+int minres_init(const double* b, T* v, T* vprev, T* Av, T* w, T* wprev, T* sol, double* st, double* part, size_t n,
+                double rtol, int maxit, cudaStream_t s) {
   int g = red_grid(n);
   k_dot_part<<<g, kThreads, 0, s>>>(b, b, n, part);
   k_sum_final<<<1, kThreads, 0, s>>>(part, g, st + KS_BETA_NEXT2);
-  k_minres_init<<<g, kThreads, 0, s>>>(b, v, vprev, Av, w, wprev, sol, st, n, rtol, maxit);
+  k_minres_init<T><<<g, kThreads, 0, s>>>(b, v, vprev, Av, w, wprev, sol, st, n, rtol, maxit);
   return (int)cudaGetLastError();
 }
+template int minres_init<double>(const double*, double*, double*, double*, double*, double*, double*, double*,
+                                 double*, size_t, double, int, cudaStream_t);
+template int minres_init<float>(const double*, float*, float*, float*, float*, float*, float*, double*, double*,
+                                size_t, double, int, cudaStream_t);
 
 
 // Rotating-buffer form of the update: the new search direction overwrites
 // w_{k-2} (wp) and the Lanczos vectors stay unnormalised (their scales are
 // device scalars), so nothing is copied or rescaled: 6 vector passes; the
 // caller then renames (v, vprev, Av) -> (Av, v, vprev) and (w, wp) -> (wp, w).
-__global__ void k_minres_vec_rot(const double* __restrict__ v, const double* __restrict__ w, double* __restrict__ wp,
-                                 double* __restrict__ sol, const double* __restrict__ st, size_t n) {
-  const double cu = st[KS_WU], cp = st[KS_WP], cw = st[KS_WW], phi = st[KS_PHI];
+template <class T>
+__global__ void k_minres_vec_rot(const T* __restrict__ v, const T* __restrict__ w, T* __restrict__ wp,
+                                 T* __restrict__ sol, const double* __restrict__ st, size_t n) {
+  const T cu = (T)st[KS_WU], cp = (T)st[KS_WP], cw = (T)st[KS_WW], phi = (T)st[KS_PHI];
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double wn = fma(-cw, w[i], fma(-cp, wp[i], v[i] * cu));   // (sw v - r1 w_{k-2} - r2 w_{k-1}) / rho
+    const T wn = fma(-cw, w[i], fma(-cp, wp[i], v[i] * cu));   // (sw v - r1 w_{k-2} - r2 w_{k-1}) / rho
     wp[i] = wn;
     sol[i] = fma(phi, wn, sol[i]);
   }
 }
 
-int minres_after_hv_rot(const double* v, double* vprev, double* Av, const double* w, double* wp, double* sol,
-                        double* st, double* part, size_t n, cudaStream_t s, const double* vdot, int vdot_np) {
+template <class T>
+int minres_after_hv_rot(const T* v, T* vprev, T* Av, const T* w, T* wp, T* sol, double* st, double* part, size_t n,
+                        cudaStream_t s, const double* vdot, int vdot_np) {
   int g = red_grid(n);
   if (vdot) {  // alpha = v . (H v) from the product kernel's own partials
     k_sum_final<<<1, kThreads, 0, s>>>(vdot, vdot_np, st + KS_ALPHA);
   } else {
-    k_dot_part<<<g, kThreads, 0, s>>>(v, Av, n, part);
+    k_dot_part_t<T><<<g, kThreads, 0, s>>>(v, Av, n, part);
     k_sum_final<<<1, kThreads, 0, s>>>(part, g, st + KS_ALPHA);
   }
-  k_lanczos<<<g, kThreads, 0, s>>>(Av, v, vprev, st, n, part);
+  k_lanczos<T><<<g, kThreads, 0, s>>>(Av, v, vprev, st, n, part);
   k_minres_scalar<<<1, kThreads, 0, s>>>(part, g, st);
-  k_minres_vec_rot<<<g, kThreads, 0, s>>>(v, w, wp, sol, st, n);
+  k_minres_vec_rot<T><<<g, kThreads, 0, s>>>(v, w, wp, sol, st, n);
   return (int)cudaGetLastError();
 }
+template int minres_after_hv_rot<double>(const double*, double*, double*, const double*, double*, double*, double*,
+                                         double*, size_t, cudaStream_t, const double*, int);
+template int minres_after_hv_rot<float>(const float*, float*, float*, const float*, float*, float*, double*, double*,
+                                        size_t, cudaStream_t, const double*, int);
 
 // ---------------------------------------------------------------- preconditioned MINRES
 // Lanczos in the M^-1 inner product with the residual minimised through
 // Givens rotations (Paige and Saunders), M = diag(1 / minv). The residual
 // estimate phibar is the M^-1-norm of the residual; the solve stops when it
 // falls to rtol times its initial value.
-__global__ void k_pm_init(const double* __restrict__ b, const double* __restrict__ minv, double* r1, double* r2,
-                          double* y, double* q, double* w, double* wprev, double* sol, size_t n,
-                          double* __restrict__ part) {
-  double s = 0.0;
+template <class T>
+__global__ void k_pm_init(const double* __restrict__ b, const T* __restrict__ minv, T* r1, T* r2, T* y, T* q, T* w,
+                          T* wprev, T* sol, size_t n, double* __restrict__ part) {
+  T s = T(0);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double bi = b[i], yi = minv[i] * bi;
+    const T bi = (T)b[i], yi = minv[i] * bi;
     r1[i] = bi;
     r2[i] = bi;
     y[i] = yi;
-    q[i] = 0.0;
-    w[i] = 0.0;
-    wprev[i] = 0.0;
-    sol[i] = 0.0;
+    q[i] = T(0);
+    w[i] = T(0);
+    wprev[i] = T(0);
+    sol[i] = T(0);
     s = fma(bi, yi, s);
   }
-  s = block_sum(s);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  const double t = block_sum((double)s);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 __global__ void k_pm_init_scalar(double* st, double rtol, int maxit) {
@@ -337,18 +363,20 @@ __global__ void k_pm_init_scalar(double* st, double rtol, int maxit) {
 
 // q <- q / beta - (beta / oldb) r1 (the r1 term from the second iteration
 // on), partials of u . q (alpha = their sum / beta)
-__global__ void k_pm_a(double* __restrict__ q, const double* __restrict__ r1, const double* __restrict__ u,
+template <class T>
+__global__ void k_pm_a(T* __restrict__ q, const T* __restrict__ r1, const T* __restrict__ u,
                        const double* __restrict__ st, size_t n, double* __restrict__ part) {
-  const double oldb = st[KS_OLDB], ib = st[KS_INV_BETA];
-  const double c = oldb > 0.0 ? st[KS_BETA] / oldb : 0.0;
-  double s = 0.0;
+  const double oldb = st[KS_OLDB];
+  const T ib = (T)st[KS_INV_BETA];
+  const T c = (T)(oldb > 0.0 ? st[KS_BETA] / oldb : 0.0);
+  T s = T(0);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double qi = fma(-c, r1[i], q[i] * ib);
+    const T qi = fma(-c, r1[i], q[i] * ib);
     q[i] = qi;
     s = fma(u[i], qi, s);
   }
-  s = block_sum(s);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  const double t = block_sum((double)s);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 // out = (sum of the partials) * *scale
@@ -362,20 +390,21 @@ __global__ void k_sum_scaled(const double* __restrict__ part, int np, const doub
 
 // t = q - (alpha / beta) r2 into r1's buffer (the old r1 is dead), then
 // q <- M^-1 t (diagonal part); partials of t . q
-__global__ void k_pm_b(const double* __restrict__ minv, double* __restrict__ r1, const double* __restrict__ r2,
-                       double* __restrict__ q, const double* __restrict__ st, size_t n, double* __restrict__ part) {
+template <class T>
+__global__ void k_pm_b(const T* __restrict__ minv, T* __restrict__ r1, const T* __restrict__ r2, T* __restrict__ q,
+                       const double* __restrict__ st, size_t n, double* __restrict__ part) {
   const double beta = st[KS_BETA];
-  const double c = beta > 0.0 ? st[KS_ALPHA] / beta : 0.0;
-  double s = 0.0;
+  const T c = (T)(beta > 0.0 ? st[KS_ALPHA] / beta : 0.0);
+  T s = T(0);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double t = fma(-c, r2[i], q[i]);
+    const T t = fma(-c, r2[i], q[i]);
     r1[i] = t;
-    const double yi = minv[i] * t;
+    const T yi = minv[i] * t;
     q[i] = yi;
     s = fma(t, yi, s);
   }
-  s = block_sum(s);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  const double tt = block_sum((double)s);
+  if (threadIdx.x == 0) part[blockIdx.x] = tt;
 }
 
 __global__ void k_pm_scalar(double* st) {
@@ -429,28 +458,30 @@ __global__ void k_pm_scalar(double* st) {
 // w_{k-2}; x += phi w_k. u is read here for the last time and zeroed: it is
 // the next product's output (also once frozen, so that the frozen
 // iterations' products stay bounded).
-__global__ void k_pm_w(double* __restrict__ u, const double* __restrict__ w, double* __restrict__ wprev,
-                       double* __restrict__ sol, const double* __restrict__ st, size_t n) {
-  const double ig = st[KS_INV_GAMMA], phi = st[KS_PHI];
-  const double cu = st[KS_WU], cp = st[KS_WP], cw = st[KS_WW];
-  const bool frozen = phi == 0.0 && ig == 0.0;
+template <class T>
+__global__ void k_pm_w(T* __restrict__ u, const T* __restrict__ w, T* __restrict__ wprev, T* __restrict__ sol,
+                       const double* __restrict__ st, size_t n) {
+  const double igd = st[KS_INV_GAMMA], phid = st[KS_PHI];
+  const T phi = (T)phid, cu = (T)st[KS_WU], cp = (T)st[KS_WP], cw = (T)st[KS_WW];
+  const bool frozen = phid == 0.0 && igd == 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     if (!frozen) {
-      const double wn = fma(-cw, w[i], fma(-cp, wprev[i], u[i] * cu));
+      const T wn = fma(-cw, w[i], fma(-cp, wprev[i], u[i] * cu));
       wprev[i] = wn;
       sol[i] = fma(phi, wn, sol[i]);
     }
-    u[i] = 0.0;
+    u[i] = T(0);
   }
 }
 
-int pminres_init(const double* b, const double* minv, double* r1, double* r2, double* u, double* q, double* w,
-                 double* wprev, double* sol, double* st, double* part, size_t n, double rtol, int maxit,
-                 cudaStream_t s, const PrecondAdd* pc) {
+template <class T>
+int pminres_init(const double* b, const T* minv, T* r1, T* r2, T* u, T* q, T* w, T* wprev, T* sol, double* st,
+                 double* part, size_t n, double rtol, int maxit, cudaStream_t s, const PrecondAdd* pc) {
   int g = red_grid(n);
-  k_pm_init<<<g, kThreads, 0, s>>>(b, minv, r1, r2, u, q, w, wprev, sol, n, part);
+  k_pm_init<T><<<g, kThreads, 0, s>>>(b, minv, r1, r2, u, q, w, wprev, sol, n, part);
   if (pc) {   // u += C b, and the partials of b . C b after the diagonal part's
-    const int np = pc->apply(pc->obj, b, u, part + g, s);
+    // (the FP32 form passes its FP32 copy of b, r1 after the initialisation)
+    const int np = pc->apply_t(pc->obj, r1, u, part + g, s);
     if (np < 0) return (int)cudaErrorLaunchFailure;
     g += np;
   }
@@ -459,22 +490,50 @@ int pminres_init(const double* b, const double* minv, double* r1, double* r2, do
   return (int)cudaGetLastError();
 }
 
-int pminres_after_hv(const double* minv, double* r1, const double* r2, double* u, double* q, const double* w,
-                     double* wprev, double* sol, double* st, double* part, size_t n, cudaStream_t s,
-                     const PrecondAdd* pc) {
+template <class T>
+int pminres_after_hv(const T* minv, T* r1, const T* r2, T* u, T* q, const T* w, T* wprev, T* sol, double* st,
+                     double* part, size_t n, cudaStream_t s, const PrecondAdd* pc) {
   const int g = red_grid(n);
-  k_pm_a<<<g, kThreads, 0, s>>>(q, r1, u, st, n, part);
+  k_pm_a<T><<<g, kThreads, 0, s>>>(q, r1, u, st, n, part);
   k_sum_scaled<<<1, kThreads, 0, s>>>(part, g, st + KS_INV_BETA, st + KS_ALPHA);
   int g2 = g;
-  k_pm_b<<<g, kThreads, 0, s>>>(minv, r1, r2, q, st, n, part);
+  k_pm_b<T><<<g, kThreads, 0, s>>>(minv, r1, r2, q, st, n, part);
   if (pc) {   // q += C t (t now in r1's buffer), and the partials of t . C t after the diagonal part's
-    const int np = pc->apply(pc->obj, r1, q, part + g, s);
+    const int np = pc->apply_t(pc->obj, r1, q, part + g, s);
     if (np < 0) return (int)cudaErrorLaunchFailure;
     g2 += np;
   }
   k_sum_final<<<1, kThreads, 0, s>>>(part, g2, st + KS_BETA_NEXT2);
   k_pm_scalar<<<1, 1, 0, s>>>(st);
-  k_pm_w<<<g, kThreads, 0, s>>>(u, w, wprev, sol, st, n);
+  k_pm_w<T><<<g, kThreads, 0, s>>>(u, w, wprev, sol, st, n);
+  return (int)cudaGetLastError();
+}
+
+#define TMOP_PMINRES(T)                                                                                        \
+  template int pminres_init<T>(const double*, const T*, T*, T*, T*, T*, T*, T*, T*, double*, double*, size_t, \
+                               double, int, cudaStream_t, const PrecondAdd*);                                 \
+  template int pminres_after_hv<T>(const T*, T*, const T*, T*, T*, const T*, T*, T*, double*, double*, size_t, \
+                                   cudaStream_t, const PrecondAdd*);
+TMOP_PMINRES(double)
+TMOP_PMINRES(float)
+#undef TMOP_PMINRES
+
+// sol (FP32) -> p (FP64)
+__global__ void k_widen(const float* __restrict__ a, double* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (double)a[i];
+}
+// out = FP32 copy of a
+__global__ void k_narrow(const double* __restrict__ a, float* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (float)a[i];
+}
+int widen(const float* a, double* out, size_t n, cudaStream_t s) {
+  k_widen<<<red_grid(n), kThreads, 0, s>>>(a, out, n);
+  return (int)cudaGetLastError();
+}
+int narrow(const double* a, float* out, size_t n, cudaStream_t s) {
+  k_narrow<<<red_grid(n), kThreads, 0, s>>>(a, out, n);
   return (int)cudaGetLastError();
 }
 

@@ -1,4 +1,6 @@
-// FP64 vector kernels (reductions, MINRES/CG steps, line-search updates).
+// Vector kernels (reductions, MINRES/CG steps, line-search updates). The
+// MINRES vectors are FP64, or FP32 (T = float) for the Krylov solves of the
+// FP32 forms; scalars and reductions are FP64 either way.
 #pragma once
 #include <cuda_runtime.h>
 #include <stddef.h>
@@ -38,17 +40,18 @@ int vec_mul(const double* a, const double* b, double* out, size_t n, cudaStream_
 // (Av: the first product's output buffer, zeroed here; every later product
 // accumulates into the buffer the Lanczos step of the previous iteration
 // zeroed)
-int minres_init(const double* b, double* v, double* vprev, double* Av, double* w, double* wprev, double* sol,
-                double* st, double* part, size_t n, double rtol, int maxit, cudaStream_t s);
+template <class T>
+int minres_init(const double* b, T* v, T* vprev, T* Av, T* w, T* wprev, T* sol, double* st, double* part, size_t n,
+                double rtol, int maxit, cudaStream_t s);
 // one MINRES step after Av = H v, on rotating buffers: afterwards (v, vprev, Av) -> (Av, v, vprev),
 // (w, wp) -> (wp, w);
 // Av is the product of the stored v array (not of the scaled vector); vdot (vdot_np partials of
 // v array . Av from the product kernel) replaces the dot-product pass when given. The new Lanczos
 // vector is left in Av unnormalised, its scale in st[KS_SV]; vprev is zeroed (the next product
 // accumulates into it).
-int minres_after_hv_rot(const double* v, double* vprev, double* Av, const double* w, double* wp, double* sol,
-                        double* st, double* part, size_t n, cudaStream_t s, const double* vdot = nullptr,
-                        int vdot_np = 0);
+template <class T>
+int minres_after_hv_rot(const T* v, T* vprev, T* Av, const T* w, T* wp, T* sol, double* st, double* part, size_t n,
+                        cudaStream_t s, const double* vdot = nullptr, int vdot_np = 0);
 // Preconditioned MINRES (M^-1 = minv, a diagonal): r1, r2, y, v, w, wprev, sol
 // An additive part of the preconditioner beside the diagonal minv: y += C r,
 // with the per-block partials of r . (C r) written to part (at most
@@ -57,7 +60,14 @@ int minres_after_hv_rot(const double* v, double* vprev, double* Av, const double
 // error.
 struct PrecondAdd {
   int (*apply)(void* obj, const double* r, double* y, double* part, cudaStream_t s);
+  int (*apply32)(void* obj, const float* r, float* y, double* part, cudaStream_t s);   // FP32 vectors (or null)
   void* obj;
+  int apply_t(void* o, const double* r, double* y, double* part, cudaStream_t s) const {
+    return apply(o, r, y, part, s);
+  }
+  int apply_t(void* o, const float* r, float* y, double* part, cudaStream_t s) const {
+    return apply32 ? apply32(o, r, y, part, s) : -1;
+  }
 };
 // Preconditioned MINRES on rotating buffers. The Lanczos vector is kept
 // unnormalised: u = beta v, and the product runs on u (q = H u). Per
@@ -67,13 +77,16 @@ struct PrecondAdd {
 // Initially r1 = r2 = b, u = M^-1 b, q = w = wprev = sol = 0. The product
 // accumulates into q: the direction pass zeroes u once it has read it, so
 // the next iteration's q starts at zero.
-int pminres_init(const double* b, const double* minv, double* r1, double* r2, double* u, double* q, double* w,
-                 double* wprev, double* sol, double* st, double* part, size_t n, double rtol, int maxit,
-                 cudaStream_t s, const PrecondAdd* pc = nullptr);
+template <class T>
+int pminres_init(const double* b, const T* minv, T* r1, T* r2, T* u, T* q, T* w, T* wprev, T* sol, double* st,
+                 double* part, size_t n, double rtol, int maxit, cudaStream_t s, const PrecondAdd* pc = nullptr);
 // after the product q = H u
-int pminres_after_hv(const double* minv, double* r1, const double* r2, double* u, double* q, const double* w,
-                     double* wprev, double* sol, double* st, double* part, size_t n, cudaStream_t s,
-                     const PrecondAdd* pc = nullptr);
+template <class T>
+int pminres_after_hv(const T* minv, T* r1, const T* r2, T* u, T* q, const T* w, T* wprev, T* sol, double* st,
+                     double* part, size_t n, cudaStream_t s, const PrecondAdd* pc = nullptr);
+// FP32 <-> FP64 copies of a vector
+int widen(const float* a, double* out, size_t n, cudaStream_t s);
+int narrow(const double* a, float* out, size_t n, cudaStream_t s);
 int cg_init(const double* b, double* r, double* d, double* sol, double* st, double* part, size_t n, double rtol,
             int maxit, cudaStream_t s);
 int cg_after_hv(double* sol, double* r, double* d, const double* Hd, double* st, double* part, size_t n,

@@ -48,7 +48,7 @@ class NewtonOpts(C.Structure):
     _fields_ = [("max_newton", C.c_int), ("rtol", C.c_double), ("krylov", C.c_int), ("krylov_rtol", C.c_double),
                 ("krylov_maxit", C.c_int), ("alpha_shrink", C.c_double), ("max_halvings", C.c_int),
                 ("f_factor", C.c_double), ("g_factor", C.c_double), ("atol", C.c_double),
-                ("matrix_free", C.c_int), ("precond", C.c_int)]
+                ("matrix_free", C.c_int), ("precond", C.c_int), ("krylov_fp64", C.c_int)]
 
 
 class NewtonReport(C.Structure):

@@ -704,6 +704,25 @@ def test_minres_with_compact_records_solves_the_fp64_system(tm, delta):
     assert rel(host(p), po) <= 1e-3
 
 
+@pytest.mark.parametrize("precond", [0, 1, 2])
+def test_fp32_krylov_vectors_solve_the_same_system(tm, precond):
+    """The FP32 forms run MINRES on FP32 vectors by default (krylov_fp64 = 0):
+    the solution matches the FP64-vector solve of the same FP32 operator and
+    the oracle's FP64 system to the FP32 operator's accuracy, in about the
+    same number of iterations, for plain, Jacobi and two-level MINRES."""
+    m = make("c4", 2, nx=(6, 5, 4))
+    orc = orc_for(m)
+    b = orc.gradient(m.x)
+    ctx = tm.Context.from_mesh(m, precision=tm.FP32_MIXED)
+    p32, it32 = ctx.krylov_solve(dev(m.x), dev(b), krylov_rtol=1e-6, krylov_maxit=3000, precond=precond)
+    p64, it64 = ctx.krylov_solve(dev(m.x), dev(b), krylov_rtol=1e-6, krylov_maxit=3000, precond=precond,
+                                 krylov_fp64=1)
+    assert it32 > 0 and it64 > 0 and abs(it32 - it64) <= max(3, it64 // 10), (it32, it64)
+    assert rel(host(p32), host(p64)) <= 1e-4
+    r = orc.hess_apply(m.x, host(p32)) - b
+    assert np.linalg.norm(r) <= 1e-4 * np.linalg.norm(b), np.linalg.norm(r) / np.linalg.norm(b)
+
+
 @pytest.mark.parametrize("metric,scale", [(2, None), (7, 1.0 / 8)])
 def test_newton_matches_oracle_history(tm, metric, scale):
     """Section 3.4 Newton on 8x8 order-2: the same accepted step lengths and
