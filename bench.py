@@ -515,14 +515,18 @@ def run_ours(args):
         torch.cuda.synchronize()
         net.close()
         return 0
-    if args.kernels_only and args.profile == "pa":
+    if args.kernels_only and args.profile in ("pa", "pa32"):
         # the partially assembled product alone, in the form the Krylov loops run
-        # it (y += H v): one linearisation, then W + K products
+        # it (y += H v; pa32: on FP32 vectors): one linearisation, then W + K products
         ctx.linearize(x)
         y.zero_()
+        v32, y32 = v.to(torch.float32), torch.zeros(v.shape, dtype=torch.float32, device=v.device)
         for _ in range(args.warmup + args.steps):
             flush.fill_(1.0)
-            ctx.hess_apply_pa(v, out=y, accumulate=True)
+            if args.profile == "pa32":
+                ctx.hess_apply_pa_add_f32(v32, y32)
+            else:
+                ctx.hess_apply_pa(v, out=y, accumulate=True)
         torch.cuda.synchronize()
         return 0
     for _ in range(args.warmup):
@@ -742,7 +746,7 @@ def measure_pa(tm, m, x, v, y, flush, stream, args):
         fwd, adj = contraction_fmas(m.dim, n, m.nq, m.dim)
         flops = m.nelem * (2 * (fwd + adj) + 2 * dd * dd * m.Q)   # contractions + the d^2 x d^2 product
         ent = {"linearize_ms": lin_ms, "hess_pa_ms": hv_ms, "hess_pa_zeroing_ms": hv0_ms,
-               "product_form": "y += H v (tmop_hess_apply_pa_add, as in the Krylov loops)", "bytes_per_launch": nbytes,
+               "product_form": "y += H v on FP64 vectors (tmop_hess_apply_pa_add)", "bytes_per_launch": nbytes,
                "achieved_GBps": nbytes / (hv_ms * 1e-3) / 1e9, "achieved_TFLOPs": flops / (hv_ms * 1e-3) / 1e12}
         if pf == tm.FP64:
             alu = getattr(args, "_alu_peaks", None)
@@ -760,6 +764,19 @@ def measure_pa(tm, m, x, v, y, flush, stream, args):
             ent["values_per_point"] = ns
             if metric is not None:
                 ent["metric"] = metric
+            # the form the FP32 contexts' MINRES runs: FP32 v and y (tmop_hess_apply_pa_add_f32)
+            v32 = v.to(torch.float32)
+            y32 = torch.zeros_like(v32)
+            c.hess_apply_pa_add_f32(v32, y32)
+            torch.cuda.synchronize()
+            f32_ms = _event_ms(lambda: c.hess_apply_pa_add_f32(v32, y32), reps, stream, flush)
+            b32 = m.n_qp * ns * elt + 3 * x.numel() * 4       # stored values + v read + y read and written (FP32)
+            ent["fp32_vectors"] = {"hess_pa_ms": f32_ms, "bytes_per_launch": b32,
+                                   "product_form": "y += H v on FP32 vectors (tmop_hess_apply_pa_add_f32, "
+                                                   "the FP32 MINRES operator)",
+                                   "achieved_GBps": b32 / (f32_ms * 1e-3) / 1e9,
+                                   "frac": b32 / (f32_ms * 1e-3) / 1e9 / hbm}
+            del v32, y32
             tfile = os.path.join(ROOT, "profiles", "traffic.json")
             if os.path.exists(tfile):
                 with open(tfile) as f:
@@ -812,14 +829,17 @@ def time_to_converged(tm, m, dev, args):
     # Hessians)
     # and both forms with the two-level preconditioner (Jacobi plus the exact
     # coarse correction on the element vertices)
-    for name, pf, pc in (("fp64", tm.FP64, 0), ("mixed", tm.FP32_MIXED, 0), ("mixed_jacobi", tm.FP32_MIXED, 1),
-                         ("fp64_twolevel", tm.FP64, 2), ("mixed_twolevel", tm.FP32_MIXED, 2)):
+    # (the FP32 forms run MINRES on FP32 vectors; "mixed_fp64_vectors" keeps FP64 ones)
+    for name, pf, pc, k64 in (("fp64", tm.FP64, 0, 0), ("mixed", tm.FP32_MIXED, 0, 0),
+                              ("mixed_fp64_vectors", tm.FP32_MIXED, 0, 1), ("mixed_jacobi", tm.FP32_MIXED, 1, 0),
+                              ("fp64_twolevel", tm.FP64, 2, 0), ("mixed_twolevel", tm.FP32_MIXED, 2, 0)):
         c = tm.Context.from_mesh(m, precision=pf)
         xc = torch.tensor(m.x, device=dev)
         F0 = c.energy(xc)[1]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = c.newton_solve(xc, max_newton=args.max_newton, krylov=args.krylov, rtol=1e-12, precond=pc)
+        res = c.newton_solve(xc, max_newton=args.max_newton, krylov=args.krylov, rtol=1e-12, precond=pc,
+                             krylov_fp64=k64)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         rep = res.report
@@ -828,7 +848,7 @@ def time_to_converged(tm, m, dev, args):
                          "grad_rel": rep["grad_norm"] / max(rep["grad_norm0"], 1e-300), "min_detA": rep["min_detA"]}
         c.close()
     F64 = res_all["fp64"]["F"]
-    for k in ("mixed", "mixed_jacobi", "fp64_twolevel", "mixed_twolevel"):
+    for k in ("mixed", "mixed_fp64_vectors", "mixed_jacobi", "fp64_twolevel", "mixed_twolevel"):
         res_all[f"{k}_vs_fp64_F_rel"] = abs(res_all[k]["F"] - F64) / abs(F64)
         res_all[f"speedup_{k}_over_fp64"] = res_all["fp64"]["seconds"] / res_all[k]["seconds"]
     return res_all
@@ -1100,9 +1120,10 @@ def main():
                     help="with N > 1: split the workload's elements into z-slabs, one per rank, with a halo "
                          "sum of the shared node planes per operator application (strong scaling) instead "
                          "of N independent replicas")
-    ap.add_argument("--profile", choices=["step", "pa", "mlp", "newton", "newton_twolevel"], default="step",
+    ap.add_argument("--profile", choices=["step", "pa", "pa32", "mlp", "newton", "newton_twolevel"], default="step",
                     help="with --kernels-only: the timed step (gradient + Hessian action), the partially "
-                         "assembled Hessian action alone, training steps of the proposal MLP, or one "
+                         "assembled Hessian action alone (pa32: on FP32 vectors, with --precision mixed), "
+                         "training steps of the proposal MLP, or one "
                          "FP32-mixed Newton step (newton_twolevel: with the two-level preconditioner)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if not args.kernels_only else args.warmup

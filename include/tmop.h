@@ -169,6 +169,13 @@ int tmop_hess_apply_pa(tmop_ctx* ctx, const double* v, double* y, void* stream);
  * linearisation. Asynchronous. */
 int tmop_hess_apply_pa_add(tmop_ctx* ctx, const double* v, double* y, void* stream);
 
+/* The same accumulating product on FP32 vectors (DEVICE [dim][nnode]
+ * float): y += H(x) v at the free dofs with FP32 atomics, the form the FP32
+ * contexts' MINRES runs (tmop_newton_opts.krylov_fp64 = 0). TMOP_ERR_ARG for
+ * a TMOP_FP64 context, with the restricted-movement term, or without a
+ * linearisation. Asynchronous. */
+int tmop_hess_apply_pa_add_f32(tmop_ctx* ctx, const float* v, float* y, void* stream);
+
 /* Layout of the stored linearisation: values per quadrature point (the
  * packed upper triangle of the d^2 x d^2 A-space Hessian, 10 in 2D and 45 in
  * 3D; or, for a 3D FP32 context with an (|T|^2, det T) metric, a constant

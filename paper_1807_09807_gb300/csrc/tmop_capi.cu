@@ -1207,6 +1207,12 @@ int tmop_hess_apply_pa_add(tmop_ctx* c, const double* v, double* y, void* stream
   return launch_op(c, OP_HESS_PA, nullptr, v, y, nullptr, (cudaStream_t)stream, nullptr, true);
 }
 
+int tmop_hess_apply_pa_add_f32(tmop_ctx* c, const float* v, float* y, void* stream) {
+  if (!c || !v || !y) return TMOP_ERR_ARG;
+  if (!c->pa_valid || c->precision == TMOP_FP64 || c->delta != 0.0) return TMOP_ERR_ARG;
+  return launch_op(c, OP_HESS_PA, nullptr, nullptr, nullptr, nullptr, (cudaStream_t)stream, nullptr, true, v, y);
+}
+
 int tmop_pa_layout(const tmop_ctx* c, int* values_per_point, int* stride, int* elt_bytes) {
   if (!c || !c->pa_valid) return TMOP_ERR_ARG;
   const int dd = c->dim * c->dim;

@@ -81,6 +81,7 @@ _SIGNATURES = {
     "tmop_linearize": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_hess_apply_pa": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_hess_apply_pa_add": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "tmop_hess_apply_pa_add_f32": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_hessian_diagonal": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_pa_layout": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "tmop_sizes": ([C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
@@ -395,6 +396,17 @@ class Context:
         rc = getattr(load(), fn)(self._h, _ptr(v), _ptr(y), _stream())
         if rc != OK:
             raise TmopError(rc, fn)
+        return y
+
+    def hess_apply_pa_add_f32(self, v, y):
+        """y += H v on FP32 vectors (tmop_hess_apply_pa_add_f32; FP32 contexts)."""
+        import torch
+        for t, nm in ((v, "v"), (y, "y")):
+            if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != tuple(self.shape):
+                raise ValueError(f"{nm} must be a contiguous CUDA float32 tensor of shape {self.shape}")
+        rc = load().tmop_hess_apply_pa_add_f32(self._h, _ptr(v), _ptr(y), _stream())
+        if rc != OK:
+            raise TmopError(rc, "tmop_hess_apply_pa_add_f32")
         return y
 
     def pa_layout(self):

@@ -87,6 +87,7 @@ def test_null_arguments(lib):
     assert lib.tmop_linearize(None, None, None) == tm.ERR_ARG
     assert lib.tmop_hess_apply_pa(None, None, None, None) == tm.ERR_ARG
     assert lib.tmop_hess_apply_pa_add(None, None, None, None) == tm.ERR_ARG
+    assert lib.tmop_hess_apply_pa_add_f32(None, None, None, None) == tm.ERR_ARG
     assert lib.tmop_energy_gradient(None, None, None, None, None, None) == tm.ERR_ARG
     assert lib.tmop_hessian_diagonal(None, None, None) == tm.ERR_ARG
     assert lib.tmop_element_min_detA(None, None, None, None) == tm.ERR_ARG

@@ -499,6 +499,13 @@ def test_fp32_stored_hessian_product_3d(tm, order, nq, nx, structured):
     free = m.fixed == 0
     assert np.all(ya[~free] == y0[~free])
     assert np.abs(ya[free] - (y0[free] + y[free])).max() <= 1e-12 * (np.abs(y0).max() + np.abs(y).max())
+    # on FP32 vectors (the FP32 MINRES form): FP32 v, FP32 atomics into y
+    v32 = torch.tensor(v, dtype=torch.float32, device="cuda")
+    y32 = torch.tensor(np.where(free, 0.0, 7.0), dtype=torch.float32, device="cuda")
+    c32.hess_apply_pa_add_f32(v32, y32)
+    y32h = y32.cpu().numpy().astype(np.float64)
+    assert np.all(y32h[~free] == 7.0)
+    assert rel(np.where(free, y32h, 0.0), yo) <= 1e-5
 
 
 @pytest.mark.parametrize("case", ["mu14", "mu1", "W", "mu302", "mu98", "composite", "per_point_W", "bulk"])
