@@ -609,7 +609,8 @@ def test_partial_assembly_requires_linearize(tm):
 # ---------------------------------------------------------------- Jacobi preconditioning
 @pytest.mark.parametrize("name,kw,extras", [("c1", dict(nx=4), ""), ("c3", dict(nx=2), ""),
                                             ("c1", dict(nx=3), "composite+delta"), ("c3", dict(nx=2), "fp32"),
-                                            ("c3", dict(nx=2), "fp32+W"), ("c3", dict(nx=2), "fp32+composite")])
+                                            ("c3", dict(nx=2), "fp32+W"), ("c3", dict(nx=2), "fp32+composite"),
+                                            ("c4", dict(nx=(3, 2, 2)), "fp32"), ("c4", dict(nx=(2, 2, 3)), "fp32+W")])
 def test_hessian_diagonal_matches_oracle(tm, name, kw, extras):
     """Diagonal of the partially assembled Hessian against the oracle's
     Hessian action on every unit vector (brute force), 1 at fixed dofs; in
