@@ -309,6 +309,38 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
         MetricLin<D, R> L;
         const bool lin = !metric_dual(p.metric);
         bool ok = lin ? L.init(p.metric, T) : true;
+        if constexpr (D == 3) {
+          if (lin && p.wkind == WK_IDENTITY && !p.metric2) {
+            // W = I, an (|T|^2, det T) metric: the 45 entries in closed form,
+            //   H[(a,b),(c,d)] = 2 mu_1 d_ac d_bd + (4 mu_11 T_cd + 2 mu_1t C_cd) T_ab
+            //                    + (2 mu_1t T_cd + mu_tt C_cd) C_ab + mu_t dC_ab/dT_cd,
+            // with dC_ab/dT_cd = +-T_ef (e, f the indices other than a, c and
+            // b, d; zero if a = c or b = d): ~4 operations per entry where the
+            // directional derivative costs ~100 per column
+            const R m1 = s * L.m1, mt = s * L.mt, m11 = s * L.m11, m1t = s * L.m1t, mtt = s * L.mtt;
+            int off3 = 0;
+#pragma unroll
+            for (int kl = 0; kl < 9; ++kl) {
+              const int c = kl / 3, d = kl % 3;
+              const R Pc = fma(R(4) * m11, T[kl], R(2) * m1t * L.C[kl]);
+              const R Qc = fma(R(2) * m1t, T[kl], mtt * L.C[kl]);
+#pragma unroll
+              for (int mn = kl; mn < 9; ++mn) {
+                const int a = mn / 3, b = mn % 3;
+                R v = fma(Pc, T[mn], Qc * L.C[mn]);
+                if (mn == kl) v += R(2) * m1;
+                if (a != c && b != d) {
+                  const int ee = 3 - a - c, ff = 3 - b - d;
+                  const bool plus = (c == (a + 1) % 3) == (d == (b + 1) % 3);
+                  v = fma(plus ? mt : -mt, T[ee * 3 + ff], v);
+                }
+                H[(size_t)(off3 + mn - kl) * QP] = ok ? v : R(0);
+              }
+              off3 += 9 - kl;
+            }
+            continue;
+          }
+        }
         int off = 0;
 #pragma unroll 1
         for (int kl = 0; kl < DD; ++kl) {
