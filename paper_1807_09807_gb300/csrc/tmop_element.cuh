@@ -52,8 +52,16 @@ struct ElemCfg {
   static constexpr int B1 = round16<R>(Buf<D, N, Q1, NC>::B1);
   static constexpr int B2 = SPLIT ? round16<R>(D * D * Shape<D, N, Q1>::QP) : 0;
   static constexpr int PER_WARP = (int)sizeof(R) * (B0 + B1 + B2);
-  // up to 8 warps (elements in flight) per block within ~200 KB of shared memory
-  static constexpr int WARPS = (200 * 1024 / PER_WARP) >= 8 ? 8 : ((200 * 1024 / PER_WARP) < 1 ? 1 : 200 * 1024 / PER_WARP);
+  // up to 8 warps (elements in flight) per block within ~200 KB of shared
+  // memory; the FP64 3D energy, gradient and stored-Hessian product (16 KB
+  // per warp for order 3) run as 6-warp blocks, two per SM: 12 warps in
+  // flight instead of 8 on the FP64 pipe (gradient -2 %, stored-Hessian
+  // product -8 % on 48^3 order-3 hexes)
+  static constexpr bool TWO = D == 3 && sizeof(R) == 8 && OP != OP_LINEARIZE && OP != OP_HESS &&
+                              12 * PER_WARP <= 200 * 1024;
+  static constexpr int WARPS = TWO ? 6
+                                   : ((200 * 1024 / PER_WARP) >= 8 ? 8
+                                                                   : ((200 * 1024 / PER_WARP) < 1 ? 1 : 200 * 1024 / PER_WARP));
   static constexpr int TABLE = round16<R>(2 * kMaxQ * kMaxN + kMaxQ);
   static constexpr size_t smem_bytes() { return sizeof(R) * (TABLE + WARPS * (B0 + B1 + B2)); }
 };
