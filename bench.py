@@ -835,17 +835,23 @@ def time_to_converged(tm, m, dev, args):
     # Hessians)
     # and both forms with the two-level preconditioner (Jacobi plus the exact
     # coarse correction on the element vertices)
-    # (the FP32 forms run MINRES on FP32 vectors; "mixed_fp64_vectors" keeps FP64 ones)
-    for name, pf, pc, k64 in (("fp64", tm.FP64, 0, 0), ("mixed", tm.FP32_MIXED, 0, 0),
-                              ("mixed_fp64_vectors", tm.FP32_MIXED, 0, 1), ("mixed_jacobi", tm.FP32_MIXED, 1, 0),
-                              ("fp64_twolevel", tm.FP64, 2, 0), ("mixed_twolevel", tm.FP32_MIXED, 2, 0)):
+    # (the FP32 forms run MINRES on FP32 vectors; "mixed_fp64_vectors" keeps FP64 ones;
+    # "mixed_matrix_free[_cg]": the FP32 Hessian action recomputed from x at every product,
+    # no linearisation, with MINRES or CG)
+    arms = (("fp64", tm.FP64, 0, {}), ("mixed", tm.FP32_MIXED, 0, {}),
+            ("mixed_fp64_vectors", tm.FP32_MIXED, 0, {"krylov_fp64": 1}), ("mixed_jacobi", tm.FP32_MIXED, 1, {}),
+            ("fp64_twolevel", tm.FP64, 2, {}), ("mixed_twolevel", tm.FP32_MIXED, 2, {}),
+            ("mixed_matrix_free", tm.FP32_MIXED, 0, {"matrix_free": 1}),
+            ("mixed_matrix_free_cg", tm.FP32_MIXED, 0, {"matrix_free": 1, "krylov": "cg"}))
+    for name, pf, pc, kw in arms:
         c = tm.Context.from_mesh(m, precision=pf)
         xc = torch.tensor(m.x, device=dev)
         F0 = c.energy(xc)[1]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = c.newton_solve(xc, max_newton=args.max_newton, krylov=args.krylov, rtol=1e-12, precond=pc,
-                             krylov_fp64=k64)
+        kw = dict(kw)
+        kv = kw.pop("krylov", args.krylov)
+        res = c.newton_solve(xc, max_newton=args.max_newton, krylov=kv, rtol=1e-12, precond=pc, **kw)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         rep = res.report
@@ -854,7 +860,8 @@ def time_to_converged(tm, m, dev, args):
                          "grad_rel": rep["grad_norm"] / max(rep["grad_norm0"], 1e-300), "min_detA": rep["min_detA"]}
         c.close()
     F64 = res_all["fp64"]["F"]
-    for k in ("mixed", "mixed_fp64_vectors", "mixed_jacobi", "fp64_twolevel", "mixed_twolevel"):
+    for k in ("mixed", "mixed_fp64_vectors", "mixed_jacobi", "fp64_twolevel", "mixed_twolevel", "mixed_matrix_free",
+              "mixed_matrix_free_cg"):
         res_all[f"{k}_vs_fp64_F_rel"] = abs(res_all[k]["F"] - F64) / abs(F64)
         res_all[f"speedup_{k}_over_fp64"] = res_all["fp64"]["seconds"] / res_all[k]["seconds"]
     return res_all
