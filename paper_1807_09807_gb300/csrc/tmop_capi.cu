@@ -257,12 +257,19 @@ JacParams jac_params(const tmop_ctx* c, const double* x, double* J) {
   return jp;
 }
 
+// The 3D FP32 recomputed Hessian action runs through compact records built in
+// shared memory (OP_HESS_C) for the metrics and targets of the compact pair.
+bool hess_c_ok(const tmop_ctx* c) {
+  return c->ent[OP_HESS_C] && metric_is_lin(c->base.metric) && c->base.metric2 == 0 && c->base.wkind != WK_PER_QP;
+}
+
 // accumulate: y += the scatter op's result (y not zeroed first); v32, y32:
 // FP32 direction and output of the stored-Hessian products instead of v, y
 int launch_op(tmop_ctx* c, int op, const double* x, const double* v, double* y, double* elem_min,
               cudaStream_t s, double* vdot = nullptr, bool accumulate = false, const float* v32 = nullptr,
               float* y32 = nullptr) {
-  if ((v32 || y32) && !(v32 && y32 && op == OP_HESS_PA && c->delta == 0.0)) return TMOP_ERR_ARG;
+  if ((v32 || y32) && !(v32 && y32 && (op == OP_HESS_PA || (op == OP_HESS && hess_c_ok(c))) && c->delta == 0.0))
+    return TMOP_ERR_ARG;
   KParams p = c->base;
   p.x = x;
   p.v = v;
@@ -280,6 +287,8 @@ int launch_op(tmop_ctx* c, int op, const double* x, const double* v, double* y, 
   int kop = op;  // the stored linearisation decides which form of the pair runs
   if (c->pa_compact && op == OP_LINEARIZE) kop = OP_LINEARIZE_C;
   if (c->pa_compact && op == OP_HESS_PA) kop = OP_HESS_PA_C;
+  // the recomputed FP32 product through compact records built on the fly
+  if (op == OP_HESS && hess_c_ok(c)) kop = OP_HESS_C;
   p.vdot = kop == OP_HESS_PA_C ? vdot : nullptr;
   const bool scatter = op == OP_GRADIENT || op == OP_HESS || op == OP_HESS_PA || op == OP_ENERGY_GRAD;
   // deterministic scatter: one launch per colour, in colour order
@@ -668,7 +677,8 @@ int krylov(tmop_ctx* c, const double* x, const double* b, double* p, const tmop_
   }
   // FP32 forms: MINRES on FP32 vectors (the operator is FP32 there), unless asked otherwise
   const bool cg = o.krylov == TMOP_KRYLOV_CG;
-  const bool use32 = c->precision != TMOP_FP64 && !o.krylov_fp64 && hop == OP_HESS_PA && !cg && c->delta == 0.0;
+  const bool use32 = c->precision != TMOP_FP64 && !o.krylov_fp64 && (hop == OP_HESS_PA || hess_c_ok(c)) && !cg &&
+                     c->delta == 0.0;
   if (use32) return krylov_run<float>(c, x, b, p, o, iters, s, hop, minv, pc);
   return krylov_run<double>(c, x, b, p, o, iters, s, hop, minv, pc);
 }
@@ -810,7 +820,7 @@ int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metr
     // FP32_MIXED: FP32 only for the Hessian action (and its partial assembly);
     // FP32_BULK: every element kernel
     const bool hess = op == OP_HESS || op == OP_LINEARIZE || op == OP_HESS_PA || op == OP_LINEARIZE_C ||
-                      op == OP_HESS_PA_C;
+                      op == OP_HESS_PA_C || op == OP_HESS_C;
     const int fp32 = precision == TMOP_FP32_BULK || (precision == TMOP_FP32_MIXED && hess);
     ent[op] = find_elem(d, n, nq, fp32, op);
     // unsupported (order, points) pair; the compact pair exists for 3D FP32 only

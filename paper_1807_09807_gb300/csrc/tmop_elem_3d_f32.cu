@@ -12,7 +12,8 @@ namespace tmop {
 #define TMOP_ENTRIES(N, Q)                                                                      \
   TMOP_ENTRY(N, Q, OP_ENERGY), TMOP_ENTRY(N, Q, OP_GRADIENT), TMOP_ENTRY(N, Q, OP_HESS),         \
       TMOP_ENTRY(N, Q, OP_LINEARIZE), TMOP_ENTRY(N, Q, OP_HESS_PA), TMOP_ENTRY(N, Q, OP_LINEARIZE_C), \
-      {3, N, Q, 1, OP_HESS_PA_C, launch_pac<N, Q>, prepare_pac<N, Q>, kPacWarps}
+      {3, N, Q, 1, OP_HESS_PA_C, launch_pac<N, Q>, prepare_pac<N, Q>, kPacWarps}, \
+      {3, N, Q, 1, OP_HESS_C, launch_pacr<N, Q>, prepare_pacr<N, Q>, kPacrWarps}
 
 extern const ElemEntry kElem_3d_f32[] = {
     TMOP_ENTRIES(2,2),

@@ -20,7 +20,7 @@ constexpr int kMaxN = 5;   // 1D nodes (order <= 4)
 // (one pass where the line search of the Newton step needs both).
 enum {
   OP_ENERGY = 0, OP_GRADIENT = 1, OP_HESS = 2, OP_LINEARIZE = 3, OP_HESS_PA = 4,
-  OP_LINEARIZE_C = 5, OP_HESS_PA_C = 6, OP_ENERGY_GRAD = 7, OP_COUNT = 8
+  OP_LINEARIZE_C = 5, OP_HESS_PA_C = 6, OP_ENERGY_GRAD = 7, OP_HESS_C = 8, OP_COUNT = 9
 };
 constexpr int kCompactRec = 14;  // values per point of the compact record (3D)
 enum { WK_IDENTITY = 0, WK_CONST = 1, WK_PER_QP = 2 };

@@ -473,6 +473,191 @@ __global__ void __launch_bounds__(kPacWarps * 32, N == 4 ? 2 : 0) pac_kernel(con
   }
 }
 
+// ---------------------------------------------------------------- recomputed (matrix-free) product
+// The FP32 Hessian action recomputed from x (OP_HESS_C, the matrix-free
+// Krylov operator of the FP32 forms for (|T|^2, det T) metrics with a
+// constant target): per element, A(x) by the same forward contraction as
+// dA, the compact record of the point (T and w det W times the five partials
+// of mu) into shared memory, then the product exactly as from stored
+// records. x is taken relative to the element's first node in FP64 before
+// rounding (A is translation invariant), so A keeps FP32 relative accuracy.
+template <int N, int Q1>
+struct PacrCfg {
+  using P = PacCfg<N, Q1>;
+  static constexpr int QP = P::QP;
+  static constexpr int REC = round4(kCompactRec * QP);    // the element's records [value][q]
+  static constexpr int PER_WARP = P::B0 + P::B1 + REC;
+  static constexpr size_t smem_bytes() { return sizeof(float) * (kPacrWarps * PER_WARP + round4(QP)); }
+};
+
+// x at the nodes this lane gathers, relative to the element's first node
+template <int N, int NT>
+__device__ __forceinline__ void fetch_x(const KParams& p, const NodeMap<N>& m, int lane, float (&xr)[NT][3]) {
+  constexpr int NDOF = N * N * N;
+  const int g0 = m(0);
+  double x0[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) x0[c] = __ldg(p.x + (size_t)c * p.nnode + g0);
+#pragma unroll
+  for (int s = 0; s < NT; ++s) {
+    const int t = lane + 32 * s;
+    if (t < NDOF) {
+      const int g = m(t);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) xr[s][c] = __double2float_rn(__ldg(p.x + (size_t)c * p.nnode + g) - x0[c]);
+    }
+  }
+}
+
+// A at point q (Z buffer) -> the point's compact record, in shared memory
+template <class L, bool IDENT>
+__device__ __forceinline__ void pacr_record(int metric, const float (&Wi)[9], const float* buf, float* rec, int q,
+                                            int QP, float s) {
+  const float2* zp = reinterpret_cast<const float2*>(buf) + q;
+  const float* zs = buf + L::ZS + q;
+  float A[9], T[9];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float2 a = zp[c * (L::ZC / 2)];
+    A[c * 3 + 0] = zs[c * L::ZT];
+    A[c * 3 + 1] = a.x;
+    A[c * 3 + 2] = a.y;
+  }
+  if constexpr (IDENT) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) T[i] = A[i];
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        T[a * 3 + b] = fmaf(A[a * 3 + 0], Wi[0 * 3 + b], fmaf(A[a * 3 + 1], Wi[1 * 3 + b], A[a * 3 + 2] * Wi[2 * 3 + b]));
+  }
+  MetricLin<3, float> M;
+  const bool ok = M.init(metric, T);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) rec[i * QP + q] = T[i];
+  rec[9 * QP + q] = ok ? s * M.m1 : 0.f;
+  rec[10 * QP + q] = ok ? s * M.mt : 0.f;
+  rec[11 * QP + q] = ok ? s * M.m11 : 0.f;
+  rec[12 * QP + q] = ok ? s * M.m1t : 0.f;
+  rec[13 * QP + q] = ok ? s * M.mtt : 0.f;
+}
+
+template <int N, int Q1, bool IDENT, bool IO32>
+__global__ void __launch_bounds__(kPacrWarps * 32, N == 4 ? 2 : 1) pacr_kernel(const KParams p) {
+  using Cfg = PacCfg<N, Q1>;
+  using RC = PacrCfg<N, Q1>;
+  using L = typename Cfg::L;
+  constexpr int NDOF = Cfg::NDOF, QP = Cfg::QP, NT = Cfg::NT, NPL = Cfg::NPL;
+  extern __shared__ __align__(16) float pac_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* P0 = pac_smem + warp * RC::PER_WARP;
+  float* P1 = P0 + Cfg::B0;
+  float* REC = P1 + Cfg::B1;
+  float* sWq = pac_smem + kPacrWarps * RC::PER_WARP;   // w_q det W at every point
+  for (int q = threadIdx.x; q < QP; q += blockDim.x) {
+    const int q0 = q % Q1, q1 = (q / Q1) % Q1, q2 = q / (Q1 * Q1);
+    sWq[q] = (float)(p.w1[q0] * p.w1[q1] * p.w1[q2] * p.detW);
+  }
+  float2 tBG[Q1 * N];
+  float Wi[9];
+#pragma unroll
+  for (int t = 0; t < Q1 * N; ++t) tBG[t] = make_float2(f64_to_f32(p.B[t]), f64_to_f32(p.G[t]));
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Wi[i] = IDENT ? 0.f : f64_to_f32(p.Winv[i]);
+  __syncthreads();
+  const int stride = gridDim.x * kPacrWarps;
+  const int ecount = p.elist ? p.ecount : p.nelem;
+  auto elem = [&](int i) { return p.elist ? __ldg(p.elist + i) : i; };
+  int ei = blockIdx.x * kPacrWarps + warp;
+  if (ei >= ecount) return;   // whole warps only; nothing below waits on other warps
+  int e = elem(ei);
+  NodeMap<N> cur(p.elem_nodes, p.sx, p.sy), nxt(p.elem_nodes, p.sx, p.sy);
+  cur.element(e, NDOF);
+  float v[NT][3], vc[NT][3], xr[NT][3];
+  unsigned fnext;
+  fetch_x<N, NT>(p, cur, lane, xr);
+  fetch_v<N, NT, IO32>(p, cur, lane, v, fnext);
+  for (;;) {
+    // ---- x relative to the element's first node -> A at every point (Z)
+#pragma unroll
+    for (int s = 0; s < NT; ++s) {
+      const int t = lane + 32 * s;
+      if (t < NDOF) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) P0[c * L::XC + (t / N) * L::XR + t % N] = xr[s][c];
+      }
+    }
+    __syncwarp();
+    pac_fwd<N, Q1, L>(tBG, P0, P1, lane);
+    // ---- the compact record of every point
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int q = lane + 32 * k;
+      if (q < QP) pacr_record<L, IDENT>(p.metric, Wi, P1, REC, q, QP, sWq[q]);
+    }
+    __syncwarp();
+    // ---- v of this element (fixed dofs read as 0) -> dA at every point
+    const unsigned fcur = fnext;
+#pragma unroll
+    for (int s = 0; s < NT; ++s) {
+      const int t = lane + 32 * s;
+      if (t < NDOF) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          vc[s][c] = (fcur >> (s * 3 + c)) & 1u ? 0.f : v[s][c];
+          P0[c * L::XC + (t / N) * L::XR + t % N] = vc[s][c];
+        }
+      }
+    }
+    __syncwarp();
+    pac_fwd<N, Q1, L>(tBG, P0, P1, lane);
+    // ---- pointwise from the records in shared memory
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int q = lane + 32 * k;
+      if (q < QP) {
+        float h[kCompactRec];
+#pragma unroll
+        for (int i = 0; i < kCompactRec; ++i) h[i] = REC[i * QP + q];
+        pac_point<L, IDENT>(h, Wi, P1, q);
+      }
+    }
+    // ---- the next element's loads go out before this element's adjoint and scatter
+    const int eni = ei + stride;
+    const bool more = eni < ecount;
+    const int en = more ? elem(eni) : 0;
+    if (more) {
+      nxt.element(en, NDOF);
+      fetch_x<N, NT>(p, nxt, lane, xr);
+      fetch_v<N, NT, IO32>(p, nxt, lane, v, fnext);
+    }
+    __syncwarp();
+    pac_adj<N, Q1, L>(tBG, P0, P1, lane);
+#pragma unroll
+    for (int s = 0; s < NT; ++s) {
+      const int t = lane + 32 * s;
+      if (t < NDOF) {
+        const int g = cur(t);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float yf = P0[c * L::XC + (t / N) * L::XR + t % N];
+          if (!((fcur >> (s * 3 + c)) & 1u)) {
+            if constexpr (IO32) atomicAdd(p.y32 + (size_t)c * p.nnode + g, yf);
+            else atomicAdd(p.y + (size_t)c * p.nnode + g, (double)yf);
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (!more) break;
+    ei = eni;
+    e = en;
+    cur = nxt;
+  }
+}
+
 }  // namespace
 
 template <int N, int Q1>
@@ -511,8 +696,45 @@ int prepare_pac(int nelem, int* grid) {
   return 0;
 }
 
+template <int N, int Q1>
+int launch_pacr(const KParams& p, int grid, void* stream) {
+  const size_t smem = PacrCfg<N, Q1>::smem_bytes();
+  const bool id = p.wkind == WK_IDENTITY, io32 = p.v32 != nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (io32 != (p.y32 != nullptr) || !p.x) return (int)cudaErrorInvalidValue;
+  if (id && io32) pacr_kernel<N, Q1, true, true><<<grid, kPacrWarps * 32, smem, s>>>(p);
+  else if (id) pacr_kernel<N, Q1, true, false><<<grid, kPacrWarps * 32, smem, s>>>(p);
+  else if (io32) pacr_kernel<N, Q1, false, true><<<grid, kPacrWarps * 32, smem, s>>>(p);
+  else pacr_kernel<N, Q1, false, false><<<grid, kPacrWarps * 32, smem, s>>>(p);
+  return (int)cudaGetLastError();
+}
+
+template <int N, int Q1>
+int prepare_pacr(int nelem, int* grid) {
+  const size_t smem = PacrCfg<N, Q1>::smem_bytes();
+  const void* fn[4] = {(const void*)pacr_kernel<N, Q1, true, false>, (const void*)pacr_kernel<N, Q1, false, false>,
+                       (const void*)pacr_kernel<N, Q1, true, true>, (const void*)pacr_kernel<N, Q1, false, true>};
+  int per_sm = 1 << 30, dev = 0, sms = 0;
+  for (const void* f : fn) {
+    cudaError_t err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return (int)err;
+    int b = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kPacrWarps * 32, smem);
+    if (err != cudaSuccess) return (int)err;
+    per_sm = b < per_sm ? b : per_sm;
+  }
+  if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int need = (nelem + kPacrWarps - 1) / kPacrWarps, full = per_sm * sms;
+  *grid = need < full ? need : full;
+  return 0;
+}
+
 #define TMOP_PAC(N, Q) template int launch_pac<N, Q>(const KParams&, int, void*); \
-  template int prepare_pac<N, Q>(int, int*);
+  template int prepare_pac<N, Q>(int, int*); \
+  template int launch_pacr<N, Q>(const KParams&, int, void*); \
+  template int prepare_pacr<N, Q>(int, int*);
 TMOP_PAC(2, 2)
 TMOP_PAC(2, 3)
 TMOP_PAC(3, 3)

@@ -12,5 +12,12 @@ template <int N, int Q1>
 int launch_pac(const KParams& p, int grid, void* stream);
 template <int N, int Q1>
 int prepare_pac(int nelem, int* grid);
+// the FP32 Hessian action recomputed from x through compact records built in
+// shared memory (OP_HESS_C)
+constexpr int kPacrWarps = 6;
+template <int N, int Q1>
+int launch_pacr(const KParams& p, int grid, void* stream);
+template <int N, int Q1>
+int prepare_pacr(int nelem, int* grid);
 
 }  // namespace tmop

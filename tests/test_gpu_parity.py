@@ -508,6 +508,32 @@ def test_fp32_stored_hessian_product_3d(tm, order, nq, nx, structured):
     assert rel(np.where(free, y32h, 0.0), yo) <= 1e-5
 
 
+@pytest.mark.parametrize("order,nq,nx,structured,W", [(1, 2, (3, 3, 2), True, False), (2, 3, (3, 2, 3), False, True),
+                                                      (3, 5, (7, 5, 3), True, False), (3, 5, (6, 4, 4), False, True),
+                                                      (4, 5, (3, 2, 2), True, False), (4, 6, (3, 3, 3), True, True)])
+def test_fp32_recomputed_hessian_action_3d(tm, order, nq, nx, structured, W):
+    """The 3D FP32 Hessian action recomputed from x (the matrix-free Krylov
+    operator of the FP32 forms; compact records built per element in shared
+    memory) against the oracle's FP64 Hessian action: every order, ragged
+    grids, both node-numbering paths, W = I and a constant non-symmetric W,
+    boundary fixed, more elements than resident warps."""
+    m = make("c4", 3, order=order, nq=nq, nx=nx)
+    okw = {}
+    if W:
+        Wm = (np.eye(3) + 0.2 * np.random.default_rng(4).standard_normal((3, 3))) / 4
+        if np.linalg.det(Wm) < 0:
+            Wm[:, 0] *= -1
+        m.W = Wm
+        okw.update(wkind=oracle.W_CONST, W=Wm)
+    orc = oracle.Problem(m.dim, m.order, m.elem_nodes, m.nnode, m.fixed, m.nq, m.metric, **okw)
+    v = np.random.default_rng(order).standard_normal(m.x.shape)
+    yo = orc.hess_apply(m.x, v)
+    c32 = tm.Context.from_mesh(m, precision=tm.FP32_MIXED, structured=structured)
+    y = host(c32.hess_apply(dev(m.x), dev(v)))
+    assert rel(y, yo) <= 1e-5, rel(y, yo)
+    assert np.all(y[m.fixed == 1] == 0.0)
+
+
 @pytest.mark.parametrize("case", ["mu14", "mu1", "W", "mu302", "mu98", "composite", "per_point_W", "bulk"])
 def test_fp32_compact_and_packed_records_3d(tm, case):
     """Which record a 3D FP32 linearisation stores, and that the product
