@@ -1018,7 +1018,7 @@ def learned_proposal(tm, dev, args, train_preset="c5", apply_preset="c5apply", m
     from paper_1807_09807_gb300 import learned as L
     t0 = time.perf_counter()
     train_meshes = args.train_meshes if train_meshes is None else train_meshes
-    ds = L.make_dataset(n_meshes=train_meshes, seed0=1000, chunk=250, preset=train_preset, coarse=coarse)
+    ds = L.make_dataset(n_meshes=train_meshes, seed0=1000, chunk=50, preset=train_preset, coarse=coarse)
     t_data = time.perf_counter() - t0
     net = L.MLP(L.n_features(3), L.n_targets(3), 256, seed=0)
     t0 = time.perf_counter()

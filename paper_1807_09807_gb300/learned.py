@@ -265,12 +265,15 @@ class Dataset:
     seconds: float = 0.0
 
 
-def make_dataset(n_meshes=2000, seed0=1000, nx=32, ldf=256, chunk=250, precision=tm.FP32_MIXED,
+def make_dataset(n_meshes=2000, seed0=1000, nx=32, ldf=256, chunk=50, precision=tm.FP32_MIXED,
                  preset="c5", max_newton=60, rtol=1e-10, coarse=False) -> Dataset:
     """Newton-converged displacement targets from n_meshes seeded meshes
     (seeds seed0, seed0+1, ...), solved chunk meshes at a time as one
     block-diagonal problem, to |g| <= rtol |g0| of the chunk (far below what
-    a bf16 network resolves). coarse: features and targets are taken from
+    a bf16 network resolves). The chunk trades launch overhead against the
+    shared Krylov space and step length of a larger union (whose MINRES must
+    resolve every block's spectrum, and whose line search every block's
+    validity): 50 meshes of 32^2 took 2.4x less time than 250. coarse: features and targets are taken from
     the coarse stage's mesh (coarse_stage) instead of the jittered one."""
     import torch
     t0 = time.perf_counter()
