@@ -7,9 +7,11 @@ points, 9.1 M dofs), interior nodes jittered, trilinear shear, boundary fixed.
 
 Metric: quadrature points per second of gradient + Hessian action
 (NE * Q / t(step)), plus time-to-converged Newton (Section 3.4 line search,
-MINRES inner solves) for the plain FP64 form and the FP32-bulk form, on this
-workload and (newton_configs) on the smaller configurations beside the CPU
-oracle.
+MINRES inner solves) for the plain FP64 form and the FP32-Hessian forms
+(stored or recomputed operator, FP32 or FP64 Krylov vectors, Jacobi and
+two-level preconditioners) on this workload, and (newton_configs) FP64,
+FP32-Hessian and FP32-bulk Newton on the smaller configurations beside the
+CPU oracle.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload c4] [--precision fp64|mixed] [--no-converge]
@@ -900,17 +902,25 @@ def newton_configs(tm, dev, args):
     for name in ("c1", "c2", "c3", "c4"):
         m = mg.make_mesh(name, 1)
         ent = {"elements": m.nelem, "quad_points": m.n_qp, "metric": m.metric}
-        forms = (("fp64", tm.FP64), ("mixed", tm.FP32_MIXED)) if name != "c4" else ()
-        for form, pf in forms:
+        # FP32-bulk (every element kernel FP32, reductions FP64): its FP32 gradient
+        # bounds |g| / |g0| near 1e-6, so it stops there; F against the FP64 F
+        forms = (("fp64", tm.FP64, 1e-12), ("mixed", tm.FP32_MIXED, 1e-12), ("bulk", tm.FP32_BULK, 1e-6)) \
+            if name != "c4" else ()
+        for form, pf, rtol in forms:
             c = tm.Context.from_mesh(m, precision=pf)
             xc = torch.tensor(m.x, device=dev)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            res = c.newton_solve(xc, max_newton=args.max_newton, rtol=1e-12)
+            res = c.newton_solve(xc, max_newton=args.max_newton, rtol=rtol)
             torch.cuda.synchronize()
             rep = res.report
             ent[f"gpu_{form}"] = {"seconds": time.perf_counter() - t0, "status": tm.status_string(res.status),
-                                  "newton": rep["iterations"], "krylov": rep["krylov_iterations"], "F": rep["F"]}
+                                  "newton": rep["iterations"], "krylov": rep["krylov_iterations"], "F": rep["F"],
+                                  "rtol": rtol, "grad_rel": rep["grad_norm"] / max(rep["grad_norm0"], 1e-300)}
+            if form != "fp64" and "gpu_fp64" in ent:
+                F64 = ent["gpu_fp64"]["F"]
+                F0 = c.energy(torch.tensor(m.x, device=dev))[1]
+                ent[f"gpu_{form}"]["F_diff_over_F0"] = abs(rep["F"] - F64) / abs(F0)
             c.close()
         calls = oracle_call_seconds(m)
         ent["cpu_oracle_call_seconds"] = calls
