@@ -919,7 +919,8 @@ def oracle_call_seconds(m, budget_s=1.5):
 
 def newton_configs(tm, dev, args):
     """Newton to |g| <= 1e-12 |g0| on the smaller configurations (C1-C3) on
-    the GPU, plain FP64 and the FP32 Hessian-action form, beside the CPU
+    the GPU, plain FP64 and the FP32 Hessian-action form (each also with the
+    two-level preconditioner) and the FP32-bulk form, beside the CPU
     oracle: its own Newton measured on C1 (single thread); for C2-C4 the CPU
     time is extrapolated from single-thread per-call times of the oracle
     (gradient, matrix-free Hessian action) times the GPU run's Newton and
@@ -931,14 +932,16 @@ def newton_configs(tm, dev, args):
         ent = {"elements": m.nelem, "quad_points": m.n_qp, "metric": m.metric}
         # FP32-bulk (every element kernel FP32, reductions FP64): its FP32 gradient
         # bounds |g| / |g0| near 1e-6, so it stops there; F against the FP64 F
-        forms = (("fp64", tm.FP64, 1e-12), ("mixed", tm.FP32_MIXED, 1e-12), ("bulk", tm.FP32_BULK, 1e-6)) \
+        # and the two-level preconditioner (Jacobi + exact coarse vertex correction) in FP64 and FP32-mixed
+        forms = (("fp64", tm.FP64, 1e-12, 0), ("mixed", tm.FP32_MIXED, 1e-12, 0), ("bulk", tm.FP32_BULK, 1e-6, 0),
+                 ("fp64_twolevel", tm.FP64, 1e-12, 2), ("mixed_twolevel", tm.FP32_MIXED, 1e-12, 2)) \
             if name != "c4" else ()
-        for form, pf, rtol in forms:
+        for form, pf, rtol, pc in forms:
             c = tm.Context.from_mesh(m, precision=pf)
             xc = torch.tensor(m.x, device=dev)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            res = c.newton_solve(xc, max_newton=args.max_newton, rtol=rtol)
+            res = c.newton_solve(xc, max_newton=args.max_newton, rtol=rtol, precond=pc)
             torch.cuda.synchronize()
             rep = res.report
             ent[f"gpu_{form}"] = {"seconds": time.perf_counter() - t0, "status": tm.status_string(res.status),
