@@ -326,6 +326,33 @@ def test_fp32_compact_product_full_c4_sampled(tm):
     assert rel(host(c64.hess_apply_pa(dev(v)))[:, nodes], yo) <= RTOL
 
 
+def test_fp32_hessian_step_full_c4_sampled(tm):
+    """The FP32-Hessian form of the benchmark step at full size (48^3
+    order-3 hexes, the launch shapes bench.py times): the FP64 gradient and
+    the fused FP64 energy + gradient of the line search at 1e-12, and the
+    FP32 Hessian action recomputed from x (matrix-free) within the FP32
+    bound, at 64 sampled free nodes against the oracle restricted to the
+    elements around them."""
+    m = make("c4", 1)
+    orc = orc_for(m)
+    x = dev(m.x)
+    rng = np.random.default_rng(6)
+    free = np.nonzero(m.fixed[0] == 0)[0]
+    nodes = rng.choice(free, 64, replace=False)
+    els = _patch(m, nodes)
+    v = rng.standard_normal(m.x.shape)
+    go = orc.gradient(m.x, elems=els)[:, nodes]
+    yo = orc.hess_apply(m.x, v, elems=els)[:, nodes]
+    _, Fo, mdo = orc.energy(m.x)
+    c = tm.Context.from_mesh(m, precision=tm.FP32_MIXED)
+    assert rel(host(c.gradient(x))[:, nodes], go) <= RTOL
+    g, F, md = c.energy_gradient(x)
+    assert rel(host(g)[:, nodes], go) <= RTOL
+    assert abs(float(F) - Fo) <= RTOL * Fo and abs(float(md) - mdo) <= RTOL * abs(mdo)
+    assert rel(host(c.hess_apply(x, dev(v)))[:, nodes], yo) <= 1e-5
+    c.close()
+
+
 def test_fp32_packed_product_full_c4_sampled(tm):
     """The 45-value FP32 product at full size, as bench.py times it: mu302
     (not written in |T|^2 and det T, so the packed A-space Hessians are
