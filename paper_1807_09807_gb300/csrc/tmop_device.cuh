@@ -567,6 +567,241 @@ __device__ __forceinline__ void adj3(const R* __restrict__ B, const R* __restric
   __syncwarp();
 }
 
+// ---------------------------------------------------------------- folded (even-odd) 3D contractions
+// The Gauss points and the Gauss-Lobatto nodes are symmetric about the
+// element centre, so B[Q-1-q][N-1-i] = B[q][i] and G[Q-1-q][N-1-i] =
+// -G[q][i]. In the mirror basis of each direction -- the butterfly F,
+// (v_i, v_{L-1-i}) -> (v_i + v_{L-1-i}, v_i - v_{L-1-i}) stored in place at
+// (i, L-1-i), the middle entry of an odd length kept -- symmetric vectors
+// live on the "even" positions p < ceil(L/2) and antisymmetric ones on the
+// "odd" positions, and B maps each class to itself while G swaps them. The
+// folded tables Bf = S_Q^-1 F_Q B F_N S_N^-1 and Gf alike (S = F F: 2 on
+// pair positions, 1 in the middle) are therefore block-sparse: an output
+// position needs only the inputs of one parity, half the multiply-adds of
+// the plain 1D contraction. Since F S^-1 F = I and F, S are symmetric, the
+// 3D maps become
+//   forward  A = F_Q^3 (Bf/Gf contractions) F_N^3 x
+//   adjoint  y = F_N^3 (Bf^T/Gf^T contractions) F_Q^3 R
+// with butterfly passes in place around the stage loops. For order-3 hexes
+// (N = 4, Q = 5) a forward or adjoint map takes 5 010 multiply-adds and
+// 3 276 butterfly operations per element where the plain one takes 10 020
+// multiply-adds. Written for an even N (every output then reads N/2 inputs
+// of its parity, and the adjoint stages pair the outputs (l, N-1-l)).
+
+// Entry (p, q) of the mirror butterfly of length L (symmetric).
+__device__ __forceinline__ double mirror_entry(int L, int p, int q) {
+  const int m = L - 1 - p;
+  if (p == m) return q == p ? 1.0 : 0.0;
+  if (q == p) return p < m ? 1.0 : -1.0;
+  return q == m ? 1.0 : 0.0;
+}
+
+// Bf and Gf [Q1][N] from the physical tables B, G [Q1][N] (row-major),
+// computed by threads tid, tid + nth, ... of the block.
+template <int N, int Q1, class R>
+__device__ void folded_tables(const double* B, const double* G, R* Bf, R* Gf, int tid, int nth) {
+  for (int t = tid; t < Q1 * N; t += nth) {
+    const int p = t / N, r = t % N;
+    double b = 0.0, g = 0.0;
+    for (int q = 0; q < Q1; ++q) {
+      const double fq = mirror_entry(Q1, p, q);
+      if (fq == 0.0) continue;
+      for (int i = 0; i < N; ++i) {
+        const double fi = mirror_entry(N, i, r);
+        if (fi == 0.0) continue;
+        b = fma(fq * fi, B[q * N + i], b);
+        g = fma(fq * fi, G[q * N + i], g);
+      }
+    }
+    const double sp = (2 * p == Q1 - 1) ? 1.0 : 0.5, sr = (2 * r == N - 1) ? 1.0 : 0.5;
+    Bf[t] = R(b * sp * sr);
+    Gf[t] = R(g * sp * sr);
+  }
+}
+
+// In-place butterfly along axis AX (0 fastest) of NF consecutive fields,
+// each an [L2][L1][L0] array.
+template <int NF, int L0, int L1, int L2, int AX, class R>
+__device__ __forceinline__ void mirror3(R* buf, int lane) {
+  constexpr int L = AX == 0 ? L0 : (AX == 1 ? L1 : L2);
+  constexpr int H = L / 2, FS = L0 * L1 * L2, LINES = FS / L;
+  constexpr int ST = AX == 0 ? 1 : (AX == 1 ? L0 : L0 * L1);
+#pragma unroll 1
+  for (int t = lane; t < NF * LINES * H; t += 32) {
+    const int i = t % H, line = (t / H) % LINES, f = t / (H * LINES);
+    int base;
+    if constexpr (AX == 0) base = line * L0;
+    else if constexpr (AX == 1) base = (line / L0) * (L0 * L1) + line % L0;
+    else base = line;
+    R* v = buf + f * FS + base;
+    const R a = v[i * ST], b = v[(L - 1 - i) * ST];
+    v[i * ST] = a + b;
+    v[(L - 1 - i) * ST] = a - b;
+  }
+  __syncwarp();
+}
+
+// The butterfly along all three axes.
+template <int NF, int L, class R>
+__device__ __forceinline__ void mirror3_all(R* buf, int lane) {
+  mirror3<NF, L, L, L, 0, R>(buf, lane);
+  mirror3<NF, L, L, L, 1, R>(buf, lane);
+  mirror3<NF, L, L, L, 2, R>(buf, lane);
+}
+
+// Forward stages in the folded basis; same buffer layouts as fwd3. P0 holds
+// F_N^3 x on entry; P1 holds the folded A (F_Q^3 of it is A) on exit.
+template <int N, int Q1, int NC, class R>
+__device__ __forceinline__ void fwd3_eo(const R* __restrict__ Bf, const R* __restrict__ Gf, R* P0, R* P1, int lane) {
+  static_assert(N % 2 == 0, "folded contractions need an even node count");
+  constexpr int H = N / 2, QE = (Q1 + 1) / 2;
+  constexpr int NNQ = N * N * Q1, NQQ = N * Q1 * Q1, QQ = Q1 * Q1, QQQ = Q1 * Q1 * Q1;
+  for (int t = lane; t < NC * N * N * Q1; t += 32) {            // rows (c, l, j) along i -> q0
+    const int q0 = t % Q1, lj = (t / Q1) % (N * N), c = t / (Q1 * N * N);
+    const int ob = q0 < QE ? 0 : H, og = H - ob;                 // inputs of the output's parity (B), the other (G)
+    const R* xr = P0 + (c * N * N + lj) * N;
+    const R* tb = Bf + q0 * N;
+    const R* tg = Gf + q0 * N;
+    R sb = R(0), sg = R(0);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      sb = fma(xr[ob + k], tb[ob + k], sb);
+      sg = fma(xr[og + k], tg[og + k], sg);
+    }
+    P1[(c * 2 + 0) * NNQ + lj * Q1 + q0] = sb;
+    P1[(c * 2 + 1) * NNQ + lj * Q1 + q0] = sg;
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * N * QQ; t += 32) {                // (c, l, q1, q0) along j -> q1
+    const int q0 = t % Q1, q1 = (t / Q1) % Q1, l = (t / QQ) % N, c = t / (QQ * N);
+    const int ob = q1 < QE ? 0 : H, og = H - ob;
+    const R* xb = P1 + (c * 2 + 0) * NNQ + l * N * Q1 + q0;
+    const R* xg = P1 + (c * 2 + 1) * NNQ + l * N * Q1 + q0;
+    const R* tb = Bf + q1 * N;
+    const R* tg = Gf + q1 * N;
+    R bb = R(0), bg = R(0), gb = R(0);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      bb = fma(xb[(ob + k) * Q1], tb[ob + k], bb);
+      bg = fma(xb[(og + k) * Q1], tg[og + k], bg);
+      gb = fma(xg[(ob + k) * Q1], tb[ob + k], gb);
+    }
+    const int o = l * QQ + q1 * Q1 + q0;
+    P0[(c * 3 + 0) * NQQ + o] = bb;
+    P0[(c * 3 + 1) * NQQ + o] = bg;
+    P0[(c * 3 + 2) * NQQ + o] = gb;
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * QQQ; t += 32) {                   // (c, q2, q1, q0) along l -> q2
+    const int q01 = t % QQ, q2 = (t / QQ) % Q1, c = t / QQQ;
+    const int ob = q2 < QE ? 0 : H, og = H - ob;
+    const R* sbb = P0 + (c * 3 + 0) * NQQ + q01;
+    const R* sbg = P0 + (c * 3 + 1) * NQQ + q01;
+    const R* sgb = P0 + (c * 3 + 2) * NQQ + q01;
+    const R* tb = Bf + q2 * N;
+    const R* tg = Gf + q2 * N;
+    R a0 = R(0), a1 = R(0), a2 = R(0);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      a0 = fma(sgb[(ob + k) * QQ], tb[ob + k], a0);
+      a1 = fma(sbg[(ob + k) * QQ], tb[ob + k], a1);
+      a2 = fma(sbb[(og + k) * QQ], tg[og + k], a2);
+    }
+    const int o = q2 * QQ + q01;
+    P1[(c * 3 + 0) * QQQ + o] = a0;
+    P1[(c * 3 + 1) * QQQ + o] = a1;
+    P1[(c * 3 + 2) * QQQ + o] = a2;
+  }
+  __syncwarp();
+}
+
+// Adjoint stages in the folded basis; same buffer layouts as adj3. P1 holds
+// F_Q^3 R on entry; P0 holds the folded y (F_N^3 of it is y) on exit. Each
+// unit computes a mirror pair of outputs: the even position l, which reads
+// the even inputs through Bf and the odd ones through Gf, and the odd
+// position N-1-l, the other way round.
+template <int N, int Q1, int NC, class R>
+__device__ __forceinline__ void adj3_eo(const R* __restrict__ Bf, const R* __restrict__ Gf, R* P0, R* P1, int lane) {
+  static_assert(N % 2 == 0, "folded contractions need an even node count");
+  constexpr int H = N / 2, QE = (Q1 + 1) / 2;
+  constexpr int NNQ = N * N * Q1, NQQ = N * Q1 * Q1, QQ = Q1 * Q1, QQQ = Q1 * Q1 * Q1;
+  for (int t = lane; t < NC * H * QQ; t += 32) {                // (c, l pair, q1, q0) along q2 -> l
+    const int q01 = t % QQ, lp = (t / QQ) % H, c = t / (QQ * H);
+    const int le = lp, lo = N - 1 - lp;
+    const R* r0 = P1 + (c * 3 + 0) * QQQ + q01;
+    const R* r1 = P1 + (c * 3 + 1) * QQQ + q01;
+    const R* r2 = P1 + (c * 3 + 2) * QQQ + q01;
+    R u0e = R(0), u1e = R(0), u2e = R(0), u0o = R(0), u1o = R(0), u2o = R(0);
+#pragma unroll
+    for (int q = 0; q < QE; ++q) {                              // even inputs
+      const R be = Bf[q * N + le], go = Gf[q * N + lo];
+      u0e = fma(r0[q * QQ], be, u0e);
+      u1e = fma(r1[q * QQ], be, u1e);
+      u2o = fma(r2[q * QQ], go, u2o);
+    }
+#pragma unroll
+    for (int q = QE; q < Q1; ++q) {                             // odd inputs
+      const R bo = Bf[q * N + lo], ge = Gf[q * N + le];
+      u0o = fma(r0[q * QQ], bo, u0o);
+      u1o = fma(r1[q * QQ], bo, u1o);
+      u2e = fma(r2[q * QQ], ge, u2e);
+    }
+    R* u = P0 + c * 3 * NQQ + q01;
+    u[0 * NQQ + le * QQ] = u0e; u[0 * NQQ + lo * QQ] = u0o;
+    u[1 * NQQ + le * QQ] = u1e; u[1 * NQQ + lo * QQ] = u1o;
+    u[2 * NQQ + le * QQ] = u2e; u[2 * NQQ + lo * QQ] = u2o;
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * N * H * Q1; t += 32) {            // (c, l, j pair, q0) along q1 -> j
+    const int q0 = t % Q1, jp = (t / Q1) % H, l = (t / (Q1 * H)) % N, c = t / (Q1 * H * N);
+    const int je = jp, jo = N - 1 - jp;
+    const R* u0 = P0 + (c * 3 + 0) * NQQ + l * QQ + q0;
+    const R* u1 = P0 + (c * 3 + 1) * NQQ + l * QQ + q0;
+    const R* u2 = P0 + (c * 3 + 2) * NQQ + l * QQ + q0;
+    R vge = R(0), vgo = R(0), vbe = R(0), vbo = R(0);
+#pragma unroll
+    for (int q = 0; q < QE; ++q) {
+      const R be = Bf[q * N + je], go = Gf[q * N + jo];
+      vge = fma(u0[q * Q1], be, vge);
+      vbe = fma(u2[q * Q1], be, vbe);
+      vbo = fma(u1[q * Q1], go, vbo);
+    }
+#pragma unroll
+    for (int q = QE; q < Q1; ++q) {
+      const R bo = Bf[q * N + jo], ge = Gf[q * N + je];
+      vgo = fma(u0[q * Q1], bo, vgo);
+      vbo = fma(u2[q * Q1], bo, vbo);
+      vbe = fma(u1[q * Q1], ge, vbe);
+    }
+    R* vg = P1 + (c * 2 + 0) * NNQ + l * N * Q1 + q0;
+    R* vb = P1 + (c * 2 + 1) * NNQ + l * N * Q1 + q0;
+    vg[je * Q1] = vge; vg[jo * Q1] = vgo;
+    vb[je * Q1] = vbe; vb[jo * Q1] = vbo;
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * N * N * H; t += 32) {             // (c, l, j, i pair) along q0 -> i
+    const int ip = t % H, lj = (t / H) % (N * N), c = t / (H * N * N);
+    const int ie = ip, io = N - 1 - ip;
+    const R* vg = P1 + (c * 2 + 0) * NNQ + lj * Q1;
+    const R* vb = P1 + (c * 2 + 1) * NNQ + lj * Q1;
+    R ye = R(0), yo = R(0);
+#pragma unroll
+    for (int q = 0; q < QE; ++q) {
+      ye = fma(vb[q], Bf[q * N + ie], ye);
+      yo = fma(vg[q], Gf[q * N + io], yo);
+    }
+#pragma unroll
+    for (int q = QE; q < Q1; ++q) {
+      yo = fma(vb[q], Bf[q * N + io], yo);
+      ye = fma(vg[q], Gf[q * N + ie], ye);
+    }
+    R* y = P0 + (c * N * N + lj) * N;
+    y[ie] = ye;
+    y[io] = yo;
+  }
+  __syncwarp();
+}
+
 // ---------------------------------------------------------------- register-blocked 3D contractions
 // Same maps as fwd3/adj3 with the same buffer layouts, but each lane owns a
 // whole row of outputs: it loads the row's inputs once into registers and

@@ -106,7 +106,7 @@ __device__ __forceinline__ bool metric_dP(int id, const R* T, const R* dT, R* S)
 }
 
 template <int D, int N, int Q1, class R, int OP>
-__global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
+__global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32, ElemCfg<D, N, Q1, R, OP>::TWO ? 2 : 1)
     elem_kernel(const KParams p) {
   using Cfg = ElemCfg<D, N, Q1, R, OP>;
   constexpr int NDOF = Shape<D, N, Q1>::NDOF, QP = Shape<D, N, Q1>::QP, DD = D * D;
@@ -120,9 +120,16 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
   R* P1 = P0 + Cfg::B0;
   R* P2 = P1 + Cfg::B1;  // A(x) of the split 3D Hessian action
 
-  for (int t = threadIdx.x; t < Q1 * N; t += blockDim.x) {
-    sB[t] = R(p.B[t]);
-    sG[t] = R(p.G[t]);
+  // FP64 3D kernels with an even node count contract in the mirror basis
+  // (fwd3_eo / adj3_eo): sB, sG then hold the folded tables
+  constexpr bool EO = D == 3 && sizeof(R) == 8 && N % 2 == 0;
+  if constexpr (EO) {
+    folded_tables<N, Q1, R>(p.B, p.G, sB, sG, threadIdx.x, blockDim.x);
+  } else {
+    for (int t = threadIdx.x; t < Q1 * N; t += blockDim.x) {
+      sB[t] = R(p.B[t]);
+      sG[t] = R(p.G[t]);
+    }
   }
   for (int t = threadIdx.x; t < Q1; t += blockDim.x) sw[t] = R(p.w1[t]);
   R Wi[DD];
@@ -206,8 +213,15 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
     // ---- forward contraction: A (and dA) at every point
     if constexpr (Cfg::SPLIT) {
       // A(x) into P2 (P2 also serves as the first stage buffer), then v
-      if constexpr (RB) fwd3_rb<N, Q1, D, R>(tB, tG, P0, P2, lane);
-      else fwd3<N, Q1, D, R>(sB, sG, P0, P2, lane);
+      if constexpr (EO) {
+        mirror3_all<D, N, R>(P0, lane);
+        fwd3_eo<N, Q1, D, R>(sB, sG, P0, P2, lane);
+        mirror3_all<D * D, Q1, R>(P2, lane);
+      } else if constexpr (RB) {
+        fwd3_rb<N, Q1, D, R>(tB, tG, P0, P2, lane);
+      } else {
+        fwd3<N, Q1, D, R>(sB, sG, P0, P2, lane);
+      }
       for (int t = lane; t < NDOF; t += 32) {
         const int g = nodes(t);
 #pragma unroll
@@ -218,10 +232,21 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
         }
       }
       __syncwarp();
-      if constexpr (RB) fwd3_rb<N, Q1, D, R>(tB, tG, P0, P1, lane);
-      else fwd3<N, Q1, D, R>(sB, sG, P0, P1, lane);
+      if constexpr (EO) {
+        mirror3_all<D, N, R>(P0, lane);
+        fwd3_eo<N, Q1, D, R>(sB, sG, P0, P1, lane);
+        mirror3_all<D * D, Q1, R>(P1, lane);
+      } else if constexpr (RB) {
+        fwd3_rb<N, Q1, D, R>(tB, tG, P0, P1, lane);
+      } else {
+        fwd3<N, Q1, D, R>(sB, sG, P0, P1, lane);
+      }
     } else if constexpr (D == 2) {
       fwd2<N, Q1, Cfg::NC, R>(sB, sG, P0, P1, lane);
+    } else if constexpr (EO) {
+      mirror3_all<Cfg::NC, N, R>(P0, lane);
+      fwd3_eo<N, Q1, Cfg::NC, R>(sB, sG, P0, P1, lane);
+      mirror3_all<Cfg::NC * D, Q1, R>(P1, lane);
     } else if constexpr (RB) {
       fwd3_rb<N, Q1, Cfg::NC, R>(tB, tG, P0, P1, lane);
     } else {
@@ -531,9 +556,17 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32)
       if constexpr (EG) accMin = fmin(accMin, emin);
       __syncwarp();
       // ---- adjoint contraction and scatter
-      if constexpr (D == 2) adj2<N, Q1, D, R>(sB, sG, P0, P1, lane);
-      else if constexpr (RB) adj3_rb<N, Q1, D, R>(tB, tG, P0, P1, lane);
-      else adj3<N, Q1, D, R>(sB, sG, P0, P1, lane);
+      if constexpr (D == 2) {
+        adj2<N, Q1, D, R>(sB, sG, P0, P1, lane);
+      } else if constexpr (EO) {
+        mirror3_all<D * D, Q1, R>(P1, lane);
+        adj3_eo<N, Q1, D, R>(sB, sG, P0, P1, lane);
+        mirror3_all<D, N, R>(P0, lane);
+      } else if constexpr (RB) {
+        adj3_rb<N, Q1, D, R>(tB, tG, P0, P1, lane);
+      } else {
+        adj3<N, Q1, D, R>(sB, sG, P0, P1, lane);
+      }
       for (int t = lane; t < NDOF; t += 32) {
         const int g = nodes(t);
 #pragma unroll
