@@ -106,7 +106,7 @@ __device__ __forceinline__ bool metric_dP(int id, const R* T, const R* dT, R* S)
 }
 
 template <int D, int N, int Q1, class R, int OP>
-__global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32, ElemCfg<D, N, Q1, R, OP>::TWO ? 2 : 1)
+__global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32, ElemCfg<D, N, Q1, R, OP>::TWO ? 2 : 0)
     elem_kernel(const KParams p) {
   using Cfg = ElemCfg<D, N, Q1, R, OP>;
   constexpr int NDOF = Shape<D, N, Q1>::NDOF, QP = Shape<D, N, Q1>::QP, DD = D * D;
