@@ -266,41 +266,64 @@ class Dataset:
 
 
 def make_dataset(n_meshes=2000, seed0=1000, nx=32, ldf=256, chunk=50, precision=tm.FP32_MIXED,
-                 preset="c5", max_newton=60, rtol=1e-10, coarse=False) -> Dataset:
+                 preset="c5", max_newton=60, rtol=1e-10, coarse=False, workers=4) -> Dataset:
     """Newton-converged displacement targets from n_meshes seeded meshes
     (seeds seed0, seed0+1, ...), solved chunk meshes at a time as one
     block-diagonal problem, to |g| <= rtol |g0| of the chunk (far below what
     a bf16 network resolves). The chunk trades launch overhead against the
     shared Krylov space and step length of a larger union (whose MINRES must
     resolve every block's spectrum, and whose line search every block's
-    validity): 50 meshes of 32^2 took 2.4x less time than 250. coarse: features and targets are taken from
-    the coarse stage's mesh (coarse_stage) instead of the jittered one."""
+    validity): 50 meshes of 32^2 took 2.4x less time than 250. The chunks'
+    solves are small, latency-bound kernels, so `workers` host threads run
+    chunks at once, each on its own CUDA stream and context (the library's
+    graph captures are thread-local); the samples keep the chunk order.
+    coarse: features and targets are taken from the coarse stage's mesh
+    (coarse_stage) instead of the jittered one."""
     import torch
+    from concurrent.futures import ThreadPoolExecutor
     t0 = time.perf_counter()
-    Xs, Ts, log = [], [], []
-    for c0 in range(0, n_meshes, chunk):
-        ms = [mg.make_mesh(preset, seed0 + i, nx=nx) for i in range(c0, min(c0 + chunk, n_meshes))]
-        ctx, xh = union_context(ms, precision)
-        x0 = torch.tensor(xh, device="cuda")
-        if coarse:
-            fx = torch.tensor(np.concatenate([m.fixed for m in ms], axis=1), device="cuda")
-            xc, _ = coarse_stage(ms[0], x0, fx, count=len(ms))
-            if ctx.energy(xc)[2] > 0:    # valid everywhere: the base of this chunk
-                x0 = xc
-        x1 = x0.clone()
-        # a stack of boundary-fixed grids takes the two-level preconditioner
-        pc = 2 if ctx.stacked and all(np.array_equal(m.fixed, ms[0].fixed) for m in ms) else 0
-        r = ctx.newton_solve(x1, max_newton=max_newton, rtol=rtol, precond=pc)
-        log.append((r.status, r.report["iterations"], r.report["krylov_iterations"]))
-        if r.status != tm.OK:
-            raise RuntimeError(f"data generation: Newton failed on chunk {c0}: {tm.status_string(r.status)}")
-        N = ms[0].nnode
-        for i, m in enumerate(ms):
-            # component stride of the union positions is the union node count
-            xa, xb = x0[:, i * N:], x1[:, i * N:]
-            Xs.append(features(m, xa, ldf, ldx=x0.shape[1]))
-            Ts.append(targets(m, xa, xb, ldx=x0.shape[1]))
-        ctx.close()
+    device = torch.cuda.current_device()
+
+    def solve_chunk(c0):
+        torch.cuda.set_device(device)
+        stream = torch.cuda.Stream()
+        Xc, Tc = [], []
+        with torch.cuda.stream(stream):
+            ms = [mg.make_mesh(preset, seed0 + i, nx=nx) for i in range(c0, min(c0 + chunk, n_meshes))]
+            ctx, xh = union_context(ms, precision)
+            try:
+                x0 = torch.tensor(xh, device="cuda")
+                if coarse:
+                    fx = torch.tensor(np.concatenate([m.fixed for m in ms], axis=1), device="cuda")
+                    xc, _ = coarse_stage(ms[0], x0, fx, count=len(ms))
+                    if ctx.energy(xc)[2] > 0:    # valid everywhere: the base of this chunk
+                        x0 = xc
+                x1 = x0.clone()
+                # a stack of boundary-fixed grids takes the two-level preconditioner
+                pc = 2 if ctx.stacked and all(np.array_equal(m.fixed, ms[0].fixed) for m in ms) else 0
+                r = ctx.newton_solve(x1, max_newton=max_newton, rtol=rtol, precond=pc)
+                if r.status != tm.OK:
+                    raise RuntimeError(f"data generation: Newton failed on chunk {c0}: {tm.status_string(r.status)}")
+                N = ms[0].nnode
+                for i, m in enumerate(ms):
+                    # component stride of the union positions is the union node count
+                    xa, xb = x0[:, i * N:], x1[:, i * N:]
+                    Xc.append(features(m, xa, ldf, ldx=x0.shape[1]))
+                    Tc.append(targets(m, xa, xb, ldx=x0.shape[1]))
+            finally:
+                stream.synchronize()   # nothing of this chunk in flight when its buffers are freed
+                ctx.close()
+        return Xc, Tc, (r.status, r.report["iterations"], r.report["krylov_iterations"])
+
+    starts = list(range(0, n_meshes, chunk))
+    if workers > 1 and len(starts) > 1:
+        with ThreadPoolExecutor(max_workers=min(workers, len(starts))) as ex:
+            results = list(ex.map(solve_chunk, starts))
+    else:
+        results = [solve_chunk(c0) for c0 in starts]
+    Xs = [x for r in results for x in r[0]]
+    Ts = [t for r in results for t in r[1]]
+    log = [r[2] for r in results]
     torch.cuda.synchronize()
     return Dataset(torch.cat(Xs), torch.cat(Ts), n_meshes, log, time.perf_counter() - t0)
 

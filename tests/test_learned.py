@@ -165,6 +165,20 @@ def test_patch_features_targets_apply(L):
     assert np.abs(xh - (m.x + 0.25 * (x1 - m.x))).max() <= 1e-9
 
 
+def test_concurrent_data_generation_matches_sequential(L):
+    """Chunks solved by four host threads on their own streams give the
+    samples of the one-thread run, in the same order: features bitwise, the
+    Newton-converged targets within the solver tolerance, every chunk
+    converged."""
+    from paper_1807_09807_gb300 import tmop as tm
+    a = L.make_dataset(n_meshes=12, seed0=1000, nx=16, chunk=2, workers=4)
+    b = L.make_dataset(n_meshes=12, seed0=1000, nx=16, chunk=2, workers=1)
+    assert len(a.newton) == len(b.newton) == 6 and all(s == tm.OK for s, _, _ in a.newton + b.newton)
+    assert torch.equal(a.X, b.X)
+    Ta, Tb = a.T.double(), b.T.double()
+    assert float((Ta - Tb).abs().max()) <= 1e-6 * float(Tb.abs().max())
+
+
 def test_learned_proposal_gain(L):
     """Train on Newton-converged displacements of 256 seeded 32x32 order-3
     meshes (mu2, jitter 0.15h), apply to unseen 64x64 meshes: the proposal is
