@@ -25,6 +25,7 @@ and predicts only the residual from there.
 from __future__ import annotations
 
 import ctypes as C
+import threading
 import time
 from dataclasses import dataclass, field
 
@@ -192,13 +193,18 @@ def lattice_prolong_add(m: mg.Mesh, xv0, xv1, ldv: int, x_in, fixed_dev, ldx: in
            "tmop_lattice_prolong_add")
 
 
-_coarse_ctx = {}
+# coarse contexts by (grid, metric, count), one cache per host thread: a
+# context's workspace serves one solve at a time
+_coarse_tls = threading.local()
 
 
 def coarse_context(m: mg.Mesh, count: int):
     """The order-1 TMOP problem of the element vertices of `count` meshes
     shaped like m (same metric, boundary vertices fixed), one block each."""
     key = (tuple(m.nx), m.metric, count)
+    _coarse_ctx = getattr(_coarse_tls, "ctx", None)
+    if _coarse_ctx is None:
+        _coarse_ctx = _coarse_tls.ctx = {}
     if key not in _coarse_ctx:
         xv, en, fx = mg.structured(m.dim, 1, m.nx)
         Nv = xv.shape[1]

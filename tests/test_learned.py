@@ -177,6 +177,13 @@ def test_concurrent_data_generation_matches_sequential(L):
     assert torch.equal(a.X, b.X)
     Ta, Tb = a.T.double(), b.T.double()
     assert float((Ta - Tb).abs().max()) <= 1e-6 * float(Tb.abs().max())
+    # with the coarse stage (each thread solves the vertex grids in its own coarse context)
+    a = L.make_dataset(n_meshes=8, seed0=1000, nx=16, chunk=2, preset="c5curved", coarse=True, workers=4)
+    b = L.make_dataset(n_meshes=8, seed0=1000, nx=16, chunk=2, preset="c5curved", coarse=True, workers=1)
+    assert all(s == tm.OK for s, _, _ in a.newton + b.newton)
+    assert a.X.shape == b.X.shape and a.T.shape == b.T.shape   # features of the coarse-stage mesh (FP64 atomics)
+    Ta, Tb = a.T.double(), b.T.double()
+    assert float((Ta - Tb).abs().max()) <= 1e-5 * float(Tb.abs().max())
 
 
 def test_learned_proposal_gain(L):
