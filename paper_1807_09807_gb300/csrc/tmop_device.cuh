@@ -649,6 +649,114 @@ __device__ __forceinline__ void mirror3_all(R* buf, int lane) {
   mirror3<NF, L, L, L, 2, R>(buf, lane);
 }
 
+// Normalised forward: every folded dot of the forward map has N/2 terms of
+// one parity; scaling it by its larger coefficient (the pivot) leaves
+// x[k] + r x[k^1] (N = 4: one multiply-add instead of a multiply and a
+// multiply-add) or the plain copy x[k] (N = 2). For table t (0 = B, 1 = G)
+// and output position p, entry t * Q1 + p of kf is the pivot's input
+// position and of rt the other coefficient over the pivot (0 for a zero
+// pivot, whose outputs the scale then zeroes). The stage outputs are the
+// true ones divided by the pivots along the axes done so far, so the point
+// fields come out divided by Sc[d][q2][q1][q0], the product of the pivots
+// of direction d's tables (G along axis d, B along the others), which the
+// first unfold pass multiplies back (mirror3_scaled).
+template <int N, int Q1, class R>
+__device__ void normalised_tables(const R* Bf, const R* Gf, int* kf, R* rt, R* piv, R* Sc, int tid, int nth) {
+  static_assert(N == 2 || N == 4, "normalised folded dots are written for N / 2 = 1 or 2 terms");
+  constexpr int H = N / 2, QE = (Q1 + 1) / 2, QQQ = Q1 * Q1 * Q1;
+  for (int t = tid; t < 2 * Q1; t += nth) {
+    const int tb = t / Q1, p = t % Q1;
+    const R* T = (tb ? Gf : Bf) + p * N;
+    const int base = ((p >= QE) != (tb == 1)) ? H : 0;   // B keeps the parity, G swaps it
+    int k = base;
+    R b = T[base];
+    if (H == 2 && fabs(T[base + 1]) > fabs(b)) {
+      k = base + 1;
+      b = T[base + 1];
+    }
+    kf[t] = k;
+    rt[t] = (H == 2 && b != R(0)) ? T[k ^ 1] / b : R(0);
+    piv[t] = b;
+  }
+  __syncthreads();
+  for (int t = tid; t < 3 * QQQ; t += nth) {
+    const int q0 = t % Q1, q1 = (t / Q1) % Q1, q2 = (t / (Q1 * Q1)) % Q1, d = t / QQQ;
+    Sc[t] = piv[(d == 0) * Q1 + q0] * piv[(d == 1) * Q1 + q1] * piv[(d == 2) * Q1 + q2];
+  }
+}
+
+// The folded dot of table entry t over inputs x[0], x[stride], ...
+template <int H, class R>
+__device__ __forceinline__ R norm_dot(const R* x, int stride, const int* __restrict__ kf, const R* __restrict__ rt,
+                                      int t) {
+  const int k = kf[t];
+  if constexpr (H == 2) return fma(x[(k ^ 1) * stride], rt[t], x[k * stride]);
+  else return x[k * stride];
+}
+
+// Forward stages of fwd3_eo with normalised dots; P1 holds the folded A
+// divided by Sc on exit.
+template <int N, int Q1, int NC, class R>
+__device__ __forceinline__ void fwd3_eon(const int* __restrict__ kf, const R* __restrict__ rt, R* P0, R* P1,
+                                         int lane) {
+  constexpr int H = N / 2;
+  constexpr int NNQ = N * N * Q1, NQQ = N * Q1 * Q1, QQ = Q1 * Q1, QQQ = Q1 * Q1 * Q1;
+  for (int t = lane; t < NC * N * N * Q1; t += 32) {            // rows (c, l, j) along i -> q0
+    const int q0 = t % Q1, lj = (t / Q1) % (N * N), c = t / (Q1 * N * N);
+    const R* xr = P0 + (c * N * N + lj) * N;
+    P1[(c * 2 + 0) * NNQ + lj * Q1 + q0] = norm_dot<H>(xr, 1, kf, rt, q0);
+    P1[(c * 2 + 1) * NNQ + lj * Q1 + q0] = norm_dot<H>(xr, 1, kf, rt, Q1 + q0);
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * N * QQ; t += 32) {                // (c, l, q1, q0) along j -> q1
+    const int q0 = t % Q1, q1 = (t / Q1) % Q1, l = (t / QQ) % N, c = t / (QQ * N);
+    const R* xb = P1 + (c * 2 + 0) * NNQ + l * N * Q1 + q0;
+    const R* xg = P1 + (c * 2 + 1) * NNQ + l * N * Q1 + q0;
+    const int o = l * QQ + q1 * Q1 + q0;
+    P0[(c * 3 + 0) * NQQ + o] = norm_dot<H>(xb, Q1, kf, rt, q1);
+    P0[(c * 3 + 1) * NQQ + o] = norm_dot<H>(xb, Q1, kf, rt, Q1 + q1);
+    P0[(c * 3 + 2) * NQQ + o] = norm_dot<H>(xg, Q1, kf, rt, q1);
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * QQQ; t += 32) {                   // (c, q2, q1, q0) along l -> q2
+    const int q01 = t % QQ, q2 = (t / QQ) % Q1, c = t / QQQ;
+    const int o = q2 * QQ + q01;
+    P1[(c * 3 + 0) * QQQ + o] = norm_dot<H>(P0 + (c * 3 + 2) * NQQ + q01, QQ, kf, rt, q2);
+    P1[(c * 3 + 1) * QQQ + o] = norm_dot<H>(P0 + (c * 3 + 1) * NQQ + q01, QQ, kf, rt, q2);
+    P1[(c * 3 + 2) * QQQ + o] = norm_dot<H>(P0 + (c * 3 + 0) * NQQ + q01, QQ, kf, rt, Q1 + q2);
+  }
+  __syncwarp();
+}
+
+// The axis-0 butterfly of fwd3_eon's point fields with Sc multiplied back
+// (field f has direction f % 3; the middle entry of an odd length is scaled
+// by the unit of pair 0).
+template <int NF, int L, class R>
+__device__ __forceinline__ void mirror3_scaled(R* buf, const R* __restrict__ Sc, int lane) {
+  constexpr int H = L / 2, FS = L * L * L, LINES = L * L;
+#pragma unroll 1
+  for (int t = lane; t < NF * LINES * H; t += 32) {
+    const int i = t % H, line = (t / H) % LINES, f = t / (H * LINES);
+    R* v = buf + f * FS + line * L;
+    const R* sc = Sc + (f % 3) * FS + line * L;
+    const R bs = v[L - 1 - i] * sc[L - 1 - i];
+    const R a = v[i], sa = sc[i];
+    v[i] = fma(a, sa, bs);
+    v[L - 1 - i] = fma(a, sa, -bs);
+    if (L % 2 == 1 && i == 0) v[H] *= sc[H];
+  }
+  __syncwarp();
+}
+
+// F_Q^3 of fwd3_eon's output, Sc multiplied back on the way: A at the points.
+template <int NF, int L, class R>
+__device__ __forceinline__ void unfold_points(R* buf, const R* __restrict__ Sc, int lane) {
+  mirror3_scaled<NF, L, R>(buf, Sc, lane);
+  mirror3<NF, L, L, L, 1, R>(buf, lane);
+  mirror3<NF, L, L, L, 2, R>(buf, lane);
+}
+
+
 // Forward stages in the folded basis; same buffer layouts as fwd3. P0 holds
 // F_N^3 x on entry; P1 holds the folded A (F_Q^3 of it is A) on exit.
 template <int N, int Q1, int NC, class R>

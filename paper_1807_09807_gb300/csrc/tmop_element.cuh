@@ -62,7 +62,10 @@ struct ElemCfg {
   static constexpr int WARPS = TWO ? 6
                                    : ((200 * 1024 / PER_WARP) >= 8 ? 8
                                                                    : ((200 * 1024 / PER_WARP) < 1 ? 1 : 200 * 1024 / PER_WARP));
-  static constexpr int TABLE = round16<R>(2 * kMaxQ * kMaxN + kMaxQ);
+  // FP64 3D with an even node count: contractions in the mirror basis, whose
+  // normalised forward stages need the pivot tables and their products
+  static constexpr bool EO = D == 3 && sizeof(R) == 8 && N % 2 == 0;
+  static constexpr int TABLE = round16<R>(2 * kMaxQ * kMaxN + kMaxQ + (EO ? 4 * kMaxQ + 3 * Q1 * Q1 * Q1 : 0));
   static constexpr size_t smem_bytes() { return sizeof(R) * (TABLE + WARPS * (B0 + B1 + B2)); }
 };
 
@@ -121,10 +124,17 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32, ElemCfg<
   R* P2 = P1 + Cfg::B1;  // A(x) of the split 3D Hessian action
 
   // FP64 3D kernels with an even node count contract in the mirror basis
-  // (fwd3_eo / adj3_eo): sB, sG then hold the folded tables
-  constexpr bool EO = D == 3 && sizeof(R) == 8 && N % 2 == 0;
+  // (fwd3_eon / adj3_eo): sB, sG then hold the folded tables, followed by
+  // the normalised forward's pivots, ratios and scale products
+  constexpr bool EO = Cfg::EO;
+  R* s_piv = sw + kMaxQ;
+  R* s_rt = s_piv + 2 * kMaxQ;
+  R* s_Sc = s_rt + 2 * kMaxQ;
+  __shared__ int s_kf[2 * kMaxQ];
   if constexpr (EO) {
     folded_tables<N, Q1, R>(p.B, p.G, sB, sG, threadIdx.x, blockDim.x);
+    __syncthreads();
+    normalised_tables<N, Q1, R>(sB, sG, s_kf, s_rt, s_piv, s_Sc, threadIdx.x, blockDim.x);
   } else {
     for (int t = threadIdx.x; t < Q1 * N; t += blockDim.x) {
       sB[t] = R(p.B[t]);
@@ -215,8 +225,8 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32, ElemCfg<
       // A(x) into P2 (P2 also serves as the first stage buffer), then v
       if constexpr (EO) {
         mirror3_all<D, N, R>(P0, lane);
-        fwd3_eo<N, Q1, D, R>(sB, sG, P0, P2, lane);
-        mirror3_all<D * D, Q1, R>(P2, lane);
+        fwd3_eon<N, Q1, D, R>(s_kf, s_rt, P0, P2, lane);
+        unfold_points<D * D, Q1, R>(P2, s_Sc, lane);
       } else if constexpr (RB) {
         fwd3_rb<N, Q1, D, R>(tB, tG, P0, P2, lane);
       } else {
@@ -234,8 +244,8 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32, ElemCfg<
       __syncwarp();
       if constexpr (EO) {
         mirror3_all<D, N, R>(P0, lane);
-        fwd3_eo<N, Q1, D, R>(sB, sG, P0, P1, lane);
-        mirror3_all<D * D, Q1, R>(P1, lane);
+        fwd3_eon<N, Q1, D, R>(s_kf, s_rt, P0, P1, lane);
+        unfold_points<D * D, Q1, R>(P1, s_Sc, lane);
       } else if constexpr (RB) {
         fwd3_rb<N, Q1, D, R>(tB, tG, P0, P1, lane);
       } else {
@@ -245,8 +255,8 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32, ElemCfg<
       fwd2<N, Q1, Cfg::NC, R>(sB, sG, P0, P1, lane);
     } else if constexpr (EO) {
       mirror3_all<Cfg::NC, N, R>(P0, lane);
-      fwd3_eo<N, Q1, Cfg::NC, R>(sB, sG, P0, P1, lane);
-      mirror3_all<Cfg::NC * D, Q1, R>(P1, lane);
+      fwd3_eon<N, Q1, Cfg::NC, R>(s_kf, s_rt, P0, P1, lane);
+      unfold_points<Cfg::NC * D, Q1, R>(P1, s_Sc, lane);
     } else if constexpr (RB) {
       fwd3_rb<N, Q1, Cfg::NC, R>(tB, tG, P0, P1, lane);
     } else {
