@@ -823,6 +823,183 @@ __device__ __forceinline__ void fwd3_eo(const R* __restrict__ Bf, const R* __res
   __syncwarp();
 }
 
+// Normalised adjoint, first stage: the folded dots along q2 read Q1/2 or
+// (Q1+1)/2 inputs of one parity; each is scaled by its largest coefficient
+// (the pivot), taken first, so it costs one multiply-add fewer. For table
+// tb (0 = B, 1 = G) and node position r, row tb * N + r of aperm lists the
+// inputs in that order and of arat their coefficients over the pivot;
+// apiv holds the pivot. The stage-1 outputs of node position l are then
+// u0, u1 over the B pivot and u2 over the G pivot; the second stage takes
+// them through C[w][l][q][j] = (pivot / s(l)) x (Bf for w = 0, 2; Gf for
+// w = 1), s(l) the larger of the two pivots (1 if both are zero, whose
+// outputs C then zeroes), so that its outputs, and the nodal y, carry the
+// one factor s(l): the last unfold pass multiplies it back (ysc).
+template <int N, int Q1, class R>
+__device__ void adjoint_tables(const R* Bf, const R* Gf, int* aperm, R* arat, R* apiv, R* C, R* ysc, int tid,
+                               int nth) {
+  constexpr int H = N / 2, QE = (Q1 + 1) / 2;
+  for (int t = tid; t < 2 * N; t += nth) {
+    const int tb = t / N, r = t % N;
+    const R* T = tb ? Gf : Bf;
+    const bool in_odd = (r >= H) != (tb == 1);   // B keeps the parity, G swaps it
+    const int q0 = in_odd ? QE : 0, M = in_odd ? Q1 - QE : QE;
+    int best = q0;
+    R b = T[q0 * N + r];
+    for (int k = 1; k < M; ++k) {
+      const R c = T[(q0 + k) * N + r];
+      if (fabs(c) > fabs(b)) {
+        best = q0 + k;
+        b = c;
+      }
+    }
+    int* pm = aperm + t * QE;
+    R* rt = arat + t * QE;
+    pm[0] = best;
+    rt[0] = R(1);
+    int m = 1;
+    for (int k = 0; k < M; ++k) {
+      const int q = q0 + k;
+      if (q == best) continue;
+      pm[m] = q;
+      rt[m] = b != R(0) ? T[q * N + r] / b : R(0);
+      ++m;
+    }
+    apiv[t] = b;
+  }
+  __syncthreads();
+  for (int t = tid; t < 3 * N * Q1 * N; t += nth) {
+    const int j = t % N, q = (t / N) % Q1, l = (t / (N * Q1)) % N, w = t / (N * Q1 * N);
+    const R sB = apiv[l], sG = apiv[N + l];
+    const R sl = fabs(sB) >= fabs(sG) ? sB : sG;
+    const R f = sl != R(0) ? (w == 2 ? sG : sB) / sl : R(0);
+    C[t] = f * (w == 1 ? Gf : Bf)[q * N + j];
+  }
+  for (int t = tid; t < N; t += nth) {
+    const R sB = apiv[t], sG = apiv[N + t];
+    const R sl = fabs(sB) >= fabs(sG) ? sB : sG;
+    ysc[t] = sl != R(0) ? sl : R(1);
+  }
+}
+
+// adj3_eo with the normalised first stage and the stage-2 tables C; P0
+// holds the folded y divided by ysc[l] on exit.
+template <int N, int Q1, int NC, class R>
+__device__ __forceinline__ void adj3_eon(const R* __restrict__ Bf, const R* __restrict__ Gf,
+                                         const int* __restrict__ aperm, const R* __restrict__ arat,
+                                         const R* __restrict__ C, R* P0, R* P1, int lane) {
+  static_assert(N % 2 == 0, "folded contractions need an even node count");
+  constexpr int H = N / 2, QE = (Q1 + 1) / 2, QO = Q1 / 2;
+  constexpr int NNQ = N * N * Q1, NQQ = N * Q1 * Q1, QQ = Q1 * Q1, QQQ = Q1 * Q1 * Q1;
+  for (int t = lane; t < NC * H * QQ; t += 32) {                // (c, l pair, q1, q0) along q2 -> l
+    const int q01 = t % QQ, lp = (t / QQ) % H, c = t / (QQ * H);
+    const int le = lp, lo = N - 1 - lp;
+    const R* r0 = P1 + (c * 3 + 0) * QQQ + q01;
+    const R* r1 = P1 + (c * 3 + 1) * QQQ + q01;
+    const R* r2 = P1 + (c * 3 + 2) * QQQ + q01;
+    const int* pBe = aperm + le * QE;        // B column le: the even inputs
+    const int* pBo = aperm + lo * QE;        // B column lo: the odd inputs
+    const int* pGe = aperm + (N + le) * QE;  // G column le: the odd inputs
+    const int* pGo = aperm + (N + lo) * QE;  // G column lo: the even inputs
+    const R* wBe = arat + le * QE;
+    const R* wBo = arat + lo * QE;
+    const R* wGe = arat + (N + le) * QE;
+    const R* wGo = arat + (N + lo) * QE;
+    R u0e = r0[pBe[0] * QQ], u1e = r1[pBe[0] * QQ];
+#pragma unroll
+    for (int k = 1; k < QE; ++k) {
+      const int q = pBe[k] * QQ;
+      u0e = fma(r0[q], wBe[k], u0e);
+      u1e = fma(r1[q], wBe[k], u1e);
+    }
+    R u0o = r0[pBo[0] * QQ], u1o = r1[pBo[0] * QQ];
+#pragma unroll
+    for (int k = 1; k < QO; ++k) {
+      const int q = pBo[k] * QQ;
+      u0o = fma(r0[q], wBo[k], u0o);
+      u1o = fma(r1[q], wBo[k], u1o);
+    }
+    R u2e = r2[pGe[0] * QQ];
+#pragma unroll
+    for (int k = 1; k < QO; ++k) u2e = fma(r2[pGe[k] * QQ], wGe[k], u2e);
+    R u2o = r2[pGo[0] * QQ];
+#pragma unroll
+    for (int k = 1; k < QE; ++k) u2o = fma(r2[pGo[k] * QQ], wGo[k], u2o);
+    R* u = P0 + c * 3 * NQQ + q01;
+    u[0 * NQQ + le * QQ] = u0e; u[0 * NQQ + lo * QQ] = u0o;
+    u[1 * NQQ + le * QQ] = u1e; u[1 * NQQ + lo * QQ] = u1o;
+    u[2 * NQQ + le * QQ] = u2e; u[2 * NQQ + lo * QQ] = u2o;
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * N * H * Q1; t += 32) {            // (c, l, j pair, q0) along q1 -> j
+    const int q0 = t % Q1, jp = (t / Q1) % H, l = (t / (Q1 * H)) % N, c = t / (Q1 * H * N);
+    const int je = jp, jo = N - 1 - jp;
+    const R* u0 = P0 + (c * 3 + 0) * NQQ + l * QQ + q0;
+    const R* u1 = P0 + (c * 3 + 1) * NQQ + l * QQ + q0;
+    const R* u2 = P0 + (c * 3 + 2) * NQQ + l * QQ + q0;
+    const R* C0 = C + (0 * N + l) * Q1 * N;
+    const R* C1 = C + (1 * N + l) * Q1 * N;
+    const R* C2 = C + (2 * N + l) * Q1 * N;
+    R vge = R(0), vgo = R(0), vbe = R(0), vbo = R(0);
+#pragma unroll
+    for (int q = 0; q < QE; ++q) {
+      vge = fma(u0[q * Q1], C0[q * N + je], vge);
+      vbe = fma(u2[q * Q1], C2[q * N + je], vbe);
+      vbo = fma(u1[q * Q1], C1[q * N + jo], vbo);
+    }
+#pragma unroll
+    for (int q = QE; q < Q1; ++q) {
+      vgo = fma(u0[q * Q1], C0[q * N + jo], vgo);
+      vbo = fma(u2[q * Q1], C2[q * N + jo], vbo);
+      vbe = fma(u1[q * Q1], C1[q * N + je], vbe);
+    }
+    R* vg = P1 + (c * 2 + 0) * NNQ + l * N * Q1 + q0;
+    R* vb = P1 + (c * 2 + 1) * NNQ + l * N * Q1 + q0;
+    vg[je * Q1] = vge; vg[jo * Q1] = vgo;
+    vb[je * Q1] = vbe; vb[jo * Q1] = vbo;
+  }
+  __syncwarp();
+  for (int t = lane; t < NC * N * N * H; t += 32) {             // (c, l, j, i pair) along q0 -> i
+    const int ip = t % H, lj = (t / H) % (N * N), c = t / (H * N * N);
+    const int ie = ip, io = N - 1 - ip;
+    const R* vg = P1 + (c * 2 + 0) * NNQ + lj * Q1;
+    const R* vb = P1 + (c * 2 + 1) * NNQ + lj * Q1;
+    R ye = R(0), yo = R(0);
+#pragma unroll
+    for (int q = 0; q < QE; ++q) {
+      ye = fma(vb[q], Bf[q * N + ie], ye);
+      yo = fma(vg[q], Gf[q * N + io], yo);
+    }
+#pragma unroll
+    for (int q = QE; q < Q1; ++q) {
+      yo = fma(vb[q], Bf[q * N + io], yo);
+      ye = fma(vg[q], Gf[q * N + ie], ye);
+    }
+    R* y = P0 + (c * N * N + lj) * N;
+    y[ie] = ye;
+    y[io] = yo;
+  }
+  __syncwarp();
+}
+
+// F_N^3 of adj3_eon's output, ysc multiplied back in the axis-2 pass: y at the nodes.
+template <int NF, int L, class R>
+__device__ __forceinline__ void unfold_nodes(R* buf, const R* __restrict__ ysc, int lane) {
+  static_assert(L % 2 == 0, "even node count");
+  mirror3<NF, L, L, L, 0, R>(buf, lane);
+  mirror3<NF, L, L, L, 1, R>(buf, lane);
+  constexpr int H = L / 2, FS = L * L * L, LINES = L * L, ST = L * L;
+#pragma unroll 1
+  for (int t = lane; t < NF * LINES * H; t += 32) {
+    const int i = t % H, line = (t / H) % LINES, f = t / (H * LINES);
+    R* v = buf + f * FS + line;
+    const R bs = v[(L - 1 - i) * ST] * ysc[L - 1 - i];
+    const R a = v[i * ST], sa = ysc[i];
+    v[i * ST] = fma(a, sa, bs);
+    v[(L - 1 - i) * ST] = fma(a, sa, -bs);
+  }
+  __syncwarp();
+}
+
 // Adjoint stages in the folded basis; same buffer layouts as adj3. P1 holds
 // F_Q^3 R on entry; P0 holds the folded y (F_N^3 of it is y) on exit. Each
 // unit computes a mirror pair of outputs: the even position l, which reads

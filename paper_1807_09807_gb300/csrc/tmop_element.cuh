@@ -65,7 +65,9 @@ struct ElemCfg {
   // FP64 3D with an even node count: contractions in the mirror basis, whose
   // normalised forward stages need the pivot tables and their products
   static constexpr bool EO = D == 3 && sizeof(R) == 8 && N % 2 == 0;
-  static constexpr int TABLE = round16<R>(2 * kMaxQ * kMaxN + kMaxQ + (EO ? 4 * kMaxQ + 3 * Q1 * Q1 * Q1 : 0));
+  static constexpr int EO_FWD = 4 * kMaxQ + 3 * Q1 * Q1 * Q1;                           // pivots, ratios, scales
+  static constexpr int EO_ADJ = 2 * kMaxN * kMaxQ + 2 * kMaxN + 3 * N * Q1 * N + kMaxN;  // ratios, pivots, C, ysc
+  static constexpr int TABLE = round16<R>(2 * kMaxQ * kMaxN + kMaxQ + (EO ? EO_FWD + EO_ADJ : 0));
   static constexpr size_t smem_bytes() { return sizeof(R) * (TABLE + WARPS * (B0 + B1 + B2)); }
 };
 
@@ -124,17 +126,23 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32, ElemCfg<
   R* P2 = P1 + Cfg::B1;  // A(x) of the split 3D Hessian action
 
   // FP64 3D kernels with an even node count contract in the mirror basis
-  // (fwd3_eon / adj3_eo): sB, sG then hold the folded tables, followed by
-  // the normalised forward's pivots, ratios and scale products
+  // (fwd3_eon / adj3_eon): sB, sG then hold the folded tables, followed by
+  // the normalised maps' pivots, ratios, scale products and stage-2 tables
   constexpr bool EO = Cfg::EO;
   R* s_piv = sw + kMaxQ;
   R* s_rt = s_piv + 2 * kMaxQ;
   R* s_Sc = s_rt + 2 * kMaxQ;
+  R* s_arat = s_Sc + 3 * Q1 * Q1 * Q1;
+  R* s_apiv = s_arat + 2 * kMaxN * kMaxQ;
+  R* s_C = s_apiv + 2 * kMaxN;
+  R* s_ysc = s_C + 3 * N * Q1 * N;
   __shared__ int s_kf[2 * kMaxQ];
+  __shared__ int s_aperm[2 * kMaxN * kMaxQ];
   if constexpr (EO) {
     folded_tables<N, Q1, R>(p.B, p.G, sB, sG, threadIdx.x, blockDim.x);
     __syncthreads();
     normalised_tables<N, Q1, R>(sB, sG, s_kf, s_rt, s_piv, s_Sc, threadIdx.x, blockDim.x);
+    adjoint_tables<N, Q1, R>(sB, sG, s_aperm, s_arat, s_apiv, s_C, s_ysc, threadIdx.x, blockDim.x);
   } else {
     for (int t = threadIdx.x; t < Q1 * N; t += blockDim.x) {
       sB[t] = R(p.B[t]);
@@ -570,8 +578,8 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32, ElemCfg<
         adj2<N, Q1, D, R>(sB, sG, P0, P1, lane);
       } else if constexpr (EO) {
         mirror3_all<D * D, Q1, R>(P1, lane);
-        adj3_eo<N, Q1, D, R>(sB, sG, P0, P1, lane);
-        mirror3_all<D, N, R>(P0, lane);
+        adj3_eon<N, Q1, D, R>(sB, sG, s_aperm, s_arat, s_C, P0, P1, lane);
+        unfold_nodes<D, N, R>(P0, s_ysc, lane);
       } else if constexpr (RB) {
         adj3_rb<N, Q1, D, R>(tB, tG, P0, P1, lane);
       } else {
