@@ -72,30 +72,34 @@ def contraction_fmas(dim: int, n: int, q: int, nc: int) -> tuple[int, int]:
     return fwd, adj
 
 
-def folded_contraction_ops(dim: int, n: int, q: int, nc: int):
-    """What the FP64 3D kernels with an even node count run instead of the
-    plain contractions (the mirror basis: fwd3_eo / adj3_eo and the in-place
-    butterflies around them): (forward FMAs, forward adds, adjoint FMAs,
-    adjoint adds) per element, or None where the plain contractions run."""
+def folded_contraction_flops(dim: int, n: int, q: int, nc: int):
+    """Flops the FP64 3D kernels with an even node count execute for one
+    element's forward map (nodes -> A) and adjoint map (per-point matrices ->
+    nodes) in the mirror basis with normalised dots (fwd3_eon, adj3_eon and
+    the butterfly passes around them), FMAs as two flops, multiplies and adds
+    as one; None where the plain contractions run."""
     if dim != 3 or n % 2:
         return None
-    h = n // 2
-    fwd_fma = nc * (n * n * q * 2 * h + n * q * q * 3 * h + q ** 3 * 3 * h)
-    adj_fma = nc * (h * q * q * 3 * q + n * h * q * 3 * q + n * n * h * 2 * q)
-    fold_nodes = nc * 3 * n * n * h * 2            # three axes of the nodal field
-    fold_points = 3 * nc * 3 * q * q * (q // 2) * 2  # three axes of the nc x 3 point fields
-    return fwd_fma, fold_nodes + fold_points, adj_fma, fold_points + fold_nodes
+    h, qe, qo = n // 2, (q + 1) // 2, q // 2
+    outs = nc * (n * n * q * 2 + n * q * q * 3 + q ** 3 * 3)          # forward stage outputs
+    fwd = (nc * 3 * n * n * h * 2                                     # butterflies of the nodal field
+           + 2 * (h - 1) * outs                                       # one FMA per output (n = 4)
+           + 3 * nc * q * q * qo * 5 + (q % 2) * 3 * nc * q * q       # scaled axis-0 unfold
+           + 2 * 3 * nc * q * q * qo * 2)                             # axes 1 and 2
+    adj = (3 * nc * 3 * q * q * qo * 2                                # butterflies of the point fields
+           + 2 * (nc * h * q * q * 3 * (q - 2) + nc * n * h * q * 3 * q + nc * n * n * h * 2 * q)
+           + 2 * nc * n * n * h * 2 + nc * n * n * h * 5)             # nodal unfold, the last pass scaled
+    return fwd, adj
 
 
 def hess_executed_flops_per_element(dim, n, q, metric):
     """Flops the FP64 matrix-free Hessian action executes per element: the
-    folded contractions (FMAs as two flops, butterfly adds as one) where they
-    run, else the plain ones, and dP at every point."""
-    f = folded_contraction_ops(dim, n, q, dim)
+    folded, normalised contractions where they run, else the plain ones,
+    and dP at every point."""
+    f = folded_contraction_flops(dim, n, q, dim)
     if f is None:
         return hess_flops_per_element(dim, n, q, metric)
-    ff, fa, af, aa = f
-    return 2 * (2 * ff + af) + 2 * fa + aa + METRIC_DP_FLOPS[metric] * q ** dim
+    return 2 * f[0] + f[1] + METRIC_DP_FLOPS[metric] * q ** dim
 
 
 def hess_flops_per_element(dim, n, q, metric):
@@ -804,9 +808,9 @@ def measure_pa(tm, m, x, v, y, flush, stream, args):
             ent["roofline"] = {"bound": "alu", "achieved": ent["achieved_TFLOPs"], "peak": pk,
                                "unit": "TFLOP/s", "frac": ent["achieved_TFLOPs"] / pk,
                                "peak_source": "measured: tmop_fma_peak DFMA" if alu else "nominal (unit counts x clock)"}
-            fo = folded_contraction_ops(m.dim, n, m.nq, m.dim)
+            fo = folded_contraction_flops(m.dim, n, m.nq, m.dim)
             if fo is not None:   # the mirror-basis contractions the FP64 kernel runs
-                ex = m.nelem * (2 * (fo[0] + fo[2]) + fo[1] + fo[3] + 2 * dd * dd * m.Q)
+                ex = m.nelem * (fo[0] + fo[1] + 2 * dd * dd * m.Q)
                 ent["roofline"]["executed_flops_per_launch"] = ex
                 ent["roofline"]["frac_executed"] = ex / (hv_ms * 1e-3) / 1e12 / pk
         else:
