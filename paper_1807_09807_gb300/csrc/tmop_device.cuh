@@ -144,9 +144,11 @@ __device__ __forceinline__ double f32_to_f64(float f) {
 
 __device__ __forceinline__ double rcbrt_nr(double a) {
   if (!(a >= 0x1p-120 && a <= 0x1p120)) return rcbrt(a);
+  // y <- y (4 - a y^3) / 3 = y (4/3 - (a/3) y^3), a/3 formed once
   double y = f32_to_f64(rcbrtf(f64_to_f32(a)));
-  y = y * fma(-a, y * y * y, 4.0) * (1.0 / 3.0);
-  y = y * fma(-a, y * y * y, 4.0) * (1.0 / 3.0);
+  const double a3 = a * (1.0 / 3.0);
+  y = y * fma(-a3, y * y * y, 4.0 / 3.0);
+  y = y * fma(-a3, y * y * y, 4.0 / 3.0);
   return y;
 }
 
@@ -188,76 +190,87 @@ __device__ __forceinline__ void cof_m(const S* M, S* C) {
 // ---------------------------------------------------------------- metrics
 // mu(T) and P = dmu/dT. Returns false when a barrier metric meets
 // tau <= 0 (mu is +inf there, P is left unset).
+//
+// metric_P(id, T, mu, P, s) returns s P instead (mu unscaled): the factor
+// joins the one or two scalars P is built from, so the caller's weight
+// w det W costs no multiply per entry of P.
 template <int D, class S>
-__device__ __forceinline__ bool metric_P(int id, const S* T, S& mu, S* P) {
+__device__ __forceinline__ bool metric_P(int id, const S* T, S& mu, S* P, typename base_of<S>::type s) {
+  using B = typename base_of<S>::type;
   constexpr int DD = D * D;
   S I1 = T[0] * T[0];
 #pragma unroll
   for (int i = 1; i < DD; ++i) I1 = I1 + T[i] * T[i];
   if (id == 1) {  // |T|^2
     mu = I1;
+    const B c = sc<S>(2.0) * s;
 #pragma unroll
-    for (int i = 0; i < DD; ++i) P[i] = sc<S>(2.0) * T[i];
+    for (int i = 0; i < DD; ++i) P[i] = c * T[i];
     return true;
   }
   if (id == 14) {  // |T - I|^2
+    const B c = sc<S>(2.0) * s;
     S e0 = T[0] - sc<S>(1.0);
-    S s = e0 * e0;
-    P[0] = sc<S>(2.0) * e0;
+    S acc = e0 * e0;
+    P[0] = c * e0;
 #pragma unroll
     for (int i = 1; i < DD; ++i) {
       S e = (i % (D + 1) == 0) ? T[i] - sc<S>(1.0) : T[i];
-      s = s + e * e;
-      P[i] = sc<S>(2.0) * e;
+      acc = acc + e * e;
+      P[i] = c * e;
     }
-    mu = s;
+    mu = acc;
     return true;
   }
-  S tau = det_m<D>(T);
-  if (!(value(tau) > 0)) return false;
+  // det T by expansion along the first row, from the cofactors P needs anyway
   S C[DD];
   cof_m<D>(T, C);
+  S tau = T[0] * C[0];
+#pragma unroll
+  for (int j = 1; j < D; ++j) tau = tau + T[j] * C[j];
+  if (!(value(tau) > 0)) return false;
   if (id == 98) {  // |T - I|^2 / tau (Section 4.3.2); P = (2 (T - I) - mu C) / tau
     S it = recip(tau);
     S E[DD];
 #pragma unroll
     for (int i = 0; i < DD; ++i) E[i] = (i % (D + 1) == 0) ? T[i] - sc<S>(1.0) : T[i];
-    S s = E[0] * E[0];
+    S acc = E[0] * E[0];
 #pragma unroll
-    for (int i = 1; i < DD; ++i) s = s + E[i] * E[i];
-    mu = s * it;
+    for (int i = 1; i < DD; ++i) acc = acc + E[i] * E[i];
+    mu = acc * it;
+    const S its = it * s;
 #pragma unroll
-    for (int i = 0; i < DD; ++i) P[i] = it * (sc<S>(2.0) * E[i] - mu * C[i]);
+    for (int i = 0; i < DD; ++i) P[i] = its * (sc<S>(2.0) * E[i] - mu * C[i]);
     return true;
   }
   if constexpr (D == 2) {
     S it = recip(tau);
     if (id == 2) {  // |T|^2 / (2 tau) - 1
       mu = sc<S>(0.5) * I1 * it - sc<S>(1.0);
-      S b = sc<S>(0.5) * I1 * it * it;
+      S a = it * s, b = (sc<S>(0.5) * s) * I1 * it * it;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) P[i] = it * T[i] - b * C[i];
+      for (int i = 0; i < 4; ++i) P[i] = a * T[i] - b * C[i];
       return true;
     }
     S it2 = it * it;
     if (id == 7) {  // |T - T^-t|^2 = I1 (1 + tau^-2) - 4
       mu = I1 * (it2 + sc<S>(1.0)) - sc<S>(4.0);
-      S a = sc<S>(2.0) * (it2 + sc<S>(1.0)), b = sc<S>(2.0) * I1 * it2 * it;
+      S a = (sc<S>(2.0) * s) * (it2 + sc<S>(1.0)), b = (sc<S>(2.0) * s) * I1 * it2 * it;
 #pragma unroll
       for (int i = 0; i < 4; ++i) P[i] = a * T[i] - b * C[i];
       return true;
     }
     if (id == 9) {  // tau |T - T^-t|^2 = tau I1 + I1 / tau - 4 tau
       mu = tau * I1 + I1 * it - sc<S>(4.0) * tau;
-      S a = sc<S>(2.0) * (tau + it), b = I1 - I1 * it2 - sc<S>(4.0);
+      S a = (sc<S>(2.0) * s) * (tau + it), b = (I1 - I1 * it2 - sc<S>(4.0)) * s;
 #pragma unroll
       for (int i = 0; i < 4; ++i) P[i] = a * T[i] + b * C[i];
       return true;
     }
     if (id == 77) {  // (tau - 1/tau)^2 / 2
-      S s = tau - it;
-      mu = sc<S>(0.5) * s * s;
-      S a = s * (it2 + sc<S>(1.0));
+      S d = tau - it;
+      mu = sc<S>(0.5) * d * d;
+      S a = d * (it2 + sc<S>(1.0)) * s;
 #pragma unroll
       for (int i = 0; i < 4; ++i) P[i] = a * C[i];
       return true;
@@ -268,7 +281,7 @@ __device__ __forceinline__ bool metric_P(int id, const S* T, S& mu, S* P) {
       S r2 = r * r;
       S it = r2 * r;
       mu = sc<S>(1.0 / 3.0) * I1 * r2 - sc<S>(1.0);
-      S a = sc<S>(2.0 / 3.0) * r2, b = sc<S>(2.0 / 9.0) * I1 * r2 * it;
+      S a = (sc<S>(2.0 / 3.0) * s) * r2, b = (sc<S>(2.0 / 9.0) * s) * I1 * r2 * it;
 #pragma unroll
       for (int i = 0; i < 9; ++i) P[i] = a * T[i] - b * C[i];
       return true;
@@ -287,18 +300,24 @@ __device__ __forceinline__ bool metric_P(int id, const S* T, S& mu, S* P) {
       S a = sc<S>(1.0 / 9.0) * it * it;
       mu = a * I1 * K - sc<S>(1.0);
       S c = sc<S>(2.0) * a * I1 * K * it;
+      S as = a * s, cs = c * s;
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
           S M = T[i * 3 + 0] * TtT[0 * 3 + j] + T[i * 3 + 1] * TtT[1 * 3 + j] + T[i * 3 + 2] * TtT[2 * 3 + j];
           S Kp = sc<S>(2.0) * (I1 * T[i * 3 + j] - M);
-          P[i * 3 + j] = a * (I1 * Kp + sc<S>(2.0) * K * T[i * 3 + j]) - c * C[i * 3 + j];
+          P[i * 3 + j] = as * (I1 * Kp + sc<S>(2.0) * K * T[i * 3 + j]) - cs * C[i * 3 + j];
         }
       return true;
     }
   }
   return false;
+}
+
+template <int D, class S>
+__device__ __forceinline__ bool metric_P(int id, const S* T, S& mu, S* P) {
+  return metric_P<D, S>(id, T, mu, P, typename base_of<S>::type(1));
 }
 
 // ---------------------------------------------------------------- linearised metric
@@ -388,6 +407,91 @@ struct MetricLin {
     }
 #pragma unroll
     for (int i = 0; i < DD; ++i) out[i] = fma(a, dT[i], fma(bT, T[i], fma(bC, C[i], mdC[i])));
+  }
+};
+
+// The same second derivative for a matrix-free Hessian action, with the
+// point's weight s = w det W and the constant factors folded into five
+// coefficients when T is set, so that dP costs ~10 multiplies fewer per
+// point (GB300 issues only two FP64 operations per SM and clock):
+//   s dP = cA dT + (c11 t + c1t d) T + (c1t t + ctt d) C + s mu_t dC,
+// with t = T:dT, d = C:dT, cA = 2 s mu_1, c11 = 4 s mu_11, c1t = 2 s mu_1t,
+// ctt = s mu_tt.
+template <int D, class R>
+struct MetricAct {
+  static constexpr int DD = D * D;
+  R T[DD], C[DD];
+  R cA, c11, c1t, ctt, ct;
+
+  __device__ __forceinline__ bool init(int id, const R* Tin, R s) {
+    if constexpr (D == 3) {
+      if (id == 303) {  // I1 tau^{-2/3} / 3 - 1: mu_11 = 0
+#pragma unroll
+        for (int i = 0; i < DD; ++i) T[i] = Tin[i];
+        R I1 = R(0);
+#pragma unroll
+        for (int i = 0; i < DD; ++i) I1 = fma(T[i], T[i], I1);
+        cof_m<D>(T, C);
+        R tau = R(0);
+#pragma unroll
+        for (int j = 0; j < D; ++j) tau = fma(T[j], C[j], tau);
+        if (!(tau > R(0))) return false;
+        // mu_1 = r^2 / 3, mu_1t = -2/9 r^5, mu_t = I1 mu_1t, mu_tt = -5/3 mu_t r^3 (r = tau^{-1/3})
+        const R r = rcbrt_(tau), r2 = r * r, it = r2 * r, t53 = r2 * it;
+        cA = (R(2.0 / 3.0) * s) * r2;
+        c11 = R(0);
+        c1t = (R(-4.0 / 9.0) * s) * t53;
+        ct = c1t * (R(0.5) * I1);
+        ctt = (ct * it) * R(-5.0 / 3.0);
+        return true;
+      }
+    }
+    MetricLin<D, R> L;
+    if (!L.init(id, Tin)) return false;
+#pragma unroll
+    for (int i = 0; i < DD; ++i) {
+      T[i] = L.T[i];
+      C[i] = L.C[i];
+    }
+    const R s2 = R(2) * s;
+    cA = s2 * L.m1;
+    c11 = (R(2) * s2) * L.m11;
+    c1t = s2 * L.m1t;
+    ctt = s * L.mtt;
+    ct = s * L.mt;
+    return true;
+  }
+
+  __device__ __forceinline__ void dP(const R* dT, R* out) const {
+    R t = R(0), d = R(0);
+#pragma unroll
+    for (int i = 0; i < DD; ++i) {
+      t = fma(T[i], dT[i], t);
+      d = fma(C[i], dT[i], d);
+    }
+    const R bT = fma(c11, t, c1t * d);
+    const R bC = fma(c1t, t, ctt * d);
+    R mdC[DD];  // s mu_t dC
+    if constexpr (D == 2) {
+      mdC[0] = ct * dT[3]; mdC[1] = -ct * dT[2]; mdC[2] = -ct * dT[1]; mdC[3] = ct * dT[0];
+    } else {
+      R U[DD];
+#pragma unroll
+      for (int i = 0; i < DD; ++i) U[i] = ct * T[i];
+#define TMOP_DMINOR(a_, b_, c_, e_) fma(dT[a_], U[b_], fma(U[a_], dT[b_], -fma(dT[c_], U[e_], U[c_] * dT[e_])))
+      mdC[0] = TMOP_DMINOR(4, 8, 5, 7);
+      mdC[1] = TMOP_DMINOR(5, 6, 3, 8);
+      mdC[2] = TMOP_DMINOR(3, 7, 4, 6);
+      mdC[3] = TMOP_DMINOR(2, 7, 1, 8);
+      mdC[4] = TMOP_DMINOR(0, 8, 2, 6);
+      mdC[5] = TMOP_DMINOR(1, 6, 0, 7);
+      mdC[6] = TMOP_DMINOR(1, 5, 2, 4);
+      mdC[7] = TMOP_DMINOR(2, 3, 0, 5);
+      mdC[8] = TMOP_DMINOR(0, 4, 1, 3);
+#undef TMOP_DMINOR
+    }
+#pragma unroll
+    for (int i = 0; i < DD; ++i) out[i] = fma(cA, dT[i], fma(bT, T[i], fma(bC, C[i], mdC[i])));
   }
 };
 

@@ -67,7 +67,9 @@ struct ElemCfg {
   static constexpr bool EO = D == 3 && sizeof(R) == 8 && N % 2 == 0;
   static constexpr int EO_FWD = 4 * kMaxQ + 3 * Q1 * Q1 * Q1;                           // pivots, ratios, scales
   static constexpr int EO_ADJ = 2 * kMaxN * kMaxQ + 2 * kMaxN + 3 * N * Q1 * N + kMaxN;  // ratios, pivots, C, ysc
-  static constexpr int TABLE = round16<R>(2 * kMaxQ * kMaxN + kMaxQ + (EO ? EO_FWD + EO_ADJ : 0));
+  // after the 1D tables: the product weight w_q0 w_q1 (w_q2) of every point
+  static constexpr int WQ_OFF = 2 * kMaxQ * kMaxN + kMaxQ + (EO ? EO_FWD + EO_ADJ : 0);
+  static constexpr int TABLE = round16<R>(WQ_OFF + Shape<D, N, Q1>::QP);
   static constexpr size_t smem_bytes() { return sizeof(R) * (TABLE + WARPS * (B0 + B1 + B2)); }
 };
 
@@ -150,6 +152,14 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32, ElemCfg<
     }
   }
   for (int t = threadIdx.x; t < Q1; t += blockDim.x) sw[t] = R(p.w1[t]);
+  // point weights, rounded as (w_q0 w_q1) w_q2 in R: two multiplies per point
+  // fewer on GB300's narrow FP64 pipe
+  R* sWq = sB + Cfg::WQ_OFF;
+  for (int t = threadIdx.x; t < QP; t += blockDim.x) {
+    R w = R(p.w1[t % Q1]) * R(p.w1[(t / Q1) % Q1]);
+    if constexpr (D == 3) w *= R(p.w1[t / (Q1 * Q1)]);
+    sWq[t] = w;
+  }
   R Wi[DD];
 #pragma unroll
   for (int i = 0; i < DD; ++i) Wi[i] = R(p.Winv[i]);
@@ -312,9 +322,7 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32, ElemCfg<
       for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int b = 0; b < D; ++b) A[a * D + b] = Abuf[(a * D + b) * QP + q];
-      const int q0 = q % Q1, q1 = (q / Q1) % Q1;
-      R wq = sw[q0] * sw[q1];
-      if constexpr (D == 3) wq *= sw[q / (Q1 * Q1)];
+      const R wq = sWq[q];
       R detW = R(p.detW);
       if (p.wkind == WK_PER_QP) {
         const double* Wq = p.Winv_qp + ((size_t)e * QP + q) * DD;
@@ -468,11 +476,14 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32, ElemCfg<
           else accF = INFINITY;
         }
       } else {
+        // S below is already scaled by s = w det W (folded into the metric's
+        // coefficients)
+        const R s = wq * detW;
         R S[DD], dA[DD];
         bool ok;
         if constexpr (GRADLIKE) {
           R mu;
-          ok = metric_P<D>(p.metric, T, mu, S);
+          ok = metric_P<D>(p.metric, T, mu, S, s);
           if constexpr (EG) {   // the energy of OP_ENERGY from the same point
             double Ad[DD];
 #pragma unroll
@@ -493,10 +504,10 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32, ElemCfg<
             for (int a = 0; a < D; ++a)
 #pragma unroll
               for (int b = 0; b < D; ++b) {
-                R s = R(0);
+                R acc = R(0);
 #pragma unroll
-                for (int c = 0; c < D; ++c) s = fma(dA[a * D + c], Wi[c * D + b], s);
-                dT[a * D + b] = s;
+                for (int c = 0; c < D; ++c) acc = fma(dA[a * D + c], Wi[c * D + b], acc);
+                dT[a * D + b] = acc;
               }
           }
           if (metric_dual(p.metric)) {
@@ -506,15 +517,14 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32, ElemCfg<
             for (int i = 0; i < DD; ++i) Td[i] = Dual<R>{T[i], dT[i]};
             ok = metric_P<D>(p.metric, Td, mud, Pd);
 #pragma unroll
-            for (int i = 0; i < DD; ++i) S[i] = Pd[i].d;
+            for (int i = 0; i < DD; ++i) S[i] = s * Pd[i].d;
           } else {
-            MetricLin<D, R> L;
-            ok = L.init(p.metric, T);
+            MetricAct<D, R> L;
+            ok = L.init(p.metric, T, s);
             if (ok) L.dP(dT, S);
           }
         }
-        const R s = wq * detW;
-        // R = s * S W^-t, stored in place of A at this point
+        // R = s S W^-t (S already carries s), stored in place of A at this point
 #pragma unroll
         for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -526,7 +536,7 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32, ElemCfg<
 #pragma unroll
               for (int c = 0; c < D; ++c) r = fma(S[a * D + c], Wi[b * D + c], r);
             }
-            Rbuf[(a * D + b) * QP + q] = ok ? s * r : R(0);
+            Rbuf[(a * D + b) * QP + q] = ok ? r : R(0);
           }
         if (p.metric2) {
           // + eta w det W2 S2 W2^-t (S2 = P2 or dP2 at T2 = A W2^-1)
