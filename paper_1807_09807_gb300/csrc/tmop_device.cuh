@@ -49,10 +49,10 @@ template <class R> __device__ __forceinline__ Dual<R> recip(Dual<R> a) {
   R r = R(1) / a.v;
   return {r, -a.d * r * r};
 }
-// tau^{-1/3}. In FP64 by Newton's method on y^-3 = tau from the FP32
-// estimate: y <- y (4 - tau y^3) / 3 squares the relative error, so two
-// steps take the ~1e-7 start to rounding level (a few ulp) with ~10 FP64
-// operations, on GB300's narrow FP64 pipe the cheaper route. Outside
+// tau^{-1/3}. In FP64 from the FP32 estimate y by one third-order step
+// (the cube of the start's ~1e-7 relative error is below FP64 rounding: a
+// few ulp) with 6 FP64 operations, on GB300's narrow FP64 pipe the cheaper
+// route. Outside
 // [2^-120, 2^120] (where the FP32 start would over- or underflow) and for
 // non-finite input it defers to rcbrt.
 __device__ __forceinline__ double rcbrt_nr(double a);
@@ -144,12 +144,12 @@ __device__ __forceinline__ double f32_to_f64(float f) {
 
 __device__ __forceinline__ double rcbrt_nr(double a) {
   if (!(a >= 0x1p-120 && a <= 0x1p120)) return rcbrt(a);
-  // y <- y (4 - a y^3) / 3 = y (4/3 - (a/3) y^3), a/3 formed once
-  double y = f32_to_f64(rcbrtf(f64_to_f32(a)));
-  const double a3 = a * (1.0 / 3.0);
-  y = y * fma(-a3, y * y * y, 4.0 / 3.0);
-  y = y * fma(-a3, y * y * y, 4.0 / 3.0);
-  return y;
+  // one step of the series y (1 + e)^(-1/3) = y (1 - e/3 + 2 e^2 / 9 - ...)
+  // with e = a y^3 - 1: the FP32 start has |e| < ~1e-6, so the dropped
+  // O(e^3) term is far below FP64 rounding
+  const double y = f32_to_f64(rcbrtf(f64_to_f32(a)));
+  const double e = fma(a, y * y * y, -1.0);
+  return fma(y, e * fma(e, 2.0 / 9.0, -1.0 / 3.0), y);
 }
 
 // FP64 value -> the kernel's arithmetic type, and back
@@ -281,7 +281,7 @@ __device__ __forceinline__ bool metric_P(int id, const S* T, S& mu, S* P, typena
       S r2 = r * r;
       S it = r2 * r;
       mu = sc<S>(1.0 / 3.0) * I1 * r2 - sc<S>(1.0);
-      S a = (sc<S>(2.0 / 3.0) * s) * r2, b = (sc<S>(2.0 / 9.0) * s) * I1 * r2 * it;
+      S a = (sc<S>(2.0 / 3.0) * s) * r2, b = a * ((sc<S>(1.0 / 3.0) * I1) * it);   // b = 2/9 s I1 r^5
 #pragma unroll
       for (int i = 0; i < 9; ++i) P[i] = a * T[i] - b * C[i];
       return true;
@@ -436,11 +436,12 @@ struct MetricAct {
 #pragma unroll
         for (int j = 0; j < D; ++j) tau = fma(T[j], C[j], tau);
         if (!(tau > R(0))) return false;
-        // mu_1 = r^2 / 3, mu_1t = -2/9 r^5, mu_t = I1 mu_1t, mu_tt = -5/3 mu_t r^3 (r = tau^{-1/3})
-        const R r = rcbrt_(tau), r2 = r * r, it = r2 * r, t53 = r2 * it;
+        // mu_1 = r^2 / 3, mu_1t = -2/9 r^5 = -2/3 mu_1 r^3, mu_t = I1 mu_1t,
+        // mu_tt = -5/3 mu_t r^3 (r = tau^{-1/3})
+        const R r = rcbrt_(tau), r2 = r * r, it = r2 * r;
         cA = (R(2.0 / 3.0) * s) * r2;
         c11 = R(0);
-        c1t = (R(-4.0 / 9.0) * s) * t53;
+        c1t = cA * (R(-2.0 / 3.0) * it);
         ct = c1t * (R(0.5) * I1);
         ctt = (ct * it) * R(-5.0 / 3.0);
         return true;
