@@ -115,6 +115,24 @@ def grad_flops_per_element(dim, n, q, metric):
     return 2 * (fwd + adj) + (METRIC_DP_FLOPS[metric] // 2) * q ** dim
 
 
+def fused_flops_per_element(dim, n, q, metric):
+    """Algorithmic flops of the gradient and the Hessian action at the same x
+    in one pass: the Hessian action's work, a second adjoint contraction, and
+    s P assembled at every point from the coefficients dP's evaluation
+    already holds (dim^2 multiplies and dim^2 FMAs)."""
+    _, adj = contraction_fmas(dim, n, q, dim)
+    return hess_flops_per_element(dim, n, q, metric) + 2 * adj + 3 * dim * dim * q ** dim
+
+
+def fused_executed_flops_per_element(dim, n, q, metric):
+    """The same with the contractions the FP64 kernel runs (folded and
+    normalised where they are)."""
+    f = folded_contraction_flops(dim, n, q, dim)
+    if f is None:
+        return fused_flops_per_element(dim, n, q, metric)
+    return hess_executed_flops_per_element(dim, n, q, metric) + f[1] + 3 * dim * dim * q ** dim
+
+
 ELEM_SOURCES = ("tmop_device.cuh", "tmop_element.cuh", "tmop_kparams.h")
 PAC_SOURCES = ("tmop_device.cuh", "tmop_pa_compact.cu", "tmop_pa_compact.h", "tmop_kparams.h")
 
@@ -515,7 +533,18 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    # the step: g = dF/dx and y = H(x) v at the same x, through the one-pass
+    # entry point (FP64: one element kernel; --separate: the two kernels)
+    fused = not args.separate
+
     def step(ev=None):
+        if fused:
+            if ev is not None:
+                ev[0].record(stream)
+            ctx.gradient_hess_apply(x, v, g=g, y=y)
+            if ev is not None:
+                ev[1].record(stream)
+            return
         ctx.gradient(x, out=g)
         if ev is not None:
             ev[0].record(stream)
@@ -620,9 +649,13 @@ def run_ours(args):
         stream.wait_event(ev["in"][b])
         if k >= 2:
             stream.wait_event(ev["out"][b])        # step k-2's results have left gd[b], yd[b]
-        ctx.gradient(xd[b], out=gd[b])
-        ev["g"][b].record(stream)
-        ctx.hess_apply(xd[b], vd[b], out=yd[b])
+        if fused:
+            ctx.gradient_hess_apply(xd[b], vd[b], g=gd[b], y=yd[b])
+            ev["g"][b].record(stream)
+        else:
+            ctx.gradient(xd[b], out=gd[b])
+            ev["g"][b].record(stream)
+            ctx.hess_apply(xd[b], vd[b], out=yd[b])
         ev["done"][b].record(stream)
         ev["used"][b].record(stream)
         with torch.cuda.stream(down):
@@ -664,34 +697,57 @@ def run_ours(args):
     alu = measure_alu_peaks(tm, dev.index if dev.index is not None else 0)
     args._alu_peaks = alu
     n = m.order + 1
-    hess_ms_avg = statistics.mean(hess_ms)
-    flops = hess_flops_per_element(m.dim, n, m.nq, m.metric) * m.nelem
-    achieved = flops / (hess_ms_avg * 1e-3) / 1e12
     peak = (alu["fp64"]["gflops"] if prec == tm.FP64 else alu["fp32_best"]) / 1e3
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": f"elem_kernel<{m.dim},{n},{m.nq},{'double' if prec == tm.FP64 else 'float'},"
-                                           f"OP_HESS> (matrix-free Hessian action)",
-                "peak_source": ("measured: tmop_fma_peak " + ("DFMA" if prec == tm.FP64 else "FFMA / paired FFMA")
-                                + f" at SM {alu['fp64' if prec == tm.FP64 else 'fp32']['clocks']['sm_mhz']} MHz"
-                                + " (multiply-add chains on every SM, CUDA events)"),
-                "peak_nominal": (FP64_PEAK_GFLOPS if prec == tm.FP64 else FP32_PEAK_GFLOPS) / 1e3,
-                "frac_of_nominal": achieved / ((FP64_PEAK_GFLOPS if prec == tm.FP64 else FP32_PEAK_GFLOPS) / 1e3),
-                "flops_per_launch": flops, "hess_ms": hess_ms_avg}
-    if prec == tm.FP64:
-        # the kernel runs the contractions in the mirror basis: fewer flops than
-        # the plain sum factorisation that flops_per_launch counts
-        ex = hess_executed_flops_per_element(m.dim, n, m.nq, m.metric) * m.nelem
-        roofline["executed_flops_per_launch"] = ex
-        roofline["frac_executed"] = ex / (hess_ms_avg * 1e-3) / 1e12 / peak
-        roofline["work"] = ("flops_per_launch: the plain sum-factorised contractions + dP (the algorithmic work); "
-                            "executed_flops_per_launch: what the folded (mirror-basis) kernel runs")
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    traffic = {}
     if os.path.exists(tfile):
         with open(tfile) as f:
-            tr = json.load(f).get(f"{args.workload}:{args.precision}")
+            traffic = json.load(f)
+
+    def alu_roofline(kernel_ms, one_pass):
+        """Roofline of the step's dominant kernel: the one-pass gradient +
+        Hessian action, or (two kernels) the Hessian action."""
+        flops = (fused_flops_per_element if one_pass else hess_flops_per_element)(m.dim, n, m.nq, m.metric) * m.nelem
+        achieved = flops / (kernel_ms * 1e-3) / 1e12
+        op = "OP_GRAD_HESS> (gradient + matrix-free Hessian action, one pass)" if one_pass \
+            else "OP_HESS> (matrix-free Hessian action)"
+        r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+             "traffic": None, "kernel": f"elem_kernel<{m.dim},{n},{m.nq},{'double' if prec == tm.FP64 else 'float'},"
+                                        + op,
+             "peak_source": ("measured: tmop_fma_peak " + ("DFMA" if prec == tm.FP64 else "FFMA / paired FFMA")
+                             + f" at SM {alu['fp64' if prec == tm.FP64 else 'fp32']['clocks']['sm_mhz']} MHz"
+                             + " (multiply-add chains on every SM, CUDA events)"),
+             "peak_nominal": (FP64_PEAK_GFLOPS if prec == tm.FP64 else FP32_PEAK_GFLOPS) / 1e3,
+             "frac_of_nominal": achieved / ((FP64_PEAK_GFLOPS if prec == tm.FP64 else FP32_PEAK_GFLOPS) / 1e3),
+             "flops_per_launch": flops, "kernel_ms": kernel_ms,
+             "timed": "CUDA events around the call: the output memsets and the kernel"}
+        if prec == tm.FP64:
+            # the kernel runs the contractions in the mirror basis: fewer flops than
+            # the plain sum factorisation that flops_per_launch counts
+            ex = (fused_executed_flops_per_element if one_pass else hess_executed_flops_per_element)(
+                m.dim, n, m.nq, m.metric) * m.nelem
+            r["executed_flops_per_launch"] = ex
+            r["frac_executed"] = ex / (kernel_ms * 1e-3) / 1e12 / peak
+            r["work"] = ("flops_per_launch: the plain sum-factorised contractions + the metric terms (the "
+                         "algorithmic work); executed_flops_per_launch: what the folded (mirror-basis) kernel runs")
+        tr = traffic.get(f"{args.workload}:{args.precision}" + (":fused" if one_pass else ""))
         # only counters taken on the kernel sources as they are now
         if tr and tr.get("kernel_src_sha256") == kernel_src_hash():
-            roofline["traffic"] = tr["dram_bytes_per_launch"]
+            r["traffic"] = tr["dram_bytes_per_launch"]
+        return r
+
+    one_pass = fused and prec == tm.FP64
+    roofline = alu_roofline(statistics.mean(hess_ms), one_pass)
+    # the same step as two kernels (gradient, then Hessian action), outside the timed region
+    step_separate = None
+    if fused and rank == 0:
+        reps = max(3, min(args.steps, 10))
+        sep_ms = _event_ms(lambda: (ctx.gradient(x, out=g), ctx.hess_apply(x, v, out=y)), reps, stream, flush)
+        hv_ms = _event_ms(lambda: ctx.hess_apply(x, v, out=y), reps, stream, flush)
+        step_separate = {"ms_per_step": sep_ms, "value": m.n_qp / (sep_ms * 1e-3), "unit": UNIT,
+                         "hess_ms": hv_ms, "gradient_ms": sep_ms - hv_ms,
+                         "form": "tmop_gradient then tmop_hess_apply (two element kernels)",
+                         "roofline": alu_roofline(hv_ms, False) if prec == tm.FP64 else None}
 
     # ---- time to converged mesh, both precision forms (outside the timed region)
     # ---- partial assembly: linearize once, then the stored-Hessian product
@@ -729,9 +785,13 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == tm.FP64 else "f32 (f64 reductions)",
             "data": "synthetic", "config": workload_config(m, args), "clocks": clocks.summary(),
-            "e2e": e2e, "gpu_launches": 2 * args.steps, "roofline": roofline, "alu_peaks": alu,
+            "e2e": e2e, "gpu_launches": (1 if one_pass else 2) * args.steps, "roofline": roofline, "alu_peaks": alu,
             "wall_s_timed_region": t_wall,
+            "step_form": ("tmop_gradient_hess_apply: gradient and Hessian action in one element pass" if one_pass
+                          else "tmop_gradient then tmop_hess_apply"),
         }
+        if step_separate is not None:
+            line["step_separate"] = step_separate
         if pa is not None:
             line["partial_assembly"] = pa
         if step_mixed is not None:
@@ -1212,6 +1272,8 @@ def main():
     ap.add_argument("--train-meshes-curved", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels-only", action="store_true")
+    ap.add_argument("--separate", action="store_true",
+                    help="time the step as two kernels (tmop_gradient, tmop_hess_apply) instead of the one-pass call")
     ap.add_argument("--shard", action="store_true",
                     help="with N > 1: split the workload's elements into z-slabs, one per rank, with a halo "
                          "sum of the shared node planes per operator application (strong scaling) instead "

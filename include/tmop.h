@@ -146,6 +146,18 @@ int tmop_energy_gradient(tmop_ctx* ctx, const double* x, double* g, double* F, d
  * y: DEVICE [d][nnode], overwritten. Asynchronous. */
 int tmop_hess_apply(tmop_ctx* ctx, const double* x, const double* v, double* y, void* stream);
 
+/* The gradient g = dF/dx (as tmop_gradient) and the Hessian action
+ * y = H(x) v (as tmop_hess_apply) at the same x (Section 3.4: both are
+ * built from the same T = A W^-1, its P = dmu/dT and d^2mu/dT^2), in one
+ * element pass: x is gathered and A(x) contracted once, the metric's terms
+ * at each point serve both outputs, and two adjoint contractions scatter g
+ * and y. The pass covers FP64 contexts with atomic sums, no composite term
+ * and no restricted movement; any other context runs tmop_gradient and then
+ * tmop_hess_apply. Results equal the two calls' up to rounding.
+ * g, y: DEVICE [d][nnode], distinct, overwritten (zero at fixed dofs).
+ * TMOP_ERR_ARG for a null pointer or g == y. Asynchronous. */
+int tmop_gradient_hess_apply(tmop_ctx* ctx, const double* x, const double* v, double* g, double* y, void* stream);
+
 /* Partial assembly of the Hessian (Section 3.4: the Hessian from d^2mu/dT^2):
  * stores, at every quadrature point of x, the symmetric A-space matrix
  *   H_q = w_q det W (d^2mu/dT^2 composed with W^-1 on both sides)

@@ -33,10 +33,18 @@ extern const ElemEntry kElem_3d_f64[];
 extern const int kElem_3d_f64_len;
 extern const ElemEntry kElem_3d_f32[];
 extern const int kElem_3d_f32_len;
+extern const ElemEntry kElem_gh_f64[];
+extern const int kElem_gh_f64_len;
 
 const ElemEntry* find_elem(int dim, int n, int q, int fp32, int op) {
   const ElemEntry* t;
   int len;
+  if (op == OP_GRAD_HESS) {  // FP64 only, both dimensions in one table
+    if (fp32) return nullptr;
+    for (int i = 0; i < kElem_gh_f64_len; ++i)
+      if (kElem_gh_f64[i].dim == dim && kElem_gh_f64[i].n == n && kElem_gh_f64[i].q == q) return &kElem_gh_f64[i];
+    return nullptr;
+  }
   if (dim == 2) { t = fp32 ? kElem_2d_f32 : kElem_2d_f64; len = fp32 ? kElem_2d_f32_len : kElem_2d_f64_len; }
   else { t = fp32 ? kElem_3d_f32 : kElem_3d_f64; len = fp32 ? kElem_3d_f32_len : kElem_3d_f64_len; }
   for (int i = 0; i < len; ++i)
@@ -820,7 +828,7 @@ int tmop_setup(const tmop_mesh* mesh, int order, const tmop_quad* quad, int metr
     // FP32_MIXED: FP32 only for the Hessian action (and its partial assembly);
     // FP32_BULK: every element kernel
     const bool hess = op == OP_HESS || op == OP_LINEARIZE || op == OP_HESS_PA || op == OP_LINEARIZE_C ||
-                      op == OP_HESS_PA_C || op == OP_HESS_C;
+                      op == OP_HESS_PA_C || op == OP_HESS_C || op == OP_GRAD_HESS;
     const int fp32 = precision == TMOP_FP32_BULK || (precision == TMOP_FP32_MIXED && hess);
     ent[op] = find_elem(d, n, nq, fp32, op);
     // unsupported (order, points) pair; the compact pair exists for 3D FP32 only
@@ -1198,6 +1206,26 @@ int tmop_gradient(tmop_ctx* c, const double* x, double* g, void* stream) {
 int tmop_hess_apply(tmop_ctx* c, const double* x, const double* v, double* y, void* stream) {
   if (!c || !x || !v || !y) return TMOP_ERR_ARG;
   return launch_op(c, OP_HESS, x, v, y, nullptr, (cudaStream_t)stream);
+}
+
+int tmop_gradient_hess_apply(tmop_ctx* c, const double* x, const double* v, double* g, double* y, void* stream) {
+  if (!c || !x || !v || !g || !y || g == y) return TMOP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  // one element pass where the fused kernel covers the context (FP64, no
+  // composite term, no restricted movement, atomic sums); else the two kernels
+  if (!c->ent[OP_GRAD_HESS] || c->base.metric2 || c->delta != 0.0 || c->det) {
+    const int rc = launch_op(c, OP_GRADIENT, x, nullptr, g, nullptr, s);
+    return rc != TMOP_OK ? rc : launch_op(c, OP_HESS, x, v, y, nullptr, s);
+  }
+  KParams p = c->base;
+  p.x = x;
+  p.v = v;
+  p.y = y;
+  p.g = g;
+  CUDA_TRY(cudaMemsetAsync(g, 0, sizeof(double) * c->ndof, s));
+  CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * c->ndof, s));
+  if (c->ent[OP_GRAD_HESS]->launch(p, c->grid[OP_GRAD_HESS], s) != 0) return TMOP_ERR_CUDA;
+  return TMOP_OK;
 }
 
 int tmop_linearize(tmop_ctx* c, const double* x, void* stream) {

@@ -46,8 +46,9 @@ struct ElemCfg {
   // A(x) is kept (buffer B2) while v runs through the stage buffers, so the
   // stage buffers hold D components; 2D contracts both at once (2D
   // components, no B2).
-  static constexpr bool SPLIT = (OP == OP_HESS) && D == 3;
-  static constexpr int NC = (OP == OP_HESS && !SPLIT) ? 2 * D : D;
+  static constexpr bool HV = OP == OP_HESS || OP == OP_GRAD_HESS;  // contracts x and v
+  static constexpr bool SPLIT = HV && D == 3;
+  static constexpr int NC = (HV && !SPLIT) ? 2 * D : D;
   static constexpr int B0 = round16<R>(Buf<D, N, Q1, NC>::B0);
   static constexpr int B1 = round16<R>(Buf<D, N, Q1, NC>::B1);
   static constexpr int B2 = SPLIT ? round16<R>(D * D * Shape<D, N, Q1>::QP) : 0;
@@ -57,7 +58,7 @@ struct ElemCfg {
   // per warp for order 3) run as 6-warp blocks, two per SM: 12 warps in
   // flight instead of 8 on the FP64 pipe (gradient -2 %, stored-Hessian
   // product -8 % on 48^3 order-3 hexes)
-  static constexpr bool TWO = D == 3 && sizeof(R) == 8 && OP != OP_LINEARIZE && OP != OP_HESS &&
+  static constexpr bool TWO = D == 3 && sizeof(R) == 8 && OP != OP_LINEARIZE && !HV &&
                               12 * PER_WARP <= 200 * 1024;
   static constexpr int WARPS = TWO ? 6
                                    : ((200 * 1024 / PER_WARP) >= 8 ? 8
@@ -183,6 +184,9 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32, ElemCfg<
   constexpr bool GRADLIKE = OP == OP_GRADIENT || EG;
   constexpr int NSH = PA_APPLY ? D * D * (D * D + 1) / 2 : 1;
   static_assert(OP != OP_HESS_PA_C, "OP_HESS_PA_C runs in pac_kernel");
+  static_assert(OP != OP_GRAD_HESS || sizeof(R) == 8, "the fused gradient + Hessian action is FP64");
+  // its second 3D adjoint runs its stage 2 in the A(x) buffer
+  static_assert(!(OP == OP_GRAD_HESS && D == 3) || 2 * D * N * N * Q1 <= Cfg::B2, "B2 too small");
   static_assert(OP != OP_LINEARIZE_C || D == 3, "compact records are 3D");
   NodeMap<N> nodes(p.elem_nodes, p.sx, p.sy, D == 3 ? N - 1 : 1);
   const int ecount = p.elist ? p.ecount : p.nelem;
@@ -228,7 +232,7 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32, ElemCfg<
         if constexpr (sizeof(R) == 4) P0[c * NDOF + t] = from_f64<R>(xv - xref[c]);
         else P0[c * NDOF + t] = R(xv);
       }
-      if constexpr (OP == OP_HESS && !Cfg::SPLIT) {
+      if constexpr (Cfg::HV && !Cfg::SPLIT) {
 #pragma unroll
         for (int c = 0; c < D; ++c) {
           const size_t dof = (size_t)c * p.nnode + g;
@@ -344,6 +348,77 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32, ElemCfg<
             for (int c = 0; c < D; ++c) s = fma(A[a * D + c], Wi[c * D + b], s);
             T[a * D + b] = s;
           }
+      }
+      if constexpr (OP == OP_GRAD_HESS) {
+        // s P and s dP[dT] at the same point (s = w det W): one evaluation of
+        // the metric's terms for both. For an (|T|^2, det T) metric
+        // P = 2 mu_1 T + mu_t C, i.e. s P = cA T + ct C with MetricAct's scaled
+        // coefficients (mu14 = |T - I|^2 is the exception: its P from metric_P);
+        // the other metrics take P and dP from one dual-number evaluation.
+        const R s = wq * detW;
+        R dA[DD], dT[DD], Sg[DD], Sh[DD];
+#pragma unroll
+        for (int i = 0; i < DD; ++i) dA[i] = dAbuf[i * QP + q];
+        if (p.wkind == WK_IDENTITY) {
+#pragma unroll
+          for (int i = 0; i < DD; ++i) dT[i] = dA[i];
+        } else {
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = 0; b < D; ++b) {
+              R acc = R(0);
+#pragma unroll
+              for (int c = 0; c < D; ++c) acc = fma(dA[a * D + c], Wi[c * D + b], acc);
+              dT[a * D + b] = acc;
+            }
+        }
+        bool ok;
+        if (metric_dual(p.metric)) {
+          Dual<R> Td[DD], Pd[DD], mud;
+#pragma unroll
+          for (int i = 0; i < DD; ++i) Td[i] = Dual<R>{T[i], dT[i]};
+          ok = metric_P<D>(p.metric, Td, mud, Pd);
+#pragma unroll
+          for (int i = 0; i < DD; ++i) {
+            Sg[i] = s * Pd[i].v;
+            Sh[i] = s * Pd[i].d;
+          }
+        } else {
+          MetricAct<D, R> L;
+          ok = L.init(p.metric, T, s);
+          if (ok) {
+            L.dP(dT, Sh);
+            if (p.metric == 14) {
+              R mu;
+              metric_P<D>(p.metric, T, mu, Sg, s);
+            } else {
+#pragma unroll
+              for (int i = 0; i < DD; ++i) Sg[i] = fma(L.cA, L.T[i], L.ct * L.C[i]);
+            }
+          }
+        }
+        // R = S W^-t for both: the Hessian action's in place of dA, the
+        // gradient's in place of A
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int b = 0; b < D; ++b) {
+            R rg = R(0), rh = R(0);
+            if (p.wkind == WK_IDENTITY) {
+              rg = Sg[a * D + b];
+              rh = Sh[a * D + b];
+            } else {
+#pragma unroll
+              for (int c = 0; c < D; ++c) {
+                rg = fma(Sg[a * D + c], Wi[b * D + c], rg);
+                rh = fma(Sh[a * D + c], Wi[b * D + c], rh);
+              }
+            }
+            Abuf[(a * D + b) * QP + q] = ok ? rg : R(0);
+            dAbuf[(a * D + b) * QP + q] = ok ? rh : R(0);
+          }
+        continue;
       }
       if constexpr (OP == OP_LINEARIZE_C) {
         // compact record: T and w det W times the partials of mu in (|T|^2, det T)
@@ -579,6 +654,48 @@ __global__ void __launch_bounds__(ElemCfg<D, N, Q1, R, OP>::WARPS * 32, ElemCfg<
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) emin = fmin(emin, __shfl_xor_sync(0xffffffffu, emin, o));
         if (lane == 0) p.elem_min[e] = emin;
+      }
+    } else if constexpr (OP == OP_GRAD_HESS) {
+      __syncwarp();
+      // ---- two adjoint contractions: 3D, the Hessian action's fields (P1)
+      // into y, then the gradient's (P2) into g, each through P0 and its own
+      // buffer; 2D, both at once (components 0..D-1 the gradient's fields,
+      // D..2D-1 the Hessian action's)
+      if constexpr (D == 2) {
+        adj2<N, Q1, 2 * D, R>(sB, sG, P0, P1, lane);
+        for (int t = lane; t < NDOF; t += 32) {
+          const int gn = nodes(t);
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            const size_t dof = (size_t)c * p.nnode + gn;
+            if (p.fixed && __ldg(p.fixed + dof)) continue;
+            atomicAdd(p.g + dof, to_f64(P0[c * NDOF + t]));
+            atomicAdd(p.y + dof, to_f64(P0[(D + c) * NDOF + t]));
+          }
+        }
+      } else {
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+          R* Rin = pass == 0 ? P1 : P2;
+          double* out = pass == 0 ? p.y : p.g;
+          if constexpr (EO) {
+            mirror3_all<D * D, Q1, R>(Rin, lane);
+            adj3_eon<N, Q1, D, R>(sB, sG, s_aperm, s_arat, s_C, P0, Rin, lane);
+            unfold_nodes<D, N, R>(P0, s_ysc, lane);
+          } else {
+            adj3<N, Q1, D, R>(sB, sG, P0, Rin, lane);
+          }
+          for (int t = lane; t < NDOF; t += 32) {
+            const int gn = nodes(t);
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+              const size_t dof = (size_t)c * p.nnode + gn;
+              if (p.fixed && __ldg(p.fixed + dof)) continue;
+              atomicAdd(out + dof, to_f64(P0[c * NDOF + t]));
+            }
+          }
+          __syncwarp();
+        }
       }
     } else {
       if constexpr (EG) accMin = fmin(accMin, emin);

@@ -18,9 +18,11 @@ constexpr int kMaxN = 5;   // 1D nodes (order <= 4)
 // 45, and OP_HESS_PA_C rebuilds dP from them. OP_ENERGY_GRAD is the
 // gradient with the energy partials of OP_ENERGY taken from the same points
 // (one pass where the line search of the Newton step needs both).
+// OP_GRAD_HESS (FP64) is the gradient (into g) and the Hessian action (into y)
+// at the same x in one pass: A(x) and the point's metric terms serve both.
 enum {
   OP_ENERGY = 0, OP_GRADIENT = 1, OP_HESS = 2, OP_LINEARIZE = 3, OP_HESS_PA = 4,
-  OP_LINEARIZE_C = 5, OP_HESS_PA_C = 6, OP_ENERGY_GRAD = 7, OP_HESS_C = 8, OP_COUNT = 9
+  OP_LINEARIZE_C = 5, OP_HESS_PA_C = 6, OP_ENERGY_GRAD = 7, OP_HESS_C = 8, OP_GRAD_HESS = 9, OP_COUNT = 10
 };
 constexpr int kCompactRec = 14;  // values per point of the compact record (3D)
 enum { WK_IDENTITY = 0, WK_CONST = 1, WK_PER_QP = 2 };
@@ -33,6 +35,7 @@ struct KParams {
   const double* x;                // [d][nnode]
   const double* v;                // [d][nnode] (Hessian action)
   double* y;                      // [d][nnode] accumulated output
+  double* g;                      // [d][nnode] accumulated gradient of OP_GRAD_HESS
   // FP32 direction and output of the stored-Hessian products (the FP32
   // forms' Krylov vectors), used instead of v and y when set
   const float* v32;

@@ -71,6 +71,7 @@ _SIGNATURES = {
     "tmop_gradient": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_energy_gradient": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_hess_apply": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "tmop_gradient_hess_apply": ([C.c_void_p] * 6, C.c_int),
     "tmop_newton_step": ([C.c_void_p, C.c_void_p, C.POINTER(NewtonOpts), C.POINTER(NewtonReport), C.c_void_p],
                          C.c_int),
     "tmop_newton_solve": ([C.c_void_p, C.c_void_p, C.POINTER(NewtonOpts), C.POINTER(NewtonReport), C.c_void_p],
@@ -333,6 +334,21 @@ class Context:
         if rc != OK:
             raise TmopError(rc, "tmop_hess_apply")
         return y
+
+    def gradient_hess_apply(self, x, v, g=None, y=None):
+        """(g, y) = (dF/dx, H(x) v) at the same x, in one element pass where
+        the context allows (tmop_gradient_hess_apply)."""
+        import torch
+        _check_vec(x, self.shape, "x")
+        _check_vec(v, self.shape, "v")
+        g = torch.empty_like(x) if g is None else g
+        y = torch.empty_like(x) if y is None else y
+        _check_vec(g, self.shape, "g")
+        _check_vec(y, self.shape, "y")
+        rc = load().tmop_gradient_hess_apply(self._h, _ptr(x), _ptr(v), _ptr(g), _ptr(y), _stream())
+        if rc != OK:
+            raise TmopError(rc, "tmop_gradient_hess_apply")
+        return g, y
 
     def set_composite(self, metric2: int, W2=None, eta2=None):
         """Second metric term eta_q mu2(A W2^-1) (eq. (4.1)); metric2 = 0 removes it."""

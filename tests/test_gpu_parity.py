@@ -78,6 +78,13 @@ def check_all(tm, m, ctx, orc, rtol_F=RTOL, rtol_vec=RTOL, seed=0):
     yo = orc.hess_apply(m.x, v)
     assert rel(y, yo) <= rtol_vec, rel(y, yo)
     assert np.all(y[m.fixed == 1] == 0.0)
+    # the gradient and the Hessian action in one call (one element pass where
+    # the context allows): the two kernels' results up to the order of the
+    # sums, and the oracle's
+    gf, yf = (host(t) for t in ctx.gradient_hess_apply(x, dev(v)))
+    assert rel(gf, g) <= 1e-13 and rel(yf, y) <= 1e-13, (rel(gf, g), rel(yf, y))
+    assert rel(gf, go) <= rtol_vec and rel(yf, yo) <= rtol_vec
+    assert np.all(gf[m.fixed == 1] == 0.0) and np.all(yf[m.fixed == 1] == 0.0)
     return F, g, y
 
 
@@ -293,6 +300,9 @@ def test_fp64_full_c4_sampled(tm):
     y = host(ctx.hess_apply(x, dev(v)))[:, nodes]
     yo = orc.hess_apply(m.x, v, elems=els)[:, nodes]
     assert rel(y, yo) <= RTOL
+    # the fused gradient + Hessian action in the launch shape bench.py times
+    gf, yf = ctx.gradient_hess_apply(x, dev(v))
+    assert rel(host(gf)[:, nodes], go) <= RTOL and rel(host(yf)[:, nodes], yo) <= RTOL
     emin = host(ctx.element_min_detA(x))
     sub = rng.choice(m.nelem, 200, replace=False).astype(np.int32)
     for e in sub[:20]:
@@ -394,6 +404,34 @@ def test_deterministic_energy(tm):
     x = dev(m.x)
     vals = {ctx.energy(x)[1] for _ in range(5)}
     assert len(vals) == 1
+
+
+def test_fused_gradient_hessian_action_fallbacks_and_arguments(tm):
+    """Contexts the one-pass kernel does not cover (restricted movement,
+    deterministic sums, the FP32-mixed form) run the two kernels and give
+    their results; g and y must be distinct."""
+    m = make("c3", 6, nx=2)
+    x = dev(m.x)
+    v = dev(np.random.default_rng(6).standard_normal(m.x.shape))
+    orc = orc_for(m)
+    for setup in ("delta", "det", "fp32"):
+        ctx = tm.Context.from_mesh(m, precision=tm.FP32_MIXED if setup == "fp32" else tm.FP64)
+        if setup == "delta":
+            ctx.set_restricted_movement(20.0, dev(m.x * 0.99))
+        if setup == "det":
+            ctx.set_deterministic(True)
+        g, y = ctx.gradient(x), ctx.hess_apply(x, v)
+        gf, yf = ctx.gradient_hess_apply(x, v)
+        if setup == "det":
+            assert torch.equal(gf, g) and torch.equal(yf, y)
+        assert rel(host(gf), host(g)) <= 1e-13 and rel(host(yf), host(y)) <= 1e-13
+        if setup == "fp32":
+            assert rel(host(gf), orc.gradient(m.x)) <= RTOL
+            assert rel(host(yf), orc.hess_apply(m.x, host(v))) <= 1e-5
+    ctx = tm.Context.from_mesh(m)
+    same = torch.empty_like(x)
+    with pytest.raises(tm.TmopError):
+        ctx.gradient_hess_apply(x, v, g=same, y=same)
 
 
 # ---------------------------------------------------------------- composite metrics
