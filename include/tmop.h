@@ -415,8 +415,12 @@ int tmop_fma_peak(int kind, void* scratch, size_t scratch_bytes, double* gflops,
  * of a[c stride + first + i] b[c stride + first + i] (FP64, a fixed-order
  * two-pass reduction); scratch DEVICE, at least 2048 doubles (the block
  * partials; TMOP_ERR_CAPACITY if scratch_len is smaller than the grid).
- * Asynchronous. Errors: TMOP_ERR_ARG, TMOP_ERR_CAPACITY, TMOP_ERR_CUDA. */
+ * Asynchronous. Errors: TMOP_ERR_ARG, TMOP_ERR_CAPACITY, TMOP_ERR_CUDA.
+ * tmop_vec_axpby: y = a x + b y, DEVICE [n] FP64 (b = 0: y = a x, y's old
+ * contents not read), the vector updates of a Newton-MINRES driver over
+ * such slabs. x may be y. Asynchronous. */
 int tmop_vec_add(double* y, const double* b, size_t n, void* stream);
+int tmop_vec_axpby(double* y, double a, const double* x, double b, size_t n, void* stream);
 int tmop_vec_dot_segments(const double* a, const double* b, int ncomp, size_t stride, size_t first, size_t count,
                           double* scratch, size_t scratch_len, double* out, void* stream);
 

@@ -666,6 +666,11 @@ __global__ void k_add(double* __restrict__ y, const double* __restrict__ b, size
     y[i] += b[i];
 }
 
+__global__ void k_axpby(double* __restrict__ y, double a, const double* __restrict__ x, double b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = b == 0.0 ? a * x[i] : fma(a, x[i], b * y[i]);
+}
+
 // partials of sum_c sum_{i < count} a[c stride + first + i] b[...]
 __global__ void k_dot_seg(const double* __restrict__ a, const double* __restrict__ b, int ncomp, size_t stride,
                           size_t first, size_t count, double* __restrict__ part) {
@@ -686,6 +691,14 @@ extern "C" int tmop_vec_add(double* y, const double* b, size_t n, void* stream) 
   if (n == 0) return TMOP_OK;
   if (!y || !b) return TMOP_ERR_ARG;
   k_add<<<red_grid(n), kThreads, 0, (cudaStream_t)stream>>>(y, b, n);
+  return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
+}
+
+extern "C" int tmop_vec_axpby(double* y, double a, const double* x, double b, size_t n, void* stream) {
+  using namespace tmop;
+  if (n == 0) return TMOP_OK;
+  if (!y || !x) return TMOP_ERR_ARG;
+  k_axpby<<<red_grid(n), kThreads, 0, (cudaStream_t)stream>>>(y, a, x, b, n);
   return cudaGetLastError() == cudaSuccess ? TMOP_OK : TMOP_ERR_CUDA;
 }
 

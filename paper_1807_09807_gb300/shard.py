@@ -26,6 +26,7 @@ also run on CPU ranks (gloo) with other arithmetic behind it.
 """
 from __future__ import annotations
 
+import math
 from dataclasses import replace
 
 import numpy as np
@@ -165,5 +166,115 @@ class ShardedOperator:
         y = self.ctx.hess_apply(x_local, v_local, out=out)
         return self.part.halo_sum(y, self.dist)
 
+    def dot(self, a, b):
+        return self.part.dot(a, b, self.dist)
+
     def close(self):
         self.ctx.close()
+
+
+# ------------------------------------------------------------------ Newton-MINRES on slabs
+def _axpby_library(y, a, x, b):
+    from . import tmop as tm
+    tm.vec_axpby(y, a, x, b)
+
+
+def sharded_minres(op, x, b, p, rtol=1e-10, maxit=2000, axpby=None):
+    """MINRES (Paige and Saunders' recurrences, zero initial guess) for
+    H(x) p = b on halo-consistent slab vectors: op.hess_apply gives H v with
+    the shared planes summed, op.dot the global dot product, so every rank
+    runs the same scalar recurrence on its slab. Stops when the residual
+    estimate is at most rtol |b|. axpby(y, a, x, b): y = a x + b y (default:
+    tmop_vec_axpby). Returns the iteration count."""
+    import torch
+    axpby = axpby or _axpby_library
+    axpby(p, 0.0, b, 0.0)
+    beta1 = math.sqrt(max(op.dot(b, b), 0.0))
+    if beta1 == 0.0:
+        return 0
+    buf = [torch.empty_like(b) for _ in range(7)]
+    r1, r2, t, v, w, w1, w2 = buf
+    axpby(r1, 1.0, b, 0.0)
+    axpby(r2, 1.0, b, 0.0)
+    axpby(w, 0.0, b, 0.0)
+    axpby(w1, 0.0, b, 0.0)
+    axpby(w2, 0.0, b, 0.0)
+    oldb, beta, dbar, epsln, phibar, cs, sn = 0.0, beta1, 0.0, 0.0, beta1, -1.0, 0.0
+    itn = 0
+    while itn < maxit:
+        itn += 1
+        axpby(v, 1.0 / beta, r2, 0.0)                  # Lanczos vector
+        op.hess_apply(x, v, out=t)
+        if itn >= 2:
+            axpby(t, -beta / oldb, r1, 1.0)
+        alfa = op.dot(v, t)
+        axpby(t, -alfa / beta, r2, 1.0)
+        r1, r2, t = r2, t, r1                          # rotate: r1 <- r2, r2 <- new
+        oldb, beta = beta, math.sqrt(max(op.dot(r2, r2), 0.0))
+        oldeps = epsln
+        delta = cs * dbar + sn * alfa                  # previous rotation applied
+        gbar = sn * dbar - cs * alfa
+        epsln = sn * beta
+        dbar = -cs * beta
+        gamma = max(math.hypot(gbar, beta), 1e-300)    # next rotation
+        cs, sn = gbar / gamma, beta / gamma
+        phi, phibar = cs * phibar, sn * phibar
+        w1, w2, w = w2, w, w1                          # new direction into the oldest buffer
+        axpby(w, 1.0 / gamma, v, 0.0)
+        axpby(w, -oldeps / gamma, w1, 1.0)
+        axpby(w, -delta / gamma, w2, 1.0)
+        axpby(p, phi, w, 1.0)
+        if phibar <= rtol * beta1 or beta == 0.0:
+            break
+    return itn
+
+
+def sharded_newton(op, x, max_newton=12, rtol=1e-12, krylov_rtol=1e-10, krylov_maxit=2000, f_factor=1.2,
+                   g_factor=1.2, alpha_shrink=0.5, max_halvings=30, axpby=None):
+    """Newton's method with the Section 3.4 line search over a slab-sharded
+    mesh: the direction from sharded_minres (H p = g), trial x - alpha p,
+    accepted when min det A > 0, F < f_factor F and |g| < g_factor |g|
+    (alpha shrunk otherwise); stops when |g| <= rtol |g0|. op provides
+    energy(x) -> (F, min det A), gradient(x, out), hess_apply(x, v, out)
+    and dot(a, b), all global (ShardedOperator on GPUs). x (the local
+    positions) is updated in place. Returns a report dict."""
+    import torch
+    axpby = axpby or _axpby_library
+    rep = {"status": "ok", "iterations": 0, "krylov_iterations": 0, "alpha": 0.0}
+    F, md = op.energy(x)
+    if not md > 0.0:
+        rep.update(status="inverted", F=F, min_detA=md)
+        return rep
+    xc, xt = x, torch.empty_like(x)
+    g, gt, p = op.gradient(xc), torch.empty_like(x), torch.empty_like(x)
+    gn = math.sqrt(max(op.dot(g, g), 0.0))
+    gn0 = gn
+    while True:
+        if gn <= rtol * gn0:
+            break
+        if rep["iterations"] >= max_newton:
+            rep["status"] = "iteration limit reached"
+            break
+        rep["krylov_iterations"] += sharded_minres(op, xc, g, p, krylov_rtol, krylov_maxit, axpby)
+        alpha, accepted = 1.0, False
+        for _ in range(max_halvings + 1):
+            axpby(xt, 1.0, xc, 0.0)
+            axpby(xt, -alpha, p, 1.0)
+            Ft, mdt = op.energy(xt)
+            if mdt > 0.0 and Ft < f_factor * F:
+                op.gradient(xt, out=gt)
+                gnt = math.sqrt(max(op.dot(gt, gt), 0.0))
+                if gnt < g_factor * gn:
+                    xc, xt, g, gt = xt, xc, gt, g
+                    F, md, gn, accepted = Ft, mdt, gnt, True
+                    break
+            alpha *= alpha_shrink
+        rep["iterations"] += 1
+        if not accepted:
+            rep["status"] = "line search exhausted"
+            break
+        rep["alpha"] = alpha
+    if xc is not x:
+        axpby(x, 1.0, xc, 0.0)
+    rep.update(F=F, min_detA=md, grad_norm=gn, grad_norm0=gn0)
+    return rep

@@ -101,6 +101,7 @@ _SIGNATURES = {
                             C.c_void_p], C.c_int),
     "tmop_set_deterministic": ([C.c_void_p, C.c_int], C.c_int),
     "tmop_vec_add": ([C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p], C.c_int),
+    "tmop_vec_axpby": ([C.c_void_p, C.c_double, C.c_void_p, C.c_double, C.c_size_t, C.c_void_p], C.c_int),
     "tmop_vec_dot_segments": ([C.c_void_p, C.c_void_p, C.c_int, C.c_size_t, C.c_size_t, C.c_size_t, C.c_void_p,
                                C.c_size_t, C.c_void_p, C.c_void_p], C.c_int),
     "tmop_destroy": ([C.c_void_p], None),
@@ -176,6 +177,16 @@ def vec_add(y, b):
     rc = load().tmop_vec_add(_ptr(y), _ptr(b), y.numel(), _stream())
     if rc != OK:
         raise TmopError(rc, "tmop_vec_add")
+
+
+def vec_axpby(y, a, x, b):
+    """y = a x + b y (contiguous float64 CUDA tensors of equal size), tmop_vec_axpby."""
+    if y.numel() != x.numel() or not (y.is_contiguous() and x.is_contiguous()):
+        raise TypeError("y and x must be contiguous and of equal size")
+    rc = load().tmop_vec_axpby(_ptr(y), float(a), _ptr(x), float(b), y.numel(), _stream())
+    if rc != OK:
+        raise TmopError(rc, "tmop_vec_axpby")
+    return y
 
 
 def vec_dot_segments(a, b, first, count, scratch, out):

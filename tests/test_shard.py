@@ -81,6 +81,93 @@ def test_slab_sharding_reproduces_the_single_rank_operator(case, ws):
     assert np.all(covered == 1)          # every node counted once in the dot products
 
 
+def _axpby_cpu(y, a, x, b):
+    # the CPU stand-in of tmop_vec_axpby (b = 0: y's old contents unread)
+    y.copy_(a * x if b == 0.0 else a * x + b * y)
+
+
+class _OracleSlabOp:
+    """One rank's slab evaluated by the FP64 oracle (standing in for the
+    rank's GPU kernels), made global by the partition's collectives: the
+    operator interface sharded_newton drives."""
+
+    def __init__(self, part, lm):
+        import oracle
+        self.part = part
+        self.orc = oracle.Problem(lm.dim, lm.order, lm.elem_nodes, lm.nnode, lm.fixed, lm.nq, lm.metric)
+        self.add = lambda dst, src: dst.add_(src)                          # noqa: E731
+        self.seg = lambda a, b, i, n: (a[:, i:i + n] * b[:, i:i + n]).sum()  # noqa: E731
+
+    def energy(self, x):
+        _, F, md = self.orc.energy(x.numpy())
+        return self.part.energy(F, md, dist)
+
+    def _put(self, val, out):
+        t = self.part.halo_sum(torch.tensor(val), dist, self.add)
+        if out is None:
+            return t
+        out.copy_(t)
+        return out
+
+    def gradient(self, x, out=None):
+        return self._put(self.orc.gradient(x.numpy()), out)
+
+    def hess_apply(self, x, v, out=None):
+        return self._put(self.orc.hess_apply(x.numpy(), v.numpy()), out)
+
+    def dot(self, a, b):
+        return self.part.dot(a, b, dist, self.seg)
+
+
+NEWTON_CASE = ("c3", dict(nx=(2, 2, 6)))
+
+
+def _newton_rank(rank, ws, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    from paper_1807_09807_gb300.shard import SlabPartition, sharded_newton
+    name, kw = NEWTON_CASE
+    m = mg.make_mesh(name, 4, **kw)
+    part = SlabPartition(m.dim, m.order, m.nx, ws, rank)
+    lm = part.local_mesh(m)
+    x = torch.tensor(lm.x)
+    rep = sharded_newton(_OracleSlabOp(part, lm), x, axpby=_axpby_cpu)
+    out.put((rank, rep, x.numpy()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("ws", [2, 3])
+def test_sharded_newton_reaches_the_single_rank_minimiser(ws):
+    """Newton-MINRES with the det A > 0 line search on slab vectors (the
+    global dots and the halo sums of each product), 2 and 3 gloo ranks:
+    converged, with the F and the nodes of the oracle's single-rank Newton."""
+    import oracle
+    from paper_1807_09807_gb300.shard import SlabPartition
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_newton_rank, args=(r, ws, port, q)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=600) for _ in range(ws)), key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    name, kw = NEWTON_CASE
+    m = mg.make_mesh(name, 4, **kw)
+    orc = oracle.Problem(m.dim, m.order, m.elem_nodes, m.nnode, m.fixed, m.nq, m.metric)
+    rc, xo, hist = orc.newton(m.x, max_newton=12)
+    assert rc == oracle.OK
+    F0 = hist[0, 0]
+    for rank, rep, xr in res:
+        assert rep["status"] == "ok" and rep["grad_norm"] <= 1e-12 * rep["grad_norm0"], rep
+        assert abs(rep["F"] - hist[-1, 0]) <= 1e-12 * F0 and rep["min_detA"] > 0
+        assert rep["F"] == res[0][1]["F"] and rep["iterations"] == res[0][1]["iterations"]
+        xl = SlabPartition(m.dim, m.order, m.nx, ws, rank).to_local(xo)
+        assert np.abs(xr - xl).max() <= 1e-9 * np.abs(xo).max()
+
+
 def test_slab_partition_shapes():
     from paper_1807_09807_gb300.shard import SlabPartition
     parts = [SlabPartition(3, 3, (4, 4, 10), 4, r) for r in range(4)]
@@ -122,6 +209,18 @@ def test_sharded_operator_single_rank_gpu_and_vector_helpers():
         y = a.clone()
         tm.vec_add(y[1], b[1].contiguous())
         assert torch.equal(y[1], a[1] + b[1]) and torch.equal(y[0], a[0])
+        z = torch.full_like(a, float("nan"))
+        tm.vec_axpby(z, 2.5, a, 0.0)                       # b = 0: z's old contents unread
+        assert torch.equal(z, 2.5 * a)
+        tm.vec_axpby(z, -0.5, b, 3.0)
+        assert torch.allclose(z, 7.5 * a - 0.5 * b, rtol=1e-15, atol=1e-15)
+        # Newton-MINRES on the sharded operator (one rank): the context's own Newton's F
+        from paper_1807_09807_gb300.shard import sharded_newton
+        xs = x.clone()
+        rep = sharded_newton(op, xs)
+        r = ctx.newton_solve(x.clone(), max_newton=12)
+        assert rep["status"] == "ok" and r.status == tm.OK
+        assert abs(rep["F"] - r.report["F"]) <= 1e-12 * ctx.energy(x)[1] and rep["min_detA"] > 0
         op.close()
     finally:
         dist.destroy_process_group()
