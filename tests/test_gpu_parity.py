@@ -248,6 +248,8 @@ def test_all_dofs_fixed_and_zero_rhs(tm, prec):
         assert np.all(host(ctx.gradient(x)) == 0.0)
         v = dev(np.random.default_rng(0).standard_normal(m.x.shape))
         assert np.all(host(ctx.hess_apply(x, v)) == 0.0)
+        gf, yf = ctx.gradient_hess_apply(x, v)
+        assert np.all(host(gf) == 0.0) and np.all(host(yf) == 0.0)
         ctx.linearize(x)
         assert np.all(host(ctx.hess_apply_pa(v)) == 0.0)
         res = ctx.newton_solve(x, max_newton=5)
