@@ -119,6 +119,41 @@ class _OracleSlabOp:
         return self.part.dot(a, b, dist, self.seg)
 
 
+class _DenseOp:
+    """A dense symmetric matrix acting on [2][n/2] vectors, for the MINRES
+    recurrences alone (no partition, no collectives)."""
+
+    def __init__(self, A):
+        self.A = torch.tensor(A)
+
+    def hess_apply(self, x, v, out=None):
+        out.copy_((self.A @ v.reshape(-1)).reshape(v.shape))
+        return out
+
+    def dot(self, a, b):
+        return float((a * b).sum())
+
+
+def test_sharded_minres_solves_symmetric_indefinite_systems():
+    """sharded_minres against a dense solve: a symmetric indefinite matrix
+    (MINRES's case, where CG would not apply), a positive definite one, and a
+    zero right-hand side (p = 0, no iteration)."""
+    from paper_1807_09807_gb300.shard import sharded_minres
+    rng = np.random.default_rng(5)
+    Qm, _ = np.linalg.qr(rng.standard_normal((40, 40)))
+    for eig in (np.concatenate([-np.linspace(1, 3, 15), np.linspace(0.5, 4, 25)]), np.linspace(0.2, 5, 40)):
+        A = (Qm * eig) @ Qm.T
+        b = torch.tensor(rng.standard_normal((2, 20)))
+        p = torch.empty_like(b)
+        it = sharded_minres(_DenseOp(A), None, b, p, rtol=1e-13, maxit=200, axpby=_axpby_cpu)
+        ref = np.linalg.solve(A, b.numpy().reshape(-1))
+        assert 0 < it <= 200
+        assert np.linalg.norm(p.numpy().reshape(-1) - ref) <= 1e-10 * np.linalg.norm(ref)
+    p = torch.full((2, 20), 7.0)
+    assert sharded_minres(_DenseOp(A), None, torch.zeros(2, 20), p, axpby=_axpby_cpu) == 0
+    assert torch.equal(p, torch.zeros(2, 20))
+
+
 NEWTON_CASE = ("c3", dict(nx=(2, 2, 6)))
 
 
