@@ -81,6 +81,7 @@ def test_null_arguments(lib):
     assert lib.tmop_energy_device(None, None, None, None, None) == tm.ERR_ARG
     assert lib.tmop_gradient(None, None, None, None) == tm.ERR_ARG
     assert lib.tmop_hess_apply(None, None, None, None, None) == tm.ERR_ARG
+    assert lib.tmop_gradient_hess_apply(None, None, None, None, None, None) == tm.ERR_ARG
     assert lib.tmop_newton_step(None, None, None, None, None) == tm.ERR_ARG
     assert lib.tmop_newton_solve(None, None, None, None, None) == tm.ERR_ARG
     assert lib.tmop_krylov_solve(None, None, None, None, None, None, None) == tm.ERR_ARG
@@ -102,6 +103,10 @@ def test_null_arguments(lib):
     assert lib.tmop_selftest_convert(None, None, None, 5, None) == tm.ERR_ARG
     assert lib.tmop_selftest_rcbrt(None, None, 0, None) == tm.OK
     assert lib.tmop_selftest_rcbrt(None, None, 3, None) == tm.ERR_ARG
+    assert lib.tmop_vec_axpby(None, 1.0, None, 0.0, 0, None) == tm.OK      # empty: no device work
+    assert lib.tmop_vec_axpby(None, 1.0, None, 0.0, 4, None) == tm.ERR_ARG
+    assert lib.tmop_vec_add(None, None, 0, None) == tm.OK
+    assert lib.tmop_vec_add(None, None, 4, None) == tm.ERR_ARG
     lib.tmop_destroy(None)
 
 
