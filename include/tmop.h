@@ -154,8 +154,9 @@ int tmop_hess_apply(tmop_ctx* ctx, const double* x, const double* v, double* y, 
  * and y. The pass covers FP64 contexts with atomic sums, no composite term
  * and no restricted movement; any other context runs tmop_gradient and then
  * tmop_hess_apply. Results equal the two calls' up to rounding.
- * g, y: DEVICE [d][nnode], distinct, overwritten (zero at fixed dofs).
- * TMOP_ERR_ARG for a null pointer or g == y. Asynchronous. */
+ * g, y: DEVICE [d][nnode], distinct from each other and from x and v,
+ * overwritten (zero at fixed dofs). TMOP_ERR_ARG for a null pointer or an
+ * output aliasing another argument. Asynchronous. */
 int tmop_gradient_hess_apply(tmop_ctx* ctx, const double* x, const double* v, double* g, double* y, void* stream);
 
 /* Partial assembly of the Hessian (Section 3.4: the Hessian from d^2mu/dT^2):

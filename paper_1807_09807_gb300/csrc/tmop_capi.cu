@@ -1209,7 +1209,8 @@ int tmop_hess_apply(tmop_ctx* c, const double* x, const double* v, double* y, vo
 }
 
 int tmop_gradient_hess_apply(tmop_ctx* c, const double* x, const double* v, double* g, double* y, void* stream) {
-  if (!c || !x || !v || !g || !y || g == y) return TMOP_ERR_ARG;
+  // g and y are zeroed before x and v are read: no output may alias an input
+  if (!c || !x || !v || !g || !y || g == y || g == x || g == v || y == x || y == v) return TMOP_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   // one element pass where the fused kernel covers the context (FP64, no
   // composite term, no restricted movement, atomic sums); else the two kernels
